@@ -1,0 +1,194 @@
+"""ctypes loader for the plain FP64 C oracle (``kf_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the package smoke check and
+by the CPU-baseline leg of the benchmark.  Nothing in the library imports it.
+
+The C code processes a contiguous range of tracks; ``fit_tracks`` splits a
+batch into ranges and runs them on a thread pool (ctypes releases the GIL
+during the call), so the oracle uses the host's cores without any threading
+inside the C source.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kf_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libkf_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+FLAG_UNREACHABLE = 1
+FLAG_LEFT_BARREL = 2
+FLAG_INVERSION_FAILED = 4
+FLAG_NAN_INPUT = 8
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no fast-math, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = [_SRC] + [os.path.join(_HERE, f) for f in sorted(os.listdir(_HERE))
+                     if f.endswith(".c") and f != "kf_oracle.c"]
+    stale = force or not os.path.exists(_LIB) or any(
+        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in srcs)
+    if stale:
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", "-o", tmp] + srcs + ["-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            _lib.orc_propagate.restype = ctypes.c_int
+            _lib.orc_propagate.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           _dp, _dp, _dp]
+            _lib.orc_ms_noise.argtypes = [_dp, ctypes.c_double, _dp]
+            _lib.orc_inv3_cholesky.restype = ctypes.c_int
+            _lib.orc_inv3_cholesky.argtypes = [_dp, _dp]
+            _lib.orc_update.restype = ctypes.c_int
+            _lib.orc_update.argtypes = [_dp, _dp, _dp, _dp, _dp]
+            _lib.orc_transport.argtypes = [_dp, _dp, _dp]
+            for fn in (_lib.orc_fit_tracks, _lib.orc_fit_tracks_f64):
+                fn.restype = ctypes.c_int
+                fn.argtypes = ([ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+                               + [ctypes.c_void_p] * 13)
+        return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# single-state helpers (pins call these)
+
+
+def propagate(state, q, bz, r, jacobian=True):
+    """Returns (ok, new_state, J or None, s)."""
+    st = _f64(state).copy()
+    out = np.zeros(6)
+    J = np.zeros(36) if jacobian else None
+    s = ctypes.c_double(0.0)
+    rc = lib().orc_propagate(_p(st), int(q), float(bz), float(r), _p(out),
+                             _p(J) if jacobian else None, ctypes.byref(s))
+    return rc == 0, out, (J.reshape(6, 6) if jacobian else None), s.value
+
+
+def ms_noise(state, x_over_x0):
+    Q = np.zeros(36)
+    lib().orc_ms_noise(_p(_f64(state).copy()), float(x_over_x0), _p(Q))
+    return Q.reshape(6, 6)
+
+
+def inv3(S):
+    out = np.zeros(9)
+    rc = lib().orc_inv3_cholesky(_p(_f64(S).reshape(9).copy()), _p(out))
+    return rc == 0, out.reshape(3, 3)
+
+
+def update(x, C, m, V_packed):
+    """Returns (ok, x', C', dchi2)."""
+    x = _f64(x).copy()
+    C = _f64(C).reshape(36).copy()
+    d = ctypes.c_double(0.0)
+    rc = lib().orc_update(_p(x), _p(C), _p(_f64(m).copy()), _p(_f64(V_packed).copy()),
+                          ctypes.byref(d))
+    return rc == 0, x, C.reshape(6, 6), d.value
+
+
+def transport(J, C, Q):
+    C = _f64(C).reshape(36).copy()
+    lib().orc_transport(_p(_f64(J).reshape(36).copy()), _p(C), _p(_f64(Q).reshape(36).copy()))
+    return C.reshape(6, 6)
+
+
+# ---------------------------------------------------------------------------
+# batch fit
+
+
+def fit_arrays(radii, x_over_x0, z_half, bz, seed_state, seed_cov, charge, hit_pos, hit_cov,
+               hit_mask, threads: int | None = None, per_layer: bool = False,
+               track_range: tuple[int, int] | None = None, double_inputs: bool = False):
+    """Fit a batch with the FP64 oracle.  Input arrays use the library layout
+    (float32 SoA, or float64 with ``double_inputs``).  Returns a dict of
+    float64 results; with ``track_range`` only that slice is fitted (other
+    entries are left zero)."""
+    T = int(charge.shape[0])
+    L = int(len(radii))
+    real = np.float64 if double_inputs else np.float32
+    ss = np.ascontiguousarray(seed_state, dtype=real)
+    sc = np.ascontiguousarray(seed_cov, dtype=real)
+    ch = np.ascontiguousarray(charge, dtype=np.int8)
+    hp = np.ascontiguousarray(hit_pos, dtype=real)
+    hc = np.ascontiguousarray(hit_cov, dtype=real)
+    hm = np.ascontiguousarray(hit_mask, dtype=np.uint32)
+    rad = _f64(radii)
+    xx0 = _f64(x_over_x0)
+    out = dict(state=np.zeros((6, T)), cov=np.zeros((21, T)), chi2=np.zeros(T),
+               ndof=np.zeros(T, dtype=np.int32), flags=np.zeros(T, dtype=np.uint32))
+    if per_layer:
+        out["layer_state"] = np.zeros((L, 6, T))
+        out["layer_cov"] = np.zeros((L, 21, T))
+    t0, t1 = track_range if track_range is not None else (0, T)
+    if t1 <= t0:
+        return out
+    threads = threads or os.cpu_count() or 1
+    chunk = max(1, -(-(t1 - t0) // (threads * 4)))
+    ranges = [(a, min(a + chunk, t1)) for a in range(t0, t1, chunk)]
+    L_ = lib()
+    fn = L_.orc_fit_tracks_f64 if double_inputs else L_.orc_fit_tracks
+    ptr = lambda a: a.ctypes.data if a is not None else None
+
+    def run(rg):
+        return fn(L, _p(rad), _p(xx0), float(z_half), float(bz), rg[0], rg[1], T,
+                                 ptr(ss), ptr(sc), ptr(ch), ptr(hp), ptr(hc), ptr(hm),
+                                 ptr(out["state"]), ptr(out["cov"]), ptr(out["chi2"]),
+                                 ptr(out["ndof"]), ptr(out["flags"]),
+                                 ptr(out.get("layer_state")), ptr(out.get("layer_cov")))
+
+    if threads == 1 or len(ranges) == 1:
+        for rg in ranges:
+            run(rg)
+    else:
+        with cf.ThreadPoolExecutor(threads) as ex:
+            list(ex.map(run, ranges))
+    return out
+
+
+def fit_batch(batch, threads=None, per_layer=False, track_range=None):
+    """Fit a ``synth.FitBatch``."""
+    g = batch.geom
+    f32 = lambda v: np.asarray(v, dtype=np.float32).astype(np.float64)  # the library's inputs
+    return fit_arrays(f32(g.radii), f32(g.x_over_x0), float(np.float32(g.z_half)),
+                      float(np.float32(g.bz)), batch.seed_state, batch.seed_cov,
+                      batch.charge, batch.hit_pos, batch.hit_cov, batch.hit_mask, threads,
+                      per_layer, track_range)
+
+
+def fit_batch_exact(batch, threads=None, per_layer=False):
+    """Fit a ``synth.FitBatch`` from its float64 arrays (before the rounding to
+    float32 that the library's inputs carry), in the batch's float64 geometry."""
+    g, e = batch.geom, batch.exact
+    return fit_arrays(g.radii, g.x_over_x0, g.z_half, g.bz, e["seed_state"], e["seed_cov"],
+                      batch.charge, e["hit_pos"], e["hit_cov"], batch.hit_mask, threads,
+                      per_layer, None, double_inputs=True)
