@@ -1,0 +1,180 @@
+/*
+ * kf.h -- C interface of the GB300 Kalman-filter track fit and build step.
+ *
+ * The operations follow arXiv:1705.02876 (Cerati et al., "Parallelized
+ * Kalman-Filter-Based Reconstruction of Particle Tracks on Many-Core
+ * Processors and GPUs"):
+ *   - Section 2.1: the track state is 6 global parameters (x, y, z, px, py,
+ *     pz) with a 6x6 covariance, a hit is a 3-D point with a 3x3 covariance;
+ *   - Section 2: the Kalman filter folds multiple-scattering estimates into
+ *     the trajectory; fitting applies the filter over a known hit set
+ *     without branching; building explores several candidates per seed;
+ *   - Section 4.1: matrices are stored matrix-major (element (i,j) of all
+ *     tracks contiguous) so that consecutive threads read consecutive words;
+ *   - Section 4.2: one GPU thread per track for fitting; one event does not
+ *     fill the GPU, so several events are processed together;
+ *   - Sections 3 and 4.3: building keeps the best N candidates per seed,
+ *     ranked by number of hits and chi2 ("clone engine"), hits partitioned
+ *     into spatial bins.
+ *
+ * Conventions shared by every call:
+ *   - Layout is structure-of-arrays, track index fastest: an array written
+ *     [a][b][T] holds element (a, b) of track t at ((a * B) + b) * T + t.
+ *   - A symmetric matrix is packed as its lower triangle, row by row:
+ *     (0,0), (1,0), (1,1), (2,0), (2,1), (2,2), ...  (21 floats for 6x6,
+ *     6 floats for 3x3).
+ *   - Units: cm, GeV, tesla.  Charge is +1 or -1.
+ *   - Every array pointer is device memory owned by the caller unless its
+ *     comment says "host".  Pointers must be aligned to their element size.
+ *     The library never frees, reallocates or retains caller memory after a
+ *     call's work has completed on the stream.
+ *   - Calls enqueue work on the caller's stream and return without
+ *     synchronising; results are valid once that stream reaches them.
+ *   - Return value: KF_OK (0) or a negative KF_ERR_* code; kf_last_error()
+ *     describes the last failure on that context.  Per-track problems never
+ *     fail a call: they set bits in out_flags.
+ *   - A context may be used by one host thread at a time, and the work of
+ *     its calls must not overlap on the GPU (one stream per context, or
+ *     synchronise between streams): calls share the context's scratch.
+ */
+#ifndef KF_H
+#define KF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kf_context kf_context;
+typedef struct CUstream_st *kf_stream; /* a cudaStream_t; NULL is the legacy default stream */
+
+/* status codes */
+#define KF_OK 0
+#define KF_ERR_ARG (-1)         /* null / misaligned pointer, bad size or option */
+#define KF_ERR_CUDA (-2)        /* a CUDA runtime or driver call failed */
+#define KF_ERR_TIMEOUT (-3)     /* a bounded device-side wait expired */
+#define KF_ERR_NOMEM (-4)       /* the context could not grow its scratch */
+#define KF_ERR_UNSUPPORTED (-5) /* no sm_103a device, or a feature off on this device */
+
+/* per-track flags in out_flags */
+#define KF_FLAG_UNREACHABLE 1u       /* a layer's cylinder is not reached: fit stops there */
+#define KF_FLAG_LEFT_BARREL 2u       /* the crossing lies beyond |z| = z_half: fit stops */
+#define KF_FLAG_INVERSION_FAILED 4u  /* S = H C H^T + V not positive definite: update skipped */
+#define KF_FLAG_NAN_INPUT 8u         /* non-finite seed or used hit: outputs are the seed */
+#define KF_FLAG_FP64_PATH 16u        /* at least one update took the FP64 path */
+#define KF_FLAG_PSD_REPAIRED 32u     /* the FP64 path clamped the covariance */
+
+#define KF_MAX_LAYERS 32
+
+/* precision_mode */
+#define KF_PRECISION_FP32 0   /* every step in FP32 */
+#define KF_PRECISION_ROUTED 1 /* FP32, with ill-conditioned updates redone in FP64 */
+
+/* launch_mode */
+#define KF_LAUNCH_AUTO 0      /* one persistent launch over all events, graph-captured */
+#define KF_LAUNCH_PER_EVENT 1 /* one plain launch per event (needs event_offsets) */
+#define KF_LAUNCH_FLAT 2      /* one plain launch over all tracks */
+
+/*
+ * Detector: n_layers concentric cylinders of radius r[l] (strictly
+ * increasing, > 0) and length 2 z_half, each x_over_x0[l] radiation lengths
+ * thick at normal incidence, in a uniform field bz_tesla along z
+ * (Section 3.2: equally spaced fixed-length cylinders).  Host memory.
+ */
+typedef struct {
+    int n_layers;            /* 1 .. KF_MAX_LAYERS */
+    const float *r;          /* host, [n_layers] */
+    const float *x_over_x0;  /* host, [n_layers], >= 0 */
+    float z_half;
+    float bz_tesla;
+} kf_geometry;
+
+typedef struct {
+    /* precision routing (fit and build) */
+    int precision_mode;      /* KF_PRECISION_* */
+    float cond_max;          /* Frobenius condition estimate of S above which FP64 is used */
+    float pt_lo, pt_hi;      /* tracks with pT outside [pt_lo, pt_hi] GeV update in FP64 */
+    /* launch shape (fit) */
+    int launch_mode;         /* KF_LAUNCH_* */
+    int tracks_per_block;    /* 0 = autotuned, else 32, 64, 128 or 256 */
+    int layer_tile;          /* 0 = autotuned; > 0 layers of hits per shared-memory stage;
+                                -1 = hits read straight from global memory */
+    /* building */
+    int max_cands;           /* N candidates kept per seed, 1 (best hit) .. 8 */
+    float chi2_cut;          /* hits with a larger chi2 increment are incompatible */
+    float window_nsigma;     /* search window half-width in sigmas */
+    float hit_sigma_rphi;    /* nominal hit resolution used for the window, cm */
+    float hit_sigma_z;
+    int n_phi_bins;          /* hit bins per layer, in phi ... */
+    int n_z_bins;            /* ... and in z */
+    int use_proposal;        /* 1: the learned proposal keeps the top-k in-window hits */
+    int topk;
+} kf_options;
+
+/* Fill *opt with the defaults: routed precision (cond_max 1e6, pT in
+ * [0.25, 200]), automatic launch, N = 6, chi2 cut 30, 3-sigma window,
+ * 0.01/0.1 cm nominal resolution, 256 x 64 bins, proposal off, top-k 4. */
+void kf_options_default(kf_options *opt);
+
+/* Create a context on CUDA device `device` (requires compute capability
+ * 10.3).  The context owns scratch memory, the autotuner's choices, captured
+ * CUDA graphs and the proposal network's weights. */
+int kf_context_create(kf_context **ctx, int device);
+void kf_context_destroy(kf_context *ctx);
+
+/* Text of the last error on ctx (never NULL; "" after success). */
+const char *kf_last_error(const kf_context *ctx);
+
+/*
+ * Kalman-filter fit of n_tracks tracks (Sections 2 and 4.2).
+ *
+ * For each track, starting from its seed, for each layer l in order:
+ *   1. propagate the state along the helix of the uniform field to its first
+ *      forward crossing of cylinder l; if there is none, set
+ *      KF_FLAG_UNREACHABLE and stop; if |z| > z_half there, set
+ *      KF_FLAG_LEFT_BARREL and stop (the state stays at the previous layer);
+ *   2. transport the covariance, C' = J C J^T, with J the Jacobian of the
+ *      crossing state with respect to the previous state;
+ *   3. add multiple-scattering noise on the momentum block,
+ *      Q = theta0^2 (|p|^2 I3 - p p^T), theta0 the Highland width for
+ *      x_over_x0[l] / |cos(incidence)| radiation lengths and beta = 1;
+ *   4. if bit l of hit_mask is set, update with the hit: S = C_xx + V,
+ *      K = C[:, 0:3] S^-1, x += K (m - x_xyz), C -= K C[0:3, :],
+ *      chi2 += (m - x_xyz)^T S^-1 (m - x_xyz).
+ *
+ * Inputs (device, caller-owned, read only):
+ *   seed_state [6][T], seed_cov [21][T] packed, charge [T] (int8, +1/-1),
+ *   hit_pos [L][3][T], hit_cov [L][6][T] packed, hit_mask [T]
+ *   (bit l set = a hit on layer l; values of absent hits are not read).
+ * event_offsets: host, [n_events + 1], event e holds tracks
+ *   event_offsets[e] .. event_offsets[e+1]-1; may be NULL (one event).  Only
+ *   KF_LAUNCH_PER_EVENT launches by event; the other modes pack all events
+ *   into one launch.
+ * Outputs (device, caller-owned, written): out_state [6][T], out_cov [21][T]
+ *   packed, out_chi2 [T], out_ndof [T] = 3 n_hits - 6, out_flags [T].
+ * n_tracks may be 0 (nothing is launched).  Inputs and outputs must not
+ * overlap.  opt may be NULL (defaults).
+ */
+int kf_fit_tracks(kf_context *ctx, const kf_geometry *geom, int64_t n_tracks,
+                  const int64_t *event_offsets, int n_events,
+                  const float *seed_state, const float *seed_cov, const int8_t *charge,
+                  const float *hit_pos, const float *hit_cov, const uint32_t *hit_mask,
+                  float *out_state, float *out_cov, float *out_chi2, int16_t *out_ndof,
+                  uint32_t *out_flags, const kf_options *opt, kf_stream stream);
+
+/*
+ * Launch shape the autotuner picked for the persistent fit of n_layers layers
+ * and a batch of n_tracks' size class (powers of two), once a KF_LAUNCH_AUTO
+ * fit of that class has run on ctx.  Writes tracks per block and the layer
+ * tile (-1: hits read straight from global memory).  KF_ERR_ARG if that class
+ * has not been tuned yet.
+ */
+int kf_fit_tuned_shape(kf_context *ctx, int n_layers, int64_t n_tracks, int *tracks_per_block,
+                       int *layer_tile);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KF_H */

@@ -323,6 +323,8 @@ static int finite_all(const double *v, int n)
  * For each layer in order: propagate; stop (flag) if the cylinder is not
  * reached or the crossing lies beyond |z| = z_half; otherwise transport the
  * covariance, add the layer's scattering and, if the hit is present, update.
+ * A non-finite seed, or a non-finite value in a hit the fit reaches and uses,
+ * stops the fit and returns the seed unchanged (flag NAN_INPUT).
  * ls[L][6] and lc[L][21] (may be NULL) receive the state after each layer
  * (NaN where the track did not reach it).
  */
@@ -338,9 +340,6 @@ static void fit_one(int n_layers, const double *radii, const double *x_over_x0, 
     memcpy(x, x0, sizeof x);
     orc_unpack_sym(c0, 6, C);
     if (!finite_all(x0, 6) || !finite_all(c0, 21)) flags |= ORC_FLAG_NAN_INPUT;
-    for (int l = 0; l < n_layers; ++l)
-        if ((mask >> l & 1u) && (!finite_all(m + 3 * l, 3) || !finite_all(V + 6 * l, 6)))
-            flags |= ORC_FLAG_NAN_INPUT;
     if (ls)
         for (int i = 0; i < 6 * n_layers; ++i) ls[i] = NAN;
     if (lc)
@@ -361,6 +360,10 @@ static void fit_one(int n_layers, const double *radii, const double *x_over_x0, 
         memcpy(x, xn, sizeof x);
         if (mask >> l & 1u) {
             double d;
+            if (!finite_all(m + 3 * l, 3) || !finite_all(V + 6 * l, 6)) {
+                flags |= ORC_FLAG_NAN_INPUT;
+                break;
+            }
             if (orc_update(x, C, m + 3 * l, V + 6 * l, &d)) {
                 flags |= ORC_FLAG_INVERSION_FAILED;
             } else {
@@ -370,6 +373,12 @@ static void fit_one(int n_layers, const double *radii, const double *x_over_x0, 
         }
         if (ls) memcpy(ls + 6 * l, x, sizeof x);
         if (lc) pack_sym6(C, lc + 21 * l);
+    }
+    if (flags & ORC_FLAG_NAN_INPUT) { /* a track with a non-finite input returns its seed */
+        memcpy(x, x0, sizeof x);
+        orc_unpack_sym(c0, 6, C);
+        chi2 = 0.0;
+        nhits = 0;
     }
     memcpy(x_out, x, sizeof x);
     pack_sym6(C, c_out);

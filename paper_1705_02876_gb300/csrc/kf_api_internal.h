@@ -1,0 +1,24 @@
+// Internal helpers shared by the C-ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kf.h"
+#include "kf_fit.cuh"
+
+namespace kf {
+
+struct BuildState;  // device scratch of the build step (kf_build.cu)
+void destroy_build_state(BuildState *s);
+
+int set_error(kf_context *ctx, int code, const char *fmt, ...);
+int cuda_error(kf_context *ctx, cudaError_t e, const char *what);
+int check_geometry(kf_context *ctx, const kf_geometry *geom, FitGeom *g);
+int check_ptr(kf_context *ctx, const void *p, size_t align, const char *name);
+int check_options(kf_context *ctx, const kf_options &o);
+Routing make_routing(const kf_options &o);
+int context_device(const kf_context *ctx);
+int context_sm_count(const kf_context *ctx);
+BuildState *&context_build_state(kf_context *ctx);
+
+}  // namespace kf

@@ -1,0 +1,333 @@
+// Per-track Kalman-filter arithmetic in registers (Sections 2, 2.1 and 4.2 of
+// arXiv:1705.02876): one thread owns one track's state x[6] and its packed
+// covariance c[21]; every function below works on those registers.
+//
+// Packed symmetric storage: lower triangle row by row, index(i,j) = i(i+1)/2+j.
+#pragma once
+
+#include <stdint.h>
+
+namespace kf {
+
+constexpr float kField = 0.00299792458f;  // GeV / (cm T)
+
+__host__ __device__ constexpr int pk(int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
+
+// Propagation result and the non-trivial part of its Jacobian.  With
+// P = {x, y, px, py} (state indices 0, 1, 3, 4), J has the block structure
+//   J[P][P] = T (4x4), J[z][P] = jz (4), J[z][z] = 1, J[z][pz] = jzpz,
+//   J[P][z] = J[P][pz] = 0, J[pz] = e_pz,
+// because the crossing of a z-parallel cylinder does not depend on z or pz.
+struct Jac {
+    float T[4][4];
+    float jz[4];
+    float jzpz;
+};
+
+// Helix propagation to the first forward crossing of radius r (uniform field
+// along z; transverse path length s, omega = q k Bz / pT).  Writing
+// tau = tan(omega s / 2), the crossing condition |P(s)|^2 = r^2 is the
+// quadratic  B' tau^2 + omega u tau - omega^2 D / 4 = 0  with
+// u = P.t, w = P x t, D = r^2 - |P|^2, B' = 1 + omega w - omega^2 D / 4.
+// Its first-crossing root, rationalised so that it stays exact as omega -> 0,
+// is tau = omega sigma / 2 with sigma = D / (u + sqrt(u^2 + D B')); sigma is
+// the straight-line path length at omega = 0.  sin and cos of the turning
+// angle are rational in tau, so only one atan (for z) is evaluated.
+// Returns false if the cylinder is not reached.
+__device__ __forceinline__ bool propagate(const float x[6], float qkb, float r, float xn[6],
+                                          float &s_out, Jac *J)
+{
+    const float px = x[3], py = x[4], pz = x[5];
+    const float pt2 = px * px + py * py;
+    const float ipt = rsqrtf(pt2);
+    const float tx = px * ipt, ty = py * ipt;
+    const float om = qkb * ipt;
+    const float u = x[0] * tx + x[1] * ty;
+    const float w = x[0] * ty - x[1] * tx;
+    const float D = r * r - (x[0] * x[0] + x[1] * x[1]);
+    const float Bp = 1.0f + om * w - 0.25f * om * om * D;
+    const float Qd = u * u + D * Bp;
+    if (!(Qd >= 0.0f) || !(pt2 > 0.0f)) return false;
+    const float sq = sqrtf(Qd);
+    float s, tau, sigma;
+    if (Bp > 0.0f && u + sq > 0.0f) {
+        sigma = D / (u + sq);
+        tau = 0.5f * om * sigma;
+        const float t2 = tau * tau;
+        const float ratio = t2 < 1e-6f ? 1.0f - t2 * (1.0f / 3.0f) : atanf(tau) / tau;  // atan(tau)/tau
+        s = sigma * ratio;
+    } else {
+        // Crossing beyond half a turn, or a start moving inwards: both roots of
+        // the quadratic, each mapped to its smallest positive path length.
+        if (om == 0.0f) return false;
+        const float period = 6.283185307179586f / fabsf(om);
+        float best = INFINITY;
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            float phi;
+            if (Bp != 0.0f) {
+                const float tr = om * (-u + sgn * copysignf(sq, om)) / (2.0f * Bp);
+                phi = 2.0f * atanf(tr);
+            } else {
+                phi = sgn < 0 ? 2.0f * atanf(om * D / (4.0f * u)) : copysignf(3.14159265358979f, om);
+            }
+            float sk = phi / om;
+            if (sk <= 0.0f) sk += period;
+            best = fminf(best, sk);
+        }
+        s = best;
+        tau = tanf(0.5f * om * s);
+        sigma = om != 0.0f ? 2.0f * tau / om : s;
+        if (!(s < INFINITY)) return false;
+    }
+    const float g = 1.0f / (1.0f + tau * tau);
+    const float a = sigma * g;          // sin(phi) / omega
+    const float b = sigma * tau * g;    // (1 - cos(phi)) / omega
+    const float sn = 2.0f * tau * g;    // sin(phi)
+    const float c = 1.0f - 2.0f * tau * tau * g;  // cos(phi)
+    xn[0] = x[0] + tx * a + ty * b;
+    xn[1] = x[1] + ty * a - tx * b;
+    xn[2] = x[2] + pz * s * ipt;
+    xn[3] = px * c + py * sn;
+    xn[4] = py * c - px * sn;
+    xn[5] = pz;
+    s_out = s;
+    if (J) {
+        const float phi = om * s;
+        const float txn = xn[3] * ipt, tyn = xn[4] * ipt;
+        // D = dF/dx0 at fixed s (phi depends on pT through omega)
+        const float d03 = (a - s * tx * txn) * ipt, d04 = (b - s * ty * txn) * ipt;
+        const float d13 = (-b - s * tx * tyn) * ipt, d14 = (a - s * ty * tyn) * ipt;
+        const float d33 = c - phi * tx * tyn, d34 = sn - phi * ty * tyn;
+        const float d43 = -sn + phi * tx * txn, d44 = c + phi * ty * txn;
+        const float lz = pz * ipt;  // dz/ds
+        const float d23 = -s * lz * tx * ipt, d24 = -s * lz * ty * ipt;
+        // ds/dx0 from the constraint x'^2 + y'^2 = r^2
+        const float iden = -1.0f / (xn[0] * txn + xn[1] * tyn);
+        const float ds0 = xn[0] * iden, ds1 = xn[1] * iden;
+        const float ds3 = (xn[0] * d03 + xn[1] * d13) * iden;
+        const float ds4 = (xn[0] * d04 + xn[1] * d14) * iden;
+        const float f0 = txn, f1 = tyn, f3 = om * xn[4], f4 = -om * xn[3];  // dF/ds on P
+        J->T[0][0] = 1.0f + f0 * ds0; J->T[0][1] = f0 * ds1; J->T[0][2] = d03 + f0 * ds3; J->T[0][3] = d04 + f0 * ds4;
+        J->T[1][0] = f1 * ds0; J->T[1][1] = 1.0f + f1 * ds1; J->T[1][2] = d13 + f1 * ds3; J->T[1][3] = d14 + f1 * ds4;
+        J->T[2][0] = f3 * ds0; J->T[2][1] = f3 * ds1; J->T[2][2] = d33 + f3 * ds3; J->T[2][3] = d34 + f3 * ds4;
+        J->T[3][0] = f4 * ds0; J->T[3][1] = f4 * ds1; J->T[3][2] = d43 + f4 * ds3; J->T[3][3] = d44 + f4 * ds4;
+        J->jz[0] = lz * ds0; J->jz[1] = lz * ds1; J->jz[2] = d23 + lz * ds3; J->jz[3] = d24 + lz * ds4;
+        J->jzpz = s * ipt;
+    }
+    return true;
+}
+
+// C <- J C J^T using the block structure of J (178 FMA instead of 432 for a
+// dense 6x6 triple product on the packed lower triangle).
+__device__ __forceinline__ void transport(const Jac &J, float c[21])
+{
+    constexpr int P[4] = {0, 1, 3, 4};
+    float A[4][4];  // A = T C[P][P]
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int n = 0; n < 4; ++n) acc = fmaf(J.T[k][n], c[pk(P[n], P[m])], acc);
+            A[k][m] = acc;
+        }
+    float w[4], w2 = c[pk(2, 2)], w5 = c[pk(5, 2)];  // W = row z of J times C
+    w2 = fmaf(J.jzpz, c[pk(5, 2)], w2);
+    w5 = fmaf(J.jzpz, c[pk(5, 5)], c[pk(5, 2)]);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        float acc = fmaf(J.jzpz, c[pk(5, P[m])], c[pk(2, P[m])]);
+#pragma unroll
+        for (int n = 0; n < 4; ++n) acc = fmaf(J.jz[n], c[pk(P[n], P[m])], acc);
+        w[m] = acc;
+    }
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        w2 = fmaf(J.jz[n], c[pk(P[n], 2)], w2);
+        w5 = fmaf(J.jz[n], c[pk(P[n], 5)], w5);
+    }
+    float c5[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) acc = fmaf(c[pk(5, P[n])], J.T[m][n], acc);
+        c5[m] = acc;
+    }
+    float nc[21];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int m = 0; m <= k; ++m) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int n = 0; n < 4; ++n) acc = fmaf(A[k][n], J.T[m][n], acc);
+            nc[pk(P[k], P[m])] = acc;
+        }
+    float c22 = w2;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) acc = fmaf(w[n], J.T[m][n], acc);
+        nc[pk(2, P[m])] = acc;
+        c22 = fmaf(J.jz[m], w[m], c22);
+    }
+    nc[pk(2, 2)] = fmaf(J.jzpz, w5, c22);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) nc[pk(5, P[m])] = c5[m];
+    nc[pk(5, 2)] = w5;
+    nc[pk(5, 5)] = c[pk(5, 5)];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) c[i] = nc[i];
+}
+
+// Multiple scattering of a thin layer at the crossing xn on radius r:
+// Q = theta0^2 (|p|^2 I3 - p p^T) on the momentum block; theta0 from the
+// Highland formula (beta = 1) for x_over_x0 / |cos(incidence)|.
+__device__ __forceinline__ void add_scattering(const float xn[6], float r, float x_over_x0, float c[21])
+{
+    if (!(x_over_x0 > 0.0f)) return;
+    const float px = xn[3], py = xn[4], pz = xn[5];
+    const float p2 = px * px + py * py + pz * pz;
+    const float ip = rsqrtf(p2);
+    const float cosi = fabsf(px * xn[0] + py * xn[1]) * ip / r;
+    const float xx0 = x_over_x0 / cosi;
+    const float th = 0.0136f * ip * sqrtf(xx0) * (1.0f + 0.038f * __logf(xx0));
+    const float t2 = th * th;
+    c[pk(3, 3)] = fmaf(t2, p2 - px * px, c[pk(3, 3)]);
+    c[pk(4, 3)] = fmaf(-t2, px * py, c[pk(4, 3)]);
+    c[pk(4, 4)] = fmaf(t2, p2 - py * py, c[pk(4, 4)]);
+    c[pk(5, 3)] = fmaf(-t2, pz * px, c[pk(5, 3)]);
+    c[pk(5, 4)] = fmaf(-t2, pz * py, c[pk(5, 4)]);
+    c[pk(5, 5)] = fmaf(t2, p2 - pz * pz, c[pk(5, 5)]);
+}
+
+// Update with a 3-D hit m (packed V) in FP64: S^-1 by adjugate, gain, state,
+// covariance C - K C[0:3,:] on the packed lower triangle (symmetric by
+// construction), then the PSD repair: diagonal clamped to at least
+// 1e-12 trace, off-diagonals to |C_ij| <= 0.999 sqrt(C_ii C_jj).
+// Returns 0 (updated), 1 (S not positive definite); *repaired set if clamped.
+static __device__ __noinline__ int update_fp64(float x[6], float c[21], const float m[3], const float v[6],
+                                        float *dchi2, bool *repaired)
+{
+    double C[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) C[i] = (double)c[i];
+    const double a = C[0] + (double)v[0], b = C[1] + (double)v[1], cc = C[2] + (double)v[2];
+    const double d = C[3] + (double)v[3], e = C[4] + (double)v[4], f = C[5] + (double)v[5];
+    const double i00 = cc * f - e * e, i10 = d * e - b * f, i11 = a * f - d * d;
+    const double i20 = b * e - cc * d, i21 = b * d - a * e, i22 = a * cc - b * b;
+    const double det = a * i00 + b * i10 + d * i20;
+    if (!(a > 0.0) || !(i22 > 0.0) || !(det > 0.0)) return 1;
+    const double id = 1.0 / det;
+    const double S[3][3] = {{i00 * id, i10 * id, i20 * id}, {i10 * id, i11 * id, i21 * id}, {i20 * id, i21 * id, i22 * id}};
+    const double r0 = (double)m[0] - (double)x[0], r1 = (double)m[1] - (double)x[1], r2 = (double)m[2] - (double)x[2];
+    double K[6][3];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            K[i][j] = C[pk(i, 0)] * S[0][j] + C[pk(i, 1)] * S[1][j] + C[pk(i, 2)] * S[2][j];
+    const double q0 = S[0][0] * r0 + S[0][1] * r1 + S[0][2] * r2;
+    const double q1 = S[1][0] * r0 + S[1][1] * r1 + S[1][2] * r2;
+    const double q2 = S[2][0] * r0 + S[2][1] * r1 + S[2][2] * r2;
+    *dchi2 = (float)(r0 * q0 + r1 * q1 + r2 * q2);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) x[i] = (float)((double)x[i] + K[i][0] * r0 + K[i][1] * r1 + K[i][2] * r2);
+    double N[21];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j)
+            N[pk(i, j)] = C[pk(i, j)] - (K[i][0] * C[pk(0, j)] + K[i][1] * C[pk(1, j)] + K[i][2] * C[pk(2, j)]);
+    double tr = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) tr += fabs(N[pk(i, i)]);
+    const double floor_ = 1e-12 * tr;
+    bool rep = false;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        if (!(N[pk(i, i)] >= floor_)) { N[pk(i, i)] = floor_; rep = true; }
+#pragma unroll
+    for (int i = 1; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            const double lim = 0.999 * sqrt(N[pk(i, i)] * N[pk(j, j)]);
+            if (fabs(N[pk(i, j)]) > lim) { N[pk(i, j)] = copysign(lim, N[pk(i, j)]); rep = true; }
+        }
+#pragma unroll
+    for (int i = 0; i < 21; ++i) c[i] = (float)N[i];
+    *repaired = rep;
+    return 0;
+}
+
+struct Routing {
+    int mode;        // 0 FP32, 1 routed
+    float cond2_max; // squared condition threshold
+    float pt_lo, pt_hi;
+};
+
+// Update with a 3-D hit (Section 2.1: 3x3 measurement covariance V).
+//   S = C_xx + V, S^-1 by adjugate / determinant, K = C[:, 0:3] S^-1,
+//   x += K r, C -= K C[0:3, :] (packed lower triangle), dchi2 = r^T S^-1 r.
+// Routing: the update is redone in FP64 (update_fp64) when S is not positive
+// definite in FP32, when its Frobenius condition estimate
+// ||S||_F ||S^-1||_F exceeds the threshold, or when pT lies outside
+// [pt_lo, pt_hi].  Returns 0 updated in FP32, 2 updated in FP64, 3 updated
+// in FP64 with a PSD repair, 1 failed (S not positive definite).
+__device__ __forceinline__ int update(float x[6], float c[21], const float m[3], const float v[6],
+                                      const Routing &rt, float *dchi2)
+{
+    const float a = c[0] + v[0], b = c[1] + v[1], cc = c[2] + v[2];
+    const float d = c[3] + v[3], e = c[4] + v[4], f = c[5] + v[5];
+    const float i00 = cc * f - e * e, i10 = d * e - b * f, i11 = a * f - d * d;
+    const float i20 = b * e - cc * d, i21 = b * d - a * e, i22 = a * cc - b * b;
+    const float det = fmaf(a, i00, fmaf(b, i10, d * i20));
+    const bool pd = a > 0.0f && i22 > 0.0f && det > 0.0f;
+    if (rt.mode == 1) {
+        const float sS = a * a + cc * cc + f * f + 2.0f * (b * b + d * d + e * e);
+        const float sI = i00 * i00 + i11 * i11 + i22 * i22 + 2.0f * (i10 * i10 + i20 * i20 + i21 * i21);
+        const float pt2 = x[3] * x[3] + x[4] * x[4];
+        const bool ill = !pd || sS * sI > rt.cond2_max * det * det || pt2 < rt.pt_lo * rt.pt_lo ||
+                         pt2 > rt.pt_hi * rt.pt_hi;
+        if (ill) {
+            bool rep = false;
+            if (update_fp64(x, c, m, v, dchi2, &rep)) return 1;
+            return rep ? 3 : 2;
+        }
+    } else if (!pd) {
+        return 1;
+    }
+    const float id = 1.0f / det;
+    const float s00 = i00 * id, s10 = i10 * id, s11 = i11 * id, s20 = i20 * id, s21 = i21 * id, s22 = i22 * id;
+    const float r0 = m[0] - x[0], r1 = m[1] - x[1], r2 = m[2] - x[2];
+    float K[6][3];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const float c0 = c[pk(i, 0)], c1 = c[pk(i, 1)], c2 = c[pk(i, 2)];
+        K[i][0] = fmaf(c0, s00, fmaf(c1, s10, c2 * s20));
+        K[i][1] = fmaf(c0, s10, fmaf(c1, s11, c2 * s21));
+        K[i][2] = fmaf(c0, s20, fmaf(c1, s21, c2 * s22));
+    }
+    const float q0 = fmaf(s00, r0, fmaf(s10, r1, s20 * r2));
+    const float q1 = fmaf(s10, r0, fmaf(s11, r1, s21 * r2));
+    const float q2 = fmaf(s20, r0, fmaf(s21, r1, s22 * r2));
+    *dchi2 = fmaf(r0, q0, fmaf(r1, q1, r2 * q2));
+    float h[3][6];  // rows 0..2 of C before the update
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) h[k][j] = c[pk(k, j)];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) x[i] = fmaf(K[i][0], r0, fmaf(K[i][1], r1, fmaf(K[i][2], r2, x[i])));
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j)
+            c[pk(i, j)] = fmaf(-K[i][0], h[0][j], fmaf(-K[i][1], h[1][j], fmaf(-K[i][2], h[2][j], c[pk(i, j)])));
+    return 0;
+}
+
+}  // namespace kf

@@ -1,0 +1,214 @@
+"""Python binding of the C library (``include/kf.h``): argument marshalling only.
+
+Every step of the fit and the build runs in the library's CUDA kernels; this
+module turns torch CUDA tensors into the pointers, sizes and stream the C
+entry points take, and allocates output tensors.  It has no fallback: if the
+compiled library is missing or no sm_103a device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+HEADER = os.path.join(_build.INCLUDE, "kf.h")
+
+KF_OK = 0
+FLAG_UNREACHABLE = 1
+FLAG_LEFT_BARREL = 2
+FLAG_INVERSION_FAILED = 4
+FLAG_NAN_INPUT = 8
+FLAG_FP64_PATH = 16
+FLAG_PSD_REPAIRED = 32
+PRECISION_FP32 = 0
+PRECISION_ROUTED = 1
+LAUNCH_AUTO = 0
+LAUNCH_PER_EVENT = 1
+LAUNCH_FLAT = 2
+
+
+class KFError(RuntimeError):
+    pass
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_int), ("r", ctypes.POINTER(ctypes.c_float)),
+                ("x_over_x0", ctypes.POINTER(ctypes.c_float)), ("z_half", ctypes.c_float),
+                ("bz_tesla", ctypes.c_float)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision_mode", ctypes.c_int), ("cond_max", ctypes.c_float),
+                ("pt_lo", ctypes.c_float), ("pt_hi", ctypes.c_float),
+                ("launch_mode", ctypes.c_int), ("tracks_per_block", ctypes.c_int),
+                ("layer_tile", ctypes.c_int), ("max_cands", ctypes.c_int),
+                ("chi2_cut", ctypes.c_float), ("window_nsigma", ctypes.c_float),
+                ("hit_sigma_rphi", ctypes.c_float), ("hit_sigma_z", ctypes.c_float),
+                ("n_phi_bins", ctypes.c_int), ("n_z_bins", ctypes.c_int),
+                ("use_proposal", ctypes.c_int), ("topk", ctypes.c_int)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load the compiled library (``build()`` must have produced it)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise KFError(f"{path} is missing: run paper_1705_02876_gb300.build.build() first")
+        L = ctypes.CDLL(path)
+        L.kf_options_default.argtypes = [ctypes.POINTER(Options)]
+        L.kf_options_default.restype = None
+        L.kf_context_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int]
+        L.kf_context_destroy.argtypes = [_vp]
+        L.kf_context_destroy.restype = None
+        L.kf_last_error.argtypes = [_vp]
+        L.kf_last_error.restype = ctypes.c_char_p
+        L.kf_fit_tracks.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int64, _vp, ctypes.c_int] + \
+            [_vp] * 11 + [ctypes.POINTER(Options), _vp]
+        L.kf_fit_tuned_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/kf.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kf_[a-z0-9_]+)\s*\(", text)))
+
+
+def options(**kw) -> Options:
+    o = Options()
+    load().kf_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """A library context on one CUDA device."""
+
+    def __init__(self, device: int | None = None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        self._h = _vp()
+        rc = load().kf_context_create(ctypes.byref(self._h), self.device)
+        if rc != KF_OK:
+            raise KFError(f"kf_context_create failed with {rc} (needs an sm_103 device)")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def check(self, rc: int, what: str):
+        if rc != KF_OK:
+            msg = load().kf_last_error(self._h).decode()
+            raise KFError(f"{what} failed ({rc}): {msg}")
+
+    def close(self):
+        if self._h:
+            load().kf_context_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tuned_shape(self, n_layers: int, n_tracks: int):
+        b, t = ctypes.c_int(), ctypes.c_int()
+        rc = load().kf_fit_tuned_shape(self._h, n_layers, n_tracks, ctypes.byref(b), ctypes.byref(t))
+        return (b.value, t.value) if rc == KF_OK else None
+
+
+class GeometryArgs:
+    """Host-side geometry struct with its arrays kept alive."""
+
+    def __init__(self, radii, x_over_x0, z_half, bz):
+        self.r = np.ascontiguousarray(radii, dtype=np.float32)
+        self.x = np.ascontiguousarray(x_over_x0, dtype=np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        self.struct = Geometry(len(self.r), self.r.ctypes.data_as(fp), self.x.ctypes.data_as(fp),
+                               float(z_half), float(bz))
+
+    @classmethod
+    def of(cls, geom):
+        return cls(geom.radii, geom.x_over_x0, geom.z_half, geom.bz)
+
+
+def _ptr(t: torch.Tensor, dtype, shape=None, name=""):
+    if t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+        raise KFError(f"{name}: expected a contiguous CUDA {dtype} tensor, got {t.dtype} "
+                      f"{'cuda' if t.is_cuda else 'cpu'} contiguous={t.is_contiguous()}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise KFError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
+    return t.data_ptr() if t.numel() else None
+
+
+def fit_outputs(n_tracks: int, device) -> dict:
+    return dict(state=torch.empty((6, n_tracks), dtype=torch.float32, device=device),
+                cov=torch.empty((21, n_tracks), dtype=torch.float32, device=device),
+                chi2=torch.empty(n_tracks, dtype=torch.float32, device=device),
+                ndof=torch.empty(n_tracks, dtype=torch.int16, device=device),
+                flags=torch.empty(n_tracks, dtype=torch.int32, device=device))
+
+
+def fit_tracks(ctx: Context, geom: GeometryArgs, seed_state, seed_cov, charge, hit_pos, hit_cov,
+               hit_mask, event_offsets=None, opt: Options | None = None, out: dict | None = None,
+               stream: torch.cuda.Stream | None = None) -> dict:
+    """kf_fit_tracks on CUDA tensors; returns (or fills) the output tensors."""
+    T = int(charge.shape[0])
+    L = geom.struct.n_layers
+    if out is None:
+        out = fit_outputs(T, charge.device)
+    args = [
+        _ptr(seed_state, torch.float32, (6, T), "seed_state"),
+        _ptr(seed_cov, torch.float32, (21, T), "seed_cov"),
+        _ptr(charge, torch.int8, (T,), "charge"),
+        _ptr(hit_pos, torch.float32, (L, 3, T), "hit_pos"),
+        _ptr(hit_cov, torch.float32, (L, 6, T), "hit_cov"),
+        _ptr(hit_mask, torch.int32, (T,), "hit_mask"),
+        _ptr(out["state"], torch.float32, (6, T), "out_state"),
+        _ptr(out["cov"], torch.float32, (21, T), "out_cov"),
+        _ptr(out["chi2"], torch.float32, (T,), "out_chi2"),
+        _ptr(out["ndof"], torch.int16, (T,), "out_ndof"),
+        _ptr(out["flags"], torch.int32, (T,), "out_flags"),
+    ]
+    n_ev = 0
+    ev_ptr = None
+    if event_offsets is not None:
+        ev = np.ascontiguousarray(event_offsets, dtype=np.int64)
+        n_ev = len(ev) - 1
+        ev_ptr = ev.ctypes.data
+    s = stream if stream is not None else torch.cuda.current_stream(charge.device)
+    rc = load().kf_fit_tracks(ctx.handle, ctypes.byref(geom.struct), T, ev_ptr, n_ev, *args,
+                              ctypes.byref(opt) if opt is not None else None, s.cuda_stream)
+    ctx.check(rc, "kf_fit_tracks")
+    return out
+
+
+def to_device(batch, device="cuda") -> dict:
+    """Copy a ``synth.FitBatch``'s input arrays to the device."""
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(device=device, dtype=dt)
+    return dict(seed_state=t(batch.seed_state, torch.float32), seed_cov=t(batch.seed_cov, torch.float32),
+                charge=t(batch.charge, torch.int8), hit_pos=t(batch.hit_pos, torch.float32),
+                hit_cov=t(batch.hit_cov, torch.float32),
+                hit_mask=t(batch.hit_mask.view(np.int32), torch.int32))

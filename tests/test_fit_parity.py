@@ -1,0 +1,147 @@
+"""GPU fit against the FP64 oracle, element by element, on the same seeded
+inputs, through the C interface.
+
+Tolerances (stated for the fit): positions |dx| / r_last <= 1e-4, momenta
+|dp_i| / |p| <= 1e-4, chi2 |d| <= 1e-3 max(chi2, ndof); ndof and the stop
+flags (unreachable, left barrel, NaN input) exact.  r_last is the radius of
+the last layer the track reached.
+"""
+import numpy as np
+import pytest
+
+from paper_1705_02876_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+STOP = 1 | 2 | 8  # unreachable, left barrel, NaN input
+
+
+@pytest.fixture(scope="module")
+def kf():
+    from paper_1705_02876_gb300 import build, kf as kf_
+    build.build()
+    return kf_
+
+
+@pytest.fixture(scope="module")
+def ctx(kf):
+    return kf.Context(0)
+
+
+def run_gpu(kf, ctx, batch, **opt):
+    dev = kf.to_device(batch)
+    out = kf.fit_tracks(ctx, kf.GeometryArgs.of(batch.geom), **dev, event_offsets=batch.event_offsets,
+                        opt=kf.options(**opt))
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def compare(gpu, ref, sel=None, tol_pos=1e-4, tol_mom=1e-4, tol_chi2=1e-3):
+    """GPU results (optionally restricted to the tracks ``sel``) against the
+    oracle's results for the same tracks; asserts the tolerances and returns
+    the worst relative errors."""
+    sel = slice(None) if sel is None else sel
+    gf = gpu["flags"].view(np.uint32)[sel]
+    rf = ref["flags"]
+    bad = np.nonzero((gf & STOP) != (rf & STOP))[0]
+    assert bad.size == 0, ("stop flags differ", bad[:10], gf[bad[:10]], rf[bad[:10]])
+    nd = ref["ndof"]
+    assert np.array_equal(gpu["ndof"][sel].astype(np.int32), nd)
+    rs, gs = ref["state"], gpu["state"][:, sel].astype(np.float64)
+    r_last = np.maximum(np.hypot(rs[0], rs[1]), 1.0)  # radius of the last layer reached
+    pmag = np.linalg.norm(rs[3:], axis=0)
+    e_pos = (np.abs(gs[:3] - rs[:3]) / r_last).max(0, initial=0)
+    e_mom = (np.abs(gs[3:] - rs[3:]) / pmag).max(0, initial=0)
+    e_chi = np.abs(gpu["chi2"][sel] - ref["chi2"]) / np.maximum(np.maximum(ref["chi2"], nd), 1.0)
+    assert e_pos.max(initial=0) <= tol_pos, (e_pos.max(), np.argmax(e_pos))
+    assert e_mom.max(initial=0) <= tol_mom, (e_mom.max(), np.argmax(e_mom))
+    assert e_chi.max(initial=0) <= tol_chi2, (e_chi.max(), np.argmax(e_chi))
+    return dict(pos=float(e_pos.max(initial=0)), mom=float(e_mom.max(initial=0)),
+                chi2=float(e_chi.max(initial=0)))
+
+
+@pytest.mark.parametrize("launch", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_parity_workload(kf, ctx, oracle, launch, precision):
+    """1 event x 1,000 tracks, 10 layers, seeds smeared 10%."""
+    b = synth.workload("parity")
+    ref = oracle.fit_batch(b)
+    gpu = run_gpu(kf, ctx, b, launch_mode=launch, precision_mode=precision)
+    compare(gpu, ref)
+
+
+@pytest.mark.parametrize("block", [32, 64, 128, 256])
+def test_ragged_events_missing_hits(kf, ctx, oracle, block):
+    """17 layers, 95% hit efficiency, uneven events with a ragged tail
+    (several persistent units and a partial one)."""
+    b = synth.make_fit_batch(31, [517, 1, 2049, 33, 700], geom=synth.toy_geometry(17), hit_eff=0.95)
+    ref = oracle.fit_batch(b)
+    for launch in (0, 1):
+        gpu = run_gpu(kf, ctx, b, launch_mode=launch, tracks_per_block=block)
+        compare(gpu, ref)
+
+
+def test_stops_flags_and_anisotropic_hits(kf, ctx, oracle):
+    """Loopers that cannot reach the outer layers, tracks leaving the barrel,
+    off-diagonal hit covariances (sigma_r != sigma_rphi), NaN inputs."""
+    b = synth.make_fit_batch(32, [3000], pt_lo=0.2, pt_hi=3.0, pt_dist="loguniform", eta_max=2.4,
+                             sigma_r=0.03)
+    deep = np.nonzero(b.crossed[:6].all(0) & (b.hit_mask >> 4 & 1).astype(bool))[0]
+    t_seed, t_hit, t_absent = deep[:3]
+    b.seed_state[3, t_seed] = np.nan
+    b.hit_pos[4, 1, t_hit] = np.inf
+    b.hit_mask[t_absent] &= ~np.uint32(1 << 4)
+    b.hit_pos[4, 1, t_absent] = np.nan  # absent hit: its value must not matter
+    ref = oracle.fit_batch(b)
+    assert (ref["flags"] & 1).any() and (ref["flags"] & 2).any()
+    gpu = run_gpu(kf, ctx, b)
+    gf = gpu["flags"].view(np.uint32)
+    assert gf[t_seed] & 8 and gf[t_hit] & 8 and not gf[t_absent] & 8
+    np.testing.assert_array_equal(gpu["state"][:, t_hit], b.seed_state[:, t_hit])
+    # crossings within float rounding of z_half may legitimately differ; none here
+    compare(gpu, ref)
+
+
+def test_empty_and_single(kf, ctx, oracle):
+    for n in (0, 1, 31, 32, 33):
+        b = synth.make_fit_batch(33, [n])
+        ref = oracle.fit_batch(b)
+        gpu = run_gpu(kf, ctx, b)
+        if n:
+            compare(gpu, ref)
+
+
+def test_deterministic_and_idempotent(kf, ctx):
+    b = synth.make_fit_batch(34, [5000])
+    g1 = run_gpu(kf, ctx, b)
+    g2 = run_gpu(kf, ctx, b)
+    for k in g1:
+        assert np.array_equal(g1[k], g2[k]), k
+
+
+def test_argument_errors(kf, ctx):
+    b = synth.make_fit_batch(35, [64])
+    dev = kf.to_device(b)
+    bad = synth.Geometry(b.geom.radii[::-1].copy(), b.geom.x_over_x0, b.geom.z_half, b.geom.bz)
+    with pytest.raises(kf.KFError, match="increasing"):
+        kf.fit_tracks(ctx, kf.GeometryArgs.of(bad), **dev)
+    with pytest.raises(kf.KFError, match="event_offsets"):
+        kf.fit_tracks(ctx, kf.GeometryArgs.of(b.geom), **dev, opt=kf.options(launch_mode=1))
+    with pytest.raises(kf.KFError, match="precision_mode"):
+        kf.fit_tracks(ctx, kf.GeometryArgs.of(b.geom), **dev, opt=kf.options(precision_mode=7))
+
+
+@pytest.mark.slow
+def test_full_size_fit_sampled(kf, ctx, oracle):
+    """100 events x 20,000 tracks in the benchmark's launch configuration;
+    4,000 sampled tracks compared with the oracle one by one."""
+    b = synth.workload("fit")
+    gpu = run_gpu(kf, ctx, b)
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(b.n_tracks, 4000, replace=False))
+    sub = synth.FitBatch(b.geom, b.seed_state[:, sel], b.seed_cov[:, sel], b.charge[sel],
+                         b.hit_pos[:, :, sel], b.hit_cov[:, :, sel], b.hit_mask[sel],
+                         np.array([0, len(sel)]), b.truth[:, :, sel], b.crossed[:, sel], b.vertex[:, sel])
+    ref = oracle.fit_batch(sub)
+    compare(gpu, ref, sel=sel)
