@@ -121,6 +121,7 @@ Routing make_routing(const kf_options &o)
     rt.cond2_max = o.cond_max * o.cond_max;
     rt.pt_lo = o.pt_lo;
     rt.pt_hi = o.pt_hi;
+    rt.gain_max = o.gain_max;
     return rt;
 }
 
@@ -129,8 +130,8 @@ int check_options(kf_context *ctx, const kf_options &o)
     if (o.precision_mode != KF_PRECISION_FP32 && o.precision_mode != KF_PRECISION_ROUTED)
         return set_error(ctx, KF_ERR_ARG, "precision_mode %d", o.precision_mode);
     if (o.precision_mode == KF_PRECISION_ROUTED &&
-        (!(o.cond_max > 1.0f) || !(o.pt_lo >= 0.0f) || !(o.pt_hi > o.pt_lo)))
-        return set_error(ctx, KF_ERR_ARG, "routing thresholds: cond_max > 1, 0 <= pt_lo < pt_hi");
+        (!(o.cond_max > 1.0f) || !(o.pt_lo >= 0.0f) || !(o.pt_hi > o.pt_lo) || !(o.gain_max > 0.0f)))
+        return set_error(ctx, KF_ERR_ARG, "routing thresholds: cond_max > 1, 0 <= pt_lo < pt_hi, gain_max > 0");
     if (o.launch_mode < KF_LAUNCH_AUTO || o.launch_mode > KF_LAUNCH_FLAT)
         return set_error(ctx, KF_ERR_ARG, "launch_mode %d", o.launch_mode);
     if (o.tracks_per_block != 0 && o.tracks_per_block != 32 && o.tracks_per_block != 64 &&
@@ -151,6 +152,7 @@ void kf_options_default(kf_options *o)
     o->cond_max = 1e6f;
     o->pt_lo = 0.25f;
     o->pt_hi = 200.0f;
+    o->gain_max = 100.0f;
     o->launch_mode = KF_LAUNCH_AUTO;
     o->tracks_per_block = 0;
     o->layer_tile = 0;

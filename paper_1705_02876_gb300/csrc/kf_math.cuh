@@ -267,16 +267,52 @@ struct Routing {
     int mode;        // 0 FP32, 1 routed
     float cond2_max; // squared condition threshold
     float pt_lo, pt_hi;
+    float gain_max;  // information-gain threshold: C_ii / V_ii above it routes the gain
 };
+
+// Gain of the update in FP64: S^-1 by adjugate and K = C[:, 0:3] S^-1 from
+// the FP32 covariance and hit, rounded back to FP32; also the chi2 increment
+// r^T S^-1 r.  Returns false if S is not positive definite.
+static __device__ __noinline__ bool gain_fp64(const float c[21], const float v[6], const float r[3], float K[6][3],
+                                             float *dchi2)
+{
+    const double a = (double)c[0] + (double)v[0], b = (double)c[1] + (double)v[1], cc = (double)c[2] + (double)v[2];
+    const double d = (double)c[3] + (double)v[3], e = (double)c[4] + (double)v[4], f = (double)c[5] + (double)v[5];
+    const double i00 = cc * f - e * e, i10 = d * e - b * f, i11 = a * f - d * d;
+    const double i20 = b * e - cc * d, i21 = b * d - a * e, i22 = a * cc - b * b;
+    const double det = a * i00 + b * i10 + d * i20;
+    if (!(a > 0.0) || !(i22 > 0.0) || !(det > 0.0)) return false;
+    const double id = 1.0 / det;
+    const double S[3][3] = {{i00 * id, i10 * id, i20 * id}, {i10 * id, i11 * id, i21 * id}, {i20 * id, i21 * id, i22 * id}};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const double c0 = c[pk(i, 0)], c1 = c[pk(i, 1)], c2 = c[pk(i, 2)];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) K[i][j] = (float)(c0 * S[0][j] + c1 * S[1][j] + c2 * S[2][j]);
+    }
+    double chi = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) chi += (double)r[i] * S[i][j] * (double)r[j];
+    *dchi2 = (float)chi;
+    return true;
+}
 
 // Update with a 3-D hit (Section 2.1: 3x3 measurement covariance V).
 //   S = C_xx + V, S^-1 by adjugate / determinant, K = C[:, 0:3] S^-1,
 //   x += K r, C -= K C[0:3, :] (packed lower triangle), dchi2 = r^T S^-1 r.
-// Routing: the update is redone in FP64 (update_fp64) when S is not positive
-// definite in FP32, when its Frobenius condition estimate
-// ||S||_F ||S^-1||_F exceeds the threshold, or when pT lies outside
-// [pt_lo, pt_hi].  Returns 0 updated in FP32, 2 updated in FP64, 3 updated
-// in FP64 with a PSD repair, 1 failed (S not positive definite).
+// Routing (mode 1):
+//   * the whole update is redone in FP64 with a PSD repair (update_fp64) when
+//     S is not positive definite in FP32, when its Frobenius condition
+//     estimate ||S||_F ||S^-1||_F exceeds the threshold, or when pT lies
+//     outside [pt_lo, pt_hi];
+//   * the gain alone (S^-1 and K) is computed in FP64 when the update shrinks
+//     the covariance strongly, C_ii > gain_max V_ii for some i: there K
+//     carries the information as small differences from the identity, which
+//     FP32 cannot resolve.
+// Returns 0 updated in FP32, 2 updated with FP64 arithmetic, 3 updated in
+// FP64 with a PSD repair, 1 failed (S not positive definite).
 __device__ __forceinline__ int update(float x[6], float c[21], const float m[3], const float v[6],
                                       const Routing &rt, float *dchi2)
 {
@@ -286,6 +322,7 @@ __device__ __forceinline__ int update(float x[6], float c[21], const float m[3],
     const float i20 = b * e - cc * d, i21 = b * d - a * e, i22 = a * cc - b * b;
     const float det = fmaf(a, i00, fmaf(b, i10, d * i20));
     const bool pd = a > 0.0f && i22 > 0.0f && det > 0.0f;
+    bool gain64 = false;
     if (rt.mode == 1) {
         const float sS = a * a + cc * cc + f * f + 2.0f * (b * b + d * d + e * e);
         const float sI = i00 * i00 + i11 * i11 + i22 * i22 + 2.0f * (i10 * i10 + i20 * i20 + i21 * i21);
@@ -297,37 +334,42 @@ __device__ __forceinline__ int update(float x[6], float c[21], const float m[3],
             if (update_fp64(x, c, m, v, dchi2, &rep)) return 1;
             return rep ? 3 : 2;
         }
+        gain64 = c[0] > rt.gain_max * v[0] || c[2] > rt.gain_max * v[2] || c[5] > rt.gain_max * v[5];
     } else if (!pd) {
         return 1;
     }
-    const float id = 1.0f / det;
-    const float s00 = i00 * id, s10 = i10 * id, s11 = i11 * id, s20 = i20 * id, s21 = i21 * id, s22 = i22 * id;
-    const float r0 = m[0] - x[0], r1 = m[1] - x[1], r2 = m[2] - x[2];
+    const float r[3] = {m[0] - x[0], m[1] - x[1], m[2] - x[2]};
     float K[6][3];
+    if (gain64) {
+        if (!gain_fp64(c, v, r, K, dchi2)) return 1;
+    } else {
+        const float id = 1.0f / det;
+        const float s00 = i00 * id, s10 = i10 * id, s11 = i11 * id, s20 = i20 * id, s21 = i21 * id, s22 = i22 * id;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        const float c0 = c[pk(i, 0)], c1 = c[pk(i, 1)], c2 = c[pk(i, 2)];
-        K[i][0] = fmaf(c0, s00, fmaf(c1, s10, c2 * s20));
-        K[i][1] = fmaf(c0, s10, fmaf(c1, s11, c2 * s21));
-        K[i][2] = fmaf(c0, s20, fmaf(c1, s21, c2 * s22));
+        for (int i = 0; i < 6; ++i) {
+            const float c0 = c[pk(i, 0)], c1 = c[pk(i, 1)], c2 = c[pk(i, 2)];
+            K[i][0] = fmaf(c0, s00, fmaf(c1, s10, c2 * s20));
+            K[i][1] = fmaf(c0, s10, fmaf(c1, s11, c2 * s21));
+            K[i][2] = fmaf(c0, s20, fmaf(c1, s21, c2 * s22));
+        }
+        const float q0 = fmaf(s00, r[0], fmaf(s10, r[1], s20 * r[2]));
+        const float q1 = fmaf(s10, r[0], fmaf(s11, r[1], s21 * r[2]));
+        const float q2 = fmaf(s20, r[0], fmaf(s21, r[1], s22 * r[2]));
+        *dchi2 = fmaf(r[0], q0, fmaf(r[1], q1, r[2] * q2));
     }
-    const float q0 = fmaf(s00, r0, fmaf(s10, r1, s20 * r2));
-    const float q1 = fmaf(s10, r0, fmaf(s11, r1, s21 * r2));
-    const float q2 = fmaf(s20, r0, fmaf(s21, r1, s22 * r2));
-    *dchi2 = fmaf(r0, q0, fmaf(r1, q1, r2 * q2));
     float h[3][6];  // rows 0..2 of C before the update
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int j = 0; j < 6; ++j) h[k][j] = c[pk(k, j)];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) x[i] = fmaf(K[i][0], r0, fmaf(K[i][1], r1, fmaf(K[i][2], r2, x[i])));
+    for (int i = 0; i < 6; ++i) x[i] = fmaf(K[i][0], r[0], fmaf(K[i][1], r[1], fmaf(K[i][2], r[2], x[i])));
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
         for (int j = 0; j <= i; ++j)
             c[pk(i, j)] = fmaf(-K[i][0], h[0][j], fmaf(-K[i][1], h[1][j], fmaf(-K[i][2], h[2][j], c[pk(i, j)])));
-    return 0;
+    return gain64 ? 2 : 0;
 }
 
 }  // namespace kf

@@ -44,7 +44,7 @@ class Geometry(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision_mode", ctypes.c_int), ("cond_max", ctypes.c_float),
-                ("pt_lo", ctypes.c_float), ("pt_hi", ctypes.c_float),
+                ("pt_lo", ctypes.c_float), ("pt_hi", ctypes.c_float), ("gain_max", ctypes.c_float),
                 ("launch_mode", ctypes.c_int), ("tracks_per_block", ctypes.c_int),
                 ("layer_tile", ctypes.c_int), ("max_cands", ctypes.c_int),
                 ("chi2_cut", ctypes.c_float), ("window_nsigma", ctypes.c_float),

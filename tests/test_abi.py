@@ -26,8 +26,8 @@ def test_options_defaults_and_struct_size():
     o = kf.options()
     assert o.precision_mode == kf.PRECISION_ROUTED
     assert o.max_cands == 6 and abs(o.chi2_cut - 30.0) < 1e-6 and o.topk == 4
-    # the ctypes mirror has the C struct's size: 16 four-byte fields
-    assert ctypes.sizeof(kf.Options) == 16 * 4
+    # the ctypes mirror has the C struct's size: 17 four-byte fields
+    assert ctypes.sizeof(kf.Options) == 17 * 4
 
 
 def test_context_create_fails_cleanly_without_gpu():
