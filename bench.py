@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--events", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--precision", default="routed", choices=["routed", "fp32"],
+                   help="precision of the timed fit (the chosen form is routed)")
     return p.parse_args()
 
 
@@ -238,7 +240,7 @@ def main():
     d_in = kf.to_device(batch, dev)
     out = kf.fit_outputs(T, dev)
     stream = torch.cuda.current_stream(dev)
-    chosen = kf.options()  # routed precision, persistent graph launch, autotuned block
+    chosen = kf.options(precision_mode=kf.PRECISION_ROUTED if args.precision == "routed" else kf.PRECISION_FP32)
 
     def step(opt=chosen, o=out):
         kf.fit_tracks(ctx, geom, **d_in, event_offsets=batch.event_offsets, opt=opt, out=o, stream=stream)
@@ -332,7 +334,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "tracks_per_gpu": T, "layers": N_LAYERS,
                    "l2": "inputs larger than L2 (1.18 GB per step), not flushed",
-                   "tracks_per_block": tuned[0] if tuned else None, "parallelism": f"replicas{world}"},
+                   "tracks_per_block": tuned[0] if tuned else None, "reg_cap": tuned[1] if tuned else None,
+                   "parallelism": f"replicas{world}"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": traffic,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
@@ -349,7 +352,7 @@ def main():
         "wall_s_timed": t_wall,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(batch, 200_000)
+        line["cpu_baseline"] = cpu_baseline(batch, T)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

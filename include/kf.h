@@ -63,7 +63,8 @@ typedef struct CUstream_st *kf_stream; /* a cudaStream_t; NULL is the legacy def
 #define KF_FLAG_LEFT_BARREL 2u       /* the crossing lies beyond |z| = z_half: fit stops */
 #define KF_FLAG_INVERSION_FAILED 4u  /* S = H C H^T + V not positive definite: update skipped */
 #define KF_FLAG_NAN_INPUT 8u         /* non-finite seed or used hit: outputs are the seed */
-#define KF_FLAG_FP64_PATH 16u        /* at least one update took the FP64 path */
+#define KF_FLAG_FP64_PATH 16u        /* at least one update used extended precision: a float-float
+                                        gain or the FP64 update */
 #define KF_FLAG_PSD_REPAIRED 32u     /* the FP64 path clamped the covariance */
 
 #define KF_MAX_LAYERS 32
@@ -101,8 +102,8 @@ typedef struct {
     /* launch shape (fit) */
     int launch_mode;         /* KF_LAUNCH_* */
     int tracks_per_block;    /* 0 = autotuned, else 32, 64, 128 or 256 */
-    int layer_tile;          /* 0 = autotuned; > 0 layers of hits per shared-memory stage;
-                                -1 = hits read straight from global memory */
+    int reg_cap;             /* registers per thread of the persistent fit: 0 = autotuned,
+                                -1 = uncapped, 128 or 80 */
     /* building */
     int max_cands;           /* N candidates kept per seed, 1 (best hit) .. 8 */
     float chi2_cut;          /* hits with a larger chi2 increment are incompatible */
@@ -169,12 +170,11 @@ int kf_fit_tracks(kf_context *ctx, const kf_geometry *geom, int64_t n_tracks,
 /*
  * Launch shape the autotuner picked for the persistent fit of n_layers layers
  * and a batch of n_tracks' size class (powers of two), once a KF_LAUNCH_AUTO
- * fit of that class has run on ctx.  Writes tracks per block and the layer
- * tile (-1: hits read straight from global memory).  KF_ERR_ARG if that class
- * has not been tuned yet.
+ * fit of that class has run on ctx.  Writes tracks per block and the register
+ * cap per thread (-1: uncapped).  KF_ERR_ARG if that class has not been tuned.
  */
 int kf_fit_tuned_shape(kf_context *ctx, int n_layers, int64_t n_tracks, int *tracks_per_block,
-                       int *layer_tile);
+                       int *reg_cap);
 
 #ifdef __cplusplus
 }

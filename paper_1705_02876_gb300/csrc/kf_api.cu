@@ -38,7 +38,7 @@ struct GraphEntry {
     FitGeom g;
     Routing rt;
     FitIO io;
-    int block, grid;
+    int block, cap, grid;
     cudaGraphExec_t exec;
     uint64_t last_use;
 };
@@ -53,7 +53,7 @@ struct kf_context {
     unsigned *d_counter = nullptr;  // persistent-kernel work counter
     cudaStream_t capture_stream = nullptr;
     std::string err;
-    std::map<std::tuple<int, int, int>, int> tuned_block;  // (L, log2 size, precision) -> block
+    std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;  // (L, log2 size, precision) -> (block, cap)
     std::vector<GraphEntry> graphs;
     uint64_t clock = 0;
     kf::BuildState *build = nullptr;
@@ -137,6 +137,8 @@ int check_options(kf_context *ctx, const kf_options &o)
     if (o.tracks_per_block != 0 && o.tracks_per_block != 32 && o.tracks_per_block != 64 &&
         o.tracks_per_block != 128 && o.tracks_per_block != 256)
         return set_error(ctx, KF_ERR_ARG, "tracks_per_block must be 0, 32, 64, 128 or 256");
+    if (o.reg_cap != 0 && o.reg_cap != -1 && o.reg_cap != 128 && o.reg_cap != 80)
+        return set_error(ctx, KF_ERR_ARG, "reg_cap must be 0, -1, 128 or 80");
     return KF_OK;
 }
 
@@ -155,7 +157,7 @@ void kf_options_default(kf_options *o)
     o->gain_max = 100.0f;
     o->launch_mode = KF_LAUNCH_AUTO;
     o->tracks_per_block = 0;
-    o->layer_tile = 0;
+    o->reg_cap = 0;
     o->max_cands = 6;
     o->chi2_cut = 30.0f;
     o->window_nsigma = 3.0f;
@@ -221,23 +223,23 @@ int size_class(int64_t n)
 // Enqueue the persistent fit: counter reset + kernel, replayed from a cached
 // CUDA graph when this exact launch was captured before.
 cudaError_t enqueue_persistent(kf_context *ctx, const FitGeom &g, const Routing &rt, const FitIO &io, int block,
-                               cudaStream_t stream, bool use_graph)
+                               int cap, cudaStream_t stream, bool use_graph)
 {
-    const int per_sm = persistent_blocks_per_sm(block);
+    const int per_sm = persistent_blocks_per_sm(block, cap);
     if (per_sm <= 0) return cudaErrorInvalidConfiguration;
     const int64_t units = (io.T + 31) / 32;
     const int64_t want = (units * 32 + block - 1) / block;
     const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * per_sm, std::max<int64_t>(want, 1));
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(stream, &cap);
-    if (!use_graph || cap != cudaStreamCaptureStatusNone) {
+    cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(stream, &capst);
+    if (!use_graph || capst != cudaStreamCaptureStatusNone) {
         cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned), stream);
         if (e != cudaSuccess) return e;
-        return launch_fit_persistent(g, rt, io, block, grid, ctx->d_counter, stream);
+        return launch_fit_persistent(g, rt, io, block, cap, grid, ctx->d_counter, stream);
     }
     for (auto &e : ctx->graphs) {
-        if (e.block == block && e.grid == grid && same_bytes(&e.g, &g, sizeof g) && same_bytes(&e.rt, &rt, sizeof rt) &&
-            same_bytes(&e.io, &io, sizeof io)) {
+        if (e.block == block && e.cap == cap && e.grid == grid && same_bytes(&e.g, &g, sizeof g) &&
+            same_bytes(&e.rt, &rt, sizeof rt) && same_bytes(&e.io, &io, sizeof io)) {
             e.last_use = ++ctx->clock;
             return cudaGraphLaunch(e.exec, stream);
         }
@@ -246,8 +248,9 @@ cudaError_t enqueue_persistent(kf_context *ctx, const FitGeom &g, const Routing 
     cudaError_t e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t e1 = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned), ctx->capture_stream);
-    cudaError_t e2 = e1 == cudaSuccess ? launch_fit_persistent(g, rt, io, block, grid, ctx->d_counter, ctx->capture_stream)
-                                       : e1;
+    cudaError_t e2 = e1 == cudaSuccess
+                         ? launch_fit_persistent(g, rt, io, block, cap, grid, ctx->d_counter, ctx->capture_stream)
+                         : e1;
     e = cudaStreamEndCapture(ctx->capture_stream, &graph);
     if (e2 != cudaSuccess) e = e2;
     if (e != cudaSuccess) {
@@ -265,43 +268,46 @@ cudaError_t enqueue_persistent(kf_context *ctx, const FitGeom &g, const Routing 
         cudaGraphExecDestroy(ctx->graphs[lru].exec);
         ctx->graphs.erase(ctx->graphs.begin() + lru);
     }
-    ctx->graphs.push_back(GraphEntry{g, rt, io, block, grid, exec, ++ctx->clock});
+    ctx->graphs.push_back(GraphEntry{g, rt, io, block, cap, grid, exec, ++ctx->clock});
     return cudaGraphLaunch(exec, stream);
 }
 
-// Time each tracks-per-block choice on the caller's own buffers (the fit is
-// idempotent: it reads its inputs and overwrites its outputs) and keep the
-// fastest.  Skipped while the stream is being captured.
-int tune_block(kf_context *ctx, const FitGeom &g, const Routing &rt, const FitIO &io, cudaStream_t stream)
+// Time every compiled (tracks per block, register cap) shape on the caller's
+// own buffers (the fit is idempotent: it reads its inputs and overwrites its
+// outputs) and keep the fastest for this layer count, size class and
+// precision.  Skipped while the stream is being captured.
+std::pair<int, int> tune_shape(kf_context *ctx, const FitGeom &g, const Routing &rt, const FitIO &io,
+                               cudaStream_t stream)
 {
     const auto key = std::make_tuple(g.L, size_class(io.T), rt.mode);
-    auto it = ctx->tuned_block.find(key);
-    if (it != ctx->tuned_block.end()) return it->second;
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(stream, &cap);
-    if (cap != cudaStreamCaptureStatusNone) return 128;
-    static const int choices[] = {32, 64, 128, 256};
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) return it->second;
+    cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(stream, &capst);
+    if (capst != cudaStreamCaptureStatusNone) return {128, 0};
+    int blocks[32], caps[32];
+    const int n = persistent_shapes(blocks, caps, 32);
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    int best = 128;
+    std::pair<int, int> best{128, 0};
     float best_ms = 1e30f;
-    for (int block : choices) {
-        if (enqueue_persistent(ctx, g, rt, io, block, stream, false) != cudaSuccess) continue;  // warm-up
+    for (int i = 0; i < n; ++i) {
+        if (enqueue_persistent(ctx, g, rt, io, blocks[i], caps[i], stream, false) != cudaSuccess) continue;
         cudaEventRecord(a, stream);
-        for (int rep = 0; rep < 3; ++rep) enqueue_persistent(ctx, g, rt, io, block, stream, false);
+        for (int rep = 0; rep < 3; ++rep) enqueue_persistent(ctx, g, rt, io, blocks[i], caps[i], stream, false);
         cudaEventRecord(b, stream);
         if (cudaEventSynchronize(b) != cudaSuccess) break;
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, a, b);
         if (ms < best_ms) {
             best_ms = ms;
-            best = block;
+            best = {blocks[i], caps[i]};
         }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    ctx->tuned_block[key] = best;
+    ctx->tuned[key] = best;
     return best;
 }
 
@@ -359,22 +365,27 @@ int kf_fit_tracks(kf_context *ctx, const kf_geometry *geom, int64_t n_tracks, co
             e = launch_fit_plain(g, rt, io, event_offsets[ev], event_offsets[ev + 1], block ? block : 128, stream);
         break;
     default: {
-        const int b = block ? block : tune_block(ctx, g, rt, io, stream);
-        e = enqueue_persistent(ctx, g, rt, io, b, stream, true);
+        std::pair<int, int> shape{block, o.reg_cap < 0 ? 0 : o.reg_cap};
+        if (!block || !o.reg_cap) {
+            const std::pair<int, int> t = tune_shape(ctx, g, rt, io, stream);
+            if (!block) shape.first = t.first;
+            if (!o.reg_cap) shape.second = t.second;
+        }
+        e = enqueue_persistent(ctx, g, rt, io, shape.first, shape.second, stream, true);
     }
     }
     if (e != cudaSuccess) return cuda_error(ctx, e, "fit launch");
     return KF_OK;
 }
 
-int kf_fit_tuned_shape(kf_context *ctx, int n_layers, int64_t n_tracks, int *tracks_per_block, int *layer_tile)
+int kf_fit_tuned_shape(kf_context *ctx, int n_layers, int64_t n_tracks, int *tracks_per_block, int *reg_cap)
 {
-    if (!ctx || !tracks_per_block || !layer_tile) return KF_ERR_ARG;
-    for (int mode = 0; mode <= 1; ++mode) {
-        auto it = ctx->tuned_block.find(std::make_tuple(n_layers, size_class(n_tracks), mode));
-        if (it != ctx->tuned_block.end()) {
-            *tracks_per_block = it->second;
-            *layer_tile = -1;
+    if (!ctx || !tracks_per_block || !reg_cap) return KF_ERR_ARG;
+    for (int mode = 1; mode >= 0; --mode) {
+        auto it = ctx->tuned.find(std::make_tuple(n_layers, size_class(n_tracks), mode));
+        if (it != ctx->tuned.end()) {
+            *tracks_per_block = it->second.first;
+            *reg_cap = it->second.second ? it->second.second : -1;
             return KF_OK;
         }
     }

@@ -115,11 +115,12 @@ __global__ void __launch_bounds__(256) fit_plain_kernel(const FitGeom g, const R
 
 // Persistent kernel: each warp claims 32-track units from *counter until the
 // batch is exhausted (Section 4.2: fill the GPU with the tracks of many events
-// in one launch).  Warps schedule themselves, so a warp slowed by an FP64
-// update does not hold the rest of its block.
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) fit_persistent_kernel(const FitGeom g, const Routing rt, const FitIO io,
-                                                                unsigned *counter)
+// in one launch).  Warps schedule themselves, so a warp slowed by an
+// extended-precision update does not hold the rest of its block.  MINB > 1
+// caps the registers per thread at 65536 / (BLOCK * MINB) to raise occupancy.
+template <int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) fit_persistent_kernel(const FitGeom g, const Routing rt,
+                                                                      const FitIO io, unsigned *counter)
 {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned n_units = (unsigned)((io.T + 31) / 32);
@@ -131,6 +132,29 @@ __global__ void __launch_bounds__(BLOCK) fit_persistent_kernel(const FitGeom g, 
         const int64_t t = (int64_t)u * 32 + lane;
         if (t < io.T) fit_track(g, rt, io, t);
     }
+}
+
+using PersistentFn = void (*)(FitGeom, Routing, FitIO, unsigned *);
+
+// (block, register cap) shapes the autotuner chooses from; cap 0 = none
+struct Shape {
+    int block, cap;
+    PersistentFn fn;
+};
+const Shape kShapes[] = {
+    {32, 0, fit_persistent_kernel<32, 1>},     {64, 0, fit_persistent_kernel<64, 1>},
+    {128, 0, fit_persistent_kernel<128, 1>},   {256, 0, fit_persistent_kernel<256, 1>},
+    {32, 128, fit_persistent_kernel<32, 16>},  {64, 128, fit_persistent_kernel<64, 8>},
+    {128, 128, fit_persistent_kernel<128, 4>}, {256, 128, fit_persistent_kernel<256, 2>},
+    {32, 80, fit_persistent_kernel<32, 24>},   {64, 80, fit_persistent_kernel<64, 12>},
+    {128, 80, fit_persistent_kernel<128, 6>},  {256, 80, fit_persistent_kernel<256, 3>},
+};
+
+const Shape *find_shape(int block, int cap)
+{
+    for (const Shape &sh : kShapes)
+        if (sh.block == block && sh.cap == cap) return &sh;
+    return nullptr;
 }
 
 }  // namespace
@@ -145,30 +169,32 @@ cudaError_t launch_fit_plain(const FitGeom &g, const Routing &rt, const FitIO &i
     return cudaGetLastError();
 }
 
-int persistent_blocks_per_sm(int block)
+int persistent_blocks_per_sm(int block, int cap)
 {
+    const Shape *sh = find_shape(block, cap);
     int n = 0;
-    cudaError_t e = cudaErrorInvalidValue;
-    switch (block) {
-    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fit_persistent_kernel<32>, 32, 0); break;
-    case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fit_persistent_kernel<64>, 64, 0); break;
-    case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fit_persistent_kernel<128>, 128, 0); break;
-    case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fit_persistent_kernel<256>, 256, 0); break;
-    default: break;
-    }
-    return e == cudaSuccess ? n : 0;
+    if (!sh || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sh->fn, block, 0) != cudaSuccess) return 0;
+    return n;
 }
 
-cudaError_t launch_fit_persistent(const FitGeom &g, const Routing &rt, const FitIO &io, int block, int grid,
+int persistent_shapes(int *blocks, int *caps, int max_n)
+{
+    int n = 0;
+    for (const Shape &sh : kShapes)
+        if (n < max_n) {
+            blocks[n] = sh.block;
+            caps[n] = sh.cap;
+            ++n;
+        }
+    return n;
+}
+
+cudaError_t launch_fit_persistent(const FitGeom &g, const Routing &rt, const FitIO &io, int block, int cap, int grid,
                                   unsigned *counter, cudaStream_t stream)
 {
-    switch (block) {
-    case 32: fit_persistent_kernel<32><<<grid, 32, 0, stream>>>(g, rt, io, counter); break;
-    case 64: fit_persistent_kernel<64><<<grid, 64, 0, stream>>>(g, rt, io, counter); break;
-    case 128: fit_persistent_kernel<128><<<grid, 128, 0, stream>>>(g, rt, io, counter); break;
-    case 256: fit_persistent_kernel<256><<<grid, 256, 0, stream>>>(g, rt, io, counter); break;
-    default: return cudaErrorInvalidValue;
-    }
+    const Shape *sh = find_shape(block, cap);
+    if (!sh) return cudaErrorInvalidValue;
+    sh->fn<<<grid, block, 0, stream>>>(g, rt, io, counter);
     return cudaGetLastError();
 }
 

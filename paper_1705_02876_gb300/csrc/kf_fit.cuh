@@ -39,11 +39,14 @@ constexpr unsigned kStatusTimeout = 1u;
 // Launchers (kf_fit.cu).  All enqueue on `stream` and return the launch error.
 cudaError_t launch_fit_plain(const FitGeom &g, const Routing &rt, const FitIO &io, int64_t t_begin,
                              int64_t t_end, int block, cudaStream_t stream);
-// Persistent kernel: grid = `grid` blocks of `block` threads; warps claim
-// 32-track units from *counter (which must read 0 at launch).
-cudaError_t launch_fit_persistent(const FitGeom &g, const Routing &rt, const FitIO &io, int block,
+// Persistent kernel: grid = `grid` blocks of `block` threads with registers
+// capped at `cap` per thread (0 = no cap); warps claim 32-track units from
+// *counter, which must read 0 at launch.
+cudaError_t launch_fit_persistent(const FitGeom &g, const Routing &rt, const FitIO &io, int block, int cap,
                                   int grid, unsigned *counter, cudaStream_t stream);
-// Blocks of `block` threads that fit on one SM at once for the persistent kernel.
-int persistent_blocks_per_sm(int block);
+// Blocks of the persistent kernel of this shape that fit on one SM at once.
+int persistent_blocks_per_sm(int block, int cap);
+// The (block, cap) shapes compiled in; returns how many were written.
+int persistent_shapes(int *blocks, int *caps, int max_n);
 
 }  // namespace kf

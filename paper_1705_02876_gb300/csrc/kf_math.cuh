@@ -206,8 +206,8 @@ __device__ __forceinline__ void add_scattering(const float xn[6], float r, float
 
 // Update with a 3-D hit m (packed V) in FP64: S^-1 by adjugate, gain, state,
 // covariance C - K C[0:3,:] on the packed lower triangle (symmetric by
-// construction), then the PSD repair: diagonal clamped to at least
-// 1e-12 trace, off-diagonals to |C_ij| <= 0.999 sqrt(C_ii C_jj).
+// construction), then the PSD repair: a non-positive variance is clamped to
+// 1e-12 of the trace.
 // Returns 0 (updated), 1 (S not positive definite); *repaired set if clamped.
 static __device__ __noinline__ int update_fp64(float x[6], float c[21], const float m[3], const float v[6],
                                         float *dchi2, bool *repaired)
@@ -242,6 +242,9 @@ static __device__ __noinline__ int update_fp64(float x[6], float c[21], const fl
 #pragma unroll
         for (int j = 0; j <= i; ++j)
             N[pk(i, j)] = C[pk(i, j)] - (K[i][0] * C[pk(0, j)] + K[i][1] * C[pk(1, j)] + K[i][2] * C[pk(2, j)]);
+    // PSD repair: a variance that cancellation drove to zero or below is
+    // clamped to 1e-12 of the trace.  Correlations are left alone: on the
+    // cylinder the covariance is of rank 5 and |rho| -> 1 is legitimate.
     double tr = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) tr += fabs(N[pk(i, i)]);
@@ -249,14 +252,7 @@ static __device__ __noinline__ int update_fp64(float x[6], float c[21], const fl
     bool rep = false;
 #pragma unroll
     for (int i = 0; i < 6; ++i)
-        if (!(N[pk(i, i)] >= floor_)) { N[pk(i, i)] = floor_; rep = true; }
-#pragma unroll
-    for (int i = 1; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j < i; ++j) {
-            const double lim = 0.999 * sqrt(N[pk(i, i)] * N[pk(j, j)]);
-            if (fabs(N[pk(i, j)]) > lim) { N[pk(i, j)] = copysign(lim, N[pk(i, j)]); rep = true; }
-        }
+        if (!(N[pk(i, i)] > 0.0)) { N[pk(i, i)] = floor_; rep = true; }
 #pragma unroll
     for (int i = 0; i < 21; ++i) c[i] = (float)N[i];
     *repaired = rep;
@@ -270,32 +266,91 @@ struct Routing {
     float gain_max;  // information-gain threshold: C_ii / V_ii above it routes the gain
 };
 
-// Gain of the update in FP64: S^-1 by adjugate and K = C[:, 0:3] S^-1 from
-// the FP32 covariance and hit, rounded back to FP32; also the chi2 increment
-// r^T S^-1 r.  Returns false if S is not positive definite.
-static __device__ __noinline__ bool gain_fp64(const float c[21], const float v[6], const float r[3], float K[6][3],
-                                             float *dchi2)
+// Float-float arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2, about 48
+// significant bits carried on the FP32 pipe.  Error-free transformations
+// (Knuth's two-sum, Dekker's fast two-sum, the FMA two-product) use the _rn
+// intrinsics, which the compiler never contracts or reassociates.
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b)
 {
-    const double a = (double)c[0] + (double)v[0], b = (double)c[1] + (double)v[1], cc = (double)c[2] + (double)v[2];
-    const double d = (double)c[3] + (double)v[3], e = (double)c[4] + (double)v[4], f = (double)c[5] + (double)v[5];
-    const double i00 = cc * f - e * e, i10 = d * e - b * f, i11 = a * f - d * d;
-    const double i20 = b * e - cc * d, i21 = b * d - a * e, i22 = a * cc - b * b;
-    const double det = a * i00 + b * i10 + d * i20;
-    if (!(a > 0.0) || !(i22 > 0.0) || !(det > 0.0)) return false;
-    const double id = 1.0 / det;
-    const double S[3][3] = {{i00 * id, i10 * id, i20 * id}, {i10 * id, i11 * id, i21 * id}, {i20 * id, i21 * id, i22 * id}};
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b)  // |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y)
+{
+    const ff s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ ff ff_mul(ff x, ff y)
+{
+    const ff p = two_prod(x.hi, y.hi);
+    return fast_two_sum(p.hi, __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo)));
+}
+__device__ __forceinline__ ff ff_neg(ff x) { return {-x.hi, -x.lo}; }
+// a*b - c*d for float-float operands
+__device__ __forceinline__ ff ff_det2(ff a, ff b, ff c, ff d) { return ff_add(ff_mul(a, b), ff_neg(ff_mul(c, d))); }
+// sum_k s_k * c_k with float-float s and plain float c, accurate to float-float
+__device__ __forceinline__ ff ff_dot3(ff s0, ff s1, ff s2, float c0, float c1, float c2)
+{
+    const ff p0 = two_prod(s0.hi, c0), p1 = two_prod(s1.hi, c1), p2 = two_prod(s2.hi, c2);
+    const ff t0 = two_sum(p0.hi, p1.hi);
+    const ff t1 = two_sum(t0.hi, p2.hi);
+    float err = __fadd_rn(__fadd_rn(p0.lo, p1.lo), __fadd_rn(p2.lo, __fadd_rn(t0.lo, t1.lo)));
+    err = __fmaf_rn(s0.lo, c0, __fmaf_rn(s1.lo, c1, __fmaf_rn(s2.lo, c2, err)));
+    return fast_two_sum(t1.hi, err);
+}
+
+// Gain of the update in float-float: S = C_xx + V and S^-1 by adjugate /
+// determinant, then K = C[:, 0:3] S^-1, rounded to FP32 at the end; also the
+// chi2 increment r^T S^-1 r with r = m - x formed exactly.  Returns false if S
+// is not positive definite.
+static __device__ __noinline__ bool gain_ff(const float c[21], const float v[6], const float m[3],
+                                           const float x[3], float K[6][3], float *dchi2)
+{
+    ff S[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) S[i] = two_sum(c[i], v[i]);
+    const ff &a = S[0], &b = S[1], &cc = S[2], &d = S[3], &e = S[4], &f = S[5];
+    const ff i00 = ff_det2(cc, f, e, e), i10 = ff_det2(d, e, b, f), i11 = ff_det2(a, f, d, d);
+    const ff i20 = ff_det2(b, e, cc, d), i21 = ff_det2(b, d, a, e), i22 = ff_det2(a, cc, b, b);
+    const ff det = ff_add(ff_mul(a, i00), ff_add(ff_mul(b, i10), ff_mul(d, i20)));
+    if (!(a.hi > 0.0f) || !(i22.hi > 0.0f) || !(det.hi > 0.0f)) return false;
+    // 1/det: one Newton step on the FP32 reciprocal, r + r (1 - det r)
+    const float r0 = 1.0f / det.hi;
+    const ff dr = ff_mul(det, ff{r0, 0.0f});
+    const ff one_minus = ff_add(ff{1.0f, 0.0f}, ff_neg(dr));
+    const ff id = ff_add(ff{r0, 0.0f}, ff_mul(one_minus, ff{r0, 0.0f}));
+    const ff s00 = ff_mul(i00, id), s10 = ff_mul(i10, id), s11 = ff_mul(i11, id);
+    const ff s20 = ff_mul(i20, id), s21 = ff_mul(i21, id), s22 = ff_mul(i22, id);
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        const double c0 = c[pk(i, 0)], c1 = c[pk(i, 1)], c2 = c[pk(i, 2)];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) K[i][j] = (float)(c0 * S[0][j] + c1 * S[1][j] + c2 * S[2][j]);
+        const float c0 = c[pk(i, 0)], c1 = c[pk(i, 1)], c2 = c[pk(i, 2)];
+        const ff k0 = ff_dot3(s00, s10, s20, c0, c1, c2);
+        const ff k1 = ff_dot3(s10, s11, s21, c0, c1, c2);
+        const ff k2 = ff_dot3(s20, s21, s22, c0, c1, c2);
+        K[i][0] = __fadd_rn(k0.hi, k0.lo);
+        K[i][1] = __fadd_rn(k1.hi, k1.lo);
+        K[i][2] = __fadd_rn(k2.hi, k2.lo);
     }
-    double chi = 0.0;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) chi += (double)r[i] * S[i][j] * (double)r[j];
-    *dchi2 = (float)chi;
+    const ff r0f = two_sum(m[0], -x[0]), r1f = two_sum(m[1], -x[1]), r2f = two_sum(m[2], -x[2]);
+    const ff q0 = ff_add(ff_mul(s00, r0f), ff_add(ff_mul(s10, r1f), ff_mul(s20, r2f)));
+    const ff q1 = ff_add(ff_mul(s10, r0f), ff_add(ff_mul(s11, r1f), ff_mul(s21, r2f)));
+    const ff q2 = ff_add(ff_mul(s20, r0f), ff_add(ff_mul(s21, r1f), ff_mul(s22, r2f)));
+    const ff chi = ff_add(ff_mul(r0f, q0), ff_add(ff_mul(r1f, q1), ff_mul(r2f, q2)));
+    *dchi2 = __fadd_rn(chi.hi, chi.lo);
     return true;
 }
 
@@ -307,12 +362,13 @@ static __device__ __noinline__ bool gain_fp64(const float c[21], const float v[6
 //     S is not positive definite in FP32, when its Frobenius condition
 //     estimate ||S||_F ||S^-1||_F exceeds the threshold, or when pT lies
 //     outside [pt_lo, pt_hi];
-//   * the gain alone (S^-1 and K) is computed in FP64 when the update shrinks
-//     the covariance strongly, C_ii > gain_max V_ii for some i: there K
-//     carries the information as small differences from the identity, which
-//     FP32 cannot resolve.
-// Returns 0 updated in FP32, 2 updated with FP64 arithmetic, 3 updated in
-// FP64 with a PSD repair, 1 failed (S not positive definite).
+//   * the gain alone (S^-1 and K) is computed in float-float when the update
+//     shrinks the covariance strongly, C_ii > gain_max V_ii for some i: there
+//     K carries the information as small differences from the identity,
+//     which FP32 arithmetic cannot resolve.  Float-float runs on the FP32
+//     pipe, which on this part is 64 times wider than the FP64 one.
+// Returns 0 updated in FP32, 2 updated with extended-precision arithmetic,
+// 3 updated in FP64 with a PSD repair, 1 failed (S not positive definite).
 __device__ __forceinline__ int update(float x[6], float c[21], const float m[3], const float v[6],
                                       const Routing &rt, float *dchi2)
 {
@@ -341,7 +397,7 @@ __device__ __forceinline__ int update(float x[6], float c[21], const float m[3],
     const float r[3] = {m[0] - x[0], m[1] - x[1], m[2] - x[2]};
     float K[6][3];
     if (gain64) {
-        if (!gain_fp64(c, v, r, K, dchi2)) return 1;
+        if (!gain_ff(c, v, m, x, K, dchi2)) return 1;
     } else {
         const float id = 1.0f / det;
         const float s00 = i00 * id, s10 = i10 * id, s11 = i11 * id, s20 = i20 * id, s21 = i21 * id, s22 = i22 * id;

@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision_mode", ctypes.c_int), ("cond_max", ctypes.c_float),
                 ("pt_lo", ctypes.c_float), ("pt_hi", ctypes.c_float), ("gain_max", ctypes.c_float),
                 ("launch_mode", ctypes.c_int), ("tracks_per_block", ctypes.c_int),
-                ("layer_tile", ctypes.c_int), ("max_cands", ctypes.c_int),
+                ("reg_cap", ctypes.c_int), ("max_cands", ctypes.c_int),
                 ("chi2_cut", ctypes.c_float), ("window_nsigma", ctypes.c_float),
                 ("hit_sigma_rphi", ctypes.c_float), ("hit_sigma_z", ctypes.c_float),
                 ("n_phi_bins", ctypes.c_int), ("n_z_bins", ctypes.c_int),
