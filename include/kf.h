@@ -103,7 +103,7 @@ typedef struct {
     int launch_mode;         /* KF_LAUNCH_* */
     int tracks_per_block;    /* 0 = autotuned, else 32, 64, 128 or 256 */
     int reg_cap;             /* registers per thread of the persistent fit: 0 = autotuned,
-                                -1 = uncapped, 128 or 80 */
+                                -1 = uncapped, 168, 128, 96 or 80 */
     /* building */
     int max_cands;           /* N candidates kept per seed, 1 (best hit) .. 8 */
     float chi2_cut;          /* hits with a larger chi2 increment are incompatible */

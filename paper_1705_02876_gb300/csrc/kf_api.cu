@@ -137,8 +137,9 @@ int check_options(kf_context *ctx, const kf_options &o)
     if (o.tracks_per_block != 0 && o.tracks_per_block != 32 && o.tracks_per_block != 64 &&
         o.tracks_per_block != 128 && o.tracks_per_block != 256)
         return set_error(ctx, KF_ERR_ARG, "tracks_per_block must be 0, 32, 64, 128 or 256");
-    if (o.reg_cap != 0 && o.reg_cap != -1 && o.reg_cap != 128 && o.reg_cap != 80)
-        return set_error(ctx, KF_ERR_ARG, "reg_cap must be 0, -1, 128 or 80");
+    if (o.reg_cap != 0 && o.reg_cap != -1 && o.reg_cap != 168 && o.reg_cap != 128 && o.reg_cap != 96 &&
+        o.reg_cap != 80)
+        return set_error(ctx, KF_ERR_ARG, "reg_cap must be 0, -1, 168, 128, 96 or 80");
     return KF_OK;
 }
 

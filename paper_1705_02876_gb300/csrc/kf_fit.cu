@@ -31,7 +31,8 @@ __device__ __forceinline__ void load_hit(const FitIO &io, int l, int64_t t, floa
 
 // Fit track t over every layer in order (the steps and stop rules are those of
 // kf_fit_tracks in kf.h).  The next present hit is loaded one layer ahead.
-__device__ __forceinline__ void fit_track(const FitGeom &g, const Routing &rt, const FitIO &io, int64_t t)
+__device__ __forceinline__ void fit_track(const FitGeom &g, const Routing &rt, const FitIO &io, int64_t t,
+                                          float *slot, int stride)
 {
     const int64_t T = io.T;
     float x[6], c[21];
@@ -71,7 +72,7 @@ __device__ __forceinline__ void fit_track(const FitGeom &g, const Routing &rt, c
                 break;
             }
             float d = 0.0f;
-            const int st = update(x, c, m, v, rt, &d);
+            const int st = update(x, c, m, v, rt, &d, slot, stride);
             if (st == 1) {
                 flags |= KF_FLAG_INVERSION_FAILED;
             } else {
@@ -109,8 +110,9 @@ __device__ __forceinline__ void fit_track(const FitGeom &g, const Routing &rt, c
 __global__ void __launch_bounds__(256) fit_plain_kernel(const FitGeom g, const Routing rt, const FitIO io,
                                                          int64_t t_begin, int64_t t_end)
 {
+    extern __shared__ float slots[];
     const int64_t t = t_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < t_end) fit_track(g, rt, io, t);
+    if (t < t_end) fit_track(g, rt, io, t, slots + threadIdx.x, blockDim.x);
 }
 
 // Persistent kernel: each warp claims 32-track units from *counter until the
@@ -122,6 +124,7 @@ template <int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) fit_persistent_kernel(const FitGeom g, const Routing rt,
                                                                       const FitIO io, unsigned *counter)
 {
+    __shared__ float slots[kSlotSize * BLOCK];
     const unsigned lane = threadIdx.x & 31u;
     const unsigned n_units = (unsigned)((io.T + 31) / 32);
     for (;;) {
@@ -130,13 +133,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) fit_persistent_kernel(const FitGe
         u = __shfl_sync(0xffffffffu, u, 0);
         if (u >= n_units) break;
         const int64_t t = (int64_t)u * 32 + lane;
-        if (t < io.T) fit_track(g, rt, io, t);
+        if (t < io.T) fit_track(g, rt, io, t, slots + threadIdx.x, BLOCK);
     }
 }
 
 using PersistentFn = void (*)(FitGeom, Routing, FitIO, unsigned *);
 
-// (block, register cap) shapes the autotuner chooses from; cap 0 = none
+// (block, register cap) shapes the autotuner chooses from; cap 0 = none.
+// A cap of R registers is __launch_bounds__(BLOCK, 65536 / (R * BLOCK)).
 struct Shape {
     int block, cap;
     PersistentFn fn;
@@ -144,8 +148,11 @@ struct Shape {
 const Shape kShapes[] = {
     {32, 0, fit_persistent_kernel<32, 1>},     {64, 0, fit_persistent_kernel<64, 1>},
     {128, 0, fit_persistent_kernel<128, 1>},   {256, 0, fit_persistent_kernel<256, 1>},
-    {32, 128, fit_persistent_kernel<32, 16>},  {64, 128, fit_persistent_kernel<64, 8>},
-    {128, 128, fit_persistent_kernel<128, 4>}, {256, 128, fit_persistent_kernel<256, 2>},
+    {32, 168, fit_persistent_kernel<32, 12>},  {64, 168, fit_persistent_kernel<64, 6>},
+    {128, 168, fit_persistent_kernel<128, 3>}, {32, 128, fit_persistent_kernel<32, 16>},
+    {64, 128, fit_persistent_kernel<64, 8>},   {128, 128, fit_persistent_kernel<128, 4>},
+    {256, 128, fit_persistent_kernel<256, 2>}, {32, 96, fit_persistent_kernel<32, 20>},
+    {64, 96, fit_persistent_kernel<64, 10>},   {128, 96, fit_persistent_kernel<128, 5>},
     {32, 80, fit_persistent_kernel<32, 24>},   {64, 80, fit_persistent_kernel<64, 12>},
     {128, 80, fit_persistent_kernel<128, 6>},  {256, 80, fit_persistent_kernel<256, 3>},
 };
@@ -165,7 +172,7 @@ cudaError_t launch_fit_plain(const FitGeom &g, const Routing &rt, const FitIO &i
     if (t_end <= t_begin) return cudaSuccess;
     const int64_t n = t_end - t_begin;
     const unsigned grid = (unsigned)((n + block - 1) / block);
-    fit_plain_kernel<<<grid, block, 0, stream>>>(g, rt, io, t_begin, t_end);
+    fit_plain_kernel<<<grid, block, kSlotSize * block * sizeof(float), stream>>>(g, rt, io, t_begin, t_end);
     return cudaGetLastError();
 }
 

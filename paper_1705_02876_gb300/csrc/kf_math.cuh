@@ -29,11 +29,16 @@ struct Jac {
 // tau = tan(omega s / 2), the crossing condition |P(s)|^2 = r^2 is the
 // quadratic  B' tau^2 + omega u tau - omega^2 D / 4 = 0  with
 // u = P.t, w = P x t, D = r^2 - |P|^2, B' = 1 + omega w - omega^2 D / 4.
-// Its first-crossing root, rationalised so that it stays exact as omega -> 0,
-// is tau = omega sigma / 2 with sigma = D / (u + sqrt(u^2 + D B')); sigma is
-// the straight-line path length at omega = 0.  sin and cos of the turning
-// angle are rational in tau, so only one atan (for z) is evaluated.
-// Returns false if the cylinder is not reached.
+// Its roots are omega (-u +- sqrt(Q)) / (2 B'), Q = u^2 + D B'.  The root
+// rationalised to tau = omega sigma / 2, sigma = D / (u + sqrt(Q)), stays
+// exact as omega -> 0 (sigma is then the straight-line path length) and is
+// the first crossing whenever u + sqrt(Q) > 0: for B' > 0 the other root lies
+// beyond half a turn, for B' < 0 (a start past the circle's closest approach
+// to the axis, crossing towards its farthest point) both roots share a sign
+// and this one is the smaller.  sin and cos of the turning angle are rational
+// in tau, so only one atan (for z) is evaluated.  A start moving inwards with
+// u + sqrt(Q) <= 0 takes the general two-root path.  Returns false if the
+// cylinder is not reached.
 __device__ __forceinline__ bool propagate(const float x[6], float qkb, float r, float xn[6],
                                           float &s_out, Jac *J)
 {
@@ -50,15 +55,15 @@ __device__ __forceinline__ bool propagate(const float x[6], float qkb, float r, 
     if (!(Qd >= 0.0f) || !(pt2 > 0.0f)) return false;
     const float sq = sqrtf(Qd);
     float s, tau, sigma;
-    if (Bp > 0.0f && u + sq > 0.0f) {
+    if (u + sq > 0.0f) {
         sigma = D / (u + sq);
         tau = 0.5f * om * sigma;
         const float t2 = tau * tau;
         const float ratio = t2 < 1e-6f ? 1.0f - t2 * (1.0f / 3.0f) : atanf(tau) / tau;  // atan(tau)/tau
         s = sigma * ratio;
     } else {
-        // Crossing beyond half a turn, or a start moving inwards: both roots of
-        // the quadratic, each mapped to its smallest positive path length.
+        // A start moving inwards: both roots of the quadratic, each mapped to
+        // its smallest positive path length.
         if (om == 0.0f) return false;
         const float period = 6.283185307179586f / fabsf(om);
         float best = INFINITY;
@@ -204,67 +209,86 @@ __device__ __forceinline__ void add_scattering(const float xn[6], float r, float
     c[pk(5, 5)] = fmaf(t2, p2 - pz * pz, c[pk(5, 5)]);
 }
 
-// Update with a 3-D hit m (packed V) in FP64: S^-1 by adjugate, gain, state,
-// covariance C - K C[0:3,:] on the packed lower triangle (symmetric by
-// construction), then the PSD repair: a non-positive variance is clamped to
-// 1e-12 of the trace.
-// Returns 0 (updated), 1 (S not positive definite); *repaired set if clamped.
-static __device__ __noinline__ int update_fp64(float x[6], float c[21], const float m[3], const float v[6],
-                                        float *dchi2, bool *repaired)
+// The extended-precision paths are out of line and rare.  A non-inlined
+// function's registers count towards the kernel's allocation, so these work
+// from a per-thread slot of shared memory ([kSlotSize][stride] floats,
+// thread-major so that a warp's accesses hit distinct banks), reading and
+// writing the covariance one row at a time: the kernel keeps the register
+// budget of the FP32 main path.
+constexpr int kSlotX = 0, kSlotC = 6, kSlotM = 27, kSlotV = 30, kSlotChi2 = 36, kSlotSize = 37;
+
+__device__ __forceinline__ void slot_write(float *slot, int stride, const float x[6], const float c[21], const float m[3],
+                                           const float v[6])
 {
-    double C[21];
 #pragma unroll
-    for (int i = 0; i < 21; ++i) C[i] = (double)c[i];
-    const double a = C[0] + (double)v[0], b = C[1] + (double)v[1], cc = C[2] + (double)v[2];
-    const double d = C[3] + (double)v[3], e = C[4] + (double)v[4], f = C[5] + (double)v[5];
+    for (int i = 0; i < 6; ++i) slot[(kSlotX + i) * stride] = x[i];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) slot[(kSlotC + i) * stride] = c[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) slot[(kSlotM + i) * stride] = m[i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) slot[(kSlotV + i) * stride] = v[i];
+}
+
+struct SlotRef {
+    float *p;
+    int stride;
+    __device__ __forceinline__ float &x(int i) const { return p[(kSlotX + i) * stride]; }
+    __device__ __forceinline__ float &c(int i, int j) const { return p[(kSlotC + pk(i, j)) * stride]; }
+    __device__ __forceinline__ float &m(int i) const { return p[(kSlotM + i) * stride]; }
+    __device__ __forceinline__ float &v(int i) const { return p[(kSlotV + i) * stride]; }
+    __device__ __forceinline__ float &chi2() const { return p[kSlotChi2 * stride]; }
+};
+
+// Update in FP64 on the slot: S^-1 by adjugate, each row of the gain
+// K = C[:, 0:3] S^-1 formed and applied at once (rows 5..3 read the untouched
+// rows 0..2; rows 2..0 use a copy of the 3x3 block), x += K r,
+// C -= K C[0:3, :] on the packed lower triangle (symmetric by construction),
+// chi2 = r^T S^-1 r; then the PSD repair: a variance that cancellation drove
+// to zero or below is clamped to 1e-12 of the trace (correlations are left
+// alone: on the cylinder the covariance has rank 5 and |rho| -> 1 is
+// legitimate).  Returns 2, 3 (repaired) or 1 (S not positive definite).
+static __device__ __noinline__ int update_fp64(float *slot_p, int stride)
+{
+    const SlotRef sl{slot_p, stride};
+    const double a = (double)sl.c(0, 0) + sl.v(0), b = (double)sl.c(1, 0) + sl.v(1);
+    const double cc = (double)sl.c(1, 1) + sl.v(2), d = (double)sl.c(2, 0) + sl.v(3);
+    const double e = (double)sl.c(2, 1) + sl.v(4), f = (double)sl.c(2, 2) + sl.v(5);
     const double i00 = cc * f - e * e, i10 = d * e - b * f, i11 = a * f - d * d;
     const double i20 = b * e - cc * d, i21 = b * d - a * e, i22 = a * cc - b * b;
     const double det = a * i00 + b * i10 + d * i20;
     if (!(a > 0.0) || !(i22 > 0.0) || !(det > 0.0)) return 1;
     const double id = 1.0 / det;
-    const double S[3][3] = {{i00 * id, i10 * id, i20 * id}, {i10 * id, i11 * id, i21 * id}, {i20 * id, i21 * id, i22 * id}};
-    const double r0 = (double)m[0] - (double)x[0], r1 = (double)m[1] - (double)x[1], r2 = (double)m[2] - (double)x[2];
-    double K[6][3];
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            K[i][j] = C[pk(i, 0)] * S[0][j] + C[pk(i, 1)] * S[1][j] + C[pk(i, 2)] * S[2][j];
-    const double q0 = S[0][0] * r0 + S[0][1] * r1 + S[0][2] * r2;
-    const double q1 = S[1][0] * r0 + S[1][1] * r1 + S[1][2] * r2;
-    const double q2 = S[2][0] * r0 + S[2][1] * r1 + S[2][2] * r2;
-    *dchi2 = (float)(r0 * q0 + r1 * q1 + r2 * q2);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) x[i] = (float)((double)x[i] + K[i][0] * r0 + K[i][1] * r1 + K[i][2] * r2);
-    double N[21];
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j <= i; ++j)
-            N[pk(i, j)] = C[pk(i, j)] - (K[i][0] * C[pk(0, j)] + K[i][1] * C[pk(1, j)] + K[i][2] * C[pk(2, j)]);
-    // PSD repair: a variance that cancellation drove to zero or below is
-    // clamped to 1e-12 of the trace.  Correlations are left alone: on the
-    // cylinder the covariance is of rank 5 and |rho| -> 1 is legitimate.
+    const double s00 = i00 * id, s10 = i10 * id, s11 = i11 * id, s20 = i20 * id, s21 = i21 * id, s22 = i22 * id;
+    const double r0 = (double)sl.m(0) - sl.x(0), r1 = (double)sl.m(1) - sl.x(1), r2 = (double)sl.m(2) - sl.x(2);
+    const double q0 = s00 * r0 + s10 * r1 + s20 * r2, q1 = s10 * r0 + s11 * r1 + s21 * r2;
+    const double q2 = s20 * r0 + s21 * r1 + s22 * r2;
+    sl.chi2() = (float)(r0 * q0 + r1 * q1 + r2 * q2);
+    // rows 5..3, then 2..0 from a copy of the 3x3 block; within a row the
+    // columns descend, so every C[0:3, j] read is still the original value
+    double h[6];
+    for (int i = 5; i >= 0; --i) {
+        if (i == 2)
+            for (int k = 0; k < 6; ++k) h[k] = sl.p[(kSlotC + k) * stride];
+        auto src = [&](int k, int j) -> double { return i >= 3 ? (double)sl.c(k, j) : h[pk(k, j)]; };
+        const double c0 = src(i, 0), c1 = src(i, 1), c2 = src(i, 2);
+        const double k0 = c0 * s00 + c1 * s10 + c2 * s20;
+        const double k1 = c0 * s10 + c1 * s11 + c2 * s21;
+        const double k2 = c0 * s20 + c1 * s21 + c2 * s22;
+        sl.x(i) = (float)((double)sl.x(i) + k0 * r0 + k1 * r1 + k2 * r2);
+        for (int j = i; j >= 0; --j)
+            sl.c(i, j) = (float)((double)sl.c(i, j) - (k0 * src(0, j) + k1 * src(1, j) + k2 * src(2, j)));
+    }
     double tr = 0.0;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) tr += fabs(N[pk(i, i)]);
-    const double floor_ = 1e-12 * tr;
+    for (int i = 0; i < 6; ++i) tr += fabs((double)sl.c(i, i));
     bool rep = false;
-#pragma unroll
     for (int i = 0; i < 6; ++i)
-        if (!(N[pk(i, i)] > 0.0)) { N[pk(i, i)] = floor_; rep = true; }
-#pragma unroll
-    for (int i = 0; i < 21; ++i) c[i] = (float)N[i];
-    *repaired = rep;
-    return 0;
+        if (!(sl.c(i, i) > 0.0f)) {
+            sl.c(i, i) = (float)(1e-12 * tr);
+            rep = true;
+        }
+    return rep ? 3 : 2;
 }
-
-struct Routing {
-    int mode;        // 0 FP32, 1 routed
-    float cond2_max; // squared condition threshold
-    float pt_lo, pt_hi;
-    float gain_max;  // information-gain threshold: C_ii / V_ii above it routes the gain
-};
 
 // Float-float arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2, about 48
 // significant bits carried on the FP32 pipe.  Error-free transformations
@@ -313,64 +337,83 @@ __device__ __forceinline__ ff ff_dot3(ff s0, ff s1, ff s2, float c0, float c1, f
     return fast_two_sum(t1.hi, err);
 }
 
-// Gain of the update in float-float: S = C_xx + V and S^-1 by adjugate /
-// determinant, then K = C[:, 0:3] S^-1, rounded to FP32 at the end; also the
-// chi2 increment r^T S^-1 r with r = m - x formed exactly.  Returns false if S
-// is not positive definite.
-static __device__ __noinline__ bool gain_ff(const float c[21], const float v[6], const float m[3],
-                                           const float x[3], float K[6][3], float *dchi2)
+// Update on the slot with the gain formed in float-float: S = C_xx + V and
+// S^-1 by adjugate / determinant, each row K_i = C[i, 0:3] S^-1 rounded to
+// FP32 and applied at once (same row order as update_fp64), x += K r and
+// C -= K C[0:3, :] in FP32; chi2 = r^T S^-1 r with r = m - x formed exactly.
+// Returns 2, or 1 if S is not positive definite.
+static __device__ __noinline__ int update_ff(float *slot_p, int stride)
 {
-    ff S[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) S[i] = two_sum(c[i], v[i]);
-    const ff &a = S[0], &b = S[1], &cc = S[2], &d = S[3], &e = S[4], &f = S[5];
+    const SlotRef sl{slot_p, stride};
+    const ff a = two_sum(sl.c(0, 0), sl.v(0)), b = two_sum(sl.c(1, 0), sl.v(1));
+    const ff cc = two_sum(sl.c(1, 1), sl.v(2)), d = two_sum(sl.c(2, 0), sl.v(3));
+    const ff e = two_sum(sl.c(2, 1), sl.v(4)), f = two_sum(sl.c(2, 2), sl.v(5));
     const ff i00 = ff_det2(cc, f, e, e), i10 = ff_det2(d, e, b, f), i11 = ff_det2(a, f, d, d);
     const ff i20 = ff_det2(b, e, cc, d), i21 = ff_det2(b, d, a, e), i22 = ff_det2(a, cc, b, b);
     const ff det = ff_add(ff_mul(a, i00), ff_add(ff_mul(b, i10), ff_mul(d, i20)));
-    if (!(a.hi > 0.0f) || !(i22.hi > 0.0f) || !(det.hi > 0.0f)) return false;
+    if (!(a.hi > 0.0f) || !(i22.hi > 0.0f) || !(det.hi > 0.0f)) return 1;
     // 1/det: one Newton step on the FP32 reciprocal, r + r (1 - det r)
-    const float r0 = 1.0f / det.hi;
-    const ff dr = ff_mul(det, ff{r0, 0.0f});
-    const ff one_minus = ff_add(ff{1.0f, 0.0f}, ff_neg(dr));
-    const ff id = ff_add(ff{r0, 0.0f}, ff_mul(one_minus, ff{r0, 0.0f}));
+    const float rc = 1.0f / det.hi;
+    const ff one_minus = ff_add(ff{1.0f, 0.0f}, ff_neg(ff_mul(det, ff{rc, 0.0f})));
+    const ff id = ff_add(ff{rc, 0.0f}, ff_mul(one_minus, ff{rc, 0.0f}));
     const ff s00 = ff_mul(i00, id), s10 = ff_mul(i10, id), s11 = ff_mul(i11, id);
     const ff s20 = ff_mul(i20, id), s21 = ff_mul(i21, id), s22 = ff_mul(i22, id);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        const float c0 = c[pk(i, 0)], c1 = c[pk(i, 1)], c2 = c[pk(i, 2)];
-        const ff k0 = ff_dot3(s00, s10, s20, c0, c1, c2);
-        const ff k1 = ff_dot3(s10, s11, s21, c0, c1, c2);
-        const ff k2 = ff_dot3(s20, s21, s22, c0, c1, c2);
-        K[i][0] = __fadd_rn(k0.hi, k0.lo);
-        K[i][1] = __fadd_rn(k1.hi, k1.lo);
-        K[i][2] = __fadd_rn(k2.hi, k2.lo);
+    const ff r0 = two_sum(sl.m(0), -sl.x(0)), r1 = two_sum(sl.m(1), -sl.x(1)), r2 = two_sum(sl.m(2), -sl.x(2));
+    const ff q0 = ff_add(ff_mul(s00, r0), ff_add(ff_mul(s10, r1), ff_mul(s20, r2)));
+    const ff q1 = ff_add(ff_mul(s10, r0), ff_add(ff_mul(s11, r1), ff_mul(s21, r2)));
+    const ff q2 = ff_add(ff_mul(s20, r0), ff_add(ff_mul(s21, r1), ff_mul(s22, r2)));
+    const ff chi = ff_add(ff_mul(r0, q0), ff_add(ff_mul(r1, q1), ff_mul(r2, q2)));
+    sl.chi2() = __fadd_rn(chi.hi, chi.lo);
+    const float rr0 = __fadd_rn(r0.hi, r0.lo), rr1 = __fadd_rn(r1.hi, r1.lo), rr2 = __fadd_rn(r2.hi, r2.lo);
+    float h[6];
+    for (int i = 5; i >= 0; --i) {
+        if (i == 2)
+            for (int k = 0; k < 6; ++k) h[k] = sl.p[(kSlotC + k) * stride];
+        auto src = [&](int k, int j) -> float { return i >= 3 ? sl.c(k, j) : h[pk(k, j)]; };
+        const float c0 = src(i, 0), c1 = src(i, 1), c2 = src(i, 2);
+        const ff k0f = ff_dot3(s00, s10, s20, c0, c1, c2);
+        const ff k1f = ff_dot3(s10, s11, s21, c0, c1, c2);
+        const ff k2f = ff_dot3(s20, s21, s22, c0, c1, c2);
+        const float k0 = __fadd_rn(k0f.hi, k0f.lo), k1 = __fadd_rn(k1f.hi, k1f.lo), k2 = __fadd_rn(k2f.hi, k2f.lo);
+        sl.x(i) = fmaf(k0, rr0, fmaf(k1, rr1, fmaf(k2, rr2, sl.x(i))));
+        for (int j = i; j >= 0; --j)
+            sl.c(i, j) = fmaf(-k0, src(0, j), fmaf(-k1, src(1, j), fmaf(-k2, src(2, j), sl.c(i, j))));
     }
-    const ff r0f = two_sum(m[0], -x[0]), r1f = two_sum(m[1], -x[1]), r2f = two_sum(m[2], -x[2]);
-    const ff q0 = ff_add(ff_mul(s00, r0f), ff_add(ff_mul(s10, r1f), ff_mul(s20, r2f)));
-    const ff q1 = ff_add(ff_mul(s10, r0f), ff_add(ff_mul(s11, r1f), ff_mul(s21, r2f)));
-    const ff q2 = ff_add(ff_mul(s20, r0f), ff_add(ff_mul(s21, r1f), ff_mul(s22, r2f)));
-    const ff chi = ff_add(ff_mul(r0f, q0), ff_add(ff_mul(r1f, q1), ff_mul(r2f, q2)));
-    *dchi2 = __fadd_rn(chi.hi, chi.lo);
-    return true;
+    return 2;
 }
+
+static __device__ __noinline__ int update_ext(float *slot, int stride, int kind)
+{
+    return kind == 2 ? update_fp64(slot, stride) : update_ff(slot, stride);
+}
+
+struct Routing {
+    int mode;        // 0 FP32, 1 routed
+    float cond2_max; // squared condition threshold
+    float pt_lo, pt_hi;
+    float gain_max;  // information-gain threshold: C_ii / V_ii above it routes the gain
+};
 
 // Update with a 3-D hit (Section 2.1: 3x3 measurement covariance V).
 //   S = C_xx + V, S^-1 by adjugate / determinant, K = C[:, 0:3] S^-1,
 //   x += K r, C -= K C[0:3, :] (packed lower triangle), dchi2 = r^T S^-1 r.
+// Each row of K is formed and applied at once: rows 5..3 first, columns
+// descending, so that every C[0:3, j] read is still the original value; then
+// rows 2..0 from a copy of the 3x3 block.
 // Routing (mode 1):
 //   * the whole update is redone in FP64 with a PSD repair (update_fp64) when
 //     S is not positive definite in FP32, when its Frobenius condition
 //     estimate ||S||_F ||S^-1||_F exceeds the threshold, or when pT lies
 //     outside [pt_lo, pt_hi];
-//   * the gain alone (S^-1 and K) is computed in float-float when the update
-//     shrinks the covariance strongly, C_ii > gain_max V_ii for some i: there
-//     K carries the information as small differences from the identity,
-//     which FP32 arithmetic cannot resolve.  Float-float runs on the FP32
-//     pipe, which on this part is 64 times wider than the FP64 one.
+//   * the gain is formed in float-float (update_ff) when the update shrinks
+//     the covariance strongly, C_ii > gain_max V_ii for some i: there K
+//     carries the information as small differences from the identity, which
+//     FP32 arithmetic cannot resolve.  Float-float runs on the FP32 pipe,
+//     which on this part is 64 times wider than the FP64 one.
 // Returns 0 updated in FP32, 2 updated with extended-precision arithmetic,
 // 3 updated in FP64 with a PSD repair, 1 failed (S not positive definite).
 __device__ __forceinline__ int update(float x[6], float c[21], const float m[3], const float v[6],
-                                      const Routing &rt, float *dchi2)
+                                      const Routing &rt, float *dchi2, float *slot, int stride)
 {
     const float a = c[0] + v[0], b = c[1] + v[1], cc = c[2] + v[2];
     const float d = c[3] + v[3], e = c[4] + v[4], f = c[5] + v[5];
@@ -378,54 +421,61 @@ __device__ __forceinline__ int update(float x[6], float c[21], const float m[3],
     const float i20 = b * e - cc * d, i21 = b * d - a * e, i22 = a * cc - b * b;
     const float det = fmaf(a, i00, fmaf(b, i10, d * i20));
     const bool pd = a > 0.0f && i22 > 0.0f && det > 0.0f;
-    bool gain64 = false;
+    int kind = 0;
     if (rt.mode == 1) {
         const float sS = a * a + cc * cc + f * f + 2.0f * (b * b + d * d + e * e);
         const float sI = i00 * i00 + i11 * i11 + i22 * i22 + 2.0f * (i10 * i10 + i20 * i20 + i21 * i21);
         const float pt2 = x[3] * x[3] + x[4] * x[4];
-        const bool ill = !pd || sS * sI > rt.cond2_max * det * det || pt2 < rt.pt_lo * rt.pt_lo ||
-                         pt2 > rt.pt_hi * rt.pt_hi;
-        if (ill) {
-            bool rep = false;
-            if (update_fp64(x, c, m, v, dchi2, &rep)) return 1;
-            return rep ? 3 : 2;
-        }
-        gain64 = c[0] > rt.gain_max * v[0] || c[2] > rt.gain_max * v[2] || c[5] > rt.gain_max * v[5];
+        if (!pd || sS * sI > rt.cond2_max * det * det || pt2 < rt.pt_lo * rt.pt_lo || pt2 > rt.pt_hi * rt.pt_hi)
+            kind = 2;
+        else if (c[0] > rt.gain_max * v[0] || c[2] > rt.gain_max * v[2] || c[5] > rt.gain_max * v[5])
+            kind = 1;
     } else if (!pd) {
         return 1;
     }
-    const float r[3] = {m[0] - x[0], m[1] - x[1], m[2] - x[2]};
-    float K[6][3];
-    if (gain64) {
-        if (!gain_ff(c, v, m, x, K, dchi2)) return 1;
-    } else {
-        const float id = 1.0f / det;
-        const float s00 = i00 * id, s10 = i10 * id, s11 = i11 * id, s20 = i20 * id, s21 = i21 * id, s22 = i22 * id;
+    if (kind) {
+        slot_write(slot, stride, x, c, m, v);
+        const int st = update_ext(slot, stride, kind);
+        if (st == 1) return 1;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            const float c0 = c[pk(i, 0)], c1 = c[pk(i, 1)], c2 = c[pk(i, 2)];
-            K[i][0] = fmaf(c0, s00, fmaf(c1, s10, c2 * s20));
-            K[i][1] = fmaf(c0, s10, fmaf(c1, s11, c2 * s21));
-            K[i][2] = fmaf(c0, s20, fmaf(c1, s21, c2 * s22));
-        }
-        const float q0 = fmaf(s00, r[0], fmaf(s10, r[1], s20 * r[2]));
-        const float q1 = fmaf(s10, r[0], fmaf(s11, r[1], s21 * r[2]));
-        const float q2 = fmaf(s20, r[0], fmaf(s21, r[1], s22 * r[2]));
-        *dchi2 = fmaf(r[0], q0, fmaf(r[1], q1, r[2] * q2));
+        for (int i = 0; i < 6; ++i) x[i] = slot[(kSlotX + i) * stride];
+#pragma unroll
+        for (int i = 0; i < 21; ++i) c[i] = slot[(kSlotC + i) * stride];
+        *dchi2 = slot[kSlotChi2 * stride];
+        return st;
     }
-    float h[3][6];  // rows 0..2 of C before the update
+    const float r[3] = {m[0] - x[0], m[1] - x[1], m[2] - x[2]};
+    const float id = 1.0f / det;
+    const float s00 = i00 * id, s10 = i10 * id, s11 = i11 * id, s20 = i20 * id, s21 = i21 * id, s22 = i22 * id;
+    const float q0 = fmaf(s00, r[0], fmaf(s10, r[1], s20 * r[2]));
+    const float q1 = fmaf(s10, r[0], fmaf(s11, r[1], s21 * r[2]));
+    const float q2 = fmaf(s20, r[0], fmaf(s21, r[1], s22 * r[2]));
+    *dchi2 = fmaf(r[0], q0, fmaf(r[1], q1, r[2] * q2));
+    // rows 5..3, then 2..0 from a copy of the 3x3 block; within a row the
+    // columns descend, so every C[0:3, j] read is still the original value
+    float h[6];
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
+    for (int i = 5; i >= 0; --i) {
+        if (i == 2) {
 #pragma unroll
-        for (int j = 0; j < 6; ++j) h[k][j] = c[pk(k, j)];
+            for (int k = 0; k < 6; ++k) h[k] = c[k];
+        }
+        const float c0 = i >= 3 ? c[pk(i, 0)] : h[pk(i, 0)];
+        const float c1 = i >= 3 ? c[pk(i, 1)] : h[pk(i, 1)];
+        const float c2 = i >= 3 ? c[pk(i, 2)] : h[pk(i, 2)];
+        const float k0 = fmaf(c0, s00, fmaf(c1, s10, c2 * s20));
+        const float k1 = fmaf(c0, s10, fmaf(c1, s11, c2 * s21));
+        const float k2 = fmaf(c0, s20, fmaf(c1, s21, c2 * s22));
+        x[i] = fmaf(k0, r[0], fmaf(k1, r[1], fmaf(k2, r[2], x[i])));
 #pragma unroll
-    for (int i = 0; i < 6; ++i) x[i] = fmaf(K[i][0], r[0], fmaf(K[i][1], r[1], fmaf(K[i][2], r[2], x[i])));
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j <= i; ++j)
-            c[pk(i, j)] = fmaf(-K[i][0], h[0][j], fmaf(-K[i][1], h[1][j], fmaf(-K[i][2], h[2][j], c[pk(i, j)])));
-    return gain64 ? 2 : 0;
+        for (int j = i; j >= 0; --j) {
+            const float h0 = i >= 3 ? c[pk(0, j)] : h[pk(0, j)];
+            const float h1 = i >= 3 ? c[pk(1, j)] : h[pk(1, j)];
+            const float h2 = i >= 3 ? c[pk(2, j)] : h[pk(2, j)];
+            c[pk(i, j)] = fmaf(-k0, h0, fmaf(-k1, h1, fmaf(-k2, h2, c[pk(i, j)])));
+        }
+    }
+    return 0;
 }
 
 }  // namespace kf
