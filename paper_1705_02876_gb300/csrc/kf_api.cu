@@ -53,7 +53,8 @@ struct kf_context {
     unsigned *d_counter = nullptr;  // persistent-kernel work counter
     cudaStream_t capture_stream = nullptr;
     std::string err;
-    std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;  // (L, log2 size, precision) -> (block, cap)
+    // (L, log2 size, precision, fixed block, fixed cap) -> (block, cap)
+    std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> tuned;
     std::vector<GraphEntry> graphs;
     uint64_t clock = 0;
     kf::BuildState *build = nullptr;
@@ -277,21 +278,33 @@ cudaError_t enqueue_persistent(kf_context *ctx, const FitGeom &g, const Routing 
 // own buffers (the fit is idempotent: it reads its inputs and overwrites its
 // outputs) and keep the fastest for this layer count, size class and
 // precision.  Skipped while the stream is being captured.
+// fixed_block / fixed_cap (0 = free) restrict the search to matching shapes.
 std::pair<int, int> tune_shape(kf_context *ctx, const FitGeom &g, const Routing &rt, const FitIO &io,
-                               cudaStream_t stream)
+                               cudaStream_t stream, int fixed_block, int fixed_cap)
 {
-    const auto key = std::make_tuple(g.L, size_class(io.T), rt.mode);
+    const auto key = std::make_tuple(g.L, size_class(io.T), rt.mode, fixed_block, fixed_cap);
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) return it->second;
+    int blocks[32], caps[32];
+    int n = 0;
+    {
+        int all_b[32], all_c[32];
+        const int m = persistent_shapes(all_b, all_c, 32);
+        for (int i = 0; i < m; ++i)
+            if ((!fixed_block || all_b[i] == fixed_block) && (!fixed_cap || all_c[i] == (fixed_cap < 0 ? 0 : fixed_cap))) {
+                blocks[n] = all_b[i];
+                caps[n] = all_c[i];
+                ++n;
+            }
+    }
+    if (n == 0) return {fixed_block ? fixed_block : 128, fixed_cap > 0 ? fixed_cap : 0};
     cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(stream, &capst);
-    if (capst != cudaStreamCaptureStatusNone) return {128, 0};
-    int blocks[32], caps[32];
-    const int n = persistent_shapes(blocks, caps, 32);
+    if (capst != cudaStreamCaptureStatusNone) return {blocks[0], caps[0]};
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    std::pair<int, int> best{128, 0};
+    std::pair<int, int> best{blocks[0], caps[0]};
     float best_ms = 1e30f;
     for (int i = 0; i < n; ++i) {
         if (enqueue_persistent(ctx, g, rt, io, blocks[i], caps[i], stream, false) != cudaSuccess) continue;
@@ -367,11 +380,7 @@ int kf_fit_tracks(kf_context *ctx, const kf_geometry *geom, int64_t n_tracks, co
         break;
     default: {
         std::pair<int, int> shape{block, o.reg_cap < 0 ? 0 : o.reg_cap};
-        if (!block || !o.reg_cap) {
-            const std::pair<int, int> t = tune_shape(ctx, g, rt, io, stream);
-            if (!block) shape.first = t.first;
-            if (!o.reg_cap) shape.second = t.second;
-        }
+        if (!block || !o.reg_cap) shape = tune_shape(ctx, g, rt, io, stream, block, o.reg_cap);
         e = enqueue_persistent(ctx, g, rt, io, shape.first, shape.second, stream, true);
     }
     }
@@ -383,7 +392,7 @@ int kf_fit_tuned_shape(kf_context *ctx, int n_layers, int64_t n_tracks, int *tra
 {
     if (!ctx || !tracks_per_block || !reg_cap) return KF_ERR_ARG;
     for (int mode = 1; mode >= 0; --mode) {
-        auto it = ctx->tuned.find(std::make_tuple(n_layers, size_class(n_tracks), mode));
+        auto it = ctx->tuned.find(std::make_tuple(n_layers, size_class(n_tracks), mode, 0, 0));
         if (it != ctx->tuned.end()) {
             *tracks_per_block = it->second.first;
             *reg_cap = it->second.second ? it->second.second : -1;

@@ -100,6 +100,22 @@ def test_ragged_events_missing_hits(kf, ctx, oracle, block):
         compare(gpu, ref)
 
 
+@pytest.mark.parametrize("cap", [-1, 168, 128, 96, 80])
+def test_register_caps(kf, ctx, oracle, cap):
+    """Each register cap, with the block size left to the autotuner and with
+    every block size it is compiled for."""
+    b = synth.make_fit_batch(36, [1500, 77], hit_eff=0.95)
+    ref = oracle.fit_batch(b)
+    compare(run_gpu(kf, ctx, b, reg_cap=cap), ref)
+    for block in (32, 64, 128, 256):
+        try:
+            gpu = run_gpu(kf, ctx, b, reg_cap=cap, tracks_per_block=block)
+        except kf.KFError as e:  # a shape that is not compiled is an argument error, not a fault
+            assert "fit launch" in str(e)
+            continue
+        compare(gpu, ref)
+
+
 def test_stops_flags_and_anisotropic_hits(kf, ctx, oracle):
     """Loopers that cannot reach the outer layers, tracks leaving the barrel,
     off-diagonal hit covariances (sigma_r != sigma_rphi), NaN inputs."""
