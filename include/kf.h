@@ -57,6 +57,7 @@ typedef struct CUstream_st *kf_stream; /* a cudaStream_t; NULL is the legacy def
 #define KF_ERR_TIMEOUT (-3)     /* a bounded device-side wait expired */
 #define KF_ERR_NOMEM (-4)       /* the context could not grow its scratch */
 #define KF_ERR_UNSUPPORTED (-5) /* no sm_103a device, or a feature off on this device */
+#define KF_ERR_TOO_LARGE (-6)   /* a size exceeds what kf_fit_tracks_noalloc's fixed scratch serves */
 
 /* per-track flags in out_flags */
 #define KF_FLAG_UNREACHABLE 1u       /* a layer's cylinder is not reached: fit stops there */
@@ -175,6 +176,42 @@ int kf_fit_tracks(kf_context *ctx, const kf_geometry *geom, int64_t n_tracks,
  */
 int kf_fit_tuned_shape(kf_context *ctx, int n_layers, int64_t n_tracks, int *tracks_per_block,
                        int *reg_cap);
+
+/*
+ * The fit for callers that cannot allocate device memory.  The paper has no
+ * counterpart to this entry point.
+ *
+ * kf_fit_tracks needs a kf_context, and kf_context_create calls cudaMalloc.
+ * Callers that work inside a device-memory pool they do not own, loops that
+ * must not touch the allocator after start-up, or hosts that forbid
+ * allocation while their own work is in flight can call this instead.  It
+ * runs the same persistent fit kernel (same steps, inputs, outputs and flags
+ * as kf_fit_tracks, all events in one launch) and allocates nothing: the
+ * kernel's only scratch, the 4-byte counter from which its warps claim
+ * 32-track units, is a fixed array in the library's device memory that every
+ * GPU loading the library holds until the process exits.
+ *
+ *   - Runs on the current CUDA device.  The first call on a device looks up
+ *     that array's device address once (cudaGetSymbolAddress); make that
+ *     first call before any stream capture.
+ *   - Each call clears the counter on `stream` before its launch.  All calls
+ *     on a device share the counter, so calls whose work overlaps on the GPU
+ *     (different streams, not ordered) race and give wrong results: order
+ *     them on one stream or synchronise.
+ *   - n_tracks must be at most KF_NOALLOC_MAX_TRACKS (the 32-bit counter
+ *     must not wrap while every resident warp makes its last claim);
+ *     larger batches return KF_ERR_TOO_LARGE.
+ *   - No tuning runs: the shape is opt->tracks_per_block / opt->reg_cap when
+ *     set, else 64 tracks per block with no register cap.  opt->launch_mode
+ *     is ignored.  There is no context, so failures are reported by the
+ *     return code only (KF_ERR_ARG, KF_ERR_TOO_LARGE, KF_ERR_CUDA).
+ */
+#define KF_NOALLOC_MAX_TRACKS (32LL * (4294967296LL - 16384LL))
+int kf_fit_tracks_noalloc(const kf_geometry *geom, int64_t n_tracks, const float *seed_state,
+                          const float *seed_cov, const int8_t *charge, const float *hit_pos,
+                          const float *hit_cov, const uint32_t *hit_mask, float *out_state,
+                          float *out_cov, float *out_chi2, int16_t *out_ndof, uint32_t *out_flags,
+                          const kf_options *opt, kf_stream stream);
 
 #ifdef __cplusplus
 }

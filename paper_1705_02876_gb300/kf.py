@@ -80,6 +80,8 @@ def load() -> ctypes.CDLL:
             [_vp] * 11 + [ctypes.POINTER(Options), _vp]
         L.kf_fit_tuned_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.kf_fit_tracks_noalloc.argtypes = [ctypes.POINTER(Geometry), ctypes.c_int64] + [_vp] * 11 + \
+            [ctypes.POINTER(Options), _vp]
         _lib = L
     return _lib
 
@@ -212,3 +214,29 @@ def to_device(batch, device="cuda") -> dict:
                 charge=t(batch.charge, torch.int8), hit_pos=t(batch.hit_pos, torch.float32),
                 hit_cov=t(batch.hit_cov, torch.float32),
                 hit_mask=t(batch.hit_mask.view(np.int32), torch.int32))
+
+
+def fit_tracks_noalloc(geom: GeometryArgs, seed_state, seed_cov, charge, hit_pos, hit_cov, hit_mask,
+                       out: dict, opt: Options | None = None,
+                       stream: torch.cuda.Stream | None = None) -> int:
+    """kf_fit_tracks_noalloc on CUDA tensors: the fit without a context, for
+    callers that cannot allocate device memory.  The caller provides the
+    output tensors; returns the C status code (KF_OK is 0)."""
+    T = int(charge.shape[0])
+    L = geom.struct.n_layers
+    args = [
+        _ptr(seed_state, torch.float32, (6, T), "seed_state"),
+        _ptr(seed_cov, torch.float32, (21, T), "seed_cov"),
+        _ptr(charge, torch.int8, (T,), "charge"),
+        _ptr(hit_pos, torch.float32, (L, 3, T), "hit_pos"),
+        _ptr(hit_cov, torch.float32, (L, 6, T), "hit_cov"),
+        _ptr(hit_mask, torch.int32, (T,), "hit_mask"),
+        _ptr(out["state"], torch.float32, (6, T), "out_state"),
+        _ptr(out["cov"], torch.float32, (21, T), "out_cov"),
+        _ptr(out["chi2"], torch.float32, (T,), "out_chi2"),
+        _ptr(out["ndof"], torch.int16, (T,), "out_ndof"),
+        _ptr(out["flags"], torch.int32, (T,), "out_flags"),
+    ]
+    s = stream if stream is not None else torch.cuda.current_stream(charge.device)
+    return load().kf_fit_tracks_noalloc(ctypes.byref(geom.struct), T, *args,
+                                        ctypes.byref(opt) if opt is not None else None, s.cuda_stream)
