@@ -98,8 +98,8 @@ typedef struct {
     int precision_mode;      /* KF_PRECISION_* */
     float cond_max;          /* Frobenius condition estimate of S above which FP64 is used */
     float pt_lo, pt_hi;      /* tracks with pT outside [pt_lo, pt_hi] GeV update in FP64 */
-    float gain_max;          /* an update with C_ii > gain_max V_ii (i = x, y, z) computes
-                                its gain (S^-1 and K) in FP64 */
+    float gain_max;          /* > 0: an update with C_ii > gain_max V_ii (i = x, y, z) forms
+                                its gain (S^-1 and K) in float-float; 0 = off */
     /* launch shape (fit) */
     int launch_mode;         /* KF_LAUNCH_* */
     int tracks_per_block;    /* 0 = autotuned, else 32, 64, 128 or 256 */
@@ -118,7 +118,7 @@ typedef struct {
 } kf_options;
 
 /* Fill *opt with the defaults: routed precision (cond_max 1e6, pT in
- * [0.25, 200], gain_max 100), automatic launch, N = 6, chi2 cut 30, 3-sigma window,
+ * [0.25, 200], gain_max 0), automatic launch, N = 6, chi2 cut 30, 3-sigma window,
  * 0.01/0.1 cm nominal resolution, 256 x 64 bins, proposal off, top-k 4. */
 void kf_options_default(kf_options *opt);
 

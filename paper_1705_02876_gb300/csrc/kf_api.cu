@@ -102,6 +102,7 @@ int check_geometry(kf_context *ctx, const kf_geometry *geom, FitGeom *g)
         if (!(x >= 0.0f) || !std::isfinite(x))
             return set_error(ctx, KF_ERR_ARG, "x_over_x0[%d] must be finite and >= 0", l);
         g->r[l] = r;
+        g->inv_r[l] = 1.0f / r;
         g->xx0[l] = x;
     }
     return KF_OK;
@@ -131,8 +132,8 @@ int check_options(kf_context *ctx, const kf_options &o)
     if (o.precision_mode != KF_PRECISION_FP32 && o.precision_mode != KF_PRECISION_ROUTED)
         return set_error(ctx, KF_ERR_ARG, "precision_mode %d", o.precision_mode);
     if (o.precision_mode == KF_PRECISION_ROUTED &&
-        (!(o.cond_max > 1.0f) || !(o.pt_lo >= 0.0f) || !(o.pt_hi > o.pt_lo) || !(o.gain_max > 0.0f)))
-        return set_error(ctx, KF_ERR_ARG, "routing thresholds: cond_max > 1, 0 <= pt_lo < pt_hi, gain_max > 0");
+        (!(o.cond_max > 1.0f) || !(o.pt_lo >= 0.0f) || !(o.pt_hi > o.pt_lo) || !(o.gain_max >= 0.0f)))
+        return set_error(ctx, KF_ERR_ARG, "routing thresholds: cond_max > 1, 0 <= pt_lo < pt_hi, gain_max >= 0");
     if (o.launch_mode < KF_LAUNCH_AUTO || o.launch_mode > KF_LAUNCH_FLAT)
         return set_error(ctx, KF_ERR_ARG, "launch_mode %d", o.launch_mode);
     if (o.tracks_per_block != 0 && o.tracks_per_block != 32 && o.tracks_per_block != 64 &&
@@ -156,7 +157,7 @@ void kf_options_default(kf_options *o)
     o->cond_max = 1e6f;
     o->pt_lo = 0.25f;
     o->pt_hi = 200.0f;
-    o->gain_max = 100.0f;
+    o->gain_max = 0.0f;
     o->launch_mode = KF_LAUNCH_AUTO;
     o->tracks_per_block = 0;
     o->reg_cap = 0;

@@ -20,17 +20,11 @@ __device__ __forceinline__ bool all_finite(const float *v)
     return acc == 0.0f;
 }
 
-__device__ __forceinline__ void load_hit(const FitIO &io, int l, int64_t t, float m[3], float v[6])
-{
-    const int64_t T = io.T;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) m[i] = __ldcs(io.hit_pos + ((int64_t)l * 3 + i) * T + t);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) v[i] = __ldcs(io.hit_cov + ((int64_t)l * 6 + i) * T + t);
-}
-
 // Fit track t over every layer in order (the steps and stop rules are those of
-// kf_fit_tracks in kf.h).  The next present hit is loaded one layer ahead.
+// kf_fit_tracks in kf.h).  The next present hit is loaded one layer ahead,
+// through pointers advanced by one layer's stride.  A non-finite value in a
+// used hit makes the chi2 increment non-finite, or makes S fail its positive
+// definiteness test, so the hit is tested only then.
 __device__ __forceinline__ void fit_track(const FitGeom &g, const Routing &rt, const FitIO &io, int64_t t,
                                           float *slot, int stride)
 {
@@ -45,13 +39,24 @@ __device__ __forceinline__ void fit_track(const FitGeom &g, const Routing &rt, c
     uint32_t flags = (all_finite<6>(x) && all_finite<21>(c)) ? 0u : (uint32_t)KF_FLAG_NAN_INPUT;
     float chi2 = 0.0f;
     int nhits = 0;
+    const float *hp = io.hit_pos + t;  // layer l, component i: hp[(3 l + i) T]
+    const float *hc = io.hit_cov + t;
+    const int64_t T3 = 3 * T, T6 = 6 * T;
     float m[3] = {0, 0, 0}, v[6] = {0, 0, 0, 0, 0, 0};
-    if (mask & 1u) load_hit(io, 0, t, m, v);
+    auto load_hit = [&](float mm[3], float vv[6]) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) mm[i] = __ldcs(hp + i * T);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) vv[i] = __ldcs(hc + i * T);
+    };
+    if (mask & 1u) load_hit(m, v);
     for (int l = 0; l < g.L && !(flags & kStop); ++l) {
         const bool has = (mask >> l) & 1u;
         const bool has_next = l + 1 < g.L && ((mask >> (l + 1)) & 1u);
+        hp += T3;
+        hc += T6;
         float mn[3], vn[6];
-        if (has_next) load_hit(io, l + 1, t, mn, vn);
+        if (has_next) load_hit(mn, vn);
         float xn[6], s;
         Jac J;
         if (!propagate(x, qkb, g.r[l], xn, s, &J)) {
@@ -63,16 +68,18 @@ __device__ __forceinline__ void fit_track(const FitGeom &g, const Routing &rt, c
             break;
         }
         transport(J, c);
-        add_scattering(xn, g.r[l], g.xx0[l], c);
+        add_scattering(xn, g.inv_r[l], g.xx0[l], c);
 #pragma unroll
         for (int i = 0; i < 6; ++i) x[i] = xn[i];
         if (has) {
-            if (!all_finite<3>(m) || !all_finite<6>(v)) {
-                flags |= KF_FLAG_NAN_INPUT;
-                break;
-            }
             float d = 0.0f;
             const int st = update(x, c, m, v, rt, &d, slot, stride);
+            if (st == 1 || !isfinite(d)) {
+                if (!all_finite<3>(m) || !all_finite<6>(v)) {
+                    flags |= KF_FLAG_NAN_INPUT;
+                    break;
+                }
+            }
             if (st == 1) {
                 flags |= KF_FLAG_INVERSION_FAILED;
             } else {

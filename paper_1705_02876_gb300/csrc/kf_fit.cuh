@@ -15,6 +15,7 @@ struct FitGeom {
     float z_half;
     float qk;  // k * Bz; a track's curvature is charge * qk / pT
     float r[kMaxLayers];
+    float inv_r[kMaxLayers];
     float xx0[kMaxLayers];
 };
 

@@ -13,6 +13,10 @@ constexpr float kField = 0.00299792458f;  // GeV / (cm T)
 
 __host__ __device__ constexpr int pk(int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
 
+// Divisions on the FP32 path use __fdividef (reciprocal approximation and a
+// multiply, within 2 ulp for divisors of magnitude 2^-126..2^126, which every
+// divisor here is) in place of the IEEE-rounded sequence.
+//
 // Propagation result and the non-trivial part of its Jacobian.  With
 // P = {x, y, px, py} (state indices 0, 1, 3, 4), J has the block structure
 //   J[P][P] = T (4x4), J[z][P] = jz (4), J[z][z] = 1, J[z][pz] = jzpz,
@@ -56,10 +60,22 @@ __device__ __forceinline__ bool propagate(const float x[6], float qkb, float r, 
     const float sq = sqrtf(Qd);
     float s, tau, sigma;
     if (u + sq > 0.0f) {
-        sigma = D / (u + sq);
+        sigma = __fdividef(D, u + sq);
         tau = 0.5f * om * sigma;
         const float t2 = tau * tau;
-        const float ratio = t2 < 1e-6f ? 1.0f - t2 * (1.0f / 3.0f) : atanf(tau) / tau;  // atan(tau)/tau
+        // atan(tau)/tau: its Taylor series sum_k (-t2)^k / (2k+1) to t2^6 for
+        // |tau| < 1/4 (truncation below 3e-10), else the library atanf
+        float ratio;
+        if (t2 < 0.0625f) {
+            ratio = fmaf(t2, -1.0f / 13.0f, 1.0f / 11.0f);
+            ratio = fmaf(t2, -ratio, 1.0f / 9.0f);
+            ratio = fmaf(t2, -ratio, 1.0f / 7.0f);
+            ratio = fmaf(t2, -ratio, 1.0f / 5.0f);
+            ratio = fmaf(t2, -ratio, 1.0f / 3.0f);
+            ratio = fmaf(t2, -ratio, 1.0f);
+        } else {
+            ratio = atanf(tau) / tau;
+        }
         s = sigma * ratio;
     } else {
         // A start moving inwards: both roots of the quadratic, each mapped to
@@ -84,7 +100,7 @@ __device__ __forceinline__ bool propagate(const float x[6], float qkb, float r, 
         sigma = om != 0.0f ? 2.0f * tau / om : s;
         if (!(s < INFINITY)) return false;
     }
-    const float g = 1.0f / (1.0f + tau * tau);
+    const float g = __fdividef(1.0f, 1.0f + tau * tau);
     const float a = sigma * g;          // sin(phi) / omega
     const float b = sigma * tau * g;    // (1 - cos(phi)) / omega
     const float sn = 2.0f * tau * g;    // sin(phi)
@@ -107,7 +123,7 @@ __device__ __forceinline__ bool propagate(const float x[6], float qkb, float r, 
         const float lz = pz * ipt;  // dz/ds
         const float d23 = -s * lz * tx * ipt, d24 = -s * lz * ty * ipt;
         // ds/dx0 from the constraint x'^2 + y'^2 = r^2
-        const float iden = -1.0f / (xn[0] * txn + xn[1] * tyn);
+        const float iden = __fdividef(-1.0f, xn[0] * txn + xn[1] * tyn);
         const float ds0 = xn[0] * iden, ds1 = xn[1] * iden;
         const float ds3 = (xn[0] * d03 + xn[1] * d13) * iden;
         const float ds4 = (xn[0] * d04 + xn[1] * d14) * iden;
@@ -188,17 +204,17 @@ __device__ __forceinline__ void transport(const Jac &J, float c[21])
     for (int i = 0; i < 21; ++i) c[i] = nc[i];
 }
 
-// Multiple scattering of a thin layer at the crossing xn on radius r:
+// Multiple scattering of a thin layer at the crossing xn on radius 1/inv_r:
 // Q = theta0^2 (|p|^2 I3 - p p^T) on the momentum block; theta0 from the
 // Highland formula (beta = 1) for x_over_x0 / |cos(incidence)|.
-__device__ __forceinline__ void add_scattering(const float xn[6], float r, float x_over_x0, float c[21])
+__device__ __forceinline__ void add_scattering(const float xn[6], float inv_r, float x_over_x0, float c[21])
 {
     if (!(x_over_x0 > 0.0f)) return;
     const float px = xn[3], py = xn[4], pz = xn[5];
     const float p2 = px * px + py * py + pz * pz;
     const float ip = rsqrtf(p2);
-    const float cosi = fabsf(px * xn[0] + py * xn[1]) * ip / r;
-    const float xx0 = x_over_x0 / cosi;
+    const float cosi = fabsf(px * xn[0] + py * xn[1]) * ip * inv_r;
+    const float xx0 = __fdividef(x_over_x0, cosi);
     const float th = 0.0136f * ip * sqrtf(xx0) * (1.0f + 0.038f * __logf(xx0));
     const float t2 = th * th;
     c[pk(3, 3)] = fmaf(t2, p2 - px * px, c[pk(3, 3)]);
@@ -395,28 +411,47 @@ struct Routing {
 };
 
 // Update with a 3-D hit (Section 2.1: 3x3 measurement covariance V).
-//   S = C_xx + V, S^-1 by adjugate / determinant, K = C[:, 0:3] S^-1,
-//   x += K r, C -= K C[0:3, :] (packed lower triangle), dchi2 = r^T S^-1 r.
-// Each row of K is formed and applied at once: rows 5..3 first, columns
-// descending, so that every C[0:3, j] read is still the original value; then
-// rows 2..0 from a copy of the 3x3 block.
+//   S = C_xx + V, K = C[:, 0:3] S^-1, x += K r, C -= K C[0:3, :],
+//   dchi2 = r^T S^-1 r.
+//
+// The FP32 path works in the local frame of the layer at the predicted
+// position: n = (x, y, 0)/|(x, y)|, t = z x n, z.  Transport onto the cylinder
+// leaves the covariance the exact null vector n (the crossing cannot move off
+// the surface), so in x/y the exactly known radial direction and the
+// uncertain tangential one share every entry and FP32 cannot resolve the gain
+// of an update that shrinks the covariance by orders of magnitude (a hit
+// after a diffuse seed).  In (n, t, z) they decouple: C's radial row is zero
+// (its rounding residue is dropped), S = [[V_nn, V_nt, V_nz], [V_nt, C_tt +
+// V_tt, C_tz + V_tz], [V_nz, C_tz + V_tz, C_zz + V_zz]], the gain's radial
+// row is zero, and only the five non-radial rows (t, z, px, py, pz) are
+// updated, each from the t and z columns.  dx and C are rotated back to x/y.
 // Routing (mode 1):
 //   * the whole update is redone in FP64 with a PSD repair (update_fp64) when
 //     S is not positive definite in FP32, when its Frobenius condition
 //     estimate ||S||_F ||S^-1||_F exceeds the threshold, or when pT lies
 //     outside [pt_lo, pt_hi];
-//   * the gain is formed in float-float (update_ff) when the update shrinks
-//     the covariance strongly, C_ii > gain_max V_ii for some i: there K
-//     carries the information as small differences from the identity, which
-//     FP32 arithmetic cannot resolve.  Float-float runs on the FP32 pipe,
+//   * with gain_max > 0, the gain is formed in float-float (update_ff) when
+//     C_ii > gain_max V_ii for some i.  Float-float runs on the FP32 pipe,
 //     which on this part is 64 times wider than the FP64 one.
 // Returns 0 updated in FP32, 2 updated with extended-precision arithmetic,
 // 3 updated in FP64 with a PSD repair, 1 failed (S not positive definite).
 __device__ __forceinline__ int update(float x[6], float c[21], const float m[3], const float v[6],
                                       const Routing &rt, float *dchi2, float *slot, int stride)
 {
-    const float a = c[0] + v[0], b = c[1] + v[1], cc = c[2] + v[2];
-    const float d = c[3] + v[3], e = c[4] + v[4], f = c[5] + v[5];
+    const float ir = rsqrtf(x[0] * x[0] + x[1] * x[1]);
+    const float nx = x[0] * ir, ny = x[1] * ir;
+    // t column of C in the local frame: C_it = -ny C_i0 + nx C_i1 (i >= 2),
+    // C_tt = t^T C_xy t; the z column is C's own
+    const float ctt = fmaf(ny * ny, c[pk(0, 0)], fmaf(-2.0f * nx * ny, c[pk(1, 0)], nx * nx * c[pk(1, 1)]));
+    float ct[6];  // ct[i] = C_l[i][t] for i = 2..5
+#pragma unroll
+    for (int i = 2; i < 6; ++i) ct[i] = fmaf(nx, c[pk(i, 1)], -ny * c[pk(i, 0)]);
+    const float vnn = fmaf(nx * nx, v[0], fmaf(2.0f * nx * ny, v[1], ny * ny * v[2]));
+    const float vnt = fmaf(nx * ny, v[2] - v[0], (nx * nx - ny * ny) * v[1]);
+    const float vtt = fmaf(ny * ny, v[0], fmaf(-2.0f * nx * ny, v[1], nx * nx * v[2]));
+    const float vnz = fmaf(nx, v[3], ny * v[4]), vtz = fmaf(nx, v[4], -ny * v[3]);
+    const float a = vnn, b = vnt, cc = ctt + vtt;
+    const float d = vnz, e = ct[2] + vtz, f = c[pk(2, 2)] + v[5];
     const float i00 = cc * f - e * e, i10 = d * e - b * f, i11 = a * f - d * d;
     const float i20 = b * e - cc * d, i21 = b * d - a * e, i22 = a * cc - b * b;
     const float det = fmaf(a, i00, fmaf(b, i10, d * i20));
@@ -428,7 +463,8 @@ __device__ __forceinline__ int update(float x[6], float c[21], const float m[3],
         const float pt2 = x[3] * x[3] + x[4] * x[4];
         if (!pd || sS * sI > rt.cond2_max * det * det || pt2 < rt.pt_lo * rt.pt_lo || pt2 > rt.pt_hi * rt.pt_hi)
             kind = 2;
-        else if (c[0] > rt.gain_max * v[0] || c[2] > rt.gain_max * v[2] || c[5] > rt.gain_max * v[5])
+        else if (rt.gain_max > 0.0f &&
+                 (c[0] > rt.gain_max * v[0] || c[2] > rt.gain_max * v[2] || c[5] > rt.gain_max * v[5]))
             kind = 1;
     } else if (!pd) {
         return 1;
@@ -444,37 +480,57 @@ __device__ __forceinline__ int update(float x[6], float c[21], const float m[3],
         *dchi2 = slot[kSlotChi2 * stride];
         return st;
     }
-    const float r[3] = {m[0] - x[0], m[1] - x[1], m[2] - x[2]};
-    const float id = 1.0f / det;
+    const float id = __fdividef(1.0f, det);
     const float s00 = i00 * id, s10 = i10 * id, s11 = i11 * id, s20 = i20 * id, s21 = i21 * id, s22 = i22 * id;
-    const float q0 = fmaf(s00, r[0], fmaf(s10, r[1], s20 * r[2]));
-    const float q1 = fmaf(s10, r[0], fmaf(s11, r[1], s21 * r[2]));
-    const float q2 = fmaf(s20, r[0], fmaf(s21, r[1], s22 * r[2]));
-    *dchi2 = fmaf(r[0], q0, fmaf(r[1], q1, r[2] * q2));
-    // rows 5..3, then 2..0 from a copy of the 3x3 block; within a row the
-    // columns descend, so every C[0:3, j] read is still the original value
-    float h[6];
+    const float d0 = m[0] - x[0], d1 = m[1] - x[1];
+    const float rn = fmaf(nx, d0, ny * d1), rt_ = fmaf(nx, d1, -ny * d0), rz = m[2] - x[2];
+    const float q0 = fmaf(s00, rn, fmaf(s10, rt_, s20 * rz));
+    const float q1 = fmaf(s10, rn, fmaf(s11, rt_, s21 * rz));
+    const float q2 = fmaf(s20, rn, fmaf(s21, rt_, s22 * rz));
+    *dchi2 = fmaf(rn, q0, fmaf(rt_, q1, rz * q2));
+    // rows u = t, z, px, py, pz (state indices 1..5 of the local frame):
+    // col_t[u] = C_l[u][t], col_z[u] = C_l[u][z], both before the update
+    float col_t[6], col_z[6];
+    col_t[1] = ctt;
+    col_z[1] = ct[2];
+    col_t[2] = ct[2];
+    col_z[2] = c[pk(2, 2)];
 #pragma unroll
-    for (int i = 5; i >= 0; --i) {
-        if (i == 2) {
+    for (int u = 3; u < 6; ++u) {
+        col_t[u] = ct[u];
+        col_z[u] = c[pk(u, 2)];
+    }
+    // K_u = (C_ut, C_uz) S^-1[{t, z}, :]; the radial row of K is zero
+    float kt[6], kz[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) h[k] = c[k];
-        }
-        const float c0 = i >= 3 ? c[pk(i, 0)] : h[pk(i, 0)];
-        const float c1 = i >= 3 ? c[pk(i, 1)] : h[pk(i, 1)];
-        const float c2 = i >= 3 ? c[pk(i, 2)] : h[pk(i, 2)];
-        const float k0 = fmaf(c0, s00, fmaf(c1, s10, c2 * s20));
-        const float k1 = fmaf(c0, s10, fmaf(c1, s11, c2 * s21));
-        const float k2 = fmaf(c0, s20, fmaf(c1, s21, c2 * s22));
-        x[i] = fmaf(k0, r[0], fmaf(k1, r[1], fmaf(k2, r[2], x[i])));
-#pragma unroll
-        for (int j = i; j >= 0; --j) {
-            const float h0 = i >= 3 ? c[pk(0, j)] : h[pk(0, j)];
-            const float h1 = i >= 3 ? c[pk(1, j)] : h[pk(1, j)];
-            const float h2 = i >= 3 ? c[pk(2, j)] : h[pk(2, j)];
-            c[pk(i, j)] = fmaf(-k0, h0, fmaf(-k1, h1, fmaf(-k2, h2, c[pk(i, j)])));
+    for (int u = 1; u < 6; ++u) {
+        const float k0 = fmaf(col_t[u], s10, col_z[u] * s20);
+        kt[u] = fmaf(col_t[u], s11, col_z[u] * s21);
+        kz[u] = fmaf(col_t[u], s21, col_z[u] * s22);
+        const float dxu = fmaf(k0, rn, fmaf(kt[u], rt_, kz[u] * rz));
+        if (u == 1) {  // t: back to x/y
+            x[0] = fmaf(-ny, dxu, x[0]);
+            x[1] = fmaf(nx, dxu, x[1]);
+        } else {
+            x[u] += dxu;
         }
     }
+    // C'_uw = C_uw - K_ut C_tw - K_uz C_zw over the non-radial 5x5 block
+    const float ntt = fmaf(-kt[1], col_t[1], fmaf(-kz[1], col_z[1], col_t[1]));
+#pragma unroll
+    for (int u = 2; u < 6; ++u) {
+        const float nt = fmaf(-kt[u], col_t[1], fmaf(-kz[u], col_z[1], col_t[u]));  // C'_u t
+        const float nz = fmaf(-kt[u], col_t[2], fmaf(-kz[u], col_z[2], col_z[u]));  // C'_u z
+        c[pk(u, 0)] = -ny * nt;
+        c[pk(u, 1)] = nx * nt;
+        if (u >= 3) c[pk(u, 2)] = nz;
+        else c[pk(2, 2)] = nz;
+#pragma unroll
+        for (int w = 3; w <= u; ++w) c[pk(u, w)] = fmaf(-kt[u], col_t[w], fmaf(-kz[u], col_z[w], c[pk(u, w)]));
+    }
+    c[pk(0, 0)] = ny * ny * ntt;
+    c[pk(1, 0)] = -nx * ny * ntt;
+    c[pk(1, 1)] = nx * nx * ntt;
     return 0;
 }
 
