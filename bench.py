@@ -37,8 +37,10 @@ WORKLOAD = ("fit: 10-layer toy barrel r=4..40 cm, |z|<100 cm, Bz=3.8 T, x/X0=0.0
             "graph-captured launch")
 N_LAYERS = 10
 # FP32 flops of one track-layer with a hit, counted on the kernel's formulation
-# (FMA = 2): propagation 45, Jacobian 75, J C J^T 356, scattering 30, update 336.
-FLOPS_PER_TRACK_LAYER = 842
+# (add, multiply, reciprocal, square root, log = 1, FMA = 2): propagation 75,
+# Jacobian 88, J C J^T 308, scattering 42, local-frame update 255.  The routed
+# form also spends about 30 flops per update on its routing tests (not counted).
+FLOPS_PER_TRACK_LAYER = 768
 # algorithmic HBM bytes per track at 10 layers: seed 108 + charge 1 + mask 4 +
 # hits 10 x 36 in, state/cov 108 + chi2 4 + ndof 2 + flags 4 out
 BYTES_PER_TRACK = 108 + 1 + 4 + 36 * N_LAYERS + 108 + 4 + 2 + 4
@@ -75,8 +77,11 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the kernel sources and of the build flags that compile them."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1705_02876_gb300", "csrc", "*"))):
+    paths = sorted(glob.glob(os.path.join(ROOT, "paper_1705_02876_gb300", "csrc", "*")))
+    paths.append(os.path.join(ROOT, "paper_1705_02876_gb300", "build.py"))
+    for p in paths:
         with open(p, "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
