@@ -169,6 +169,48 @@ int kf_fit_tracks(kf_context *ctx, const kf_geometry *geom, int64_t n_tracks,
                   uint32_t *out_flags, const kf_options *opt, kf_stream stream);
 
 /*
+ * Combinatorial track building, the clone engine (Sections 3, 3.1 and 4.3):
+ * starting from each seed, layer by layer, every candidate is propagated to
+ * the layer (same steps as kf_fit_tracks: helix, transport, scattering) and
+ * yields one child per compatible hit plus one child without a hit; the
+ * children of a seed are ranked by number of hits (more first), then chi2
+ * (less first), then candidate index, then hit index within the layer (the
+ * hole first), and the best max_cands survive, each updated with its hit.
+ * max_cands = 1 is the best-hit approach (Section 3).  A hit is compatible
+ * if it lies within the window
+ *   |dphi| <= window_nsigma sqrt(sigma_rphi,pred^2 + hit_sigma_rphi^2) / r,
+ *   |dz|   <= window_nsigma sqrt(sigma_z,pred^2 + hit_sigma_z^2)
+ * around the predicted crossing and its chi2 increment is at most chi2_cut.
+ * A candidate that cannot reach a layer, or crosses it beyond |z| = z_half,
+ * stops and yields only its hole child from then on (its flags record why).
+ * Hits are first sorted into n_phi_bins x n_z_bins bins per (event, layer)
+ * in context scratch (Section 3: hits partitioned spatially).
+ *
+ * geom: the layers to build over (host).
+ * hit_offsets: host, [n_events][L + 1]; the hits of event e on layer l are
+ *   hit_offsets[e][l] .. hit_offsets[e][l+1]-1 of hit_pos [3][n_hits] and
+ *   hit_cov [6][n_hits] (device); events stored back to back, each holding
+ *   fewer than 2^27 hits; n_hits < 2^31.
+ * Seeds (device): seed_event [S] (int32; a seed of an event outside
+ *   0..n_events-1 builds nothing), seed_state [6][S], seed_cov [21][S]
+ *   packed, seed_charge [S], all at a radius inside the first layer.
+ * Outputs (device), slot j of seed s = rank j after the last layer:
+ *   out_hit_idx [S][N][L] (index into hit_pos, -1 = no hit on that layer),
+ *   out_chi2 [S][N], out_nhits [S][N] (-1 for an empty slot),
+ *   out_state [6][S*N], out_cov [21][S*N] packed, out_flags [S][N];
+ *   N = opt->max_cands (1..8).
+ * Scratch: 12 bytes per hit plus 4 (n_phi_bins n_z_bins + 1) bytes per
+ * (event, layer), kept by the context and grown on demand (KF_ERR_NOMEM).
+ * The call copies hit_offsets to the device and waits for that copy.
+ */
+int kf_build_tracks(kf_context *ctx, const kf_geometry *geom, int n_events, const int64_t *hit_offsets,
+                    const float *hit_pos, const float *hit_cov, int64_t n_hits, int64_t n_seeds,
+                    const int32_t *seed_event, const float *seed_state, const float *seed_cov,
+                    const int8_t *seed_charge, int32_t *out_hit_idx, float *out_chi2, int16_t *out_nhits,
+                    float *out_state, float *out_cov, uint32_t *out_flags, const kf_options *opt,
+                    kf_stream stream);
+
+/*
  * Launch shape the autotuner picked for the persistent fit of n_layers layers
  * and a batch of n_tracks' size class (powers of two), once a KF_LAUNCH_AUTO
  * fit of that class has run on ctx.  Writes tracks per block and the register

@@ -1,0 +1,298 @@
+/*
+ * Plain FP64 CPU oracle for the per-layer step of combinatorial track
+ * building (Sections 3, 3.1 and 4.3 of arXiv:1705.02876).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the test suite, the package smoke check
+ * and the CPU-baseline leg of the benchmark.  Shares no code with the CUDA
+ * library.
+ *
+ * The clone engine (Section 3.1): at each layer every candidate of a seed
+ * yields one child per compatible hit plus one child without a hit (a hole);
+ * the children are ranked by number of hits (more first) and chi2 (less
+ * first) (Section 4.3), and only the best N survive, each updated with its
+ * hit.  With N = 1 this is the best-hit approach (Section 3: the hit with the
+ * lowest chi2 increment).  Readings of this build (the paper gives no
+ * numbers): a hit is compatible if it lies in the window
+ *   |dphi| <= nsigma sqrt(sigma_rphi,pred^2 + sigma_rphi,hit^2) / r,
+ *   |dz|   <= nsigma sqrt(sigma_z,pred^2 + sigma_z,hit^2)
+ * around the predicted crossing and its chi2 increment is at most chi2_cut;
+ * ties in (hits, chi2) go to the lower candidate index, then the lower hit
+ * index within the layer (the hole first); a candidate that cannot reach a
+ * layer or crosses it beyond |z| = z_half stops and yields only its hole child
+ * from then on, with its state unchanged.
+ *
+ * Hits of one (event, layer) are found through an index sorted by phi: the
+ * in-window set is exactly that of a scan over all of the layer's hits.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+#define MAXL 64
+#define MAXN 16
+
+int orc_propagate(const double *st, int q, double bz, double r, double *out, double *J, double *s_out);
+void orc_ms_noise(const double *st, double x_over_x0, double *Q);
+void orc_transport(const double *J, double *C, const double *Q);
+int orc_update(double *x, double *C, const double *m, const double *Vp, double *dchi2);
+int orc_inv3_cholesky(const double *S, double *Sinv);
+void orc_unpack_sym(const double *packed, int n, double *full);
+
+/* ------------------------------------------------------------------------ */
+/* phi index of every (event, layer) segment                                 */
+
+static const double *g_sort_phi;
+static int cmp_phi(const void *a, const void *b)
+{
+    const double pa = g_sort_phi[*(const int64_t *)a], pb = g_sort_phi[*(const int64_t *)b];
+    if (pa < pb) return -1;
+    if (pa > pb) return 1;
+    return (*(const int64_t *)a > *(const int64_t *)b) - (*(const int64_t *)a < *(const int64_t *)b);
+}
+
+/* phi[H] = atan2(y, x) of every hit; order[H] = within each segment
+ * [offsets[k], offsets[k+1]) the hit indices sorted by phi.  Not thread-safe
+ * (uses a file-scope comparator pointer); called once before the build. */
+void orc_build_prepare(int64_t n_segments, const int64_t *offsets, const float *hit_pos, int64_t H, double *phi,
+                       int64_t *order)
+{
+    for (int64_t h = 0; h < H; ++h) phi[h] = atan2((double)hit_pos[1 * H + h], (double)hit_pos[0 * H + h]);
+    for (int64_t k = 0; k < n_segments; ++k) {
+        for (int64_t h = offsets[k]; h < offsets[k + 1]; ++h) order[h] = h;
+        g_sort_phi = phi;
+        qsort(order + offsets[k], (size_t)(offsets[k + 1] - offsets[k]), sizeof(int64_t), cmp_phi);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double x[6], C[36];  /* current state */
+    double xp[6], Cp[36]; /* predicted at this layer */
+    double chi2;
+    int nhits, stopped, reached;
+    int32_t hits[MAXL];
+} cand_t;
+
+typedef struct {
+    int cand, nhits;
+    int64_t hit_local; /* -1 for the hole */
+    int64_t hit_global;
+    double chi2;       /* candidate chi2 + increment */
+    double dchi2;
+} child_t;
+
+/* (hits desc, chi2 asc, candidate asc, hit asc) */
+static int child_before(const child_t *a, const child_t *b)
+{
+    if (a->nhits != b->nhits) return a->nhits > b->nhits;
+    if (a->chi2 != b->chi2) return a->chi2 < b->chi2;
+    if (a->cand != b->cand) return a->cand < b->cand;
+    return a->hit_local < b->hit_local;
+}
+static int cmp_child(const void *a, const void *b)
+{
+    const child_t *x = a, *y = b;
+    if (child_before(x, y)) return -1;
+    if (child_before(y, x)) return 1;
+    return 0;
+}
+
+static double wrap_phi(double d)
+{
+    while (d > ORC_PI) d -= 2.0 * ORC_PI;
+    while (d <= -ORC_PI) d += 2.0 * ORC_PI;
+    return d;
+}
+
+/* first position p in order[lo, hi) with phi[order[p]] >= v */
+static int64_t lower_phi(const double *phi, const int64_t *order, int64_t lo, int64_t hi, double v)
+{
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (phi[order[mid]] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+/* Chi2 increment of hit h against the predicted state; returns 0 if S is
+ * not positive definite. */
+static int hit_chi2(const double *xp, const double *Cp, const float *hit_pos, const float *hit_cov, int64_t H,
+                    int64_t h, double *out)
+{
+    double V[9], S[9], Si[9], r[3], vp[6];
+    for (int i = 0; i < 6; ++i) vp[i] = hit_cov[(int64_t)i * H + h];
+    orc_unpack_sym(vp, 3, V);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) S[i * 3 + j] = Cp[i * 6 + j] + V[i * 3 + j];
+    if (orc_inv3_cholesky(S, Si)) return 0;
+    for (int i = 0; i < 3; ++i) r[i] = (double)hit_pos[(int64_t)i * H + h] - xp[i];
+    double c = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) c += r[i] * Si[i * 3 + j] * r[j];
+    *out = c;
+    return 1;
+}
+
+/* keep the n best hit children of one candidate, sorted by key */
+static void insert_child(child_t *list, int *count, int n, const child_t *c)
+{
+    int k = *count;
+    if (k == n && !child_before(c, &list[n - 1])) return;
+    if (k < n) ++k;
+    int p = k - 1;
+    while (p > 0 && child_before(c, &list[p - 1])) {
+        list[p] = list[p - 1];
+        --p;
+    }
+    list[p] = *c;
+    *count = k;
+}
+
+/*
+ * Build seeds [s_begin, s_end).  Geometry: the build layers only.  Hits: all
+ * layers of all events in hit_pos [3][H], hit_cov [6][H]; hit_offsets
+ * [n_events][L+1]; phi and order from orc_build_prepare.  Seeds: seed_event
+ * [S], state [6][S], cov [21][S] packed, charge [S] (float32).
+ * Outputs (slot j of seed s = rank j after the last layer): out_hit
+ * [S][N][L] global hit index or -1; out_chi2, out_nhits (-1 for an empty
+ * slot) [S][N]; out_state [6][S*N]; out_cov [21][S*N] packed; out_ncand [S].
+ */
+int orc_build_tracks(int n_layers, const double *radii, const double *x_over_x0, double z_half, double bz,
+                     const int64_t *hit_offsets, const float *hit_pos, const float *hit_cov, int64_t H,
+                     const double *phi, const int64_t *order, int64_t s_begin, int64_t s_end, int64_t n_seeds,
+                     const int32_t *seed_event, const float *seed_state, const float *seed_cov,
+                     const int8_t *seed_charge, int max_cands, double chi2_cut, double nsigma,
+                     double sigma_rphi_hit, double sigma_z_hit, int32_t *out_hit, double *out_chi2,
+                     int32_t *out_nhits, double *out_state, double *out_cov, int32_t *out_ncand)
+{
+    const int N = max_cands, L = n_layers;
+    const int64_t S = n_seeds;
+    if (N < 1 || N > MAXN || L < 1 || L > MAXL) return -1;
+    cand_t cand[MAXN], next[MAXN];
+    child_t hits_of[MAXN][MAXN], all[MAXN * (MAXN + 1)];
+    int nh[MAXN];
+    for (int64_t s = s_begin; s < s_end; ++s) {
+        const int q = seed_charge[s];
+        const int64_t *off = hit_offsets + (int64_t)seed_event[s] * (L + 1);
+        int nc = 1;
+        memset(&cand[0], 0, sizeof(cand_t));
+        for (int i = 0; i < 6; ++i) cand[0].x[i] = seed_state[(int64_t)i * S + s];
+        {
+            double cp[21];
+            for (int i = 0; i < 21; ++i) cp[i] = seed_cov[(int64_t)i * S + s];
+            orc_unpack_sym(cp, 6, cand[0].C);
+        }
+        for (int l = 0; l < L; ++l) cand[0].hits[l] = -1;
+
+        for (int l = 0; l < L; ++l) {
+            int n_all = 0;
+            const int64_t seg_lo = off[l], seg_hi = off[l + 1];
+            for (int c = 0; c < nc; ++c) {
+                cand_t *k = &cand[c];
+                nh[c] = 0;
+                k->reached = 0;
+                if (!k->stopped) {
+                    double J[36], Q[36], sd;
+                    if (orc_propagate(k->x, q, bz, radii[l], k->xp, J, &sd) || fabs(k->xp[2]) > z_half) {
+                        k->stopped = 1;
+                    } else {
+                        memcpy(k->Cp, k->C, sizeof k->C);
+                        orc_ms_noise(k->xp, x_over_x0[l], Q);
+                        orc_transport(J, k->Cp, Q);
+                        k->reached = 1;
+                    }
+                }
+                if (k->reached) {
+                    const double xp = k->xp[0], yp = k->xp[1], zp = k->xp[2];
+                    const double rc = hypot(xp, yp);
+                    const double tx = -yp / rc, ty = xp / rc;
+                    const double var_rphi = tx * tx * k->Cp[0] + 2.0 * tx * ty * k->Cp[1] + ty * ty * k->Cp[7];
+                    const double dphi = nsigma * sqrt(var_rphi + sigma_rphi_hit * sigma_rphi_hit) / radii[l];
+                    const double dz = nsigma * sqrt(k->Cp[14] + sigma_z_hit * sigma_z_hit);
+                    const double phic = atan2(yp, xp);
+                    /* phi intervals of the window, split at +-pi */
+                    double lo_[3], hi_[3];
+                    int nint = 0;
+                    double a = phic - dphi, b = phic + dphi;
+                    if (dphi >= ORC_PI) {
+                        lo_[0] = -ORC_PI - 1.0;
+                        hi_[0] = ORC_PI + 1.0;
+                        nint = 1;
+                    } else {
+                        lo_[nint] = a < -ORC_PI ? -ORC_PI - 1.0 : a;
+                        hi_[nint] = b > ORC_PI ? ORC_PI + 1.0 : b;
+                        ++nint;
+                        if (a < -ORC_PI) {
+                            lo_[nint] = a + 2.0 * ORC_PI;
+                            hi_[nint] = ORC_PI + 1.0;
+                            ++nint;
+                        }
+                        if (b > ORC_PI) {
+                            lo_[nint] = -ORC_PI - 1.0;
+                            hi_[nint] = b - 2.0 * ORC_PI;
+                            ++nint;
+                        }
+                    }
+                    for (int iv = 0; iv < nint; ++iv) {
+                        for (int64_t p = lower_phi(phi, order, seg_lo, seg_hi, lo_[iv]);
+                             p < seg_hi && phi[order[p]] <= hi_[iv]; ++p) {
+                            const int64_t h = order[p];
+                            if (!(fabs(wrap_phi(phi[h] - phic)) <= dphi)) continue;
+                            if (!(fabs((double)hit_pos[2 * H + h] - zp) <= dz)) continue;
+                            double dc;
+                            if (!hit_chi2(k->xp, k->Cp, hit_pos, hit_cov, H, h, &dc)) continue;
+                            if (!(dc <= chi2_cut)) continue;
+                            child_t ch = {c, k->nhits + 1, h - seg_lo, h, k->chi2 + dc, dc};
+                            insert_child(hits_of[c], &nh[c], N, &ch);
+                        }
+                    }
+                }
+                for (int i = 0; i < nh[c]; ++i) all[n_all++] = hits_of[c][i];
+                child_t hole = {c, k->nhits, -1, -1, k->chi2, 0.0};
+                all[n_all++] = hole;
+            }
+            qsort(all, (size_t)n_all, sizeof(child_t), cmp_child);
+            const int nn = n_all < N ? n_all : N;
+            for (int j = 0; j < nn; ++j) {
+                const child_t *ch = &all[j];
+                const cand_t *par = &cand[ch->cand];
+                cand_t *o = &next[j];
+                *o = *par;
+                o->stopped = par->stopped;
+                if (par->reached) {
+                    memcpy(o->x, par->xp, sizeof o->x);
+                    memcpy(o->C, par->Cp, sizeof o->C);
+                }
+                if (ch->hit_local >= 0) {
+                    double m[3], vp[6], d;
+                    for (int i = 0; i < 3; ++i) m[i] = hit_pos[(int64_t)i * H + ch->hit_global];
+                    for (int i = 0; i < 6; ++i) vp[i] = hit_cov[(int64_t)i * H + ch->hit_global];
+                    orc_update(o->x, o->C, m, vp, &d);
+                    o->nhits = ch->nhits;
+                    o->chi2 = ch->chi2;
+                    o->hits[l] = (int32_t)ch->hit_global;
+                } else {
+                    o->hits[l] = -1;
+                }
+            }
+            memcpy(cand, next, (size_t)nn * sizeof(cand_t));
+            nc = nn;
+        }
+        out_ncand[s] = nc;
+        for (int j = 0; j < N; ++j) {
+            const int64_t sj = s * N + j;
+            for (int l = 0; l < L; ++l) out_hit[sj * L + l] = j < nc ? cand[j].hits[l] : -1;
+            out_chi2[sj] = j < nc ? cand[j].chi2 : 0.0;
+            out_nhits[sj] = j < nc ? cand[j].nhits : -1;
+            for (int i = 0; i < 6; ++i) out_state[(int64_t)i * S * N + sj] = j < nc ? cand[j].x[i] : 0.0;
+            for (int i = 0; i < 6; ++i)
+                for (int jj = 0; jj <= i; ++jj)
+                    out_cov[(int64_t)(i * (i + 1) / 2 + jj) * S * N + sj] = j < nc ? cand[j].C[i * 6 + jj] : 0.0;
+        }
+    }
+    return 0;
+}

@@ -63,6 +63,16 @@ def lib():
             _lib.orc_update.restype = ctypes.c_int
             _lib.orc_update.argtypes = [_dp, _dp, _dp, _dp, _dp]
             _lib.orc_transport.argtypes = [_dp, _dp, _dp]
+            _lib.orc_build_prepare.restype = None
+            _lib.orc_build_prepare.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 2 + [ctypes.c_int64] + \
+                [ctypes.c_void_p] * 2
+            _lib.orc_build_tracks.restype = ctypes.c_int
+            _lib.orc_build_tracks.argtypes = (
+                [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                 ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 4 +
+                [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double] +
+                [ctypes.c_void_p] * 6)
             for fn in (_lib.orc_fit_tracks, _lib.orc_fit_tracks_f64):
                 fn.restype = ctypes.c_int
                 fn.argtypes = ([ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double,
@@ -192,3 +202,91 @@ def fit_batch_exact(batch, threads=None, per_layer=False):
     return fit_arrays(g.radii, g.x_over_x0, g.z_half, g.bz, e["seed_state"], e["seed_cov"],
                       batch.charge, e["hit_pos"], e["hit_cov"], batch.hit_mask, threads,
                       per_layer, None, double_inputs=True)
+
+
+# ---------------------------------------------------------------------------
+# combinatorial build
+
+
+def build_arrays(radii, x_over_x0, z_half, bz, hit_offsets, hit_pos, hit_cov, seed_event, seed_state,
+                 seed_cov, seed_charge, max_cands=6, chi2_cut=30.0, nsigma=3.0, sigma_rphi=0.01,
+                 sigma_z=0.1, threads: int | None = None, seed_range=None):
+    """Clone-engine build with the FP64 oracle over the given layers.  Arrays
+    in the library's layout (float32 hits [3][H] / [6][H], offsets
+    [E][L+1], seeds [6][S] / [21][S]).  Returns a dict of results."""
+    L = int(len(radii))
+    hp = np.ascontiguousarray(hit_pos, dtype=np.float32)
+    hc = np.ascontiguousarray(hit_cov, dtype=np.float32)
+    off = np.ascontiguousarray(hit_offsets, dtype=np.int64)
+    H = int(hp.shape[1])
+    S = int(len(seed_event))
+    N = int(max_cands)
+    phi = np.zeros(H)
+    order = np.zeros(H, dtype=np.int64)
+    bounds = _segment_bounds(off, L)  # kept alive across the call
+    lib().orc_build_prepare(off.shape[0] * L, bounds.ctypes.data, hp.ctypes.data, H,
+                            phi.ctypes.data, order.ctypes.data)
+    se = np.ascontiguousarray(seed_event, dtype=np.int32)
+    ss = np.ascontiguousarray(seed_state, dtype=np.float32)
+    sc = np.ascontiguousarray(seed_cov, dtype=np.float32)
+    sq = np.ascontiguousarray(seed_charge, dtype=np.int8)
+    out = dict(hit=np.zeros((S, N, L), dtype=np.int32), chi2=np.zeros((S, N)),
+               nhits=np.zeros((S, N), dtype=np.int32), state=np.zeros((6, S * N)),
+               cov=np.zeros((21, S * N)), ncand=np.zeros(S, dtype=np.int32))
+    rad, xx0 = _f64(radii), _f64(x_over_x0)
+    s0, s1 = seed_range if seed_range is not None else (0, S)
+    threads = threads or os.cpu_count() or 1
+    chunk = max(1, -(-(s1 - s0) // (threads * 4)))
+    ranges = [(a, min(a + chunk, s1)) for a in range(s0, s1, chunk)]
+
+    def run(rg):
+        rc = lib().orc_build_tracks(L, _p(rad), _p(xx0), float(z_half), float(bz), off.ctypes.data,
+                                    hp.ctypes.data, hc.ctypes.data, H, phi.ctypes.data, order.ctypes.data,
+                                    rg[0], rg[1], S, se.ctypes.data, ss.ctypes.data, sc.ctypes.data,
+                                    sq.ctypes.data, N, float(chi2_cut), float(nsigma), float(sigma_rphi),
+                                    float(sigma_z), out["hit"].ctypes.data, out["chi2"].ctypes.data,
+                                    out["nhits"].ctypes.data, out["state"].ctypes.data,
+                                    out["cov"].ctypes.data, out["ncand"].ctypes.data)
+        assert rc == 0
+
+    if len(ranges) <= 1:
+        for rg in ranges:
+            run(rg)
+    else:
+        with cf.ThreadPoolExecutor(threads) as ex:
+            list(ex.map(run, ranges))
+    return out
+
+
+def _segment_bounds(off, L):
+    """Flattened segment boundaries [E*L + 1] of the offsets table [E][L+1]
+    (segments of one event are contiguous; events may follow one another or
+    not, so each segment's end is taken from its own row)."""
+    E = off.shape[0]
+    b = np.zeros(E * L + 1, dtype=np.int64)
+    if E == 0:
+        return b
+    b[:-1] = off[:, :L].reshape(-1)
+    b[-1] = off[-1, L]
+    # an event's last segment ends at off[e, L]; the next event's first
+    # segment must start there for the flattening to hold
+    assert np.all(off[1:, 0] == off[:-1, L]), "events must be stored back to back"
+    return np.ascontiguousarray(b)
+
+
+def fit_seeds(events, threads=None):
+    """Seed states of a ``synth.BuildEvents``: the oracle fit of the seed hits."""
+    return fit_batch(events.seed_fit, threads)
+
+
+def build_events(events, seeds=None, threads=None, **opt):
+    """Build a ``synth.BuildEvents`` with the oracle; ``seeds`` is a dict with
+    float32 state [6][S] and cov [21][S] (default: the oracle's seed fit)."""
+    if seeds is None:
+        f = fit_seeds(events, threads)
+        seeds = dict(state=f["state"].astype(np.float32), cov=f["cov"].astype(np.float32))
+    g = events.build_geom
+    f32 = lambda v: np.asarray(v, dtype=np.float32).astype(np.float64)
+    return build_arrays(f32(g.radii), f32(g.x_over_x0), float(np.float32(g.z_half)), float(np.float32(g.bz)),
+                        events.hit_offsets, events.hit_pos, events.hit_cov, events.seed_event, seeds["state"],
+                        seeds["cov"], events.seed_fit.charge, threads=threads, **opt)

@@ -1,11 +1,593 @@
-// Combinatorial track building (Sections 3 and 4.3).
+// Combinatorial track building on sm_103a (Sections 3, 3.1 and 4.3):
+//   bin_hits_kernel   - counting sort of every (event, layer)'s hits into
+//                       phi x z bins (Section 3: hits partitioned spatially
+//                       for a fast look-up of the compatible ones);
+//   build_kernel      - the clone engine, all layers in one launch: each
+//                       seed's candidates occupy a group of G = 2^k >= N lanes
+//                       of a warp; every lane propagates its candidate, scans
+//                       the bins its window overlaps and keeps its N best
+//                       compatible hits; the group merges its lanes' lists
+//                       into the N best children by warp shuffles (in place of
+//                       the paper's shared-memory heaps, Section 4.3) and each
+//                       lane takes over one child and updates it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "kf.h"
 #include "kf_api_internal.h"
+#include "kf_fit.cuh"
 
 namespace kf {
 
 struct BuildState {
+    size_t hit_capacity = 0, bin_capacity = 0, seg_capacity = 0;
+    float *bphi = nullptr, *bz = nullptr;
+    int32_t *bidx = nullptr;
+    int32_t *bin_off = nullptr;
+    int64_t *seg_off = nullptr;  // device copy of the segment bounds [n_seg + 1]
+    int64_t *ev_off = nullptr;   // device copy of hit_offsets [n_events][L + 1]
+    size_t ev_capacity = 0;
 };
 
-void destroy_build_state(BuildState *s) { delete s; }
+void destroy_build_state(BuildState *s)
+{
+    if (!s) return;
+    cudaFree(s->bphi);
+    cudaFree(s->bz);
+    cudaFree(s->bidx);
+    cudaFree(s->bin_off);
+    cudaFree(s->seg_off);
+    cudaFree(s->ev_off);
+    delete s;
+}
 
+namespace {
+
+constexpr float kPi = 3.14159265358979f;
+
+struct BinGrid {
+    int n_phi, n_z;
+    float z_half;
+};
+
+__device__ __forceinline__ int phi_bin(float phi, int n_phi)
+{
+    const int b = (int)floorf((phi + kPi) * (float)n_phi * (1.0f / (2.0f * kPi)));
+    return min(max(b, 0), n_phi - 1);
+}
+__device__ __forceinline__ int z_bin(float z, const BinGrid &bg)
+{
+    const int b = (int)floorf((z + bg.z_half) * (float)bg.n_z / (2.0f * bg.z_half));
+    return min(max(b, 0), bg.n_z - 1);
+}
+
+// One block per (event, layer) segment: count hits per bin in shared memory,
+// scan, scatter phi, z and the hit's index within the segment into the same
+// positions of the binned arrays, bin by bin (bin = iz * n_phi + iphi).
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) bin_hits_kernel(const int64_t *seg_off, const float *hit_pos, int64_t H,
+                                                           BinGrid bg, float *bphi, float *bz, int32_t *bidx,
+                                                           int32_t *bin_off)
+{
+    extern __shared__ int cnt[];
+    __shared__ int warp_sums[THREADS / 32];
+    const int seg = blockIdx.x;
+    const int64_t lo = seg_off[seg], hi = seg_off[seg + 1];
+    const int nb = bg.n_phi * bg.n_z;
+    for (int i = threadIdx.x; i < nb; i += THREADS) cnt[i] = 0;
+    __syncthreads();
+    for (int64_t h = lo + threadIdx.x; h < hi; h += THREADS) {
+        const float x = hit_pos[h], y = hit_pos[H + h], z = hit_pos[2 * H + h];
+        atomicAdd(&cnt[z_bin(z, bg) * bg.n_phi + phi_bin(atan2f(y, x), bg.n_phi)], 1);
+    }
+    __syncthreads();
+    // exclusive scan: each thread owns a contiguous run of bins
+    const int per = (nb + THREADS - 1) / THREADS;
+    const int b0 = min(nb, (int)threadIdx.x * per), b1 = min(nb, b0 + per);
+    int run = 0;
+    for (int b = b0; b < b1; ++b) run += cnt[b];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += o;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < THREADS / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += o;
+        }
+        if (lane < THREADS / 32) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    int base = incl - run + (warp > 0 ? warp_sums[warp - 1] : 0);
+    int32_t *bo = bin_off + (int64_t)seg * (nb + 1);
+    for (int b = b0; b < b1; ++b) {
+        const int c = cnt[b];
+        cnt[b] = base;
+        bo[b] = base;
+        base += c;
+    }
+    if (threadIdx.x == 0) bo[nb] = (int)(hi - lo);
+    __syncthreads();
+    for (int64_t h = lo + threadIdx.x; h < hi; h += THREADS) {
+        const float x = hit_pos[h], y = hit_pos[H + h], z = hit_pos[2 * H + h];
+        const float phi = atan2f(y, x);
+        const int p = atomicAdd(&cnt[z_bin(z, bg) * bg.n_phi + phi_bin(phi, bg.n_phi)], 1);
+        bphi[lo + p] = phi;
+        bz[lo + p] = z;
+        bidx[lo + p] = (int32_t)(h - lo);
+    }
+}
+
+struct BuildParams {
+    FitGeom g;
+    Routing rt;
+    BinGrid bg;
+    int N;
+    float chi2_cut, nsigma, sig_rphi2, sig_z2;
+    int64_t S, H;
+    int n_events;
+    const int64_t *ev_off;  // [E][L + 1]
+    const float *hit_pos, *hit_cov;
+    const float *bphi, *bz;
+    const int32_t *bidx, *bin_off;
+    const int32_t *seed_event;
+    const float *seed_state, *seed_cov;
+    const int8_t *seed_charge;
+    int32_t *out_hit;
+    float *out_chi2;
+    int16_t *out_nhits;
+    float *out_state, *out_cov;
+    uint32_t *out_flags;
+};
+
+constexpr int kMaxN = 8;
+constexpr uint32_t kNoKey = 0xffffffffu;
+
+__device__ __forceinline__ float wrap_pi(float d)
+{
+    d = d > kPi ? d - 2.0f * kPi : d;
+    return d <= -kPi ? d + 2.0f * kPi : d;
+}
+
+// Chi2 increment of a hit (m, packed V) against the predicted candidate, in
+// the layer's local frame (n, t, z) with the radial row of C projected out
+// (the same arithmetic as the update): ctt = C_tt, ctz = C_tz, czz = C_zz.
+__device__ __forceinline__ bool hit_chi2(const float x[3], float nx, float ny, float ctt, float ctz, float czz,
+                                         const float m[3], const float v[6], float *out)
+{
+    const float vnn = fmaf(nx * nx, v[0], fmaf(2.0f * nx * ny, v[1], ny * ny * v[2]));
+    const float vnt = fmaf(nx * ny, v[2] - v[0], (nx * nx - ny * ny) * v[1]);
+    const float vtt = fmaf(ny * ny, v[0], fmaf(-2.0f * nx * ny, v[1], nx * nx * v[2]));
+    const float vnz = fmaf(nx, v[3], ny * v[4]), vtz = fmaf(nx, v[4], -ny * v[3]);
+    const float a = vnn, b = vnt, cc = ctt + vtt, d = vnz, e = ctz + vtz, f = czz + v[5];
+    const float i00 = cc * f - e * e, i10 = d * e - b * f, i11 = a * f - d * d;
+    const float i20 = b * e - cc * d, i21 = b * d - a * e, i22 = a * cc - b * b;
+    const float det = fmaf(a, i00, fmaf(b, i10, d * i20));
+    if (!(a > 0.0f && i22 > 0.0f && det > 0.0f)) return false;
+    const float d0 = m[0] - x[0], d1 = m[1] - x[1];
+    const float rn = fmaf(nx, d0, ny * d1), rt = fmaf(nx, d1, -ny * d0), rz = m[2] - x[2];
+    const float q0 = fmaf(i00, rn, fmaf(i10, rt, i20 * rz));
+    const float q1 = fmaf(i10, rn, fmaf(i11, rt, i21 * rz));
+    const float q2 = fmaf(i20, rn, fmaf(i21, rt, i22 * rz));
+    *out = __fdividef(fmaf(rn, q0, fmaf(rt, q1, rz * q2)), det);
+    return true;
+}
+
+// Order of children: (hits desc, chi2 asc, candidate asc, hit index asc) as
+// a two-word key compared lexicographically: k64 = (63 - hits) << 32 | the
+// bits of chi2 (non-negative floats order as their bit patterns), k32 =
+// candidate slot << 27 | (hit index within the layer + 1), 0 for the hole.
+__device__ __forceinline__ bool key_less(unsigned long long a64, uint32_t a32, unsigned long long b64, uint32_t b32)
+{
+    return a64 < b64 || (a64 == b64 && a32 < b32);
+}
+
+template <int G>
+__global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
+{
+    constexpr int SEEDS_PER_WARP = 32 / G;
+    extern __shared__ int32_t smem[];
+    const int L = p.g.L;
+    int32_t *bp = smem;                                   // [L][128] back-pointers
+    float *slots = reinterpret_cast<float *>(smem + L * 128);  // [kSlotSize][128]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int slot = lane % G, gbase = lane - slot;
+    const int64_t s = ((int64_t)blockIdx.x * 4 + warp) * SEEDS_PER_WARP + lane / G;
+    const bool seed_ok = s < p.S;
+    const int N = p.N;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << gbase);
+
+    float x[6], c[21];
+    float chi2 = 0.0f;
+    int nhits = 0;
+    bool stopped = false;
+    uint32_t flags = 0;
+    int nc = 1;
+    const int ev_in = seed_ok ? p.seed_event[s] : 0;
+    const bool ev_ok = ev_in >= 0 && ev_in < p.n_events;  // a seed of an unknown event builds nothing
+    const int ev = ev_ok ? ev_in : 0;
+    const float qkb = seed_ok ? (float)p.seed_charge[s] * p.g.qk : 0.0f;
+    if (seed_ok && ev_ok) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) x[i] = p.seed_state[i * p.S + s];
+#pragma unroll
+        for (int i = 0; i < 21; ++i) c[i] = p.seed_cov[i * p.S + s];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) x[i] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 21; ++i) c[i] = 0.0f;
+        nc = 0;
+    }
+    const int nbins = p.bg.n_phi * p.bg.n_z;
+    for (int l = 0; l < L; ++l) {
+        const bool valid = slot < nc;
+        bool reached = false;
+        if (valid && !stopped) {
+            float xn[6], sd;
+            Jac J;
+            if (!propagate(x, qkb, p.g.r[l], xn, sd, &J)) {
+                stopped = true;
+                flags |= KF_FLAG_UNREACHABLE;
+            } else if (fabsf(xn[2]) > p.g.z_half) {
+                stopped = true;
+                flags |= KF_FLAG_LEFT_BARREL;
+            } else {
+                transport(J, c);
+                add_scattering(xn, p.g.inv_r[l], p.g.xx0[l], c);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) x[i] = xn[i];
+                reached = true;
+            }
+        }
+        // this candidate's best compatible hits, sorted by (chi2, hit index)
+        float lc[kMaxN];
+        uint32_t lh[kMaxN];
+#pragma unroll
+        for (int k = 0; k < kMaxN; ++k) {
+            lc[k] = INFINITY;
+            lh[k] = kNoKey;
+        }
+        const int64_t seg = (int64_t)ev * (L + 1) + l;
+        const int64_t seg_lo = seed_ok ? p.ev_off[seg] : 0;
+        if (reached) {
+            const float ir = rsqrtf(x[0] * x[0] + x[1] * x[1]);
+            const float nx = x[0] * ir, ny = x[1] * ir;
+            const float ctt = fmaf(ny * ny, c[pk(0, 0)], fmaf(-2.0f * nx * ny, c[pk(1, 0)], nx * nx * c[pk(1, 1)]));
+            const float ctz = fmaf(nx, c[pk(2, 1)], -ny * c[pk(2, 0)]);
+            const float czz = c[pk(2, 2)];
+            const float dphi = p.nsigma * sqrtf(ctt + p.sig_rphi2) * p.g.inv_r[l];
+            const float dz = p.nsigma * sqrtf(czz + p.sig_z2);
+            const float phic = atan2f(x[1], x[0]);
+            const int32_t *bo = p.bin_off + (((int64_t)ev * L + l) * (nbins + 1));
+            // bin ranges widened by a rounding margin: a hit that passes the
+            // exact window test below always lies in a scanned bin
+            const float zm = 1e-4f * (1.0f + fabsf(x[2])), pm = 1e-5f;
+            const int iz0 = z_bin(x[2] - dz - zm, p.bg), iz1 = z_bin(x[2] + dz + zm, p.bg);
+            int ip0, ip1;
+            if (dphi >= kPi - pm) {
+                ip0 = 0;
+                ip1 = p.bg.n_phi - 1;
+            } else {
+                ip0 = (int)floorf((phic - dphi - pm + kPi) * (float)p.bg.n_phi * (1.0f / (2.0f * kPi)));
+                ip1 = (int)floorf((phic + dphi + pm + kPi) * (float)p.bg.n_phi * (1.0f / (2.0f * kPi)));
+            }
+            const int nphi = min(ip1 - ip0 + 1, p.bg.n_phi);
+            for (int iz = iz0; iz <= iz1; ++iz) {
+                for (int k = 0; k < nphi; ++k) {
+                    int ip = ip0 + k;
+                    ip = ip < 0 ? ip + p.bg.n_phi : (ip >= p.bg.n_phi ? ip - p.bg.n_phi : ip);
+                    const int b = iz * p.bg.n_phi + ip;
+                    const int h0 = bo[b], h1 = bo[b + 1];
+                    for (int hb = h0; hb < h1; ++hb) {
+                        const int64_t q = seg_lo + hb;
+                        const float hphi = p.bphi[q], hz = p.bz[q];
+                        if (!(fabsf(wrap_pi(hphi - phic)) <= dphi) || !(fabsf(hz - x[2]) <= dz)) continue;
+                        const uint32_t hl = (uint32_t)p.bidx[q];
+                        const int64_t hg = seg_lo + hl;
+                        float m[3], v[6], dc;
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) m[i] = p.hit_pos[i * p.H + hg];
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) v[i] = p.hit_cov[i * p.H + hg];
+                        if (!hit_chi2(x, nx, ny, ctt, ctz, czz, m, v, &dc) || !(dc <= p.chi2_cut)) continue;
+                        // insert (dc, hl) into the sorted list of N entries
+                        if (!(dc < lc[kMaxN - 1] || (dc == lc[kMaxN - 1] && hl < lh[kMaxN - 1]))) continue;
+                        float cv = dc;
+                        uint32_t hv = hl;
+#pragma unroll
+                        for (int k2 = 0; k2 < kMaxN; ++k2) {
+                            const bool before = cv < lc[k2] || (cv == lc[k2] && hv < lh[k2]);
+                            const float tc = lc[k2];
+                            const uint32_t th = lh[k2];
+                            lc[k2] = before ? cv : tc;
+                            lh[k2] = before ? hv : th;
+                            cv = before ? tc : cv;
+                            hv = before ? th : hv;
+                        }
+                    }
+                }
+            }
+        }
+        // merge the group's lists: N rounds of a group arg-min; the head of a
+        // lane is its best hit child, then its hole child
+        int taken = 0;  // hit children of this lane already selected
+        bool hole_taken = false;
+        unsigned long long my64 = 0;
+        uint32_t my32 = kNoKey;
+        int new_parent = -1;
+        uint32_t new_hit = 0;  // hit index + 1, 0 = hole
+        float new_chi2 = 0.0f;
+        int new_nhits = 0;
+        int n_new = 0;
+        for (int r = 0; r < N; ++r) {
+            // head of this lane
+            if (valid && taken < N && lh[0] != kNoKey) {
+                my64 = ((unsigned long long)(63 - (nhits + 1)) << 32) | __float_as_uint(chi2 + lc[0]);
+                my32 = ((uint32_t)slot << 27) | (lh[0] + 1u);
+            } else if (valid && !hole_taken) {
+                my64 = ((unsigned long long)(63 - nhits) << 32) | __float_as_uint(chi2);
+                my32 = (uint32_t)slot << 27;
+            } else {
+                my64 = ~0ull;
+                my32 = kNoKey;
+            }
+            unsigned long long b64 = my64;
+            uint32_t b32 = my32;
+#pragma unroll
+            for (int d = 1; d < G; d <<= 1) {
+                const unsigned long long o64 = __shfl_xor_sync(gmask, b64, d, G);
+                const uint32_t o32 = __shfl_xor_sync(gmask, b32, d, G);
+                if (key_less(o64, o32, b64, b32)) {
+                    b64 = o64;
+                    b32 = o32;
+                }
+            }
+            if (b32 == kNoKey) break;
+            const int win = (int)(b32 >> 27);
+            if (slot == r) {
+                new_parent = win;
+                new_hit = b32 & 0x7ffffffu;
+                new_nhits = 63 - (int)(b64 >> 32);
+                new_chi2 = __uint_as_float((uint32_t)(b64 & 0xffffffffu));
+            }
+            if (slot == win) {
+                if ((b32 & 0x7ffffffu) != 0u) {  // pop the head of the list
+#pragma unroll
+                    for (int k = 0; k < kMaxN - 1; ++k) {
+                        lc[k] = lc[k + 1];
+                        lh[k] = lh[k + 1];
+                    }
+                    lc[kMaxN - 1] = INFINITY;
+                    lh[kMaxN - 1] = kNoKey;
+                    ++taken;
+                } else {
+                    hole_taken = true;
+                }
+            }
+            ++n_new;
+        }
+        // each lane takes over child `slot` from its parent lane
+        const int src = gbase + (new_parent >= 0 ? new_parent : slot);
+        float px[6], pc[21];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) px[i] = __shfl_sync(gmask, x[i], src, 32);
+#pragma unroll
+        for (int i = 0; i < 21; ++i) pc[i] = __shfl_sync(gmask, c[i], src, 32);
+        const int pstop = __shfl_sync(gmask, (int)stopped, src, 32);
+        const uint32_t pflags = __shfl_sync(gmask, flags, src, 32);
+        nc = n_new;
+        if (slot < nc) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) x[i] = px[i];
+#pragma unroll
+            for (int i = 0; i < 21; ++i) c[i] = pc[i];
+            stopped = pstop != 0;
+            flags = pflags;
+            chi2 = new_chi2;
+            nhits = new_nhits;
+            if (new_hit) {
+                const int64_t hg = seg_lo + (new_hit - 1u);
+                float m[3], v[6], d;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) m[i] = p.hit_pos[i * p.H + hg];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) v[i] = p.hit_cov[i * p.H + hg];
+                const int st = update(x, c, m, v, p.rt, &d, slots + threadIdx.x, 128);
+                if (st == 1) flags |= KF_FLAG_INVERSION_FAILED;
+                if (st >= 2) flags |= KF_FLAG_FP64_PATH;
+                if (st == 3) flags |= KF_FLAG_PSD_REPAIRED;
+            }
+            bp[l * 128 + threadIdx.x] = (int32_t)(((uint32_t)new_parent << 27) | new_hit);
+        }
+        __syncwarp();
+    }
+    if (!seed_ok) return;
+    const int N_ = p.N;
+    const int64_t sj = s * N_ + slot;
+    if (slot < N_) {
+        const bool have = slot < nc;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) p.out_state[i * p.S * N_ + sj] = have ? x[i] : 0.0f;
+#pragma unroll
+        for (int i = 0; i < 21; ++i) p.out_cov[i * p.S * N_ + sj] = have ? c[i] : 0.0f;
+        p.out_chi2[sj] = have ? chi2 : 0.0f;
+        p.out_nhits[sj] = (int16_t)(have ? nhits : -1);
+        p.out_flags[sj] = have ? flags : 0u;
+        int cur = slot;
+        for (int l = L - 1; l >= 0; --l) {
+            int32_t out = -1;
+            if (have) {
+                const uint32_t e = (uint32_t)bp[l * 128 + (threadIdx.x - slot) + cur];
+                const uint32_t h = e & 0x7ffffffu;
+                if (h) out = (int32_t)(p.ev_off[(int64_t)ev * (L + 1) + l] + (h - 1u));
+                cur = (int)(e >> 27);
+            }
+            p.out_hit[sj * L + l] = out;
+        }
+    }
+}
+
+}  // namespace
 }  // namespace kf
+
+using namespace kf;
+
+extern "C" int kf_build_tracks(kf_context *ctx, const kf_geometry *geom, int n_events, const int64_t *hit_offsets,
+                               const float *hit_pos, const float *hit_cov, int64_t n_hits, int64_t n_seeds,
+                               const int32_t *seed_event, const float *seed_state, const float *seed_cov,
+                               const int8_t *seed_charge, int32_t *out_hit_idx, float *out_chi2, int16_t *out_nhits,
+                               float *out_state, float *out_cov, uint32_t *out_flags, const kf_options *opt,
+                               kf_stream stream_)
+{
+    if (!ctx) return KF_ERR_ARG;
+    kf_options o;
+    if (opt) o = *opt;
+    else kf_options_default(&o);
+    int rc;
+    FitGeom g;
+    if ((rc = check_geometry(ctx, geom, &g))) return rc;
+    if ((rc = check_options(ctx, o))) return rc;
+    if (o.max_cands < 1 || o.max_cands > 8) return set_error(ctx, KF_ERR_ARG, "max_cands must be 1..8");
+    if (!(o.chi2_cut > 0.0f) || !(o.window_nsigma > 0.0f) || !(o.hit_sigma_rphi >= 0.0f) || !(o.hit_sigma_z >= 0.0f))
+        return set_error(ctx, KF_ERR_ARG, "chi2_cut and window_nsigma must be positive, hit sigmas non-negative");
+    if (o.n_phi_bins < 1 || o.n_z_bins < 1 || (int64_t)o.n_phi_bins * o.n_z_bins > 16384)
+        return set_error(ctx, KF_ERR_ARG, "n_phi_bins x n_z_bins must be 1..16384");
+    if (o.use_proposal) return set_error(ctx, KF_ERR_UNSUPPORTED, "the learned proposal needs kf_load_proposal first");
+    if (n_events < 0 || n_seeds < 0 || n_hits < 0 || n_hits >= (int64_t(1) << 31))
+        return set_error(ctx, KF_ERR_ARG, "n_events, n_seeds must be >= 0 and n_hits < 2^31");
+    if (n_seeds == 0) return KF_OK;
+    if (n_events < 1 || !hit_offsets) return set_error(ctx, KF_ERR_ARG, "hit_offsets (host) needs n_events >= 1 rows");
+    const int L = g.L;
+    for (int e = 0; e < n_events; ++e) {
+        const int64_t *row = hit_offsets + (int64_t)e * (L + 1);
+        if (e > 0 && row[0] != hit_offsets[(int64_t)(e - 1) * (L + 1) + L])
+            return set_error(ctx, KF_ERR_ARG, "events must be stored back to back (event %d)", e);
+        for (int l = 0; l < L; ++l)
+            if (row[l] < 0 || row[l + 1] < row[l] || row[l + 1] > n_hits)
+                return set_error(ctx, KF_ERR_ARG, "hit_offsets row %d is not a non-decreasing run within n_hits", e);
+        if (row[L] - row[0] >= (int64_t(1) << 27))
+            return set_error(ctx, KF_ERR_ARG, "event %d holds 2^27 or more hits", e);
+    }
+    if (n_hits > 0 && ((rc = check_ptr(ctx, hit_pos, 4, "hit_pos")) || (rc = check_ptr(ctx, hit_cov, 4, "hit_cov"))))
+        return rc;
+    if ((rc = check_ptr(ctx, seed_event, 4, "seed_event")) || (rc = check_ptr(ctx, seed_state, 4, "seed_state")) ||
+        (rc = check_ptr(ctx, seed_cov, 4, "seed_cov")) || (rc = check_ptr(ctx, seed_charge, 1, "seed_charge")) ||
+        (rc = check_ptr(ctx, out_hit_idx, 4, "out_hit_idx")) || (rc = check_ptr(ctx, out_chi2, 4, "out_chi2")) ||
+        (rc = check_ptr(ctx, out_nhits, 2, "out_nhits")) || (rc = check_ptr(ctx, out_state, 4, "out_state")) ||
+        (rc = check_ptr(ctx, out_cov, 4, "out_cov")) || (rc = check_ptr(ctx, out_flags, 4, "out_flags")))
+        return rc;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != context_device(ctx)) cudaSetDevice(context_device(ctx));
+    struct Restore {
+        int prev;
+        ~Restore()
+        {
+            int cur = -1;
+            if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+        }
+    } restore{prev};
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+
+    // scratch: binned hits, bin offsets, segment and event offsets
+    BuildState *&st = context_build_state(ctx);
+    if (!st) st = new BuildState;
+    const int nb = o.n_phi_bins * o.n_z_bins;
+    const size_t n_seg = (size_t)n_events * L;
+    auto grow = [&](void **ptr, size_t &cap, size_t need, size_t elem) -> bool {
+        if (need <= cap) return true;
+        cudaFree(*ptr);
+        *ptr = nullptr;
+        cap = 0;
+        if (cudaMalloc(ptr, std::max<size_t>(need, 1) * elem) != cudaSuccess) return false;
+        cap = need;
+        return true;
+    };
+    size_t hcap = st->hit_capacity;
+    bool ok = grow((void **)&st->bphi, hcap, (size_t)n_hits, sizeof(float));
+    size_t hcap2 = st->hit_capacity;
+    ok = ok && grow((void **)&st->bz, hcap2, (size_t)n_hits, sizeof(float));
+    size_t hcap3 = st->hit_capacity;
+    ok = ok && grow((void **)&st->bidx, hcap3, (size_t)n_hits, sizeof(int32_t));
+    if (ok) st->hit_capacity = std::max(st->hit_capacity, (size_t)n_hits);
+    ok = ok && grow((void **)&st->bin_off, st->bin_capacity, n_seg * (nb + 1), sizeof(int32_t));
+    ok = ok && grow((void **)&st->seg_off, st->seg_capacity, n_seg + 1, sizeof(int64_t));
+    ok = ok && grow((void **)&st->ev_off, st->ev_capacity, (size_t)n_events * (L + 1), sizeof(int64_t));
+    if (!ok) return set_error(ctx, KF_ERR_NOMEM, "could not allocate the build's scratch");
+    std::vector<int64_t> seg(n_seg + 1);
+    for (int e = 0; e < n_events; ++e)
+        for (int l = 0; l < L; ++l) seg[(size_t)e * L + l] = hit_offsets[(int64_t)e * (L + 1) + l];
+    seg[n_seg] = hit_offsets[(int64_t)(n_events - 1) * (L + 1) + L];
+    cudaError_t e = cudaMemcpyAsync(st->seg_off, seg.data(), (n_seg + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                    stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(st->ev_off, hit_offsets, (size_t)n_events * (L + 1) * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "offsets copy");
+    // the host vector must outlive the asynchronous copy
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(ctx, e, "offsets copy");
+
+    BinGrid bg{o.n_phi_bins, o.n_z_bins, g.z_half};
+    const size_t bin_smem = (size_t)(nb + 1) * sizeof(int);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(bin_hits_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16385 * 4);
+        attr_set = true;
+    }
+    bin_hits_kernel<1024><<<(unsigned)n_seg, 1024, bin_smem, stream>>>(st->seg_off, hit_pos, n_hits, bg, st->bphi,
+                                                                        st->bz, st->bidx, st->bin_off);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(ctx, e, "binning launch");
+
+    BuildParams p;
+    p.g = g;
+    p.rt = make_routing(o);
+    p.bg = bg;
+    p.N = o.max_cands;
+    p.chi2_cut = o.chi2_cut;
+    p.nsigma = o.window_nsigma;
+    p.sig_rphi2 = o.hit_sigma_rphi * o.hit_sigma_rphi;
+    p.sig_z2 = o.hit_sigma_z * o.hit_sigma_z;
+    p.S = n_seeds;
+    p.H = n_hits;
+    p.n_events = n_events;
+    p.ev_off = st->ev_off;
+    p.hit_pos = hit_pos;
+    p.hit_cov = hit_cov;
+    p.bphi = st->bphi;
+    p.bz = st->bz;
+    p.bidx = st->bidx;
+    p.bin_off = st->bin_off;
+    p.seed_event = seed_event;
+    p.seed_state = seed_state;
+    p.seed_cov = seed_cov;
+    p.seed_charge = seed_charge;
+    p.out_hit = out_hit_idx;
+    p.out_chi2 = out_chi2;
+    p.out_nhits = out_nhits;
+    p.out_state = out_state;
+    p.out_cov = out_cov;
+    p.out_flags = out_flags;
+    const int G = p.N == 1 ? 1 : p.N <= 2 ? 2 : p.N <= 4 ? 4 : 8;
+    const int64_t seeds_per_block = 4 * (32 / G);
+    const unsigned grid = (unsigned)((n_seeds + seeds_per_block - 1) / seeds_per_block);
+    const size_t smem = (size_t)L * 128 * sizeof(int32_t) + (size_t)kSlotSize * 128 * sizeof(float);
+    switch (G) {
+    case 1: build_kernel<1><<<grid, 128, smem, stream>>>(p); break;
+    case 2: build_kernel<2><<<grid, 128, smem, stream>>>(p); break;
+    case 4: build_kernel<4><<<grid, 128, smem, stream>>>(p); break;
+    default: build_kernel<8><<<grid, 128, smem, stream>>>(p); break;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(ctx, e, "build launch");
+    return KF_OK;
+}

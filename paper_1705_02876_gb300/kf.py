@@ -80,6 +80,9 @@ def load() -> ctypes.CDLL:
             [_vp] * 11 + [ctypes.POINTER(Options), _vp]
         L.kf_fit_tuned_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.kf_build_tracks.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int, _vp, _vp, _vp,
+                                      ctypes.c_int64, ctypes.c_int64] + [_vp] * 10 + \
+            [ctypes.POINTER(Options), _vp]
         L.kf_fit_tracks_noalloc.argtypes = [ctypes.POINTER(Geometry), ctypes.c_int64] + [_vp] * 11 + \
             [ctypes.POINTER(Options), _vp]
         _lib = L
@@ -204,6 +207,48 @@ def fit_tracks(ctx: Context, geom: GeometryArgs, seed_state, seed_cov, charge, h
     rc = load().kf_fit_tracks(ctx.handle, ctypes.byref(geom.struct), T, ev_ptr, n_ev, *args,
                               ctypes.byref(opt) if opt is not None else None, s.cuda_stream)
     ctx.check(rc, "kf_fit_tracks")
+    return out
+
+
+def build_tracks(ctx: Context, geom: GeometryArgs, hit_offsets, hit_pos, hit_cov, seed_event, seed_state,
+                 seed_cov, seed_charge, opt: Options | None = None, out: dict | None = None,
+                 stream: torch.cuda.Stream | None = None) -> dict:
+    """kf_build_tracks: hit_offsets is a host int64 array [E][L+1]; every other
+    array a CUDA tensor.  Returns (or fills) the output tensors."""
+    opt = opt if opt is not None else options()
+    N = int(opt.max_cands)
+    L = geom.struct.n_layers
+    S = int(seed_event.shape[0])
+    H = int(hit_pos.shape[1])
+    off = np.ascontiguousarray(hit_offsets, dtype=np.int64)
+    dev = seed_event.device
+    if out is None:
+        out = dict(hit=torch.empty((S, N, L), dtype=torch.int32, device=dev),
+                   chi2=torch.empty((S, N), dtype=torch.float32, device=dev),
+                   nhits=torch.empty((S, N), dtype=torch.int16, device=dev),
+                   state=torch.empty((6, S * N), dtype=torch.float32, device=dev),
+                   cov=torch.empty((21, S * N), dtype=torch.float32, device=dev),
+                   flags=torch.empty((S, N), dtype=torch.int32, device=dev))
+    args = [
+        off.ctypes.data if off.size else None,
+        _ptr(hit_pos, torch.float32, (3, H), "hit_pos"),
+        _ptr(hit_cov, torch.float32, (6, H), "hit_cov"),
+        H, S,
+        _ptr(seed_event, torch.int32, (S,), "seed_event"),
+        _ptr(seed_state, torch.float32, (6, S), "seed_state"),
+        _ptr(seed_cov, torch.float32, (21, S), "seed_cov"),
+        _ptr(seed_charge, torch.int8, (S,), "seed_charge"),
+        _ptr(out["hit"], torch.int32, (S, N, L), "out_hit_idx"),
+        _ptr(out["chi2"], torch.float32, (S, N), "out_chi2"),
+        _ptr(out["nhits"], torch.int16, (S, N), "out_nhits"),
+        _ptr(out["state"], torch.float32, (6, S * N), "out_state"),
+        _ptr(out["cov"], torch.float32, (21, S * N), "out_cov"),
+        _ptr(out["flags"], torch.int32, (S, N), "out_flags"),
+    ]
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    rc = load().kf_build_tracks(ctx.handle, ctypes.byref(geom.struct), int(off.shape[0]), *args,
+                                ctypes.byref(opt), s.cuda_stream)
+    ctx.check(rc, "kf_build_tracks")
     return out
 
 

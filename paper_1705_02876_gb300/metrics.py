@@ -1,0 +1,44 @@
+"""Track-finding efficiency and fake rate of built candidates (Section 3.2).
+
+The paper counts efficiency and fake rate with the rule that candidates
+matching fewer than 7 hits of a simulated track count as neither.  Reading of
+this build: per seed the best candidate (rank 0) is taken; it *matches* the
+simulated track that owns at least half of its hits (seed hits included); it
+is *counted* if it has at least 7 hits.  Efficiency = fraction of simulated
+tracks with at least 7 hits (and a seed) matched by a counted candidate; fake
+rate = fraction of counted candidates that match no simulated track.  Host-side
+evaluation only, not part of the hot path.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def efficiency_fake_rate(best_hits, seed_track, hit_track, track_nhits, n_seed_hits=3, min_hits=7):
+    """best_hits [S, L]: global hit index per build layer (-1 = none) of each
+    seed's best candidate; seed_track [S]: the simulated track each seed came
+    from; hit_track [H]: owner of each hit (-1 = noise); track_nhits: hits of
+    every simulated track over all layers."""
+    best_hits = np.asarray(best_hits)
+    S = best_hits.shape[0]
+    owner = np.where(best_hits >= 0, np.asarray(hit_track)[np.maximum(best_hits, 0)], -2)
+    n_build = (best_hits >= 0).sum(1)
+    n_total = n_build + n_seed_hits
+    own = (owner == np.asarray(seed_track)[:, None]).sum(1) + n_seed_hits
+    # the majority owner of a candidate's hits is its seed's track whenever it
+    # has at least half; otherwise look for another owner with half
+    matched_track = np.full(S, -1, dtype=np.int64)
+    ok = 2 * own >= n_total
+    matched_track[ok] = np.asarray(seed_track)[ok]
+    for s in np.nonzero(~ok)[0]:
+        vals, cnt = np.unique(owner[s][owner[s] >= 0], return_counts=True)
+        if len(cnt) and 2 * cnt.max() >= n_total[s]:
+            matched_track[s] = vals[np.argmax(cnt)]
+    counted = n_total >= min_hits
+    fake = counted & (matched_track < 0)
+    eligible = np.unique(np.asarray(seed_track)[np.asarray(track_nhits)[np.asarray(seed_track)] >= min_hits])
+    found = np.unique(matched_track[counted & (matched_track >= 0)])
+    eff = np.isin(eligible, found).mean() if len(eligible) else float("nan")
+    fake_rate = fake.sum() / max(counted.sum(), 1)
+    return dict(efficiency=float(eff), fake_rate=float(fake_rate), n_counted=int(counted.sum()),
+                n_eligible=int(len(eligible)), mean_hits=float(n_total.mean()) if S else float("nan"))

@@ -368,3 +368,111 @@ def workload(name: str, seed: int | None = None, scale: float = 1.0) -> FitBatch
             sizes = np.maximum(1, (sizes * scale).astype(np.int64))
         return make_fit_batch(s, sizes, geom=toy_geometry(17), hit_eff=0.95)
     raise KeyError(name)
+
+
+# ----------------------------------------------------------------------------
+# build workloads (Sections 3 and 4.3)
+
+
+@dataclasses.dataclass
+class BuildEvents:
+    """Events for combinatorial building.
+
+    Seeds (Section 3.2: seeds derived from the first three hits of each
+    simulated track): for every simulated track with hits on the first
+    ``n_seed_layers`` layers, a fit of those hits from the vertex truth smeared
+    10% (the fit workload's seed recipe) gives the seed at the last seed
+    layer; ``seed_fit`` holds that fit's inputs.  Building runs over the
+    remaining layers, whose hits (true hits of every track plus uniform noise)
+    are stored per (event, layer) segment in a shuffled order.
+    """
+    geom: Geometry                 # all layers
+    n_seed_layers: int
+    seed_fit: FitBatch             # geometry = the seed layers; one entry per seed
+    seed_event: np.ndarray         # [S] int32 event of each seed
+    seed_track: np.ndarray         # [S] int64 global sim-track id of each seed
+    hit_pos: np.ndarray            # [3, H] float32, build layers only
+    hit_cov: np.ndarray            # [6, H] float32
+    hit_offsets: np.ndarray        # [E, Lb + 1] int64: segment (e, l) is hit_offsets[e, l] .. [e, l+1]
+    hit_track: np.ndarray          # [H] int64 global sim-track id, -1 for noise
+    track_nhits: np.ndarray        # [n_sim] hits of each sim track over all layers
+    n_events: int
+
+    @property
+    def build_geom(self) -> Geometry:
+        return self.geom.sub(self.n_seed_layers, self.geom.n_layers)
+
+    @property
+    def n_seeds(self) -> int:
+        return int(self.seed_event.shape[0])
+
+
+def make_build_events(seed: int, n_events: int, tracks_per_event: int, geom: Geometry | None = None,
+                      noise_factor: float = 10.0, n_seed_layers: int = 3, sigma_rphi=0.01,
+                      sigma_z=0.1, ms=True, pt_lo=0.5, pt_hi=10.0, eta_max=1.0,
+                      noise_per_layer: int | None = None) -> BuildEvents:
+    """``n_events`` events of ``tracks_per_event`` simulated tracks each, plus
+    ``noise_factor`` x tracks_per_event uniform noise hits per layer (or
+    ``noise_per_layer``), on the toy barrel (17 layers by default)."""
+    geom = geom or toy_geometry(17)
+    L = geom.n_layers
+    r_kin, r_hit, r_ms, r_eff, r_seed, r_noise, r_perm = _streams(seed, 7)
+    n = n_events * tracks_per_event
+    vertex, q = draw_vertex_tracks(r_kin, n, pt_lo, pt_hi, "uniform", eta_max)
+    sim = simulate(r_hit, r_ms, r_eff, geom, vertex, q, sigma_rphi, sigma_z, None, 1.0, ms, True)
+    track_nhits = np.zeros(n, dtype=np.int64)
+    for l in range(L):
+        track_nhits += (sim["hit_mask"] >> np.uint32(l)) & np.uint32(1)
+    event_of = np.repeat(np.arange(n_events), tracks_per_event)
+    # seeds: tracks with hits on every seed layer
+    seed_bits = np.uint32((1 << n_seed_layers) - 1)
+    is_seed = (sim["hit_mask"] & seed_bits) == seed_bits
+    sidx = np.nonzero(is_seed)[0]
+    s_state, s_cov = smeared_seed(r_seed, vertex[:, sidx], 0.1)
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    seed_fit = FitBatch(geom.sub(0, n_seed_layers), f32(s_state), f32(s_cov), q[sidx],
+                        f32(sim["hit_pos"][:n_seed_layers][:, :, sidx]),
+                        f32(sim["hit_cov"][:n_seed_layers][:, :, sidx]),
+                        np.full(len(sidx), seed_bits, dtype=np.uint32), np.array([0, len(sidx)]),
+                        sim["truth"][:n_seed_layers][:, :, sidx], sim["crossed"][:n_seed_layers][:, sidx],
+                        vertex[:, sidx])
+    # build-layer hits per (event, layer): true hits then noise, shuffled
+    Lb = L - n_seed_layers
+    n_noise = int(noise_per_layer if noise_per_layer is not None else round(noise_factor * tracks_per_event))
+    pos_parts, cov_parts, trk_parts = [], [], []
+    offsets = np.zeros((n_events, Lb + 1), dtype=np.int64)
+    cursor = 0
+    for e in range(n_events):
+        lo, hi = e * tracks_per_event, (e + 1) * tracks_per_event
+        for lb in range(Lb):
+            l = lb + n_seed_layers
+            has = ((sim["hit_mask"][lo:hi] >> np.uint32(l)) & np.uint32(1)).astype(bool)
+            tp = sim["hit_pos"][l][:, lo:hi][:, has]
+            tc = sim["hit_cov"][l][:, lo:hi][:, has]
+            tt = np.arange(lo, hi)[has]
+            phi = r_noise.uniform(0.0, 2.0 * math.pi, n_noise)
+            zz = r_noise.uniform(-geom.z_half, geom.z_half, n_noise)
+            nxp, nyp = geom.radii[l] * np.cos(phi), geom.radii[l] * np.sin(phi)
+            npos = np.stack([nxp, nyp, zz])
+            ncov = hit_covariance(nxp, nyp, sigma_rphi, sigma_rphi, sigma_z)
+            pos = np.concatenate([tp, npos], axis=1)
+            cov = np.concatenate([tc, ncov], axis=1)
+            trk = np.concatenate([tt, np.full(n_noise, -1, dtype=np.int64)])
+            perm = r_perm.permutation(pos.shape[1])
+            pos_parts.append(pos[:, perm])
+            cov_parts.append(cov[:, perm])
+            trk_parts.append(trk[perm])
+            offsets[e, lb] = cursor
+            cursor += pos.shape[1]
+            offsets[e, lb + 1] = cursor
+    hit_pos = f32(np.concatenate(pos_parts, axis=1)) if pos_parts else np.zeros((3, 0), np.float32)
+    hit_cov = f32(np.concatenate(cov_parts, axis=1)) if cov_parts else np.zeros((6, 0), np.float32)
+    hit_track = np.concatenate(trk_parts) if trk_parts else np.zeros(0, np.int64)
+    return BuildEvents(geom, n_seed_layers, seed_fit, event_of[sidx].astype(np.int32), sidx.astype(np.int64),
+                       hit_pos, hit_cov, offsets, hit_track, track_nhits, n_events)
+
+
+def build_workload(scale_events: int | None = None, seed: int = 4, tracks_per_event: int = 5000):
+    """The build workload: 17 layers, 5,000 tracks per event, 10x uniform noise
+    per layer, seeds from the first three layers, 64 events per launch."""
+    return make_build_events(seed, 64 if scale_events is None else scale_events, tracks_per_event)

@@ -1,0 +1,187 @@
+"""GPU build (binning + clone engine) against the FP64 build oracle on the
+same seeded events and the same seeds, through the C interface.
+
+Bar: at least 99.9% identical hit assignments (every (seed, slot, layer)
+entry); where a candidate's whole hit sequence agrees, chi2 within 1e-3
+max(chi2, 1) relative, state within 1e-4 (positions over r, momenta over |p|)
+and identical hit counts; efficiency and fake rate within 0.5%.  Remaining
+differences come from near-ties in chi2 and hits at the edge of the window or
+the chi2 cut, decided in FP32 on the GPU and FP64 in the oracle.
+"""
+import numpy as np
+import pytest
+
+from paper_1705_02876_gb300 import metrics, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+
+@pytest.fixture(scope="module")
+def kf():
+    from paper_1705_02876_gb300 import build, kf as kf_
+    build.build()
+    return kf_
+
+
+@pytest.fixture(scope="module")
+def ctx(kf):
+    return kf.Context(0)
+
+
+def _t(a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype=dt)
+
+
+def oracle_seeds(oracle, ev):
+    f = oracle.fit_seeds(ev)
+    return dict(state=f["state"].astype(np.float32), cov=f["cov"].astype(np.float32))
+
+
+def gpu_build(kf, ctx, ev, seeds, seed_event=None, **opt):
+    g = ev.build_geom
+    out = kf.build_tracks(ctx, kf.GeometryArgs.of(g), ev.hit_offsets, _t(ev.hit_pos, torch.float32),
+                          _t(ev.hit_cov, torch.float32),
+                          _t(ev.seed_event if seed_event is None else seed_event, torch.int32),
+                          _t(seeds["state"], torch.float32), _t(seeds["cov"], torch.float32),
+                          _t(ev.seed_fit.charge, torch.int8), opt=kf.options(**opt))
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def compare(ev, gpu, ref, N, min_identical=0.999):
+    same = gpu["hit"] == ref["hit"]
+    frac = same.mean()
+    assert frac >= min_identical, frac
+    seq = same.all(2)  # whole candidate identical
+    ok = seq & (ref["nhits"] >= 0)
+    assert np.array_equal(gpu["nhits"][ok], ref["nhits"][ok])
+    rc, gc = ref["chi2"][ok], gpu["chi2"][ok]
+    assert (np.abs(gc - rc) <= 1e-3 * np.maximum(rc, 1.0)).all(), np.abs(gc - rc).max()
+    S = gpu["hit"].shape[0]
+    gs = gpu["state"].reshape(6, S, N)[:, ok]
+    rs = ref["state"].reshape(6, S, N)[:, ok]
+    r = np.maximum(np.hypot(rs[0], rs[1]), 1.0)
+    p = np.linalg.norm(rs[3:], axis=0)
+    assert (np.abs(gs[:3] - rs[:3]) / r <= 1e-4).all()
+    assert (np.abs(gs[3:] - rs[3:]) / p <= 1e-4).all()
+    m_g = metrics.efficiency_fake_rate(gpu["hit"][:, 0], ev.seed_track, ev.hit_track, ev.track_nhits)
+    m_r = metrics.efficiency_fake_rate(ref["hit"][:, 0], ev.seed_track, ev.hit_track, ev.track_nhits)
+    assert abs(m_g["efficiency"] - m_r["efficiency"]) <= 0.005
+    assert abs(m_g["fake_rate"] - m_r["fake_rate"]) <= 0.005
+    return frac, m_g
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 6, 8])
+def test_build_parity(kf, ctx, oracle, N):
+    """2 events x 1,000 tracks, 17 layers (14 built), 10x uniform noise."""
+    ev = synth.make_build_events(21, 2, 1000)
+    seeds = oracle_seeds(oracle, ev)
+    ref = oracle.build_events(ev, seeds=seeds, max_cands=N)
+    gpu = gpu_build(kf, ctx, ev, seeds, max_cands=N)
+    compare(ev, gpu, ref, N)
+
+
+def test_build_parity_coarse_and_fine_bins(kf, ctx, oracle):
+    ev = synth.make_build_events(22, 1, 800)
+    seeds = oracle_seeds(oracle, ev)
+    ref = oracle.build_events(ev, seeds=seeds, max_cands=6)
+    for nphi, nz in ((1, 1), (7, 3), (512, 32)):
+        gpu = gpu_build(kf, ctx, ev, seeds, max_cands=6, n_phi_bins=nphi, n_z_bins=nz)
+        compare(ev, gpu, ref, 6)
+
+
+def test_build_edge_cases(kf, ctx, oracle):
+    """Low-pT loopers and forward tracks that stop, an event with no hits on
+    some layers, seeds of an unknown event, and an empty seed list."""
+    ev = synth.make_build_events(23, 3, 300, pt_lo=0.25, pt_hi=1.0, eta_max=2.0, noise_factor=2.0)
+    # empty the middle event's hits on build layer 4
+    e, l = 1, 4
+    lo, hi = ev.hit_offsets[e, l], ev.hit_offsets[e, l + 1]
+    keep = np.ones(ev.hit_pos.shape[1], bool)
+    keep[lo:hi] = False
+    ev.hit_pos, ev.hit_cov, ev.hit_track = ev.hit_pos[:, keep], ev.hit_cov[:, keep], ev.hit_track[keep]
+    ev.hit_offsets = ev.hit_offsets.copy()
+    ev.hit_offsets[ev.hit_offsets >= hi] -= hi - lo
+    ev.hit_offsets[e, l + 1] = lo
+    seeds = oracle_seeds(oracle, ev)
+    ref = oracle.build_events(ev, seeds=seeds, max_cands=6)
+    gpu = gpu_build(kf, ctx, ev, seeds, max_cands=6)
+    compare(ev, gpu, ref, 6, min_identical=0.998)
+    assert (gpu["flags"][gpu["nhits"] >= 0] & 3).any()  # some candidates stopped
+    bad_event = ev.seed_event.copy()
+    bad_event[:5] = 7
+    bad_event[5] = -1
+    gpu2 = gpu_build(kf, ctx, ev, seeds, seed_event=bad_event, max_cands=6)
+    assert (gpu2["nhits"][:6] == -1).all() and (gpu2["hit"][:6] == -1).all()
+    empty = dict(state=np.zeros((6, 0), np.float32), cov=np.zeros((21, 0), np.float32))
+    g = ev.build_geom
+    out = kf.build_tracks(ctx, kf.GeometryArgs.of(g), ev.hit_offsets, _t(ev.hit_pos, torch.float32),
+                          _t(ev.hit_cov, torch.float32), _t(np.zeros(0, np.int32), torch.int32),
+                          _t(empty["state"], torch.float32), _t(empty["cov"], torch.float32),
+                          _t(np.zeros(0, np.int8), torch.int8))
+    assert out["hit"].shape[0] == 0
+
+
+def test_build_deterministic(kf, ctx, oracle):
+    ev = synth.make_build_events(24, 1, 1500)
+    seeds = oracle_seeds(oracle, ev)
+    a = gpu_build(kf, ctx, ev, seeds)
+    b = gpu_build(kf, ctx, ev, seeds)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_full_pipeline_seed_fit_then_build(kf, ctx, oracle):
+    """Seeds fitted on the GPU from the first three layers, then built on the
+    GPU, against the oracle doing both."""
+    ev = synth.make_build_events(25, 2, 1000)
+    sf = ev.seed_fit
+    dev = kf.to_device(sf)
+    fit = kf.fit_tracks(ctx, kf.GeometryArgs.of(sf.geom), **dev)
+    torch.cuda.synchronize()
+    seeds_gpu = dict(state=fit["state"].cpu().numpy(), cov=fit["cov"].cpu().numpy())
+    ref = oracle.build_events(ev, max_cands=6)  # oracle seeds from its own fit
+    gpu = gpu_build(kf, ctx, ev, seeds_gpu, max_cands=6)
+    compare(ev, gpu, ref, 6, min_identical=0.995)
+
+
+def test_argument_errors(kf, ctx):
+    ev = synth.make_build_events(26, 1, 50)
+    seeds = dict(state=ev.seed_fit.seed_state, cov=ev.seed_fit.seed_cov)
+    for bad, match in (({"max_cands": 9}, "max_cands"), ({"n_phi_bins": 1024, "n_z_bins": 64}, "n_phi_bins")):
+        with pytest.raises(kf.KFError, match=match):
+            gpu_build(kf, ctx, ev, seeds, **bad)
+    off = ev.hit_offsets.copy()
+    off[0, 3] = off[0, 2] - 1
+    g = ev.build_geom
+    with pytest.raises(kf.KFError, match="hit_offsets"):
+        kf.build_tracks(ctx, kf.GeometryArgs.of(g), off, _t(ev.hit_pos, torch.float32), _t(ev.hit_cov, torch.float32),
+                        _t(ev.seed_event, torch.int32), _t(seeds["state"], torch.float32),
+                        _t(seeds["cov"], torch.float32), _t(ev.seed_fit.charge, torch.int8))
+
+
+@pytest.mark.slow
+def test_full_size_build_sampled(kf, ctx, oracle):
+    """The build workload (64 events x 5,000 tracks, 10x noise) in one launch;
+    the seeds of two events compared with the oracle."""
+    ev = synth.build_workload()
+    seeds = oracle_seeds(oracle, ev)
+    gpu = gpu_build(kf, ctx, ev, seeds, max_cands=6)
+    sel = np.nonzero(ev.seed_event < 2)[0]
+    ref = oracle.build_arrays(*_oracle_geom(ev), ev.hit_offsets, ev.hit_pos, ev.hit_cov, ev.seed_event, seeds["state"],
+                              seeds["cov"], ev.seed_fit.charge, max_cands=6, seed_range=(int(sel[0]), int(sel[-1]) + 1))
+    S = ev.n_seeds
+    sub = {k: (v[sel] if k in ("hit", "chi2", "nhits", "flags") else v.reshape(v.shape[0], S, 6)[:, sel].reshape(v.shape[0], -1))
+           for k, v in gpu.items()}
+    refs = {k: (v[sel] if k in ("hit", "chi2", "nhits", "ncand") else v.reshape(v.shape[0], S, 6)[:, sel].reshape(v.shape[0], -1))
+            for k, v in ref.items()}
+    evs = synth.BuildEvents(ev.geom, ev.n_seed_layers, ev.seed_fit, ev.seed_event[sel], ev.seed_track[sel],
+                            ev.hit_pos, ev.hit_cov, ev.hit_offsets, ev.hit_track, ev.track_nhits, ev.n_events)
+    compare(evs, sub, refs, 6)
+
+
+def _oracle_geom(ev):
+    g = ev.build_geom
+    f32 = lambda v: np.asarray(v, dtype=np.float32).astype(np.float64)
+    return f32(g.radii), f32(g.x_over_x0), float(np.float32(g.z_half)), float(np.float32(g.bz))
