@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--precision", default="routed", choices=["routed", "fp32"],
                    help="precision of the timed fit (the chosen form is routed)")
+    p.add_argument("--build-events", type=int, default=64, help="events of the build workload (0: skip it)")
+    p.add_argument("--build-steps", type=int, default=10)
     return p.parse_args()
 
 
@@ -220,6 +222,79 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+BUILD_WORKLOAD = ("build: 17-layer toy barrel r=4..68 cm, {E} events x 5,000 tracks, 10x uniform noise hits per "
+                  "layer (55,000 hits per layer per event), seeds fitted from the first 3 layers, 14 layers built, "
+                  "N=6 candidates, chi2 cut 30, 3-sigma window, 256 x 64 bins")
+
+
+def bench_build(args, kf, ctx, dev, stream, rank, world):
+    """Seed fit (3 layers) + binning + clone-engine build of the build workload."""
+    import torch
+    from paper_1705_02876_gb300 import metrics, synth
+    E = args.build_events
+    ev = synth.make_build_events(4 + 1000 * rank, E, 5000)
+    sf = ev.seed_fit
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dtype=dt)
+    d_sf = kf.to_device(sf, dev)
+    seed_geom = kf.GeometryArgs.of(sf.geom)
+    build_geom = kf.GeometryArgs.of(ev.build_geom)
+    hp, hc = t(ev.hit_pos, torch.float32), t(ev.hit_cov, torch.float32)
+    se, sq = t(ev.seed_event, torch.int32), t(sf.charge, torch.int8)
+    S = ev.n_seeds
+    chosen = kf.options()
+    plain = kf.options(precision_mode=kf.PRECISION_FP32, launch_mode=kf.LAUNCH_PER_EVENT)
+    fit_out = kf.fit_outputs(S, dev)
+    b_out = None
+
+    def step_chosen():
+        nonlocal b_out
+        kf.fit_tracks(ctx, seed_geom, **d_sf, opt=chosen, out=fit_out, stream=stream)
+        b_out = kf.build_tracks(ctx, build_geom, ev.hit_offsets, hp, hc, se, fit_out["state"], fit_out["cov"], sq,
+                                opt=chosen, out=b_out, stream=stream)
+
+    # plain: FP32, one fit launch and one build launch per event
+    ev_seeds = [np.nonzero(ev.seed_event == e)[0] for e in range(E)]
+    zeros = [torch.zeros(len(ix), dtype=torch.int32, device=dev) for ix in ev_seeds]
+    plain_outs = [None] * E
+    lo_hi = [(int(ix[0]), int(ix[-1]) + 1) if len(ix) else (0, 0) for ix in ev_seeds]
+    sfo = kf.fit_outputs(S, dev)
+
+    def step_plain():
+        kf.fit_tracks(ctx, seed_geom, **d_sf, event_offsets=np.array([0] + [hi for _, hi in lo_hi]),
+                      opt=plain, out=sfo, stream=stream)
+        for e in range(E):
+            lo, hi = lo_hi[e]
+            if hi <= lo:
+                continue
+            plain_outs[e] = kf.build_tracks(ctx, build_geom, ev.hit_offsets[e:e + 1], hp, hc, zeros[e],
+                                            sfo["state"][:, lo:hi].contiguous(), sfo["cov"][:, lo:hi].contiguous(),
+                                            sq[lo:hi], opt=plain, out=plain_outs[e], stream=stream)
+
+    def timed(fn, n):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    ms = timed(step_chosen, args.build_steps)
+    ms_plain = timed(step_plain, max(2, args.build_steps // 2))
+    best = b_out["hit"][:, 0].cpu().numpy()
+    q = metrics.efficiency_fake_rate(best, ev.seed_track, ev.hit_track, ev.track_nhits)
+    out = {"value": S / (ms * 1e-3), "unit": "seeds/s", "ms_per_step": ms, "seeds": S,
+           "workload": BUILD_WORKLOAD.format(E=E),
+           "form": "seed fit + binning + build of all events in one launch each, routed precision",
+           "efficiency": q["efficiency"], "fake_rate": q["fake_rate"], "mean_hits": q["mean_hits"],
+           "plain": {"value": S / (ms_plain * 1e-3), "unit": "seeds/s", "ms_per_step": ms_plain,
+                     "form": "FP32 only, one launch per event"}}
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
@@ -356,6 +431,8 @@ def main():
         "kernel_source_hash": src_hash,
         "wall_s_timed": t_wall,
     }
+    if args.build_events > 0:
+        line["build"] = bench_build(args, kf, ctx, dev, stream, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch, T)
     if rank == 0:
