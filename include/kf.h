@@ -211,6 +211,46 @@ int kf_build_tracks(kf_context *ctx, const kf_geometry *geom, int n_events, cons
                     kf_stream stream);
 
 /*
+ * The learned hit proposal.  The paper has no learned component: this network
+ * is the ranking the build step can use for a candidate's in-window hits
+ * (kf_options.use_proposal), so that only the best top-k of them get the full
+ * Kalman chi2.  It is a perceptron 12 -> 64 -> 64 -> 1 with ReLU activations
+ * whose logit scores a (candidate, hit) pair.
+ *
+ * weights: KF_PROPOSAL_PARAMS float32 values, in this order: W1 [12][64]
+ *   (input-major), b1 [64], W2 [64][64], b2 [64], W3 [64], b3.
+ * features: float32 [n][12], one row per pair: the residual of the hit in the
+ *   layer's local frame (radial, tangential, z) divided by the square roots
+ *   of the matching diagonal entries of S = H C H^T + V; log10 of the six
+ *   diagonal entries of the predicted covariance C; q / pT; the layer's index
+ *   among the build layers divided by their number; the candidate's holes so
+ *   far.  labels: float32 [n], 1 = the plain build kept the pair, 0 = not.
+ * All arrays are device memory owned by the caller.
+ */
+#define KF_PROPOSAL_PARAMS 5057
+
+/* Mean binary cross-entropy on the logits over the n pairs and its gradient
+ * with respect to the weights (grad [KF_PROPOSAL_PARAMS], device), in FP32;
+ * *loss (host, may be NULL) receives the loss and makes the call wait. */
+int kf_proposal_gradient(kf_context *ctx, const float *weights, const float *features, const float *labels,
+                         int64_t n, float *grad, float *loss, kf_stream stream);
+
+/* Train the weights in place (FP32 master weights) with Adam (beta1 0.9,
+ * beta2 0.999, eps 1e-8) on mini-batches of `batch` pairs, `epochs` passes
+ * over the data, each in a fixed pseudo-random order.  epoch_loss (host, may
+ * be NULL) receives the mean loss of each epoch and makes the call wait. */
+int kf_proposal_train(kf_context *ctx, float *weights, const float *features, const float *labels, int64_t n,
+                      int epochs, int batch, float learning_rate, float *epoch_loss, kf_stream stream);
+
+/* Load weights into the context for inference: copied, and rounded to BF16
+ * for the tensor cores (biases and W3 stay FP32). */
+int kf_proposal_load(kf_context *ctx, const float *weights, kf_stream stream);
+
+/* Logits [n] of the loaded network for the pairs' features: BF16 inputs and
+ * weights, FP32 accumulation, on the tensor cores. */
+int kf_proposal_score(kf_context *ctx, const float *features, int64_t n, float *logits, kf_stream stream);
+
+/*
  * Launch shape the autotuner picked for the persistent fit of n_layers layers
  * and a batch of n_tracks' size class (powers of two), once a KF_LAUNCH_AUTO
  * fit of that class has run on ctx.  Writes tracks per block and the register

@@ -58,6 +58,7 @@ struct kf_context {
     std::vector<GraphEntry> graphs;
     uint64_t clock = 0;
     kf::BuildState *build = nullptr;
+    kf::MlpState *mlp = nullptr;
 };
 
 namespace kf {
@@ -81,6 +82,7 @@ int cuda_error(kf_context *ctx, cudaError_t e, const char *what)
 int context_device(const kf_context *ctx) { return ctx->device; }
 int context_sm_count(const kf_context *ctx) { return ctx->sm_count; }
 BuildState *&context_build_state(kf_context *ctx) { return ctx->build; }
+MlpState *&context_mlp_state(kf_context *ctx) { return ctx->mlp; }
 
 int check_geometry(kf_context *ctx, const kf_geometry *geom, FitGeom *g)
 {
@@ -205,6 +207,7 @@ void kf_context_destroy(kf_context *ctx)
     cudaDeviceSynchronize();
     for (auto &e : ctx->graphs) cudaGraphExecDestroy(e.exec);
     kf::destroy_build_state(ctx->build);
+    kf::destroy_mlp_state(ctx->mlp);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     cudaFree(ctx->d_counter);
     delete ctx;

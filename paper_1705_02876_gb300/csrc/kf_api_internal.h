@@ -10,6 +10,8 @@ namespace kf {
 
 struct BuildState;  // device scratch of the build step (kf_build.cu)
 void destroy_build_state(BuildState *s);
+struct MlpState;  // proposal network scratch and weights (kf_mlp.cu)
+void destroy_mlp_state(MlpState *s);
 
 int set_error(kf_context *ctx, int code, const char *fmt, ...);
 int cuda_error(kf_context *ctx, cudaError_t e, const char *what);
@@ -20,5 +22,6 @@ Routing make_routing(const kf_options &o);
 int context_device(const kf_context *ctx);
 int context_sm_count(const kf_context *ctx);
 BuildState *&context_build_state(kf_context *ctx);
+MlpState *&context_mlp_state(kf_context *ctx);
 
 }  // namespace kf

@@ -1,0 +1,382 @@
+// Training and batched inference of the learned hit proposal (kf_mlp.cuh).
+//
+// Training runs in FP32 (master weights, gradients and Adam moments): each
+// block takes a tile of 64 samples, computes the forward pass, the binary
+// cross-entropy on the logits and the backward pass in shared memory, and adds
+// its part of the weight gradients to a global buffer; an Adam kernel then
+// updates the weights.  Inference copies the weights to BF16 and scores on the
+// tensor cores (mlp_score_warp).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "kf.h"
+#include "kf_api_internal.h"
+#include "kf_mlp.cuh"
+
+namespace kf {
+
+struct MlpState {
+    float *grad = nullptr, *m = nullptr, *v = nullptr;  // [kMlpParams] each
+    float *loss = nullptr;                              // one accumulator
+    float *w32 = nullptr;                               // loaded weights, FP32
+    __nv_bfloat16 *W1 = nullptr, *W2 = nullptr;         // loaded weights, BF16 [16][64], [64][64]
+    bool loaded = false;
+};
+
+void destroy_mlp_state(MlpState *s)
+{
+    if (!s) return;
+    cudaFree(s->grad);
+    cudaFree(s->m);
+    cudaFree(s->v);
+    cudaFree(s->loss);
+    cudaFree(s->w32);
+    cudaFree(s->W1);
+    cudaFree(s->W2);
+    delete s;
+}
+
+bool proposal_loaded(kf_context *ctx)
+{
+    MlpState *s = context_mlp_state(ctx);
+    return s && s->loaded;
+}
+
+void proposal_weights(kf_context *ctx, const __nv_bfloat16 **W1, const __nv_bfloat16 **W2, const float **w32)
+{
+    MlpState *s = context_mlp_state(ctx);
+    *W1 = s->W1;
+    *W2 = s->W2;
+    *w32 = s->w32;
+}
+
+namespace {
+
+constexpr int kTile = 64, kTrainThreads = 256;
+
+struct TrainSmem {
+    float X[kTile][kMlpIn];
+    float H1[kTile][kMlpHid];
+    float H2[kTile][kMlpHid];
+    float dH2[kTile][kMlpHid];
+    float dH1[kTile][kMlpHid];
+    float dz[kTile];
+    float W1[kMlpIn][kMlpHid];
+    float W2[kMlpHid][kMlpHid];
+    float b1[kMlpHid], b2[kMlpHid], W3[kMlpHid], b3;
+};
+
+// Samples [start, start + count) of the epoch's order, sample = (j P + off) mod n.
+__global__ void __launch_bounds__(kTrainThreads) mlp_grad_kernel(const float *w, const float *X, const float *y, int64_t n,
+                                                                 int64_t start, int64_t count, int64_t P, int64_t off,
+                                                                 float inv_batch, float *grad, float *loss)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TrainSmem &s = *reinterpret_cast<TrainSmem *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int64_t j0 = start + (int64_t)blockIdx.x * kTile;
+    for (int i = tid; i < kMlpIn * kMlpHid; i += kTrainThreads) s.W1[i / kMlpHid][i % kMlpHid] = w[kOffW1 + i];
+    for (int i = tid; i < kMlpHid * kMlpHid; i += kTrainThreads) s.W2[i / kMlpHid][i % kMlpHid] = w[kOffW2 + i];
+    for (int i = tid; i < kMlpHid; i += kTrainThreads) {
+        s.b1[i] = w[kOffB1 + i];
+        s.b2[i] = w[kOffB2 + i];
+        s.W3[i] = w[kOffW3 + i];
+    }
+    if (tid == 0) s.b3 = w[kOffB3];
+    for (int i = tid; i < kTile * kMlpIn; i += kTrainThreads) {
+        const int r = i / kMlpIn, f = i % kMlpIn;
+        const int64_t j = j0 + r;
+        float val = 0.0f;
+        if (j < start + count) val = X[((j * P + off) % n) * kMlpIn + f];
+        s.X[r][f] = val;
+    }
+    __syncthreads();
+    for (int i = tid; i < kTile * kMlpHid; i += kTrainThreads) {  // H1 = relu(X W1 + b1)
+        const int r = i / kMlpHid, u = i % kMlpHid;
+        float a = s.b1[u];
+#pragma unroll
+        for (int k = 0; k < kMlpIn; ++k) a = fmaf(s.X[r][k], s.W1[k][u], a);
+        s.H1[r][u] = fmaxf(a, 0.0f);
+    }
+    __syncthreads();
+    for (int i = tid; i < kTile * kMlpHid; i += kTrainThreads) {  // H2 = relu(H1 W2 + b2)
+        const int r = i / kMlpHid, u = i % kMlpHid;
+        float a = s.b2[u];
+#pragma unroll 16
+        for (int k = 0; k < kMlpHid; ++k) a = fmaf(s.H1[r][k], s.W2[k][u], a);
+        s.H2[r][u] = fmaxf(a, 0.0f);
+    }
+    __syncthreads();
+    if (tid < kTile) {  // logit, loss, dL/dz
+        const int64_t j = j0 + tid;
+        float z = s.b3;
+#pragma unroll 16
+        for (int k = 0; k < kMlpHid; ++k) z = fmaf(s.H2[tid][k], s.W3[k], z);
+        float d = 0.0f, l = 0.0f;
+        if (j < start + count) {
+            const float t = y[(j * P + off) % n];
+            l = fmaxf(z, 0.0f) - z * t + log1pf(expf(-fabsf(z)));
+            d = (1.0f / (1.0f + expf(-z)) - t) * inv_batch;
+        }
+        s.dz[tid] = d;
+        // warp sum of the loss, one atomic per warp
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+        if ((tid & 31) == 0) atomicAdd(loss, l);
+    }
+    __syncthreads();
+    for (int i = tid; i < kTile * kMlpHid; i += kTrainThreads) {  // dH2 = dz W3^T on active units
+        const int r = i / kMlpHid, u = i % kMlpHid;
+        s.dH2[r][u] = s.H2[r][u] > 0.0f ? s.dz[r] * s.W3[u] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = tid; i < kTile * kMlpHid; i += kTrainThreads) {  // dH1 = dH2 W2^T on active units
+        const int r = i / kMlpHid, k = i % kMlpHid;
+        float a = 0.0f;
+        if (s.H1[r][k] > 0.0f) {
+#pragma unroll 16
+            for (int u = 0; u < kMlpHid; ++u) a = fmaf(s.dH2[r][u], s.W2[k][u], a);
+        }
+        s.dH1[r][k] = a;
+    }
+    __syncthreads();
+    // this tile's share of the gradient
+    for (int i = tid; i < kMlpHid * kMlpHid; i += kTrainThreads) {
+        const int k = i / kMlpHid, u = i % kMlpHid;
+        float a = 0.0f;
+        for (int r = 0; r < kTile; ++r) a = fmaf(s.H1[r][k], s.dH2[r][u], a);
+        atomicAdd(&grad[kOffW2 + i], a);
+    }
+    for (int i = tid; i < kMlpIn * kMlpHid; i += kTrainThreads) {
+        const int f = i / kMlpHid, u = i % kMlpHid;
+        float a = 0.0f;
+        for (int r = 0; r < kTile; ++r) a = fmaf(s.X[r][f], s.dH1[r][u], a);
+        atomicAdd(&grad[kOffW1 + i], a);
+    }
+    for (int u = tid; u < kMlpHid; u += kTrainThreads) {
+        float g1 = 0.0f, g2 = 0.0f, g3 = 0.0f;
+        for (int r = 0; r < kTile; ++r) {
+            g1 += s.dH1[r][u];
+            g2 += s.dH2[r][u];
+            g3 = fmaf(s.H2[r][u], s.dz[r], g3);
+        }
+        atomicAdd(&grad[kOffB1 + u], g1);
+        atomicAdd(&grad[kOffB2 + u], g2);
+        atomicAdd(&grad[kOffW3 + u], g3);
+    }
+    if (tid == 0) {
+        float g = 0.0f;
+        for (int r = 0; r < kTile; ++r) g += s.dz[r];
+        atomicAdd(&grad[kOffB3], g);
+    }
+}
+
+// Adam (Kingma and Ba) on every parameter, then clear the gradient.
+__global__ void adam_kernel(float *w, float *grad, float *m, float *v, int t, float lr, float b1, float b2, float eps)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kMlpParams) return;
+    const float g = grad[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * g;
+    const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / (1.0f - powf(b1, (float)t)), vh = vi / (1.0f - powf(b2, (float)t));
+    w[i] -= lr * mh / (sqrtf(vh) + eps);
+    grad[i] = 0.0f;
+}
+
+__global__ void to_bf16_kernel(const float *w, __nv_bfloat16 *W1, __nv_bfloat16 *W2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpInPad * kMlpHid; i += gridDim.x * blockDim.x)
+        W1[i] = __float2bfloat16(i < kMlpIn * kMlpHid ? w[kOffW1 + i] : 0.0f);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpHid * kMlpHid; i += gridDim.x * blockDim.x)
+        W2[i] = __float2bfloat16(w[kOffW2 + i]);
+}
+
+constexpr int kScoreWarps = 4;
+
+struct ScoreSmem {
+    MlpSmemWeights w;
+    MlpWarpStage st[kScoreWarps];
+};
+
+// Each warp scores 32 rows at a time on the tensor cores.
+__global__ void __launch_bounds__(32 * kScoreWarps) mlp_score_kernel(const __nv_bfloat16 *W1, const __nv_bfloat16 *W2,
+                                                                     const float *w32, const float *X, int64_t n,
+                                                                     float *logits)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    ScoreSmem &s = *reinterpret_cast<ScoreSmem *>(smem_raw);
+    mlp_load_weights(&s.w, W1, W2, w32);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    MlpWarpStage *st = &s.st[warp];
+    const int64_t n_chunks = (n + 31) / 32;
+    for (int64_t ch = (int64_t)blockIdx.x * kScoreWarps + warp; ch < n_chunks; ch += (int64_t)gridDim.x * kScoreWarps) {
+        const int64_t row = ch * 32 + lane;
+#pragma unroll
+        for (int f = 0; f < kMlpInPad; ++f)
+            st->X[lane * kMlpInPad + f] = __float2bfloat16(row < n && f < kMlpIn ? X[row * kMlpIn + f] : 0.0f);
+        const float z = mlp_score_warp(&s.w, st);
+        if (row < n) logits[row] = z;
+    }
+}
+
+int ensure_state(kf_context *ctx, MlpState **out)
+{
+    MlpState *&s = context_mlp_state(ctx);
+    if (!s) {
+        s = new MlpState;
+        bool ok = cudaMalloc(&s->grad, kMlpParams * sizeof(float)) == cudaSuccess &&
+                  cudaMalloc(&s->m, kMlpParams * sizeof(float)) == cudaSuccess &&
+                  cudaMalloc(&s->v, kMlpParams * sizeof(float)) == cudaSuccess &&
+                  cudaMalloc(&s->loss, sizeof(float)) == cudaSuccess &&
+                  cudaMalloc(&s->w32, kMlpParams * sizeof(float)) == cudaSuccess &&
+                  cudaMalloc(&s->W1, kMlpInPad * kMlpHid * sizeof(__nv_bfloat16)) == cudaSuccess &&
+                  cudaMalloc(&s->W2, kMlpHid * kMlpHid * sizeof(__nv_bfloat16)) == cudaSuccess;
+        if (!ok) {
+            destroy_mlp_state(s);
+            s = nullptr;
+            return set_error(ctx, KF_ERR_NOMEM, "could not allocate the proposal's scratch");
+        }
+    }
+    *out = s;
+    return KF_OK;
+}
+
+int launch_grad(kf_context *ctx, MlpState *s, const float *w, const float *X, const float *y, int64_t n, int64_t start,
+                int64_t count, int64_t P, int64_t off, float inv_batch, cudaStream_t stream)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem));
+        attr = true;
+    }
+    const unsigned blocks = (unsigned)((count + kTile - 1) / kTile);
+    mlp_grad_kernel<<<blocks, kTrainThreads, sizeof(TrainSmem), stream>>>(w, X, y, n, start, count, P, off, inv_batch,
+                                                                          s->grad, s->loss);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? KF_OK : cuda_error(ctx, e, "proposal gradient launch");
+}
+
+int64_t gcd64(int64_t a, int64_t b) { return b ? gcd64(b, a % b) : a; }
+
+}  // namespace
+}  // namespace kf
+
+using namespace kf;
+
+extern "C" {
+
+int kf_proposal_gradient(kf_context *ctx, const float *weights, const float *features, const float *labels, int64_t n,
+                         float *grad, float *loss, kf_stream stream_)
+{
+    if (!ctx) return KF_ERR_ARG;
+    if (n < 1) return set_error(ctx, KF_ERR_ARG, "n must be >= 1");
+    int rc;
+    if ((rc = check_ptr(ctx, weights, 4, "weights")) || (rc = check_ptr(ctx, features, 4, "features")) ||
+        (rc = check_ptr(ctx, labels, 4, "labels")) || (rc = check_ptr(ctx, grad, 4, "grad")))
+        return rc;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    MlpState *s;
+    if ((rc = ensure_state(ctx, &s))) return rc;
+    cudaMemsetAsync(s->grad, 0, kMlpParams * sizeof(float), stream);
+    cudaMemsetAsync(s->loss, 0, sizeof(float), stream);
+    if ((rc = launch_grad(ctx, s, weights, features, labels, n, 0, n, 1, 0, 1.0f / (float)n, stream))) return rc;
+    cudaMemcpyAsync(grad, s->grad, kMlpParams * sizeof(float), cudaMemcpyDeviceToDevice, stream);
+    if (loss) {
+        float l = 0.0f;
+        cudaMemcpyAsync(&l, s->loss, sizeof(float), cudaMemcpyDeviceToHost, stream);
+        const cudaError_t e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "proposal gradient");
+        *loss = l / (float)n;
+    }
+    return KF_OK;
+}
+
+int kf_proposal_train(kf_context *ctx, float *weights, const float *features, const float *labels, int64_t n, int epochs,
+                      int batch, float learning_rate, float *epoch_loss, kf_stream stream_)
+{
+    if (!ctx) return KF_ERR_ARG;
+    if (n < 1 || epochs < 0 || batch < 1 || !(learning_rate > 0.0f))
+        return set_error(ctx, KF_ERR_ARG, "n >= 1, epochs >= 0, batch >= 1 and learning_rate > 0 required");
+    int rc;
+    if ((rc = check_ptr(ctx, weights, 4, "weights")) || (rc = check_ptr(ctx, features, 4, "features")) ||
+        (rc = check_ptr(ctx, labels, 4, "labels")))
+        return rc;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    MlpState *s;
+    if ((rc = ensure_state(ctx, &s))) return rc;
+    cudaMemsetAsync(s->grad, 0, kMlpParams * sizeof(float), stream);
+    cudaMemsetAsync(s->m, 0, kMlpParams * sizeof(float), stream);
+    cudaMemsetAsync(s->v, 0, kMlpParams * sizeof(float), stream);
+    // epoch order: sample = (j P + off) mod n with P coprime to n
+    int64_t P = 1000003;
+    while (gcd64(P, n) != 1) P += 2;
+    int t = 0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        cudaMemsetAsync(s->loss, 0, sizeof(float), stream);
+        const int64_t off = (int64_t)ep * 7919 % n;
+        for (int64_t b0 = 0; b0 < n; b0 += batch) {
+            const int64_t cnt = std::min<int64_t>(batch, n - b0);
+            if ((rc = launch_grad(ctx, s, weights, features, labels, n, b0, cnt, P, off, 1.0f / (float)cnt, stream)))
+                return rc;
+            adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, stream>>>(weights, s->grad, s->m, s->v, ++t, learning_rate,
+                                                                     0.9f, 0.999f, 1e-8f);
+        }
+        if (epoch_loss) {
+            float l = 0.0f;
+            cudaMemcpyAsync(&l, s->loss, sizeof(float), cudaMemcpyDeviceToHost, stream);
+            const cudaError_t e = cudaStreamSynchronize(stream);
+            if (e != cudaSuccess) return cuda_error(ctx, e, "proposal training");
+            epoch_loss[ep] = l / (float)n;
+        }
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? KF_OK : cuda_error(ctx, e, "proposal training");
+}
+
+int kf_proposal_load(kf_context *ctx, const float *weights, kf_stream stream_)
+{
+    if (!ctx) return KF_ERR_ARG;
+    int rc;
+    if ((rc = check_ptr(ctx, weights, 4, "weights"))) return rc;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    MlpState *s;
+    if ((rc = ensure_state(ctx, &s))) return rc;
+    cudaMemcpyAsync(s->w32, weights, kMlpParams * sizeof(float), cudaMemcpyDeviceToDevice, stream);
+    to_bf16_kernel<<<8, 256, 0, stream>>>(s->w32, s->W1, s->W2);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(ctx, e, "proposal load");
+    s->loaded = true;
+    return KF_OK;
+}
+
+int kf_proposal_score(kf_context *ctx, const float *features, int64_t n, float *logits, kf_stream stream_)
+{
+    if (!ctx) return KF_ERR_ARG;
+    if (!proposal_loaded(ctx)) return set_error(ctx, KF_ERR_ARG, "no proposal weights loaded (kf_proposal_load)");
+    if (n < 0) return set_error(ctx, KF_ERR_ARG, "n must be >= 0");
+    if (n == 0) return KF_OK;
+    int rc;
+    if ((rc = check_ptr(ctx, features, 4, "features")) || (rc = check_ptr(ctx, logits, 4, "logits"))) return rc;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    MlpState *s = context_mlp_state(ctx);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(mlp_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScoreSmem));
+        attr = true;
+    }
+    const int64_t chunks = (n + 31) / 32;
+    const unsigned grid = (unsigned)std::min<int64_t>((chunks + kScoreWarps - 1) / kScoreWarps,
+                                                      (int64_t)context_sm_count(ctx) * 8);
+    mlp_score_kernel<<<grid, 32 * kScoreWarps, sizeof(ScoreSmem), stream>>>(s->W1, s->W2, s->w32, features, n, logits);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? KF_OK : cuda_error(ctx, e, "proposal score launch");
+}
+
+}  // extern "C"

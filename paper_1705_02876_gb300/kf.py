@@ -83,6 +83,11 @@ def load() -> ctypes.CDLL:
         L.kf_build_tracks.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int, _vp, _vp, _vp,
                                       ctypes.c_int64, ctypes.c_int64] + [_vp] * 10 + \
             [ctypes.POINTER(Options), _vp]
+        L.kf_proposal_gradient.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_float), _vp]
+        L.kf_proposal_train.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                        ctypes.POINTER(ctypes.c_float), _vp]
+        L.kf_proposal_load.argtypes = [_vp, _vp, _vp]
+        L.kf_proposal_score.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
         L.kf_fit_tracks_noalloc.argtypes = [ctypes.POINTER(Geometry), ctypes.c_int64] + [_vp] * 11 + \
             [ctypes.POINTER(Options), _vp]
         _lib = L
@@ -250,6 +255,53 @@ def build_tracks(ctx: Context, geom: GeometryArgs, hit_offsets, hit_pos, hit_cov
                                 ctypes.byref(opt), s.cuda_stream)
     ctx.check(rc, "kf_build_tracks")
     return out
+
+
+PROPOSAL_PARAMS = 5057
+
+
+def _cur_stream(t, stream):
+    return (stream if stream is not None else torch.cuda.current_stream(t.device)).cuda_stream
+
+
+def proposal_gradient(ctx: Context, weights, features, labels, stream=None):
+    """(grad tensor [5057], mean loss) of the proposal network on (features, labels)."""
+    n = int(labels.shape[0])
+    grad = torch.empty(PROPOSAL_PARAMS, dtype=torch.float32, device=weights.device)
+    loss = ctypes.c_float()
+    rc = load().kf_proposal_gradient(ctx.handle, _ptr(weights, torch.float32, (PROPOSAL_PARAMS,), "weights"),
+                                     _ptr(features, torch.float32, (n, 12), "features"),
+                                     _ptr(labels, torch.float32, (n,), "labels"), n, grad.data_ptr(),
+                                     ctypes.byref(loss), _cur_stream(weights, stream))
+    ctx.check(rc, "kf_proposal_gradient")
+    return grad, loss.value
+
+
+def proposal_train(ctx: Context, weights, features, labels, epochs=5, batch=4096, lr=1e-3, stream=None):
+    """Train ``weights`` (CUDA float32 [5057]) in place; returns the per-epoch losses."""
+    n = int(labels.shape[0])
+    losses = (ctypes.c_float * max(epochs, 1))()
+    rc = load().kf_proposal_train(ctx.handle, _ptr(weights, torch.float32, (PROPOSAL_PARAMS,), "weights"),
+                                  _ptr(features, torch.float32, (n, 12), "features"),
+                                  _ptr(labels, torch.float32, (n,), "labels"), n, epochs, batch, lr, losses,
+                                  _cur_stream(weights, stream))
+    ctx.check(rc, "kf_proposal_train")
+    return [losses[i] for i in range(epochs)]
+
+
+def proposal_load(ctx: Context, weights, stream=None):
+    rc = load().kf_proposal_load(ctx.handle, _ptr(weights, torch.float32, (PROPOSAL_PARAMS,), "weights"),
+                                 _cur_stream(weights, stream))
+    ctx.check(rc, "kf_proposal_load")
+
+
+def proposal_score(ctx: Context, features, stream=None):
+    n = int(features.shape[0])
+    logits = torch.empty(n, dtype=torch.float32, device=features.device)
+    rc = load().kf_proposal_score(ctx.handle, _ptr(features, torch.float32, (n, 12), "features"), n,
+                                  logits.data_ptr() if n else None, _cur_stream(features, stream))
+    ctx.check(rc, "kf_proposal_score")
+    return logits
 
 
 def to_device(batch, device="cuda") -> dict:

@@ -1,0 +1,95 @@
+"""Proposal network on the GPU (training kernels in FP32, inference on the
+tensor cores in BF16) against the FP64 numpy oracle, through the C interface.
+
+Tolerances: FP32 gradient 1e-5 of the gradient's scale per entry; weights
+after full-batch Adam steps 1e-5 of the step size; BF16 logits within
+2^-6 (1 + |z|) (inputs and weights rounded to 8 significand bits, FP32
+accumulation).
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kf():
+    from paper_1705_02876_gb300 import build, kf as kf_
+    build.build()
+    return kf_
+
+
+@pytest.fixture(scope="module")
+def ctx(kf):
+    return kf.Context(0)
+
+
+def data(seed, n):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(n, 12)).astype(np.float32)
+    y = ((X[:, 0] + 0.5 * X[:, 1] - X[:, 2] + 0.3 * rng.normal(size=n)) > 0).astype(np.float32)
+    w = M.init_params(rng).astype(np.float32)
+    return X, y, w
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 1000, 20000])
+def test_gradient_matches_oracle(kf, ctx, n):
+    X, y, w = data(1, n)
+    g, loss = kf.proposal_gradient(ctx, cu(w), cu(X), cu(y))
+    torch.cuda.synchronize()
+    g_ref = M.backward(w.astype(np.float64), X, y)
+    l_ref = M.loss(w.astype(np.float64), X, y)
+    scale = np.abs(g_ref).max()
+    assert np.abs(g.cpu().numpy() - g_ref).max() <= 1e-5 * scale, np.abs(g.cpu().numpy() - g_ref).max() / scale
+    assert abs(loss - l_ref) <= 1e-5 * (1 + l_ref)
+
+
+def test_full_batch_adam_steps_match_oracle(kf, ctx):
+    X, y, w = data(2, 3000)
+    wt = cu(w.copy())
+    kf.proposal_train(ctx, wt, cu(X), cu(y), epochs=3, batch=3000, lr=1e-3)
+    torch.cuda.synchronize()
+    p = w.astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for t in range(1, 4):
+        p, m, v = M.adam_step(p, M.backward(p, X, y), m, v, t, lr=1e-3)
+    # each Adam step moves a weight by about lr; FP32 gradients near zero can
+    # flip the sign of an early step, so compare to the step size
+    d = np.abs(wt.cpu().numpy() - p)
+    assert np.quantile(d, 0.999) <= 1e-5 and d.max() <= 6e-3
+
+
+def test_training_learns(kf, ctx):
+    X, y, w = data(3, 50000)
+    wt = cu(w)
+    _, l0 = kf.proposal_gradient(ctx, wt, cu(X), cu(y))
+    losses = kf.proposal_train(ctx, wt, cu(X), cu(y), epochs=4, batch=1024, lr=3e-3)
+    assert losses[-1] < 0.5 * l0 and losses[-1] < 0.25 and losses[-1] <= losses[0], (l0, losses)
+    _, l_final = kf.proposal_gradient(ctx, wt, cu(X), cu(y))
+    assert abs(l_final - M.loss(wt.cpu().numpy().astype(np.float64), X, y)) < 1e-4
+
+
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 4097])
+def test_tensor_core_scores_match_oracle(kf, ctx, n):
+    X, y, w = data(4, n)
+    kf.proposal_load(ctx, cu(w))
+    z = kf.proposal_score(ctx, cu(X)).cpu().numpy()
+    z_ref, _ = M.forward(w.astype(np.float64), X)
+    assert (np.abs(z - z_ref) <= 2.0 ** -6 * (1 + np.abs(z_ref))).all(), np.abs(z - z_ref).max()
+    # and BF16 rounding is visible: this is not an FP32 path
+    assert np.abs(z - z_ref).max() > 1e-6
+
+
+def test_score_without_weights_fails(kf):
+    c = kf.Context(0)
+    with pytest.raises(kf.KFError, match="no proposal"):
+        kf.proposal_score(c, cu(np.zeros((4, 12), np.float32)))
+    c.close()
