@@ -211,11 +211,44 @@ int kf_build_tracks(kf_context *ctx, const kf_geometry *geom, int n_events, cons
                     kf_stream stream);
 
 /*
+ * kf_build_tracks that also records the training set of the learned proposal
+ * (kf_proposal_*): one row for every (candidate, hit) pair whose hit lies in
+ * the candidate's window, in the order the GPU meets them.  The build itself
+ * is the plain one (opt->use_proposal must be 0) and its outputs are those of
+ * kf_build_tracks.  The paper has no counterpart: the rows are the labelled
+ * examples the plain build gives for free.
+ *
+ * log_features [log_capacity][12]: the pair's proposal inputs (see below).
+ * log_labels [log_capacity]: 1 if the pair became one of the surviving
+ *   candidates at that layer, else 0.
+ * log_ref [log_capacity][4] (int32): seed, candidate slot at the start of
+ *   the layer, build layer, hit index into hit_pos.
+ * log_count (device, one uint64): set to the number of pairs met, which may
+ *   exceed log_capacity; rows beyond the capacity are not written.
+ * All device memory owned by the caller.  Rows appear in no fixed order
+ * (atomic claims), so two calls give the same rows in different orders.
+ */
+int kf_build_tracks_logged(kf_context *ctx, const kf_geometry *geom, int n_events, const int64_t *hit_offsets,
+                           const float *hit_pos, const float *hit_cov, int64_t n_hits, int64_t n_seeds,
+                           const int32_t *seed_event, const float *seed_state, const float *seed_cov,
+                           const int8_t *seed_charge, int32_t *out_hit_idx, float *out_chi2, int16_t *out_nhits,
+                           float *out_state, float *out_cov, uint32_t *out_flags, const kf_options *opt,
+                           float *log_features, float *log_labels, int32_t *log_ref, int64_t log_capacity,
+                           uint64_t *log_count, kf_stream stream);
+
+/*
  * The learned hit proposal.  The paper has no learned component: this network
  * is the ranking the build step can use for a candidate's in-window hits
  * (kf_options.use_proposal), so that only the best top-k of them get the full
  * Kalman chi2.  It is a perceptron 12 -> 64 -> 64 -> 1 with ReLU activations
  * whose logit scores a (candidate, hit) pair.
+ *
+ * In kf_build_tracks with use_proposal = 1 (weights loaded by
+ * kf_proposal_load, else KF_ERR_ARG) a candidate whose window holds more
+ * than topk (1..8) hits scores all of them and computes the chi2 of only the
+ * topk best by logit (ties to the lower hit index within the layer); the chi2
+ * cut, ranking and update are unchanged.  A window of topk hits or fewer is
+ * searched exhaustively, as without the proposal.
  *
  * weights: KF_PROPOSAL_PARAMS float32 values, in this order: W1 [12][64]
  *   (input-major), b1 [64], W2 [64][64], b2 [64], W3 [64], b3.

@@ -23,6 +23,21 @@
  *
  * Hits of one (event, layer) are found through an index sorted by phi: the
  * in-window set is exactly that of a scan over all of the layer's hits.
+ *
+ * Not in the paper: the learned hit proposal.  Optionally the build logs, for
+ * every (candidate, hit) pair with the hit in the window, the proposal's 12
+ * inputs and a label (1 if the pair became a surviving child at that layer);
+ * and optionally a perceptron 12 -> 64 -> 64 -> 1 (ReLU) scores the in-window
+ * hits of a candidate whose window holds more than topk of them, and only the
+ * topk best by logit (ties to the lower hit index within the layer) are
+ * tested against the chi2 cut.  The inputs, in the layer's local frame
+ * (n = radial unit vector at the predicted crossing, t = z x n):
+ *   0..2  (n.d, t.d, d_z) / sqrt(S_nn, S_tt, S_zz), d = hit - prediction,
+ *         S = C_pos + V;
+ *   3..8  log10 of the predicted covariance diagonal (floor 1e-30);
+ *   9     q / pT of the prediction, signed by q B;
+ *   10    the layer's index among the build layers / their number;
+ *   11    the candidate's holes so far (layer index - hits).
  */
 #include <math.h>
 #include <stdint.h>
@@ -82,6 +97,7 @@ typedef struct {
     int64_t hit_global;
     double chi2;       /* candidate chi2 + increment */
     double dchi2;
+    int64_t row;       /* row of the training log, -1 if none */
 } child_t;
 
 /* (hits desc, chi2 asc, candidate asc, hit asc) */
@@ -152,6 +168,87 @@ static void insert_child(child_t *list, int *count, int n, const child_t *c)
     *count = k;
 }
 
+/* The proposal's inputs for hit h against the predicted candidate. */
+static void pair_features(const double *xp, const double *Cp, int q, double bz, int l, int L, int nhits,
+                          const float *hit_pos, const float *hit_cov, int64_t H, int64_t h, double *f)
+{
+    double V[9], vp[6], d[3];
+    for (int i = 0; i < 6; ++i) vp[i] = hit_cov[(int64_t)i * H + h];
+    orc_unpack_sym(vp, 3, V);
+    for (int i = 0; i < 3; ++i) d[i] = (double)hit_pos[(int64_t)i * H + h] - xp[i];
+    const double rc = hypot(xp[0], xp[1]);
+    const double n[2] = {xp[0] / rc, xp[1] / rc}, t[2] = {-xp[1] / rc, xp[0] / rc};
+    double snn = 0.0, stt = 0.0;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            const double sij = Cp[i * 6 + j] + V[i * 3 + j];
+            snn += n[i] * sij * n[j];
+            stt += t[i] * sij * t[j];
+        }
+    const double szz = Cp[2 * 6 + 2] + V[2 * 3 + 2];
+    f[0] = (n[0] * d[0] + n[1] * d[1]) / sqrt(snn > 1e-30 ? snn : 1e-30);
+    f[1] = (t[0] * d[0] + t[1] * d[1]) / sqrt(stt > 1e-30 ? stt : 1e-30);
+    f[2] = d[2] / sqrt(szz > 1e-30 ? szz : 1e-30);
+    for (int i = 0; i < 6; ++i) {
+        const double c = Cp[i * 6 + i];
+        f[3 + i] = log10(c > 1e-30 ? c : 1e-30);
+    }
+    const double pt = hypot(xp[3], xp[4]);
+    f[9] = ((double)q * bz < 0.0 ? -1.0 : 1.0) / pt;
+    f[10] = (double)l / (double)L;
+    f[11] = (double)(l - nhits);
+}
+
+/* v rounded to float32, then to bfloat16 (8-bit significand, round to
+ * nearest, ties to even), returned as a double. */
+double orc_bf16_round(double v)
+{
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+/* Logit of the perceptron; w = W1 [12][64], b1 [64], W2 [64][64], b2 [64],
+ * W3 [64], b3.  bf16 != 0 takes the top-k decision in the precision of the
+ * tensor-core scoring: inputs, W1, W2 and the first hidden layer rounded to
+ * bfloat16 (the biases, W3 and the sums stay wide). */
+double orc_mlp_logit(const double *w, const double *f, int bf16)
+{
+    const double *W1 = w, *b1 = W1 + 12 * 64, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64, *b3 = W3 + 64;
+    double h1[64], x[12], z = b3[0];
+    for (int i = 0; i < 12; ++i) x[i] = bf16 ? orc_bf16_round(f[i]) : f[i];
+    for (int j = 0; j < 64; ++j) {
+        double a = 0.0;
+        for (int i = 0; i < 12; ++i) a += x[i] * (bf16 ? orc_bf16_round(W1[i * 64 + j]) : W1[i * 64 + j]);
+        a += b1[j];
+        h1[j] = a > 0.0 ? a : 0.0;
+        if (bf16) h1[j] = orc_bf16_round(h1[j]);
+    }
+    for (int j = 0; j < 64; ++j) {
+        double a = 0.0;
+        for (int i = 0; i < 64; ++i) a += h1[i] * (bf16 ? orc_bf16_round(W2[i * 64 + j]) : W2[i * 64 + j]);
+        a += b2[j];
+        z += W3[j] * (a > 0.0 ? a : 0.0);
+    }
+    return z;
+}
+
+typedef struct {
+    int64_t h;
+    double z;
+} scored_t;
+
+/* (logit desc, hit index asc) */
+static int cmp_scored(const void *a, const void *b)
+{
+    const scored_t *x = a, *y = b;
+    if (x->z != y->z) return x->z > y->z ? -1 : 1;
+    return (x->h > y->h) - (x->h < y->h);
+}
+
 /*
  * Build seeds [s_begin, s_end).  Geometry: the build layers only.  Hits: all
  * layers of all events in hit_pos [3][H], hit_cov [6][H]; hit_offsets
@@ -160,18 +257,28 @@ static void insert_child(child_t *list, int *count, int n, const child_t *c)
  * Outputs (slot j of seed s = rank j after the last layer): out_hit
  * [S][N][L] global hit index or -1; out_chi2, out_nhits (-1 for an empty
  * slot) [S][N]; out_state [6][S*N]; out_cov [21][S*N] packed; out_ncand [S].
+ * orc_build_tracks_ex adds the training log (log_f [cap][12], log_y [cap],
+ * log_ref [cap][4] = seed, candidate, layer, hit; *log_n counts the pairs met,
+ * rows past log_cap are dropped; log_n NULL = no log) and the proposal (mlp
+ * the 5,057 weights, NULL = exhaustive search; topk >= 1; mlp_bf16 as in
+ * mlp_logit).
  */
-int orc_build_tracks(int n_layers, const double *radii, const double *x_over_x0, double z_half, double bz,
+int orc_build_tracks_ex(int n_layers, const double *radii, const double *x_over_x0, double z_half, double bz,
                      const int64_t *hit_offsets, const float *hit_pos, const float *hit_cov, int64_t H,
                      const double *phi, const int64_t *order, int64_t s_begin, int64_t s_end, int64_t n_seeds,
                      const int32_t *seed_event, const float *seed_state, const float *seed_cov,
                      const int8_t *seed_charge, int max_cands, double chi2_cut, double nsigma,
                      double sigma_rphi_hit, double sigma_z_hit, int32_t *out_hit, double *out_chi2,
-                     int32_t *out_nhits, double *out_state, double *out_cov, int32_t *out_ncand)
+                     int32_t *out_nhits, double *out_state, double *out_cov, int32_t *out_ncand, double *log_f,
+                     double *log_y, int32_t *log_ref, int64_t log_cap, int64_t *log_n, const double *mlp,
+                     int topk, int mlp_bf16)
 {
     const int N = max_cands, L = n_layers;
     const int64_t S = n_seeds;
-    if (N < 1 || N > MAXN || L < 1 || L > MAXL) return -1;
+    if (N < 1 || N > MAXN || L < 1 || L > MAXL || (mlp && topk < 1)) return -1;
+    int64_t win_cap = 256;
+    scored_t *win = malloc((size_t)win_cap * sizeof(scored_t));
+    if (!win) return -2;
     cand_t cand[MAXN], next[MAXN];
     child_t hits_of[MAXN][MAXN], all[MAXN * (MAXN + 1)];
     int nh[MAXN];
@@ -237,22 +344,64 @@ int orc_build_tracks(int n_layers, const double *radii, const double *x_over_x0,
                             ++nint;
                         }
                     }
+                    /* the in-window hits */
+                    int64_t n_in = 0;
                     for (int iv = 0; iv < nint; ++iv) {
                         for (int64_t p = lower_phi(phi, order, seg_lo, seg_hi, lo_[iv]);
                              p < seg_hi && phi[order[p]] <= hi_[iv]; ++p) {
                             const int64_t h = order[p];
                             if (!(fabs(wrap_phi(phi[h] - phic)) <= dphi)) continue;
                             if (!(fabs((double)hit_pos[2 * H + h] - zp) <= dz)) continue;
-                            double dc;
-                            if (!hit_chi2(k->xp, k->Cp, hit_pos, hit_cov, H, h, &dc)) continue;
-                            if (!(dc <= chi2_cut)) continue;
-                            child_t ch = {c, k->nhits + 1, h - seg_lo, h, k->chi2 + dc, dc};
-                            insert_child(hits_of[c], &nh[c], N, &ch);
+                            if (n_in == win_cap) {
+                                scored_t *w2 = realloc(win, (size_t)(2 * win_cap) * sizeof(scored_t));
+                                if (!w2) {
+                                    free(win);
+                                    return -2;
+                                }
+                                win = w2;
+                                win_cap *= 2;
+                            }
+                            win[n_in].h = h;
+                            win[n_in].z = 0.0;
+                            ++n_in;
                         }
+                    }
+                    int64_t n_test = n_in;
+                    if (mlp && n_in > topk) {
+                        for (int64_t i = 0; i < n_in; ++i) {
+                            double f[12];
+                            pair_features(k->xp, k->Cp, q, bz, l, L, k->nhits, hit_pos, hit_cov, H, win[i].h, f);
+                            win[i].z = orc_mlp_logit(mlp, f, mlp_bf16);
+                        }
+                        qsort(win, (size_t)n_in, sizeof(scored_t), cmp_scored);
+                        n_test = topk;
+                    }
+                    for (int64_t i = 0; i < n_test; ++i) {
+                        const int64_t h = win[i].h;
+                        int64_t row = -1;
+                        if (log_n) {
+                            row = (*log_n)++;
+                            if (row < log_cap) {
+                                pair_features(k->xp, k->Cp, q, bz, l, L, k->nhits, hit_pos, hit_cov, H, h,
+                                              log_f + row * 12);
+                                log_y[row] = 0.0;
+                                log_ref[row * 4 + 0] = (int32_t)s;
+                                log_ref[row * 4 + 1] = c;
+                                log_ref[row * 4 + 2] = l;
+                                log_ref[row * 4 + 3] = (int32_t)h;
+                            } else {
+                                row = -1;
+                            }
+                        }
+                        double dc;
+                        if (!hit_chi2(k->xp, k->Cp, hit_pos, hit_cov, H, h, &dc)) continue;
+                        if (!(dc <= chi2_cut)) continue;
+                        child_t ch = {c, k->nhits + 1, h - seg_lo, h, k->chi2 + dc, dc, row};
+                        insert_child(hits_of[c], &nh[c], N, &ch);
                     }
                 }
                 for (int i = 0; i < nh[c]; ++i) all[n_all++] = hits_of[c][i];
-                child_t hole = {c, k->nhits, -1, -1, k->chi2, 0.0};
+                child_t hole = {c, k->nhits, -1, -1, k->chi2, 0.0, -1};
                 all[n_all++] = hole;
             }
             qsort(all, (size_t)n_all, sizeof(child_t), cmp_child);
@@ -269,6 +418,7 @@ int orc_build_tracks(int n_layers, const double *radii, const double *x_over_x0,
                 }
                 if (ch->hit_local >= 0) {
                     double m[3], vp[6], d;
+                    if (ch->row >= 0) log_y[ch->row] = 1.0;
                     for (int i = 0; i < 3; ++i) m[i] = hit_pos[(int64_t)i * H + ch->hit_global];
                     for (int i = 0; i < 6; ++i) vp[i] = hit_cov[(int64_t)i * H + ch->hit_global];
                     orc_update(o->x, o->C, m, vp, &d);
@@ -294,5 +444,20 @@ int orc_build_tracks(int n_layers, const double *radii, const double *x_over_x0,
                     out_cov[(int64_t)(i * (i + 1) / 2 + jj) * S * N + sj] = j < nc ? cand[j].C[i * 6 + jj] : 0.0;
         }
     }
+    free(win);
     return 0;
+}
+
+int orc_build_tracks(int n_layers, const double *radii, const double *x_over_x0, double z_half, double bz,
+                     const int64_t *hit_offsets, const float *hit_pos, const float *hit_cov, int64_t H,
+                     const double *phi, const int64_t *order, int64_t s_begin, int64_t s_end, int64_t n_seeds,
+                     const int32_t *seed_event, const float *seed_state, const float *seed_cov,
+                     const int8_t *seed_charge, int max_cands, double chi2_cut, double nsigma,
+                     double sigma_rphi_hit, double sigma_z_hit, int32_t *out_hit, double *out_chi2,
+                     int32_t *out_nhits, double *out_state, double *out_cov, int32_t *out_ncand)
+{
+    return orc_build_tracks_ex(n_layers, radii, x_over_x0, z_half, bz, hit_offsets, hit_pos, hit_cov, H, phi, order,
+                               s_begin, s_end, n_seeds, seed_event, seed_state, seed_cov, seed_charge, max_cands,
+                               chi2_cut, nsigma, sigma_rphi_hit, sigma_z_hit, out_hit, out_chi2, out_nhits,
+                               out_state, out_cov, out_ncand, NULL, NULL, NULL, 0, NULL, NULL, 1, 0);
 }

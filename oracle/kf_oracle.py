@@ -73,6 +73,13 @@ def lib():
                  ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 4 +
                 [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double] +
                 [ctypes.c_void_p] * 6)
+            _lib.orc_build_tracks_ex.restype = ctypes.c_int
+            _lib.orc_build_tracks_ex.argtypes = _lib.orc_build_tracks.argtypes + \
+                [ctypes.c_void_p] * 3 + [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+            _lib.orc_bf16_round.restype = ctypes.c_double
+            _lib.orc_bf16_round.argtypes = [ctypes.c_double]
+            _lib.orc_mlp_logit.restype = ctypes.c_double
+            _lib.orc_mlp_logit.argtypes = [_dp, _dp, ctypes.c_int]
             for fn in (_lib.orc_fit_tracks, _lib.orc_fit_tracks_f64):
                 fn.restype = ctypes.c_int
                 fn.argtypes = ([ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double,
@@ -210,10 +217,19 @@ def fit_batch_exact(batch, threads=None, per_layer=False):
 
 def build_arrays(radii, x_over_x0, z_half, bz, hit_offsets, hit_pos, hit_cov, seed_event, seed_state,
                  seed_cov, seed_charge, max_cands=6, chi2_cut=30.0, nsigma=3.0, sigma_rphi=0.01,
-                 sigma_z=0.1, threads: int | None = None, seed_range=None):
+                 sigma_z=0.1, threads: int | None = None, seed_range=None, log=False, mlp=None, topk=4,
+                 mlp_bf16=False):
     """Clone-engine build with the FP64 oracle over the given layers.  Arrays
     in the library's layout (float32 hits [3][H] / [6][H], offsets
-    [E][L+1], seeds [6][S] / [21][S]).  Returns a dict of results."""
+    [E][L+1], seeds [6][S] / [21][S]).  Returns a dict of results.
+
+    log=True adds the training log of the plain build: out["log"] = dict of
+    features [n][12], labels [n], ref [n][4] (seed, candidate, layer, hit),
+    rows in seed order.  mlp (5,057 float64 weights) turns on the learned
+    proposal with the given topk; mlp_bf16 ranks with BF16 inputs, W1, W2 and
+    first hidden layer (the tensor-core scoring's precision)."""
+    if log and mlp is not None:
+        raise ValueError("the training log records the plain build")
     L = int(len(radii))
     hp = np.ascontiguousarray(hit_pos, dtype=np.float32)
     hc = np.ascontiguousarray(hit_cov, dtype=np.float32)
@@ -239,23 +255,59 @@ def build_arrays(radii, x_over_x0, z_half, bz, hit_offsets, hit_pos, hit_cov, se
     chunk = max(1, -(-(s1 - s0) // (threads * 4)))
     ranges = [(a, min(a + chunk, s1)) for a in range(s0, s1, chunk)]
 
+    w = None if mlp is None else np.ascontiguousarray(mlp, dtype=np.float64)
+    if w is not None and w.shape != (5057,):
+        raise ValueError("mlp must hold 5,057 weights")
+
+    def call(rg, lg):
+        n = np.zeros(1, dtype=np.int64)
+        cap = 0 if lg is None else len(lg["labels"])
+        rc = lib().orc_build_tracks_ex(
+            L, _p(rad), _p(xx0), float(z_half), float(bz), off.ctypes.data, hp.ctypes.data, hc.ctypes.data, H,
+            phi.ctypes.data, order.ctypes.data, rg[0], rg[1], S, se.ctypes.data, ss.ctypes.data, sc.ctypes.data,
+            sq.ctypes.data, N, float(chi2_cut), float(nsigma), float(sigma_rphi), float(sigma_z),
+            out["hit"].ctypes.data, out["chi2"].ctypes.data, out["nhits"].ctypes.data, out["state"].ctypes.data,
+            out["cov"].ctypes.data, out["ncand"].ctypes.data,
+            None if lg is None else lg["features"].ctypes.data, None if lg is None else lg["labels"].ctypes.data,
+            None if lg is None else lg["ref"].ctypes.data, cap, n.ctypes.data if log else None,
+            None if w is None else w.ctypes.data, int(topk), int(bool(mlp_bf16)))
+        assert rc == 0, rc
+        return int(n[0])
+
     def run(rg):
-        rc = lib().orc_build_tracks(L, _p(rad), _p(xx0), float(z_half), float(bz), off.ctypes.data,
-                                    hp.ctypes.data, hc.ctypes.data, H, phi.ctypes.data, order.ctypes.data,
-                                    rg[0], rg[1], S, se.ctypes.data, ss.ctypes.data, sc.ctypes.data,
-                                    sq.ctypes.data, N, float(chi2_cut), float(nsigma), float(sigma_rphi),
-                                    float(sigma_z), out["hit"].ctypes.data, out["chi2"].ctypes.data,
-                                    out["nhits"].ctypes.data, out["state"].ctypes.data,
-                                    out["cov"].ctypes.data, out["ncand"].ctypes.data)
-        assert rc == 0
+        if not log:
+            call(rg, None)
+            return None
+        n = call(rg, None)  # count the rows, then fill them
+        lg = dict(features=np.zeros((n, 12)), labels=np.zeros(n), ref=np.zeros((n, 4), dtype=np.int32))
+        assert call(rg, lg) == n
+        return lg
 
     if len(ranges) <= 1:
-        for rg in ranges:
-            run(rg)
+        logs = [run(rg) for rg in ranges]
     else:
         with cf.ThreadPoolExecutor(threads) as ex:
-            list(ex.map(run, ranges))
+            logs = list(ex.map(run, ranges))
+    if log:
+        logs = [lg for lg in logs if lg is not None]
+        out["log"] = {k: (np.concatenate([lg[k] for lg in logs]) if logs else
+                          np.zeros((0,) + ((12,) if k == "features" else (4,) if k == "ref" else ()),
+                                   dtype=np.int32 if k == "ref" else np.float64))
+                      for k in ("features", "labels", "ref")}
     return out
+
+
+def bf16_round(v: float) -> float:
+    """v rounded to float32, then to bfloat16 (nearest, ties to even)."""
+    return lib().orc_bf16_round(float(v))
+
+
+def mlp_logit(weights, features, bf16=False) -> float:
+    """The build oracle's scoring of one (candidate, hit) pair."""
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    f = np.ascontiguousarray(features, dtype=np.float64)
+    assert w.shape == (5057,) and f.shape == (12,)
+    return lib().orc_mlp_logit(_p(w), _p(f), int(bool(bf16)))
 
 
 def _segment_bounds(off, L):

@@ -1,6 +1,7 @@
 // Internal helpers shared by the C-ABI translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "kf.h"
@@ -12,6 +13,9 @@ struct BuildState;  // device scratch of the build step (kf_build.cu)
 void destroy_build_state(BuildState *s);
 struct MlpState;  // proposal network scratch and weights (kf_mlp.cu)
 void destroy_mlp_state(MlpState *s);
+bool proposal_loaded(kf_context *ctx);
+// device copies of the loaded weights (the layouts of kf_mlp.cuh)
+void proposal_weights(kf_context *ctx, const __nv_bfloat16 **W1, const __nv_bfloat16 **W2, const float **w32);
 
 int set_error(kf_context *ctx, int code, const char *fmt, ...);
 int cuda_error(kf_context *ctx, cudaError_t e, const char *what);

@@ -19,6 +19,7 @@
 #include "kf.h"
 #include "kf_api_internal.h"
 #include "kf_fit.cuh"
+#include "kf_mlp.cuh"
 
 namespace kf {
 
@@ -148,6 +149,15 @@ struct BuildParams {
     int16_t *out_nhits;
     float *out_state, *out_cov;
     uint32_t *out_flags;
+    // training log of the plain build (null when off)
+    float *log_f, *log_y;
+    int32_t *log_ref;
+    unsigned long long *log_n;
+    unsigned long long log_cap;
+    // learned proposal
+    int topk;
+    const __nv_bfloat16 *mlp_W1, *mlp_W2;
+    const float *mlp_w32;
 };
 
 constexpr int kMaxN = 8;
@@ -162,8 +172,10 @@ __device__ __forceinline__ float wrap_pi(float d)
 // Chi2 increment of a hit (m, packed V) against the predicted candidate, in
 // the layer's local frame (n, t, z) with the radial row of C projected out
 // (the same arithmetic as the update): ctt = C_tt, ctz = C_tz, czz = C_zz.
-__device__ __forceinline__ bool hit_chi2(const float x[3], float nx, float ny, float ctt, float ctz, float czz,
-                                         const float m[3], const float v[6], float *out)
+// f3 receives the residual in that frame divided by the square roots of S's
+// diagonal (the proposal's first three inputs).
+__device__ __forceinline__ bool hit_eval(const float x[3], float nx, float ny, float ctt, float ctz, float czz,
+                                         const float m[3], const float v[6], float *out, float f3[3])
 {
     const float vnn = fmaf(nx * nx, v[0], fmaf(2.0f * nx * ny, v[1], ny * ny * v[2]));
     const float vnt = fmaf(nx * ny, v[2] - v[0], (nx * nx - ny * ny) * v[1]);
@@ -173,15 +185,58 @@ __device__ __forceinline__ bool hit_chi2(const float x[3], float nx, float ny, f
     const float i00 = cc * f - e * e, i10 = d * e - b * f, i11 = a * f - d * d;
     const float i20 = b * e - cc * d, i21 = b * d - a * e, i22 = a * cc - b * b;
     const float det = fmaf(a, i00, fmaf(b, i10, d * i20));
-    if (!(a > 0.0f && i22 > 0.0f && det > 0.0f)) return false;
     const float d0 = m[0] - x[0], d1 = m[1] - x[1];
     const float rn = fmaf(nx, d0, ny * d1), rt = fmaf(nx, d1, -ny * d0), rz = m[2] - x[2];
+    f3[0] = rn * rsqrtf(fmaxf(a, 1e-30f));
+    f3[1] = rt * rsqrtf(fmaxf(cc, 1e-30f));
+    f3[2] = rz * rsqrtf(fmaxf(f, 1e-30f));
+    if (!(a > 0.0f && i22 > 0.0f && det > 0.0f)) return false;
     const float q0 = fmaf(i00, rn, fmaf(i10, rt, i20 * rz));
     const float q1 = fmaf(i10, rn, fmaf(i11, rt, i21 * rz));
     const float q2 = fmaf(i20, rn, fmaf(i21, rt, i22 * rz));
     *out = __fdividef(fmaf(rn, q0, fmaf(rt, q1, rz * q2)), det);
     return true;
 }
+
+// The window of a candidate at the predicted crossing and the bins it overlaps.
+struct Window {
+    float phic, dphi, z, dz;
+    int iz0, iz1, ip0, nphi;
+    const int32_t *bo;
+    int64_t seg_lo;
+};
+
+// Resumable walk over the in-window hits of a candidate: next() returns the
+// next hit's index within its (event, layer), or kNoKey at the end.
+struct WindowCursor {
+    int iz, k, hb, h1;
+    __device__ __forceinline__ void start(const Window &w)
+    {
+        iz = w.iz0;
+        k = -1;
+        hb = h1 = 0;
+    }
+    __device__ __forceinline__ uint32_t next(const BuildParams &p, const Window &w)
+    {
+        for (;;) {
+            while (hb < h1) {
+                const int64_t q = w.seg_lo + hb++;
+                if (fabsf(wrap_pi(p.bphi[q] - w.phic)) <= w.dphi && fabsf(p.bz[q] - w.z) <= w.dz)
+                    return (uint32_t)p.bidx[q];
+            }
+            if (iz > w.iz1) return kNoKey;
+            if (++k >= w.nphi) {
+                k = 0;
+                if (++iz > w.iz1) return kNoKey;
+            }
+            int ip = w.ip0 + k;
+            ip = ip < 0 ? ip + p.bg.n_phi : (ip >= p.bg.n_phi ? ip - p.bg.n_phi : ip);
+            const int b = iz * p.bg.n_phi + ip;
+            hb = w.bo[b];
+            h1 = w.bo[b + 1];
+        }
+    }
+};
 
 // Order of children: (hits desc, chi2 asc, candidate asc, hit index asc) as
 // a two-word key compared lexicographically: k64 = (63 - hits) << 32 | the
@@ -192,14 +247,28 @@ __device__ __forceinline__ bool key_less(unsigned long long a64, uint32_t a32, u
     return a64 < b64 || (a64 == b64 && a32 < b32);
 }
 
-template <int G>
+// Shared memory: back-pointers [L][128], update slots [kSlotSize][128], then
+// (proposal only) the network's weights and one staging area per warp.
+__host__ __device__ constexpr size_t build_smem_base(int L) { return ((size_t)(L + kSlotSize) * 128 * 4 + 127) / 128 * 128; }
+constexpr size_t kBuildSmemMlp = sizeof(MlpSmemWeights) + 4 * sizeof(MlpWarpStage);
+
+template <int G, bool PROPOSAL>
 __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
 {
     constexpr int SEEDS_PER_WARP = 32 / G;
-    extern __shared__ int32_t smem[];
+    extern __shared__ __align__(128) int32_t smem[];
     const int L = p.g.L;
     int32_t *bp = smem;                                   // [L][128] back-pointers
     float *slots = reinterpret_cast<float *>(smem + L * 128);  // [kSlotSize][128]
+    MlpSmemWeights *mw = nullptr;
+    MlpWarpStage *mst = nullptr;
+    if (PROPOSAL) {
+        unsigned char *base = reinterpret_cast<unsigned char *>(smem) + build_smem_base(L);
+        mw = reinterpret_cast<MlpSmemWeights *>(base);
+        mst = reinterpret_cast<MlpWarpStage *>(base + sizeof(MlpSmemWeights)) + (threadIdx.x >> 5);
+        mlp_load_weights(mw, p.mlp_W1, p.mlp_W2, p.mlp_w32);
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int slot = lane % G, gbase = lane - slot;
     const int64_t s = ((int64_t)blockIdx.x * 4 + warp) * SEEDS_PER_WARP + lane / G;
@@ -250,73 +319,177 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
                 reached = true;
             }
         }
-        // this candidate's best compatible hits, sorted by (chi2, hit index)
+        // this candidate's best compatible hits, sorted by (chi2, hit index);
+        // lr = each entry's row in the training log (logging only)
         float lc[kMaxN];
-        uint32_t lh[kMaxN];
+        uint32_t lh[kMaxN], lr[kMaxN];
 #pragma unroll
         for (int k = 0; k < kMaxN; ++k) {
             lc[k] = INFINITY;
             lh[k] = kNoKey;
+            lr[k] = kNoKey;
         }
+        auto insert = [&](float dc, uint32_t hl, uint32_t row) {
+            if (!(dc < lc[kMaxN - 1] || (dc == lc[kMaxN - 1] && hl < lh[kMaxN - 1]))) return;
+            float cv = dc;
+            uint32_t hv = hl, rv = row;
+#pragma unroll
+            for (int k2 = 0; k2 < kMaxN; ++k2) {
+                const bool before = cv < lc[k2] || (cv == lc[k2] && hv < lh[k2]);
+                const float tc = lc[k2];
+                const uint32_t th = lh[k2], tr = lr[k2];
+                lc[k2] = before ? cv : tc;
+                lh[k2] = before ? hv : th;
+                lr[k2] = before ? rv : tr;
+                cv = before ? tc : cv;
+                hv = before ? th : hv;
+                rv = before ? tr : rv;
+            }
+        };
         const int64_t seg = (int64_t)ev * (L + 1) + l;
         const int64_t seg_lo = seed_ok ? p.ev_off[seg] : 0;
+        Window win{};
+        float nx = 0.0f, ny = 0.0f, ctt = 0.0f, ctz = 0.0f, czz = 0.0f;
         if (reached) {
             const float ir = rsqrtf(x[0] * x[0] + x[1] * x[1]);
-            const float nx = x[0] * ir, ny = x[1] * ir;
-            const float ctt = fmaf(ny * ny, c[pk(0, 0)], fmaf(-2.0f * nx * ny, c[pk(1, 0)], nx * nx * c[pk(1, 1)]));
-            const float ctz = fmaf(nx, c[pk(2, 1)], -ny * c[pk(2, 0)]);
-            const float czz = c[pk(2, 2)];
-            const float dphi = p.nsigma * sqrtf(ctt + p.sig_rphi2) * p.g.inv_r[l];
-            const float dz = p.nsigma * sqrtf(czz + p.sig_z2);
-            const float phic = atan2f(x[1], x[0]);
-            const int32_t *bo = p.bin_off + (((int64_t)ev * L + l) * (nbins + 1));
+            nx = x[0] * ir;
+            ny = x[1] * ir;
+            ctt = fmaf(ny * ny, c[pk(0, 0)], fmaf(-2.0f * nx * ny, c[pk(1, 0)], nx * nx * c[pk(1, 1)]));
+            ctz = fmaf(nx, c[pk(2, 1)], -ny * c[pk(2, 0)]);
+            czz = c[pk(2, 2)];
+            win.dphi = p.nsigma * sqrtf(ctt + p.sig_rphi2) * p.g.inv_r[l];
+            win.dz = p.nsigma * sqrtf(czz + p.sig_z2);
+            win.phic = atan2f(x[1], x[0]);
+            win.z = x[2];
+            win.bo = p.bin_off + (((int64_t)ev * L + l) * (nbins + 1));
+            win.seg_lo = seg_lo;
             // bin ranges widened by a rounding margin: a hit that passes the
-            // exact window test below always lies in a scanned bin
+            // exact window test always lies in a scanned bin
             const float zm = 1e-4f * (1.0f + fabsf(x[2])), pm = 1e-5f;
-            const int iz0 = z_bin(x[2] - dz - zm, p.bg), iz1 = z_bin(x[2] + dz + zm, p.bg);
+            win.iz0 = z_bin(x[2] - win.dz - zm, p.bg);
+            win.iz1 = z_bin(x[2] + win.dz + zm, p.bg);
             int ip0, ip1;
-            if (dphi >= kPi - pm) {
+            if (win.dphi >= kPi - pm) {
                 ip0 = 0;
                 ip1 = p.bg.n_phi - 1;
             } else {
-                ip0 = (int)floorf((phic - dphi - pm + kPi) * (float)p.bg.n_phi * (1.0f / (2.0f * kPi)));
-                ip1 = (int)floorf((phic + dphi + pm + kPi) * (float)p.bg.n_phi * (1.0f / (2.0f * kPi)));
+                ip0 = (int)floorf((win.phic - win.dphi - pm + kPi) * (float)p.bg.n_phi * (1.0f / (2.0f * kPi)));
+                ip1 = (int)floorf((win.phic + win.dphi + pm + kPi) * (float)p.bg.n_phi * (1.0f / (2.0f * kPi)));
             }
-            const int nphi = min(ip1 - ip0 + 1, p.bg.n_phi);
-            for (int iz = iz0; iz <= iz1; ++iz) {
-                for (int k = 0; k < nphi; ++k) {
-                    int ip = ip0 + k;
-                    ip = ip < 0 ? ip + p.bg.n_phi : (ip >= p.bg.n_phi ? ip - p.bg.n_phi : ip);
-                    const int b = iz * p.bg.n_phi + ip;
-                    const int h0 = bo[b], h1 = bo[b + 1];
-                    for (int hb = h0; hb < h1; ++hb) {
-                        const int64_t q = seg_lo + hb;
-                        const float hphi = p.bphi[q], hz = p.bz[q];
-                        if (!(fabsf(wrap_pi(hphi - phic)) <= dphi) || !(fabsf(hz - x[2]) <= dz)) continue;
-                        const uint32_t hl = (uint32_t)p.bidx[q];
-                        const int64_t hg = seg_lo + hl;
+            win.ip0 = ip0;
+            win.nphi = min(ip1 - ip0 + 1, p.bg.n_phi);
+        }
+        auto load_hit = [&](uint32_t hl, float m[3], float v[6]) {
+            const int64_t hg = seg_lo + hl;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) m[i] = p.hit_pos[i * p.H + hg];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) v[i] = p.hit_cov[i * p.H + hg];
+        };
+        // inputs of the proposal shared by every hit of this candidate
+        auto cand_features = [&](float f[kMlpIn]) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) f[3 + i] = log10f(fmaxf(c[pk(i, i)], 1e-30f));
+            f[9] = copysignf(rsqrtf(x[3] * x[3] + x[4] * x[4]), qkb);
+            f[10] = (float)l / (float)L;
+            f[11] = (float)(l - nhits);
+        };
+        if (PROPOSAL) {
+            // first pass: up to topk in-window hits kept; one more marks the
+            // window as one the network ranks
+            uint32_t hb[kMaxN];
+#pragma unroll
+            for (int k = 0; k < kMaxN; ++k) hb[k] = kNoKey;
+            int n_in = 0;
+            WindowCursor cur;
+            if (reached) {
+                cur.start(win);
+                for (uint32_t hl = cur.next(p, win); hl != kNoKey; hl = cur.next(p, win)) {
+                    if (n_in == p.topk) {
+                        ++n_in;
+                        break;
+                    }
+#pragma unroll
+                    for (int k = 0; k < kMaxN; ++k)
+                        if (k == n_in) hb[k] = hl;
+                    ++n_in;
+                }
+            }
+            const bool use = n_in > p.topk;
+            if (__any_sync(0xffffffffu, use)) {
+                // the topk best in-window hits by logit (logit desc, hit index
+                // asc); one hit per ranking lane per round, scored by the warp
+                float tz[kMaxN];
+#pragma unroll
+                for (int k = 0; k < kMaxN; ++k) tz[k] = -INFINITY;
+                if (use) {
+#pragma unroll
+                    for (int k = 0; k < kMaxN; ++k) hb[k] = kNoKey;
+                    cur.start(win);
+                }
+                bool more = use;
+                while (__any_sync(0xffffffffu, more)) {
+                    const uint32_t hr = more ? cur.next(p, win) : kNoKey;
+                    more = hr != kNoKey;
+                    float feat[kMlpIn];
+#pragma unroll
+                    for (int i = 0; i < kMlpIn; ++i) feat[i] = 0.0f;
+                    if (more) {
                         float m[3], v[6], dc;
-#pragma unroll
-                        for (int i = 0; i < 3; ++i) m[i] = p.hit_pos[i * p.H + hg];
-#pragma unroll
-                        for (int i = 0; i < 6; ++i) v[i] = p.hit_cov[i * p.H + hg];
-                        if (!hit_chi2(x, nx, ny, ctt, ctz, czz, m, v, &dc) || !(dc <= p.chi2_cut)) continue;
-                        // insert (dc, hl) into the sorted list of N entries
-                        if (!(dc < lc[kMaxN - 1] || (dc == lc[kMaxN - 1] && hl < lh[kMaxN - 1]))) continue;
-                        float cv = dc;
-                        uint32_t hv = hl;
+                        load_hit(hr, m, v);
+                        hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, feat);
+                        cand_features(feat);
+                    }
+                    mlp_stage_row(mst, feat);
+                    const float z = mlp_score_warp(mw, mst);
+                    if (more) {
+                        float cv = z;
+                        uint32_t hv = hr;
 #pragma unroll
                         for (int k2 = 0; k2 < kMaxN; ++k2) {
-                            const bool before = cv < lc[k2] || (cv == lc[k2] && hv < lh[k2]);
-                            const float tc = lc[k2];
-                            const uint32_t th = lh[k2];
-                            lc[k2] = before ? cv : tc;
-                            lh[k2] = before ? hv : th;
-                            cv = before ? tc : cv;
-                            hv = before ? th : hv;
+                            const bool before = k2 < p.topk && (cv > tz[k2] || (cv == tz[k2] && hv < hb[k2]));
+                            const float t1 = tz[k2];
+                            const uint32_t t2 = hb[k2];
+                            tz[k2] = before ? cv : t1;
+                            hb[k2] = before ? hv : t2;
+                            cv = before ? t1 : cv;
+                            hv = before ? t2 : hv;
                         }
                     }
                 }
+            }
+            // the full chi2 for the kept hits only
+#pragma unroll
+            for (int k2 = 0; k2 < kMaxN; ++k2) {
+                if (hb[k2] == kNoKey) continue;
+                float m[3], v[6], dc, f3[3];
+                load_hit(hb[k2], m, v);
+                if (hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, f3) && dc <= p.chi2_cut) insert(dc, hb[k2], kNoKey);
+            }
+        } else if (reached) {
+            WindowCursor cur;
+            cur.start(win);
+            for (uint32_t hl = cur.next(p, win); hl != kNoKey; hl = cur.next(p, win)) {
+                float m[3], v[6], dc, feat[kMlpIn];
+                load_hit(hl, m, v);
+                const bool ok = hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, feat);
+                uint32_t row = kNoKey;
+                if (p.log_n) {  // training log: features now, label 1 if the pair survives
+                    const unsigned long long r = atomicAdd(p.log_n, 1ull);
+                    if (r < p.log_cap) {
+                        cand_features(feat);
+                        row = (uint32_t)r;
+#pragma unroll
+                        for (int i = 0; i < kMlpIn; ++i) p.log_f[(int64_t)r * kMlpIn + i] = feat[i];
+                        p.log_y[r] = 0.0f;
+                        int32_t *ref = p.log_ref + (int64_t)r * 4;
+                        ref[0] = (int32_t)s;
+                        ref[1] = slot;
+                        ref[2] = l;
+                        ref[3] = (int32_t)(seg_lo + hl);
+                    }
+                }
+                if (ok && dc <= p.chi2_cut) insert(dc, hl, row);
             }
         }
         // merge the group's lists: N rounds of a group arg-min; the head of a
@@ -354,22 +527,25 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
                 }
             }
             if (b32 == kNoKey) break;
-            const int win = (int)(b32 >> 27);
+            const int win_slot = (int)(b32 >> 27);
             if (slot == r) {
-                new_parent = win;
+                new_parent = win_slot;
                 new_hit = b32 & 0x7ffffffu;
                 new_nhits = 63 - (int)(b64 >> 32);
                 new_chi2 = __uint_as_float((uint32_t)(b64 & 0xffffffffu));
             }
-            if (slot == win) {
+            if (slot == win_slot) {
                 if ((b32 & 0x7ffffffu) != 0u) {  // pop the head of the list
+                    if (lr[0] != kNoKey) p.log_y[lr[0]] = 1.0f;  // the pair survives
 #pragma unroll
                     for (int k = 0; k < kMaxN - 1; ++k) {
                         lc[k] = lc[k + 1];
                         lh[k] = lh[k + 1];
+                        lr[k] = lr[k + 1];
                     }
                     lc[kMaxN - 1] = INFINITY;
                     lh[kMaxN - 1] = kNoKey;
+                    lr[kMaxN - 1] = kNoKey;
                     ++taken;
                 } else {
                     hole_taken = true;
@@ -443,12 +619,20 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
 
 using namespace kf;
 
-extern "C" int kf_build_tracks(kf_context *ctx, const kf_geometry *geom, int n_events, const int64_t *hit_offsets,
-                               const float *hit_pos, const float *hit_cov, int64_t n_hits, int64_t n_seeds,
-                               const int32_t *seed_event, const float *seed_state, const float *seed_cov,
-                               const int8_t *seed_charge, int32_t *out_hit_idx, float *out_chi2, int16_t *out_nhits,
-                               float *out_state, float *out_cov, uint32_t *out_flags, const kf_options *opt,
-                               kf_stream stream_)
+namespace {
+
+struct BuildLog {
+    float *features, *labels;
+    int32_t *ref;
+    int64_t capacity;
+    uint64_t *count;
+};
+
+int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int64_t *hit_offsets,
+               const float *hit_pos, const float *hit_cov, int64_t n_hits, int64_t n_seeds, const int32_t *seed_event,
+               const float *seed_state, const float *seed_cov, const int8_t *seed_charge, int32_t *out_hit_idx,
+               float *out_chi2, int16_t *out_nhits, float *out_state, float *out_cov, uint32_t *out_flags,
+               const kf_options *opt, kf_stream stream_, const BuildLog *log)
 {
     if (!ctx) return KF_ERR_ARG;
     kf_options o;
@@ -463,10 +647,31 @@ extern "C" int kf_build_tracks(kf_context *ctx, const kf_geometry *geom, int n_e
         return set_error(ctx, KF_ERR_ARG, "chi2_cut and window_nsigma must be positive, hit sigmas non-negative");
     if (o.n_phi_bins < 1 || o.n_z_bins < 1 || (int64_t)o.n_phi_bins * o.n_z_bins > 16384)
         return set_error(ctx, KF_ERR_ARG, "n_phi_bins x n_z_bins must be 1..16384");
-    if (o.use_proposal) return set_error(ctx, KF_ERR_UNSUPPORTED, "the learned proposal needs kf_load_proposal first");
+    const __nv_bfloat16 *W1 = nullptr, *W2 = nullptr;
+    const float *w32 = nullptr;
+    if (o.use_proposal) {
+        if (log) return set_error(ctx, KF_ERR_ARG, "the training log records the plain build: use_proposal must be 0");
+        if (o.topk < 1 || o.topk > kMaxN) return set_error(ctx, KF_ERR_ARG, "topk must be 1..8");
+        if (!proposal_loaded(ctx)) return set_error(ctx, KF_ERR_ARG, "use_proposal needs weights (kf_proposal_load)");
+        proposal_weights(ctx, &W1, &W2, &w32);
+    }
+    if (log) {
+        if (log->capacity < 0) return set_error(ctx, KF_ERR_ARG, "log capacity must be >= 0");
+        if ((rc = check_ptr(ctx, log->count, 8, "log_count"))) return rc;
+        if (log->capacity > 0 && ((rc = check_ptr(ctx, log->features, 4, "log_features")) ||
+                                  (rc = check_ptr(ctx, log->labels, 4, "log_labels")) ||
+                                  (rc = check_ptr(ctx, log->ref, 4, "log_ref"))))
+            return rc;
+    }
     if (n_events < 0 || n_seeds < 0 || n_hits < 0 || n_hits >= (int64_t(1) << 31))
         return set_error(ctx, KF_ERR_ARG, "n_events, n_seeds must be >= 0 and n_hits < 2^31");
-    if (n_seeds == 0) return KF_OK;
+    if (n_seeds == 0) {
+        if (log) {
+            const cudaError_t e0 = cudaMemsetAsync(log->count, 0, sizeof(uint64_t), reinterpret_cast<cudaStream_t>(stream_));
+            if (e0 != cudaSuccess) return cuda_error(ctx, e0, "log counter");
+        }
+        return KF_OK;
+    }
     if (n_events < 1 || !hit_offsets) return set_error(ctx, KF_ERR_ARG, "hit_offsets (host) needs n_events >= 1 rows");
     const int L = g.L;
     for (int e = 0; e < n_events; ++e) {
@@ -578,16 +783,72 @@ extern "C" int kf_build_tracks(kf_context *ctx, const kf_geometry *geom, int n_e
     p.out_state = out_state;
     p.out_cov = out_cov;
     p.out_flags = out_flags;
+    p.log_f = log ? log->features : nullptr;
+    p.log_y = log ? log->labels : nullptr;
+    p.log_ref = log ? log->ref : nullptr;
+    p.log_n = log ? reinterpret_cast<unsigned long long *>(log->count) : nullptr;
+    p.log_cap = log ? (unsigned long long)log->capacity : 0ull;
+    p.topk = o.topk;
+    p.mlp_W1 = W1;
+    p.mlp_W2 = W2;
+    p.mlp_w32 = w32;
+    if (log && (e = cudaMemsetAsync(log->count, 0, sizeof(uint64_t), stream)) != cudaSuccess)
+        return cuda_error(ctx, e, "log counter");
     const int G = p.N == 1 ? 1 : p.N <= 2 ? 2 : p.N <= 4 ? 4 : 8;
     const int64_t seeds_per_block = 4 * (32 / G);
     const unsigned grid = (unsigned)((n_seeds + seeds_per_block - 1) / seeds_per_block);
-    const size_t smem = (size_t)L * 128 * sizeof(int32_t) + (size_t)kSlotSize * 128 * sizeof(float);
-    switch (G) {
-    case 1: build_kernel<1><<<grid, 128, smem, stream>>>(p); break;
-    case 2: build_kernel<2><<<grid, 128, smem, stream>>>(p); break;
-    case 4: build_kernel<4><<<grid, 128, smem, stream>>>(p); break;
-    default: build_kernel<8><<<grid, 128, smem, stream>>>(p); break;
+    const bool prop = o.use_proposal != 0;
+    const size_t smem = prop ? build_smem_base(L) + kBuildSmemMlp
+                             : (size_t)L * 128 * sizeof(int32_t) + (size_t)kSlotSize * 128 * sizeof(float);
+    static bool attr_prop = false;
+    if (prop && !attr_prop) {
+        const int mx = (int)(build_smem_base(KF_MAX_LAYERS) + kBuildSmemMlp);
+        cudaFuncSetAttribute(build_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(build_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(build_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(build_kernel<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        attr_prop = true;
+    }
+    switch (G * 2 + (prop ? 1 : 0)) {
+    case 2: build_kernel<1, false><<<grid, 128, smem, stream>>>(p); break;
+    case 3: build_kernel<1, true><<<grid, 128, smem, stream>>>(p); break;
+    case 4: build_kernel<2, false><<<grid, 128, smem, stream>>>(p); break;
+    case 5: build_kernel<2, true><<<grid, 128, smem, stream>>>(p); break;
+    case 8: build_kernel<4, false><<<grid, 128, smem, stream>>>(p); break;
+    case 9: build_kernel<4, true><<<grid, 128, smem, stream>>>(p); break;
+    case 16: build_kernel<8, false><<<grid, 128, smem, stream>>>(p); break;
+    default: build_kernel<8, true><<<grid, 128, smem, stream>>>(p); break;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(ctx, e, "build launch");
     return KF_OK;
+}
+
+}  // namespace
+
+extern "C" int kf_build_tracks(kf_context *ctx, const kf_geometry *geom, int n_events, const int64_t *hit_offsets,
+                               const float *hit_pos, const float *hit_cov, int64_t n_hits, int64_t n_seeds,
+                               const int32_t *seed_event, const float *seed_state, const float *seed_cov,
+                               const int8_t *seed_charge, int32_t *out_hit_idx, float *out_chi2, int16_t *out_nhits,
+                               float *out_state, float *out_cov, uint32_t *out_flags, const kf_options *opt,
+                               kf_stream stream)
+{
+    return build_impl(ctx, geom, n_events, hit_offsets, hit_pos, hit_cov, n_hits, n_seeds, seed_event, seed_state,
+                      seed_cov, seed_charge, out_hit_idx, out_chi2, out_nhits, out_state, out_cov, out_flags, opt,
+                      stream, nullptr);
+}
+
+extern "C" int kf_build_tracks_logged(kf_context *ctx, const kf_geometry *geom, int n_events,
+                                      const int64_t *hit_offsets, const float *hit_pos, const float *hit_cov,
+                                      int64_t n_hits, int64_t n_seeds, const int32_t *seed_event,
+                                      const float *seed_state, const float *seed_cov, const int8_t *seed_charge,
+                                      int32_t *out_hit_idx, float *out_chi2, int16_t *out_nhits, float *out_state,
+                                      float *out_cov, uint32_t *out_flags, const kf_options *opt, float *log_features,
+                                      float *log_labels, int32_t *log_ref, int64_t log_capacity, uint64_t *log_count,
+                                      kf_stream stream)
+{
+    if (!ctx) return KF_ERR_ARG;
+    const BuildLog log{log_features, log_labels, log_ref, log_capacity, log_count};
+    return build_impl(ctx, geom, n_events, hit_offsets, hit_pos, hit_cov, n_hits, n_seeds, seed_event, seed_state,
+                      seed_cov, seed_charge, out_hit_idx, out_chi2, out_nhits, out_state, out_cov, out_flags, opt,
+                      stream, &log);
 }

@@ -22,7 +22,7 @@ struct MlpState {
     float *grad = nullptr, *m = nullptr, *v = nullptr;  // [kMlpParams] each
     float *loss = nullptr;                              // one accumulator
     float *w32 = nullptr;                               // loaded weights, FP32
-    __nv_bfloat16 *W1 = nullptr, *W2 = nullptr;         // loaded weights, BF16 [16][64], [64][64]
+    __nv_bfloat16 *W1 = nullptr, *W2 = nullptr;         // loaded weights, BF16, transposed and padded
     bool loaded = false;
 };
 
@@ -189,12 +189,17 @@ __global__ void adam_kernel(float *w, float *grad, float *m, float *v, int t, fl
     grad[i] = 0.0f;
 }
 
-__global__ void to_bf16_kernel(const float *w, __nv_bfloat16 *W1, __nv_bfloat16 *W2)
+// FP32 master weights -> the transposed, padded BF16 copies the scoring reads.
+__global__ void to_bf16_kernel(const float *w, __nv_bfloat16 *W1t, __nv_bfloat16 *W2t)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpInPad * kMlpHid; i += gridDim.x * blockDim.x)
-        W1[i] = __float2bfloat16(i < kMlpIn * kMlpHid ? w[kOffW1 + i] : 0.0f);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpHid * kMlpHid; i += gridDim.x * blockDim.x)
-        W2[i] = __float2bfloat16(w[kOffW2 + i]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kW1Elems; i += gridDim.x * blockDim.x) {
+        const int n = i / kW1Ld, k = i % kW1Ld;
+        W1t[i] = __float2bfloat16(k < kMlpIn ? w[kOffW1 + k * kMlpHid + n] : 0.0f);
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kW2Elems; i += gridDim.x * blockDim.x) {
+        const int n = i / kW2Ld, k = i % kW2Ld;
+        W2t[i] = __float2bfloat16(k < kMlpHid ? w[kOffW2 + k * kMlpHid + n] : 0.0f);
+    }
 }
 
 constexpr int kScoreWarps = 4;
@@ -218,9 +223,10 @@ __global__ void __launch_bounds__(32 * kScoreWarps) mlp_score_kernel(const __nv_
     const int64_t n_chunks = (n + 31) / 32;
     for (int64_t ch = (int64_t)blockIdx.x * kScoreWarps + warp; ch < n_chunks; ch += (int64_t)gridDim.x * kScoreWarps) {
         const int64_t row = ch * 32 + lane;
+        float f[kMlpIn];
 #pragma unroll
-        for (int f = 0; f < kMlpInPad; ++f)
-            st->X[lane * kMlpInPad + f] = __float2bfloat16(row < n && f < kMlpIn ? X[row * kMlpIn + f] : 0.0f);
+        for (int i = 0; i < kMlpIn; ++i) f[i] = row < n ? X[row * kMlpIn + i] : 0.0f;
+        mlp_stage_row(st, f);
         const float z = mlp_score_warp(&s.w, st);
         if (row < n) logits[row] = z;
     }
@@ -236,8 +242,8 @@ int ensure_state(kf_context *ctx, MlpState **out)
                   cudaMalloc(&s->v, kMlpParams * sizeof(float)) == cudaSuccess &&
                   cudaMalloc(&s->loss, sizeof(float)) == cudaSuccess &&
                   cudaMalloc(&s->w32, kMlpParams * sizeof(float)) == cudaSuccess &&
-                  cudaMalloc(&s->W1, kMlpInPad * kMlpHid * sizeof(__nv_bfloat16)) == cudaSuccess &&
-                  cudaMalloc(&s->W2, kMlpHid * kMlpHid * sizeof(__nv_bfloat16)) == cudaSuccess;
+                  cudaMalloc(&s->W1, kW1Elems * sizeof(__nv_bfloat16)) == cudaSuccess &&
+                  cudaMalloc(&s->W2, kW2Elems * sizeof(__nv_bfloat16)) == cudaSuccess;
         if (!ok) {
             destroy_mlp_state(s);
             s = nullptr;

@@ -4,44 +4,55 @@
 // that only the best k get the full Kalman chi2.
 //
 // Inference runs on the tensor cores in BF16 with FP32 accumulation, one warp
-// scoring 32 rows at a time (warp-level mma.sync through nvcuda::wmma,
-// m16n16k16): the build kernel scores at most a few dozen hits per warp per
-// layer, inside a per-warp loop, where CTA-wide tcgen05 tiles do not fit.
+// scoring 32 rows at a time with mma.sync.m16n8k16 (inline PTX): the build
+// kernel scores a few in-window hits per lane inside its per-warp layer loop,
+// where CTA-wide tcgen05 tiles do not fit.  The layer-1 accumulators are
+// turned into the layer-2 A fragments in registers (the m16n8 accumulator
+// layout of two adjacent n-tiles is the m16k16 A layout), and the last layer
+// (64 -> 1) is a dot product in FP32 reduced over the four lanes of a group,
+// so a call touches shared memory only for its inputs and the weights.
 #pragma once
 
 #include <cuda_bf16.h>
-#include <mma.h>
 #include <stdint.h>
 
 namespace kf {
 
-constexpr int kMlpIn = 12, kMlpInPad = 16, kMlpHid = 64;
+constexpr int kMlpIn = 12, kMlpHid = 64;
 // flat parameter layout: W1 [12][64], b1 [64], W2 [64][64], b2 [64], W3 [64], b3
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kMlpIn * kMlpHid, kOffW2 = kOffB1 + kMlpHid;
 constexpr int kOffB2 = kOffW2 + kMlpHid * kMlpHid, kOffW3 = kOffB2 + kMlpHid, kOffB3 = kOffW3 + kMlpHid;
 constexpr int kMlpParams = kOffB3 + 1;  // 5057
 
+// Row strides (in bf16) of the shared-memory copies: W1 and W2 are held
+// transposed ([n][k], k contiguous, as the col-major B fragment reads them)
+// with rows padded so that the eight rows a fragment load touches fall in
+// distinct banks.
+constexpr int kW1Ld = 24, kW2Ld = 72, kXLd = 24;
+constexpr int kW1Elems = kMlpHid * kW1Ld, kW2Elems = kMlpHid * kW2Ld;
+
 // Weights as the tensor cores read them (shared memory, per block).
-struct __align__(128) MlpSmemWeights {
-    __nv_bfloat16 W1[kMlpInPad * kMlpHid];  // [16][64], rows 12..15 zero
-    __nv_bfloat16 W2[kMlpHid * kMlpHid];    // [64][64]
+struct __align__(16) MlpSmemWeights {
+    __nv_bfloat16 W1t[kW1Elems];  // [64][24]: W1t[n][k] = W1[k][n], k >= 12 zero
+    __nv_bfloat16 W2t[kW2Elems];  // [64][72]: W2t[n][k] = W2[k][n], k >= 64 zero
     float b1[kMlpHid], b2[kMlpHid], W3[kMlpHid], b3;
 };
 
-// Per-warp staging for 32 rows.
-struct __align__(128) MlpWarpStage {
-    __nv_bfloat16 X[32 * kMlpInPad];  // inputs, [32][16]
-    __nv_bfloat16 H1[32 * kMlpHid];   // first hidden layer after ReLU
-    float acc[32 * kMlpHid];          // accumulator staging
+// Per-warp staging of the 32 input rows.
+struct __align__(16) MlpWarpStage {
+    __nv_bfloat16 X[32 * kXLd];  // [32][24], columns 12..15 zero, 16..23 unused
 };
 
-// Load the BF16 device copies (prepared by kf_proposal_load) into shared
-// memory; all threads of the block call it, followed by __syncthreads().
+// Load the BF16 device copies (prepared by kf_proposal_load in the layout
+// above) into shared memory; all threads of the block call it, followed by
+// __syncthreads().
 __device__ __forceinline__ void mlp_load_weights(MlpSmemWeights *w, const __nv_bfloat16 *W1p, const __nv_bfloat16 *W2p,
                                                  const float *f32)
 {
-    for (int i = threadIdx.x; i < kMlpInPad * kMlpHid; i += blockDim.x) w->W1[i] = W1p[i];
-    for (int i = threadIdx.x; i < kMlpHid * kMlpHid; i += blockDim.x) w->W2[i] = W2p[i];
+    const uint4 *s1 = reinterpret_cast<const uint4 *>(W1p), *s2 = reinterpret_cast<const uint4 *>(W2p);
+    uint4 *d1 = reinterpret_cast<uint4 *>(w->W1t), *d2 = reinterpret_cast<uint4 *>(w->W2t);
+    for (int i = threadIdx.x; i < kW1Elems / 8; i += blockDim.x) d1[i] = s1[i];
+    for (int i = threadIdx.x; i < kW2Elems / 8; i += blockDim.x) d2[i] = s2[i];
     for (int i = threadIdx.x; i < kMlpHid; i += blockDim.x) {
         w->b1[i] = f32[kOffB1 + i];
         w->b2[i] = f32[kOffB2 + i];
@@ -50,56 +61,99 @@ __device__ __forceinline__ void mlp_load_weights(MlpSmemWeights *w, const __nv_b
     if (threadIdx.x == 0) w->b3 = f32[kOffB3];
 }
 
-// Score the 32 rows of st->X (row r belongs to lane r; rows a lane does not
-// use may hold anything).  Warp-collective: every lane of the warp calls it
-// converged.  Returns the logit of the calling lane's row.
-__device__ __forceinline__ float mlp_score_warp(const MlpSmemWeights *w, MlpWarpStage *st)
+// Write the calling lane's input row (12 features, rounded to BF16).
+__device__ __forceinline__ void mlp_stage_row(MlpWarpStage *st, const float f[kMlpIn])
 {
-    using namespace nvcuda;
     const int lane = threadIdx.x & 31;
-    __syncwarp();
+    uint32_t u[8];
 #pragma unroll
-    for (int m = 0; m < 2; ++m) {
-        wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, wmma::row_major> a;
-        wmma::load_matrix_sync(a, st->X + m * 16 * kMlpInPad, kMlpInPad);
-#pragma unroll
-        for (int n = 0; n < 4; ++n) {
-            wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, wmma::row_major> b;
-            wmma::fragment<wmma::accumulator, 16, 16, 16, float> c;
-            wmma::fill_fragment(c, 0.0f);
-            wmma::load_matrix_sync(b, w->W1 + n * 16, kMlpHid);
-            wmma::mma_sync(c, a, b, c);
-            wmma::store_matrix_sync(st->acc + m * 16 * kMlpHid + n * 16, c, kMlpHid, wmma::mem_row_major);
-        }
+    for (int i = 0; i < 8; ++i) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(2 * i < kMlpIn ? f[2 * i] : 0.0f,
+                                                       2 * i + 1 < kMlpIn ? f[2 * i + 1] : 0.0f);
+        u[i] = *reinterpret_cast<const uint32_t *>(&h);
     }
+    uint4 *d = reinterpret_cast<uint4 *>(st->X + lane * kXLd);
+    d[0] = make_uint4(u[0], u[1], u[2], u[3]);
+    d[1] = make_uint4(u[4], u[5], u[6], u[7]);
+}
+
+__device__ __forceinline__ void mma_bf16_m16n8k16(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                                  uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(lo, 0.0f), fmaxf(hi, 0.0f));
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// Score the 32 rows of st->X (row r belongs to lane r; rows a lane does not
+// use may hold anything: rows do not mix).  Warp-collective: every lane of the warp
+// calls it converged.  Returns the logit of the calling lane's row.
+//
+// Fragment layouts (PTX ISA, mma.m16n8k16 with .bf16): g = lane / 4,
+// t = lane % 4; A (16x16, row-major) registers hold rows {g, g+8} x columns
+// {2t, 2t+1} and {2t+8, 2t+9}; B (16x8, col-major) rows {2t, 2t+1} and
+// {2t+8, 2t+9} of column g; the accumulator rows {g, g+8} x columns {2t, 2t+1}.
+__device__ __forceinline__ float mlp_score_warp(const MlpSmemWeights *w, const MlpWarpStage *st)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint32_t *X32 = reinterpret_cast<const uint32_t *>(st->X);
+    const uint32_t *W1 = reinterpret_cast<const uint32_t *>(w->W1t);
+    const uint32_t *W2 = reinterpret_cast<const uint32_t *>(w->W2t);
     __syncwarp();
-#pragma unroll 8
-    for (int j = 0; j < kMlpHid; ++j)
-        st->H1[lane * kMlpHid + j] = __float2bfloat16(fmaxf(st->acc[lane * kMlpHid + j] + w->b1[j], 0.0f));
-    __syncwarp();
+    float zr[2][2];  // [m-tile][row g, row g+8]
 #pragma unroll
-    for (int m = 0; m < 2; ++m) {
+    for (int mt = 0; mt < 2; ++mt) {
+        const int r0 = (mt * 16 + g) * (kXLd / 2), r1 = r0 + 8 * (kXLd / 2);
+        const uint32_t x0 = X32[r0 + t], x1 = X32[r1 + t], x2 = X32[r0 + t + 4], x3 = X32[r1 + t + 4];
+        // layer 1 -> A fragments of layer 2 (k-step ks = n-tiles 2ks, 2ks+1)
+        uint32_t a[4][4];
 #pragma unroll
-        for (int n = 0; n < 4; ++n) {
-            wmma::fragment<wmma::accumulator, 16, 16, 16, float> c;
-            wmma::fill_fragment(c, 0.0f);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                wmma::fragment<wmma::matrix_a, 16, 16, 16, __nv_bfloat16, wmma::row_major> a;
-                wmma::fragment<wmma::matrix_b, 16, 16, 16, __nv_bfloat16, wmma::row_major> b;
-                wmma::load_matrix_sync(a, st->H1 + m * 16 * kMlpHid + k * 16, kMlpHid);
-                wmma::load_matrix_sync(b, w->W2 + k * 16 * kMlpHid + n * 16, kMlpHid);
-                wmma::mma_sync(c, a, b, c);
-            }
-            wmma::store_matrix_sync(st->acc + m * 16 * kMlpHid + n * 16, c, kMlpHid, wmma::mem_row_major);
+        for (int nt = 0; nt < 8; ++nt) {
+            const int n = nt * 8 + g, j = nt * 8 + 2 * t;
+            float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            mma_bf16_m16n8k16(c, x0, x1, x2, x3, W1[n * (kW1Ld / 2) + t], W1[n * (kW1Ld / 2) + t + 4]);
+            const float2 bb = *reinterpret_cast<const float2 *>(w->b1 + j);
+            a[nt >> 1][(nt & 1) * 2 + 0] = pack_relu_bf16(c[0] + bb.x, c[1] + bb.y);
+            a[nt >> 1][(nt & 1) * 2 + 1] = pack_relu_bf16(c[2] + bb.x, c[3] + bb.y);
         }
+        // layer 2, one n-tile at a time, folded into the 64 -> 1 dot product
+        float z0 = 0.0f, z1 = 0.0f;
+#pragma unroll 1
+        for (int nt = 0; nt < 8; ++nt) {
+            const int n = nt * 8 + g, j = nt * 8 + 2 * t;
+            float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+                mma_bf16_m16n8k16(c, a[ks][0], a[ks][1], a[ks][2], a[ks][3], W2[n * (kW2Ld / 2) + ks * 8 + t],
+                                  W2[n * (kW2Ld / 2) + ks * 8 + t + 4]);
+            const float2 bb = *reinterpret_cast<const float2 *>(w->b2 + j);
+            const float2 ww = *reinterpret_cast<const float2 *>(w->W3 + j);
+            z0 = fmaf(ww.x, fmaxf(c[0] + bb.x, 0.0f), fmaf(ww.y, fmaxf(c[1] + bb.y, 0.0f), z0));
+            z1 = fmaf(ww.x, fmaxf(c[2] + bb.x, 0.0f), fmaf(ww.y, fmaxf(c[3] + bb.y, 0.0f), z1));
+        }
+        z0 += __shfl_xor_sync(0xffffffffu, z0, 1);
+        z0 += __shfl_xor_sync(0xffffffffu, z0, 2);
+        z1 += __shfl_xor_sync(0xffffffffu, z1, 1);
+        z1 += __shfl_xor_sync(0xffffffffu, z1, 2);
+        zr[mt][0] = z0;
+        zr[mt][1] = z1;
     }
+    // row `lane` lives in group lane % 8 as (m-tile lane / 16, half (lane / 8) % 2)
+    const int src = (lane & 7) * 4;
+    const float v00 = __shfl_sync(0xffffffffu, zr[0][0], src), v01 = __shfl_sync(0xffffffffu, zr[0][1], src);
+    const float v10 = __shfl_sync(0xffffffffu, zr[1][0], src), v11 = __shfl_sync(0xffffffffu, zr[1][1], src);
+    const int mt = lane >> 4, half = (lane >> 3) & 1;
+    const float z = mt ? (half ? v11 : v10) : (half ? v01 : v00);
     __syncwarp();
-    float z = w->b3;
-#pragma unroll 8
-    for (int j = 0; j < kMlpHid; ++j) z = fmaf(w->W3[j], fmaxf(st->acc[lane * kMlpHid + j] + w->b2[j], 0.0f), z);
-    __syncwarp();
-    return z;
+    return z + w->b3;
 }
 
 }  // namespace kf

@@ -83,6 +83,9 @@ def load() -> ctypes.CDLL:
         L.kf_build_tracks.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int, _vp, _vp, _vp,
                                       ctypes.c_int64, ctypes.c_int64] + [_vp] * 10 + \
             [ctypes.POINTER(Options), _vp]
+        L.kf_build_tracks_logged.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int, _vp, _vp, _vp,
+                                             ctypes.c_int64, ctypes.c_int64] + [_vp] * 10 + \
+            [ctypes.POINTER(Options), _vp, _vp, _vp, ctypes.c_int64, _vp, _vp]
         L.kf_proposal_gradient.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_float), _vp]
         L.kf_proposal_train.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                         ctypes.POINTER(ctypes.c_float), _vp]
@@ -217,9 +220,13 @@ def fit_tracks(ctx: Context, geom: GeometryArgs, seed_state, seed_cov, charge, h
 
 def build_tracks(ctx: Context, geom: GeometryArgs, hit_offsets, hit_pos, hit_cov, seed_event, seed_state,
                  seed_cov, seed_charge, opt: Options | None = None, out: dict | None = None,
-                 stream: torch.cuda.Stream | None = None) -> dict:
+                 stream: torch.cuda.Stream | None = None, log: dict | None = None) -> dict:
     """kf_build_tracks: hit_offsets is a host int64 array [E][L+1]; every other
-    array a CUDA tensor.  Returns (or fills) the output tensors."""
+    array a CUDA tensor.  Returns (or fills) the output tensors.
+
+    With `log` (a dict from new_build_log) the call is kf_build_tracks_logged:
+    the log's tensors receive the training rows and its "count" the number of
+    in-window pairs met."""
     opt = opt if opt is not None else options()
     N = int(opt.max_cands)
     L = geom.struct.n_layers
@@ -251,10 +258,33 @@ def build_tracks(ctx: Context, geom: GeometryArgs, hit_offsets, hit_pos, hit_cov
         _ptr(out["flags"], torch.int32, (S, N), "out_flags"),
     ]
     s = stream if stream is not None else torch.cuda.current_stream(dev)
-    rc = load().kf_build_tracks(ctx.handle, ctypes.byref(geom.struct), int(off.shape[0]), *args,
-                                ctypes.byref(opt), s.cuda_stream)
-    ctx.check(rc, "kf_build_tracks")
+    if log is None:
+        rc = load().kf_build_tracks(ctx.handle, ctypes.byref(geom.struct), int(off.shape[0]), *args,
+                                    ctypes.byref(opt), s.cuda_stream)
+        ctx.check(rc, "kf_build_tracks")
+        return out
+    cap = int(log["labels"].shape[0])
+    rc = load().kf_build_tracks_logged(
+        ctx.handle, ctypes.byref(geom.struct), int(off.shape[0]), *args, ctypes.byref(opt),
+        _ptr(log["features"], torch.float32, (cap, 12), "log_features"),
+        _ptr(log["labels"], torch.float32, (cap,), "log_labels"),
+        _ptr(log["ref"], torch.int32, (cap, 4), "log_ref"), cap,
+        _ptr(log["count"], torch.int64, (1,), "log_count"), s.cuda_stream)
+    ctx.check(rc, "kf_build_tracks_logged")
     return out
+
+
+def new_build_log(capacity: int, device="cuda") -> dict:
+    """Device tensors for kf_build_tracks_logged with room for `capacity` rows."""
+    return dict(features=torch.empty((capacity, 12), dtype=torch.float32, device=device),
+                labels=torch.empty((capacity,), dtype=torch.float32, device=device),
+                ref=torch.empty((capacity, 4), dtype=torch.int32, device=device),
+                count=torch.zeros((1,), dtype=torch.int64, device=device))
+
+
+def log_rows(log: dict) -> int:
+    """Rows written into a build log (waits for the device)."""
+    return min(int(log["count"].item()), int(log["labels"].shape[0]))
 
 
 PROPOSAL_PARAMS = 5057

@@ -1,0 +1,182 @@
+"""The learned proposal inside the GPU build, through the C interface.
+
+* kf_build_tracks_logged: the plain build's outputs unchanged, and its
+  training rows against the oracle's (same (seed, candidate, layer, hit)
+  keys, features within FP32 tolerance, identical labels).
+* use_proposal: the GPU build against the oracle's proposal build with the
+  same weights, the ranking taken in the scoring's precision on both sides
+  (bfloat16 inputs, W1, W2 and first hidden layer): at least 99.9% identical
+  hit assignments, as for the plain build.
+* A network trained on the GPU from the logged rows against no network at
+  all (the same top-k cut taken in hit order): what the ranking gains.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle
+from paper_1705_02876_gb300 import metrics, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+
+@pytest.fixture(scope="module")
+def kf():
+    from paper_1705_02876_gb300 import build, kf as kf_
+    build.build()
+    return kf_
+
+
+@pytest.fixture(scope="module")
+def ctx(kf):
+    return kf.Context(0)
+
+
+def _t(a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype=dt)
+
+
+def oracle_seeds(oracle, ev):
+    f = oracle.fit_seeds(ev)
+    return dict(state=f["state"].astype(np.float32), cov=f["cov"].astype(np.float32))
+
+
+def gpu_build(kf, ctx, ev, seeds, log=None, **opt):
+    out = kf.build_tracks(ctx, kf.GeometryArgs.of(ev.build_geom), ev.hit_offsets, _t(ev.hit_pos, torch.float32),
+                          _t(ev.hit_cov, torch.float32), _t(ev.seed_event, torch.int32),
+                          _t(seeds["state"], torch.float32), _t(seeds["cov"], torch.float32),
+                          _t(ev.seed_fit.charge, torch.int8), opt=kf.options(**opt), log=log)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def identical_fraction(gpu, ref):
+    return float((gpu["hit"] == ref["hit"]).mean())
+
+
+def eff(ev, res):
+    return metrics.efficiency_fake_rate(res["hit"][:, 0], ev.seed_track, ev.hit_track, ev.track_nhits)
+
+
+def _keys(ref):
+    r = ref.astype(np.int64)
+    return ((r[:, 0] * 8 + r[:, 1]) * 64 + r[:, 2]) * (1 << 31) + r[:, 3]
+
+
+@pytest.mark.parametrize("N", [1, 6])
+def test_logged_build(kf, ctx, oracle, N):
+    ev = synth.make_build_events(51, 2, 800)
+    seeds = oracle_seeds(oracle, ev)
+    plain = gpu_build(kf, ctx, ev, seeds, max_cands=N)
+    log = kf.new_build_log(400_000)
+    logged = gpu_build(kf, ctx, ev, seeds, log=log, max_cands=N)
+    for k in plain:
+        assert np.array_equal(plain[k], logged[k]), k
+    n = kf.log_rows(log)
+    assert int(log["count"].item()) == n  # the capacity sufficed
+    g = {k: log[k][:n].cpu().numpy() for k in ("features", "labels", "ref")}
+    ref = oracle.build_events(ev, seeds=seeds, max_cands=N, log=True)
+    o = ref["log"]
+    assert abs(n - len(o["labels"])) <= 1e-3 * n
+    kg, ko = _keys(g["ref"]), _keys(o["ref"])
+    assert len(np.unique(kg)) == n  # no pair logged twice
+    common, ig, io = np.intersect1d(kg, ko, return_indices=True)
+    assert len(common) >= 0.999 * len(ko)
+    fg, fo = g["features"][ig], o["features"][io]
+    assert np.array_equal(fg[:, 10], fo[:, 10].astype(np.float32))
+    assert np.array_equal(fg[:, 11], fo[:, 11])
+    assert np.allclose(fg[:, 9], fo[:, 9], rtol=1e-4, atol=0)
+    dev = np.abs(fg[:, :9] - fo[:, :9])
+    # pulls: an FP32 residual of ~1e-3 cm at r ~ 1 m over sigma ~ 1e-2 cm
+    assert np.quantile(dev[:, :3], 0.999) <= 2e-3 and dev[:, :3].max() <= 0.05, dev[:, :3].max(0)
+    assert dev[:, 3:9].max() <= 1e-3, dev[:, 3:9].max(0)
+    assert (g["labels"][ig] == o["labels"][io]).mean() >= 0.999
+
+
+@pytest.mark.parametrize("N,topk,nf", [(1, 1, 100), (6, 1, 100), (6, 2, 300)])
+def test_proposal_parity(kf, ctx, oracle, N, topk, nf):
+    """Random network; dense noise so that many windows hold more than topk
+    hits."""
+    ev = synth.make_build_events(52, 1, 800, noise_factor=nf)
+    seeds = oracle_seeds(oracle, ev)
+    w = mlp_oracle.init_params(np.random.default_rng(7))
+    kf.proposal_load(ctx, _t(w, torch.float32))
+    gpu = gpu_build(kf, ctx, ev, seeds, max_cands=N, use_proposal=1, topk=topk)
+    ref = oracle.build_events(ev, seeds=seeds, max_cands=N, mlp=w.astype(np.float32).astype(np.float64),
+                              topk=topk, mlp_bf16=True)
+    plain = oracle.build_events(ev, seeds=seeds, max_cands=N)
+    assert identical_fraction(gpu, ref) >= 0.999
+    assert identical_fraction(ref, plain) < 0.999  # the network did choose
+    e_g, e_r = eff(ev, gpu), eff(ev, ref)
+    assert abs(e_g["efficiency"] - e_r["efficiency"]) <= 0.005
+
+
+def test_constant_network_parity(kf, ctx, oracle):
+    """All logits equal: both sides keep the lowest hit indices."""
+    ev = synth.make_build_events(53, 1, 800, noise_factor=100)
+    seeds = oracle_seeds(oracle, ev)
+    kf.proposal_load(ctx, _t(np.zeros(5057), torch.float32))
+    for topk in (1, 3):
+        gpu = gpu_build(kf, ctx, ev, seeds, max_cands=6, use_proposal=1, topk=topk)
+        ref = oracle.build_events(ev, seeds=seeds, max_cands=6, mlp=np.zeros(5057), topk=topk)
+        assert identical_fraction(gpu, ref) >= 0.999
+
+
+def test_topk_above_every_window_equals_plain(kf, ctx, oracle):
+    ev = synth.make_build_events(54, 1, 800)
+    seeds = oracle_seeds(oracle, ev)
+    log = kf.new_build_log(200_000)
+    plain = gpu_build(kf, ctx, ev, seeds, log=log, max_cands=6)
+    n = kf.log_rows(log)
+    r = log["ref"][:n].cpu().numpy().astype(np.int64)
+    widest = np.unique((r[:, 0] * 8 + r[:, 1]) * 64 + r[:, 2], return_counts=True)[1].max()
+    kf.proposal_load(ctx, _t(mlp_oracle.init_params(np.random.default_rng(8)), torch.float32))
+    prop = gpu_build(kf, ctx, ev, seeds, max_cands=6, use_proposal=1, topk=8)
+    if widest <= 8:
+        for k in plain:
+            assert np.array_equal(plain[k], prop[k]), k
+    else:
+        assert identical_fraction(prop, plain) >= 0.999
+
+
+def test_trained_network_gain(kf, ctx, oracle):
+    """Train on the plain build's rows of separate events; at top-1 in dense
+    noise the trained ranking keeps the efficiency of the exhaustive search
+    within 0.5% and beats the same cut without a network (hit order)."""
+    train_ev = synth.make_build_events(60, 4, 1000, noise_factor=100)
+    tseeds = oracle_seeds(oracle, train_ev)
+    log = kf.new_build_log(1_000_000)
+    gpu_build(kf, ctx, train_ev, tseeds, log=log, max_cands=6)
+    n = kf.log_rows(log)
+    X, y = log["features"][:n].contiguous(), log["labels"][:n].contiguous()
+    w = _t(mlp_oracle.init_params(np.random.default_rng(9)), torch.float32)
+    losses = kf.proposal_train(ctx, w, X, y, epochs=8, batch=1024, lr=2e-3)
+    assert losses[-1] < 0.7 * losses[0]
+    ev = synth.make_build_events(61, 1, 1000, noise_factor=100)
+    seeds = oracle_seeds(oracle, ev)
+    plain = eff(ev, gpu_build(kf, ctx, ev, seeds, max_cands=6))
+    kf.proposal_load(ctx, w)
+    learned = eff(ev, gpu_build(kf, ctx, ev, seeds, max_cands=6, use_proposal=1, topk=1))
+    kf.proposal_load(ctx, _t(np.zeros(5057), torch.float32))
+    blind = eff(ev, gpu_build(kf, ctx, ev, seeds, max_cands=6, use_proposal=1, topk=1))
+    assert abs(learned["efficiency"] - plain["efficiency"]) <= 0.005, (learned, plain)
+    assert learned["fake_rate"] <= plain["fake_rate"] + 0.005
+    assert learned["efficiency"] > blind["efficiency"] + 0.01 or learned["fake_rate"] < blind["fake_rate"] - 0.01, \
+        (learned, blind)
+
+
+def test_proposal_argument_errors(kf, oracle):
+    ev = synth.make_build_events(55, 1, 50)
+    seeds = dict(state=ev.seed_fit.seed_state, cov=ev.seed_fit.seed_cov)
+    fresh = kf.Context(0)
+    with pytest.raises(kf.KFError, match="kf_proposal_load"):
+        gpu_build(kf, fresh, ev, seeds, use_proposal=1)
+    kf.proposal_load(fresh, _t(np.zeros(5057), torch.float32))
+    for bad in (0, 9):
+        with pytest.raises(kf.KFError, match="topk"):
+            gpu_build(kf, fresh, ev, seeds, use_proposal=1, topk=bad)
+    with pytest.raises(kf.KFError, match="plain build"):
+        gpu_build(kf, fresh, ev, seeds, log=kf.new_build_log(10), use_proposal=1)
+    small = kf.new_build_log(5)  # rows beyond the capacity are dropped, the count is kept
+    gpu_build(kf, fresh, ev, seeds, log=small)
+    assert int(small["count"].item()) > 5 and kf.log_rows(small) == 5
