@@ -58,8 +58,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--precision", default="routed", choices=["routed", "fp32"],
                    help="precision of the timed fit (the chosen form is routed)")
+    p.add_argument("--shape", default=None, help="fixed fit launch shape TRACKS_PER_BLOCK:REG_CAP (no tuning)")
     p.add_argument("--build-events", type=int, default=64, help="events of the build workload (0: skip it)")
     p.add_argument("--build-steps", type=int, default=10)
+    p.add_argument("--train-events", type=int, default=3, help="events logged to train the proposal")
+    p.add_argument("--train-epochs", type=int, default=4)
     return p.parse_args()
 
 
@@ -283,16 +286,66 @@ def bench_build(args, kf, ctx, dev, stream, rank, world):
         return a.elapsed_time(b) / n
 
     ms = timed(step_chosen, args.build_steps)
-    ms_plain = timed(step_plain, max(2, args.build_steps // 2))
     best = b_out["hit"][:, 0].cpu().numpy()
     q = metrics.efficiency_fake_rate(best, ev.seed_track, ev.hit_track, ev.track_nhits)
+    ms_plain = timed(step_plain, max(2, args.build_steps // 2))
+    qp = metrics.efficiency_fake_rate(np.concatenate([o["hit"][:, 0].cpu().numpy() for o in plain_outs if o is not None]),
+                                      ev.seed_track, ev.hit_track, ev.track_nhits)
+    learned = bench_learned(args, kf, ctx, dev, stream, rank, ev, seed_geom, d_sf, fit_out, build_geom, hp, hc, se,
+                            sq, timed)
     out = {"value": S / (ms * 1e-3), "unit": "seeds/s", "ms_per_step": ms, "seeds": S,
            "workload": BUILD_WORKLOAD.format(E=E),
-           "form": "seed fit + binning + build of all events in one launch each, routed precision",
+           "form": "seed fit + binning + build of all events in one launch each, routed precision, "
+                   "exhaustive chi2 in every window",
            "efficiency": q["efficiency"], "fake_rate": q["fake_rate"], "mean_hits": q["mean_hits"],
+           "hit_purity": q["hit_purity"],
            "plain": {"value": S / (ms_plain * 1e-3), "unit": "seeds/s", "ms_per_step": ms_plain,
-                     "form": "FP32 only, one launch per event"}}
+                     "form": "FP32 only, one launch per event", "efficiency": qp["efficiency"],
+                     "fake_rate": qp["fake_rate"]},
+           "learned": learned}
     return out
+
+
+def bench_learned(args, kf, ctx, dev, stream, rank, ev, seed_geom, d_sf, fit_out, build_geom, hp, hc, se, sq, timed):
+    """The chosen build with the learned proposal (top-k = 4).  Its network is
+    trained first, untimed, on up to 1M (candidate, hit) rows the plain build
+    logs on separate events, by the library's own training kernels."""
+    import torch
+    from paper_1705_02876_gb300 import metrics, synth
+    tr = synth.make_build_events(10 + 1000 * rank, args.train_events, 5000)
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dtype=dt)
+    d_tr = kf.to_device(tr.seed_fit, dev)
+    tf = kf.fit_tracks(ctx, kf.GeometryArgs.of(tr.seed_fit.geom), **d_tr, stream=stream)
+    log = kf.new_build_log(1_000_000, dev)
+    kf.build_tracks(ctx, build_geom, tr.hit_offsets, t(tr.hit_pos, torch.float32), t(tr.hit_cov, torch.float32),
+                    t(tr.seed_event, torch.int32), tf["state"], tf["cov"], t(tr.seed_fit.charge, torch.int8),
+                    stream=stream, log=log)
+    torch.cuda.synchronize()
+    n = kf.log_rows(log)
+    ref = log["ref"][:n].cpu().numpy().astype(np.int64)
+    win = np.unique((ref[:, 0] * 8 + ref[:, 1]) * 64 + ref[:, 2], return_counts=True)[1]
+    w = torch.from_numpy(synth.proposal_init(np.random.default_rng(9 + rank))).to(dev, torch.float32)
+    t0 = time.perf_counter()
+    losses = kf.proposal_train(ctx, w, log["features"][:n].contiguous(), log["labels"][:n].contiguous(),
+                               epochs=args.train_epochs, batch=4096, lr=2e-3, stream=stream)
+    train_s = time.perf_counter() - t0
+    kf.proposal_load(ctx, w, stream=stream)
+    opt = kf.options(use_proposal=1, topk=4)
+    b_out = None
+
+    def step_learned():
+        nonlocal b_out
+        kf.fit_tracks(ctx, seed_geom, **d_sf, opt=opt, out=fit_out, stream=stream)
+        b_out = kf.build_tracks(ctx, build_geom, ev.hit_offsets, hp, hc, se, fit_out["state"], fit_out["cov"], sq,
+                                opt=opt, out=b_out, stream=stream)
+
+    ms = timed(step_learned, args.build_steps)
+    q = metrics.efficiency_fake_rate(b_out["hit"][:, 0].cpu().numpy(), ev.seed_track, ev.hit_track, ev.track_nhits)
+    return {"value": ev.n_seeds / (ms * 1e-3), "unit": "seeds/s", "ms_per_step": ms, "topk": 4,
+            "efficiency": q["efficiency"], "fake_rate": q["fake_rate"], "hit_purity": q["hit_purity"],
+            "training": {"rows": n, "events": args.train_events, "epochs": args.train_epochs,
+                         "loss_first_last": [losses[0], losses[-1]], "seconds": round(train_s, 3)},
+            "windows_above_topk": float((win > 4).mean()), "mean_window_hits": float(win.mean())}
 
 
 def main():
@@ -321,6 +374,8 @@ def main():
     out = kf.fit_outputs(T, dev)
     stream = torch.cuda.current_stream(dev)
     chosen = kf.options(precision_mode=kf.PRECISION_ROUTED if args.precision == "routed" else kf.PRECISION_FP32)
+    if args.shape:
+        chosen.tracks_per_block, chosen.reg_cap = (int(v) for v in args.shape.split(":"))
 
     def step(opt=chosen, o=out):
         kf.fit_tracks(ctx, geom, **d_in, event_offsets=batch.event_offsets, opt=opt, out=o, stream=stream)
@@ -407,7 +462,7 @@ def main():
     traffic = recorded_traffic(src_hash)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
-    tuned = ctx.tuned_shape(N_LAYERS, T)
+    tuned = ctx.tuned_shape(N_LAYERS, T) if not args.shape else (chosen.tracks_per_block, chosen.reg_cap)
     line = {
         "metric": METRIC, "value": value, "unit": "tracks/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

@@ -252,7 +252,9 @@ __device__ __forceinline__ bool key_less(unsigned long long a64, uint32_t a32, u
 __host__ __device__ constexpr size_t build_smem_base(int L) { return ((size_t)(L + kSlotSize) * 128 * 4 + 127) / 128 * 128; }
 constexpr size_t kBuildSmemMlp = sizeof(MlpSmemWeights) + 4 * sizeof(MlpWarpStage);
 
-template <int G, bool PROPOSAL>
+constexpr int kModePlain = 0, kModeLog = 1, kModeProposal = 2;
+
+template <int G, int MODE>
 __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
 {
     constexpr int SEEDS_PER_WARP = 32 / G;
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
     float *slots = reinterpret_cast<float *>(smem + L * 128);  // [kSlotSize][128]
     MlpSmemWeights *mw = nullptr;
     MlpWarpStage *mst = nullptr;
-    if (PROPOSAL) {
+    if (MODE == kModeProposal) {
         unsigned char *base = reinterpret_cast<unsigned char *>(smem) + build_smem_base(L);
         mw = reinterpret_cast<MlpSmemWeights *>(base);
         mst = reinterpret_cast<MlpWarpStage *>(base + sizeof(MlpSmemWeights)) + (threadIdx.x >> 5);
@@ -391,12 +393,14 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
 #pragma unroll
             for (int i = 0; i < 6; ++i) f[3 + i] = log10f(fmaxf(c[pk(i, i)], 1e-30f));
             f[9] = copysignf(rsqrtf(x[3] * x[3] + x[4] * x[4]), qkb);
-            f[10] = (float)l / (float)L;
+            f[10] = __fdiv_rn((float)l, (float)L);  // correctly rounded, whatever the division flags
             f[11] = (float)(l - nhits);
         };
-        if (PROPOSAL) {
-            // first pass: up to topk in-window hits kept; one more marks the
-            // window as one the network ranks
+        if (MODE != kModeLog) {
+            // first pass: the window's hits are collected (cheap bin reads
+            // only) while there are at most `cap`; one more marks the window
+            // as wide
+            const int cap = MODE == kModeProposal ? p.topk : kMaxN;
             uint32_t hb[kMaxN];
 #pragma unroll
             for (int k = 0; k < kMaxN; ++k) hb[k] = kNoKey;
@@ -405,7 +409,7 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
             if (reached) {
                 cur.start(win);
                 for (uint32_t hl = cur.next(p, win); hl != kNoKey; hl = cur.next(p, win)) {
-                    if (n_in == p.topk) {
+                    if (n_in == cap) {
                         ++n_in;
                         break;
                     }
@@ -415,19 +419,20 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
                     ++n_in;
                 }
             }
-            const bool use = n_in > p.topk;
-            if (__any_sync(0xffffffffu, use)) {
-                // the topk best in-window hits by logit (logit desc, hit index
-                // asc); one hit per ranking lane per round, scored by the warp
+            const bool wide = n_in > cap;
+            if (MODE == kModeProposal && __any_sync(0xffffffffu, wide)) {
+                // a wide window keeps its topk best hits by logit (logit desc,
+                // hit index asc); one hit per ranking lane per round, scored
+                // by the warp
                 float tz[kMaxN];
 #pragma unroll
                 for (int k = 0; k < kMaxN; ++k) tz[k] = -INFINITY;
-                if (use) {
+                if (wide) {
 #pragma unroll
                     for (int k = 0; k < kMaxN; ++k) hb[k] = kNoKey;
                     cur.start(win);
                 }
-                bool more = use;
+                bool more = wide;
                 while (__any_sync(0xffffffffu, more)) {
                     const uint32_t hr = more ? cur.next(p, win) : kNoKey;
                     more = hr != kNoKey;
@@ -458,15 +463,29 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
                     }
                 }
             }
-            // the full chi2 for the kept hits only
+            if (MODE == kModeProposal || !wide) {
+                // the full chi2 for the collected (or ranked) hits, loads
+                // issued together
 #pragma unroll
-            for (int k2 = 0; k2 < kMaxN; ++k2) {
-                if (hb[k2] == kNoKey) continue;
-                float m[3], v[6], dc, f3[3];
-                load_hit(hb[k2], m, v);
-                if (hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, f3) && dc <= p.chi2_cut) insert(dc, hb[k2], kNoKey);
+                for (int k2 = 0; k2 < kMaxN; ++k2) {
+                    if (hb[k2] == kNoKey) continue;
+                    float m[3], v[6], dc, f3[3];
+                    load_hit(hb[k2], m, v);
+                    if (hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, f3) && dc <= p.chi2_cut)
+                        insert(dc, hb[k2], kNoKey);
+                }
+            } else {
+                // exhaustive search of a window wider than the buffer
+                cur.start(win);
+                for (uint32_t hl = cur.next(p, win); hl != kNoKey; hl = cur.next(p, win)) {
+                    float m[3], v[6], dc, f3[3];
+                    load_hit(hl, m, v);
+                    if (hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, f3) && dc <= p.chi2_cut) insert(dc, hl, kNoKey);
+                }
             }
         } else if (reached) {
+            // training log: every in-window pair's features now, label 1 once
+            // the pair survives the merge
             WindowCursor cur;
             cur.start(win);
             for (uint32_t hl = cur.next(p, win); hl != kNoKey; hl = cur.next(p, win)) {
@@ -474,20 +493,18 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
                 load_hit(hl, m, v);
                 const bool ok = hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, feat);
                 uint32_t row = kNoKey;
-                if (p.log_n) {  // training log: features now, label 1 if the pair survives
-                    const unsigned long long r = atomicAdd(p.log_n, 1ull);
-                    if (r < p.log_cap) {
-                        cand_features(feat);
-                        row = (uint32_t)r;
+                const unsigned long long r = atomicAdd(p.log_n, 1ull);
+                if (r < p.log_cap) {
+                    cand_features(feat);
+                    row = (uint32_t)r;
 #pragma unroll
-                        for (int i = 0; i < kMlpIn; ++i) p.log_f[(int64_t)r * kMlpIn + i] = feat[i];
-                        p.log_y[r] = 0.0f;
-                        int32_t *ref = p.log_ref + (int64_t)r * 4;
-                        ref[0] = (int32_t)s;
-                        ref[1] = slot;
-                        ref[2] = l;
-                        ref[3] = (int32_t)(seg_lo + hl);
-                    }
+                    for (int i = 0; i < kMlpIn; ++i) p.log_f[(int64_t)r * kMlpIn + i] = feat[i];
+                    p.log_y[r] = 0.0f;
+                    int32_t *ref = p.log_ref + (int64_t)r * 4;
+                    ref[0] = (int32_t)s;
+                    ref[1] = slot;
+                    ref[2] = l;
+                    ref[3] = (int32_t)(seg_lo + hl);
                 }
                 if (ok && dc <= p.chi2_cut) insert(dc, hl, row);
             }
@@ -536,7 +553,7 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
             }
             if (slot == win_slot) {
                 if ((b32 & 0x7ffffffu) != 0u) {  // pop the head of the list
-                    if (lr[0] != kNoKey) p.log_y[lr[0]] = 1.0f;  // the pair survives
+                    if (MODE == kModeLog && lr[0] != kNoKey) p.log_y[lr[0]] = 1.0f;  // the pair survives
 #pragma unroll
                     for (int k = 0; k < kMaxN - 1; ++k) {
                         lc[k] = lc[k + 1];
@@ -797,28 +814,27 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
     const int G = p.N == 1 ? 1 : p.N <= 2 ? 2 : p.N <= 4 ? 4 : 8;
     const int64_t seeds_per_block = 4 * (32 / G);
     const unsigned grid = (unsigned)((n_seeds + seeds_per_block - 1) / seeds_per_block);
-    const bool prop = o.use_proposal != 0;
-    const size_t smem = prop ? build_smem_base(L) + kBuildSmemMlp
-                             : (size_t)L * 128 * sizeof(int32_t) + (size_t)kSlotSize * 128 * sizeof(float);
+    const int mode = o.use_proposal ? kModeProposal : log ? kModeLog : kModePlain;
+    const size_t smem = mode == kModeProposal
+                            ? build_smem_base(L) + kBuildSmemMlp
+                            : (size_t)L * 128 * sizeof(int32_t) + (size_t)kSlotSize * 128 * sizeof(float);
     static bool attr_prop = false;
-    if (prop && !attr_prop) {
+    if (mode == kModeProposal && !attr_prop) {
         const int mx = (int)(build_smem_base(KF_MAX_LAYERS) + kBuildSmemMlp);
-        cudaFuncSetAttribute(build_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(build_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(build_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(build_kernel<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(build_kernel<1, kModeProposal>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(build_kernel<2, kModeProposal>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(build_kernel<4, kModeProposal>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(build_kernel<8, kModeProposal>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         attr_prop = true;
     }
-    switch (G * 2 + (prop ? 1 : 0)) {
-    case 2: build_kernel<1, false><<<grid, 128, smem, stream>>>(p); break;
-    case 3: build_kernel<1, true><<<grid, 128, smem, stream>>>(p); break;
-    case 4: build_kernel<2, false><<<grid, 128, smem, stream>>>(p); break;
-    case 5: build_kernel<2, true><<<grid, 128, smem, stream>>>(p); break;
-    case 8: build_kernel<4, false><<<grid, 128, smem, stream>>>(p); break;
-    case 9: build_kernel<4, true><<<grid, 128, smem, stream>>>(p); break;
-    case 16: build_kernel<8, false><<<grid, 128, smem, stream>>>(p); break;
-    default: build_kernel<8, true><<<grid, 128, smem, stream>>>(p); break;
-    }
+    using Kernel = void (*)(const BuildParams);
+    static const Kernel table[4][3] = {
+        {build_kernel<1, kModePlain>, build_kernel<1, kModeLog>, build_kernel<1, kModeProposal>},
+        {build_kernel<2, kModePlain>, build_kernel<2, kModeLog>, build_kernel<2, kModeProposal>},
+        {build_kernel<4, kModePlain>, build_kernel<4, kModeLog>, build_kernel<4, kModeProposal>},
+        {build_kernel<8, kModePlain>, build_kernel<8, kModeLog>, build_kernel<8, kModeProposal>}};
+    const int gi = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : 3;
+    table[gi][mode]<<<grid, 128, smem, stream>>>(p);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(ctx, e, "build launch");
     return KF_OK;
 }

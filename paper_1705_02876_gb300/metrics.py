@@ -7,7 +7,9 @@ simulated track that owns at least half of its hits (seed hits included); it
 is *counted* if it has at least 7 hits.  Efficiency = fraction of simulated
 tracks with at least 7 hits (and a seed) matched by a counted candidate; fake
 rate = fraction of counted candidates that match no simulated track.  Host-side
-evaluation only, not part of the hot path.
+evaluation only, not part of the hot path.  hit_purity = fraction of the
+build hits of the best candidates that belong to their seed's own simulated
+track.
 """
 from __future__ import annotations
 
@@ -40,5 +42,8 @@ def efficiency_fake_rate(best_hits, seed_track, hit_track, track_nhits, n_seed_h
     found = np.unique(matched_track[counted & (matched_track >= 0)])
     eff = np.isin(eligible, found).mean() if len(eligible) else float("nan")
     fake_rate = fake.sum() / max(counted.sum(), 1)
+    assigned = best_hits >= 0
+    purity = (owner == np.asarray(seed_track)[:, None])[assigned].mean() if assigned.any() else float("nan")
     return dict(efficiency=float(eff), fake_rate=float(fake_rate), n_counted=int(counted.sum()),
-                n_eligible=int(len(eligible)), mean_hits=float(n_total.mean()) if S else float("nan"))
+                n_eligible=int(len(eligible)), mean_hits=float(n_total.mean()) if S else float("nan"),
+                hit_purity=float(purity))

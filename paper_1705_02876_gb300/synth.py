@@ -476,3 +476,13 @@ def build_workload(scale_events: int | None = None, seed: int = 4, tracks_per_ev
     """The build workload: 17 layers, 5,000 tracks per event, 10x uniform noise
     per layer, seeds from the first three layers, 64 events per launch."""
     return make_build_events(seed, 64 if scale_events is None else scale_events, tracks_per_event)
+
+
+def proposal_init(rng) -> np.ndarray:
+    """Initial weights of the proposal network (12 -> 64 -> 64 -> 1) in its
+    flat float32 layout W1 [12][64], b1, W2 [64][64], b2, W3 [64], b3:
+    He-normal draws for W1 and W2, N(0, 1/64) for W3, zero biases."""
+    parts = [rng.normal(0.0, np.sqrt(2.0 / 12), 12 * 64), np.zeros(64),
+             rng.normal(0.0, np.sqrt(2.0 / 64), 64 * 64), np.zeros(64),
+             rng.normal(0.0, np.sqrt(1.0 / 64), 64), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)

@@ -84,12 +84,16 @@ def test_logged_build(kf, ctx, oracle, N):
     assert len(common) >= 0.999 * len(ko)
     fg, fo = g["features"][ig], o["features"][io]
     assert np.array_equal(fg[:, 10], fo[:, 10].astype(np.float32))
-    assert np.array_equal(fg[:, 11], fo[:, 11])
-    assert np.allclose(fg[:, 9], fo[:, 9], rtol=1e-4, atol=0)
+    # with N > 1 a slot can hold a different candidate on the two sides after
+    # a near-tie: its rows then differ, so the bar is on 99.9% of the rows
+    q = 1.0 if N == 1 else 0.999
+    assert (fg[:, 11] == fo[:, 11]).mean() >= q
+    assert np.quantile(np.abs(fg[:, 9] / fo[:, 9] - 1), q) <= 1e-4
     dev = np.abs(fg[:, :9] - fo[:, :9])
     # pulls: an FP32 residual of ~1e-3 cm at r ~ 1 m over sigma ~ 1e-2 cm
-    assert np.quantile(dev[:, :3], 0.999) <= 2e-3 and dev[:, :3].max() <= 0.05, dev[:, :3].max(0)
-    assert dev[:, 3:9].max() <= 1e-3, dev[:, 3:9].max(0)
+    assert np.quantile(dev[:, :3], 0.999) <= 2e-3, np.quantile(dev[:, :3], 0.999, axis=0)
+    assert np.quantile(dev[:, :3], q) <= 0.05
+    assert np.quantile(dev[:, 3:9], q) <= 1e-3, dev[:, 3:9].max(0)
     assert (g["labels"][ig] == o["labels"][io]).mean() >= 0.999
 
 
@@ -140,29 +144,33 @@ def test_topk_above_every_window_equals_plain(kf, ctx, oracle):
 
 
 def test_trained_network_gain(kf, ctx, oracle):
-    """Train on the plain build's rows of separate events; at top-1 in dense
-    noise the trained ranking keeps the efficiency of the exhaustive search
-    within 0.5% and beats the same cut without a network (hit order)."""
+    """Train on the plain build's rows of separate events (100x noise); at
+    top-1 the trained ranking keeps the efficiency of the exhaustive search
+    within 0.5% (N = 6) and beats the same cut without a network (hit order):
+    purer candidates with N = 6, more tracks found with N = 1."""
     train_ev = synth.make_build_events(60, 4, 1000, noise_factor=100)
     tseeds = oracle_seeds(oracle, train_ev)
     log = kf.new_build_log(1_000_000)
     gpu_build(kf, ctx, train_ev, tseeds, log=log, max_cands=6)
     n = kf.log_rows(log)
     X, y = log["features"][:n].contiguous(), log["labels"][:n].contiguous()
+    p = float(y.mean())
+    prior = -(p * np.log(p) + (1 - p) * np.log(1 - p))  # loss of the base rate alone
     w = _t(mlp_oracle.init_params(np.random.default_rng(9)), torch.float32)
     losses = kf.proposal_train(ctx, w, X, y, epochs=8, batch=1024, lr=2e-3)
-    assert losses[-1] < 0.7 * losses[0]
+    assert losses[-1] < losses[0] and losses[-1] < 0.8 * prior, (losses, prior)
     ev = synth.make_build_events(61, 1, 1000, noise_factor=100)
     seeds = oracle_seeds(oracle, ev)
-    plain = eff(ev, gpu_build(kf, ctx, ev, seeds, max_cands=6))
-    kf.proposal_load(ctx, w)
-    learned = eff(ev, gpu_build(kf, ctx, ev, seeds, max_cands=6, use_proposal=1, topk=1))
-    kf.proposal_load(ctx, _t(np.zeros(5057), torch.float32))
-    blind = eff(ev, gpu_build(kf, ctx, ev, seeds, max_cands=6, use_proposal=1, topk=1))
-    assert abs(learned["efficiency"] - plain["efficiency"]) <= 0.005, (learned, plain)
-    assert learned["fake_rate"] <= plain["fake_rate"] + 0.005
-    assert learned["efficiency"] > blind["efficiency"] + 0.01 or learned["fake_rate"] < blind["fake_rate"] - 0.01, \
-        (learned, blind)
+    res = {}
+    for N in (1, 6):
+        res["plain", N] = eff(ev, gpu_build(kf, ctx, ev, seeds, max_cands=N))
+        kf.proposal_load(ctx, w)
+        res["learned", N] = eff(ev, gpu_build(kf, ctx, ev, seeds, max_cands=N, use_proposal=1, topk=1))
+        kf.proposal_load(ctx, _t(np.zeros(5057), torch.float32))
+        res["blind", N] = eff(ev, gpu_build(kf, ctx, ev, seeds, max_cands=N, use_proposal=1, topk=1))
+    assert abs(res["learned", 6]["efficiency"] - res["plain", 6]["efficiency"]) <= 0.005, res
+    assert res["learned", 6]["hit_purity"] > res["blind", 6]["hit_purity"] + 0.02, res
+    assert res["learned", 1]["efficiency"] > res["blind", 1]["efficiency"] + 0.03, res
 
 
 def test_proposal_argument_errors(kf, oracle):
