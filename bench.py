@@ -61,6 +61,7 @@ def parse():
     p.add_argument("--shape", default=None, help="fixed fit launch shape TRACKS_PER_BLOCK:REG_CAP (no tuning)")
     p.add_argument("--build-events", type=int, default=64, help="events of the build workload (0: skip it)")
     p.add_argument("--build-steps", type=int, default=10)
+    p.add_argument("--no-ragged", action="store_true", help="skip the ragged-batching comparison")
     p.add_argument("--train-events", type=int, default=3, help="events logged to train the proposal")
     p.add_argument("--train-epochs", type=int, default=4)
     return p.parse_args()
@@ -348,6 +349,44 @@ def bench_learned(args, kf, ctx, dev, stream, rank, ev, seed_geom, d_sf, fit_out
             "windows_above_topk": float((win > 4).mean()), "mean_window_hits": float(win.mean())}
 
 
+def bench_ragged(args, kf, ctx, dev, stream, rank):
+    """Ragged batching: 256 events of lognormal sizes (median 5,000, clamped
+    to 500..50,000), 17 layers, hit efficiency 0.95, fitted as one persistent
+    graph-captured launch (autotuned shape), one plain launch over all tracks,
+    and one plain launch per event."""
+    import torch
+    from paper_1705_02876_gb300 import synth
+    b = synth.workload("ragged", seed=3 + 1000 * rank)
+    T = b.n_tracks
+    geom = kf.GeometryArgs.of(b.geom)
+    d_in = kf.to_device(b, dev)
+    out = kf.fit_outputs(T, dev)
+    res = {"workload": "17-layer toy barrel r=4..68 cm, 256 events, lognormal sizes (median 5,000, "
+                       "500..50,000), hit efficiency 0.95", "tracks": T}
+    for name, mode in (("persistent", kf.LAUNCH_AUTO), ("flat", kf.LAUNCH_FLAT), ("per_event", kf.LAUNCH_PER_EVENT)):
+        opt = kf.options(launch_mode=mode)
+
+        def step():
+            kf.fit_tracks(ctx, geom, **d_in, event_offsets=b.event_offsets, opt=opt, out=out, stream=stream)
+
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        n = 20 if mode != kf.LAUNCH_PER_EVENT else 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        res[name] = {"value": T / (ms * 1e-3), "unit": "tracks/s", "ms_per_step": ms,
+                     "launches_per_step": 1 if mode != kf.LAUNCH_PER_EVENT else len(b.event_offsets) - 1}
+    shape = ctx.tuned_shape(b.geom.n_layers, T)
+    res["tuned_shape"] = {"tracks_per_block": shape[0], "reg_cap": shape[1]} if shape else None
+    return res
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
@@ -456,6 +495,7 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_ms = float(tt.item())
 
+    routed_share = float(((out["flags"] & 16) != 0).float().mean().item())
     flops = FLOPS_PER_TRACK_LAYER * N_LAYERS * T
     achieved_tflops = flops / (kern_ms * 1e-3) / 1e12
     src_hash = kernel_source_hash()
@@ -481,6 +521,7 @@ def main():
                   "form": "FP32 only, one plain launch per event (100 launches)"},
         "e2e": {"value": world * T / (e2e_ms * 1e-3), "unit": "tracks/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
+        "fp64_routed_share": routed_share,
         "gpu_launches": args.steps,
         "clocks": clocks,
         "kernel_source_hash": src_hash,
@@ -488,6 +529,8 @@ def main():
     }
     if args.build_events > 0:
         line["build"] = bench_build(args, kf, ctx, dev, stream, rank, world)
+    if not args.no_ragged:
+        line["ragged"] = bench_ragged(args, kf, ctx, dev, stream, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch, T)
     if rank == 0:

@@ -96,7 +96,9 @@ typedef struct {
 typedef struct {
     /* precision routing (fit and build) */
     int precision_mode;      /* KF_PRECISION_* */
-    float cond_max;          /* Frobenius condition estimate of S above which FP64 is used */
+    float cond_max;          /* an update whose S has a correlation matrix R (S scaled to unit
+                                diagonal) with det R < 27 / (4 cond_max) runs in FP64, so
+                                every FP32 update has cond_2(R) <= cond_max */
     float pt_lo, pt_hi;      /* tracks with pT outside [pt_lo, pt_hi] GeV update in FP64 */
     float gain_max;          /* > 0: an update with C_ii > gain_max V_ii (i = x, y, z) forms
                                 its gain (S^-1 and K) in float-float; 0 = off */
@@ -117,7 +119,7 @@ typedef struct {
     int topk;
 } kf_options;
 
-/* Fill *opt with the defaults: routed precision (cond_max 1e6, pT in
+/* Fill *opt with the defaults: routed precision (cond_max 1e4, pT in
  * [0.25, 200], gain_max 0), automatic launch, N = 6, chi2 cut 30, 3-sigma window,
  * 0.01/0.1 cm nominal resolution, 256 x 64 bins, proposal off, top-k 4. */
 void kf_options_default(kf_options *opt);

@@ -122,7 +122,7 @@ Routing make_routing(const kf_options &o)
 {
     Routing rt;
     rt.mode = o.precision_mode;
-    rt.cond2_max = o.cond_max * o.cond_max;
+    rt.det_min = 6.75f / o.cond_max;
     rt.pt_lo = o.pt_lo;
     rt.pt_hi = o.pt_hi;
     rt.gain_max = o.gain_max;
@@ -156,7 +156,7 @@ void kf_options_default(kf_options *o)
     if (!o) return;
     std::memset(o, 0, sizeof *o);
     o->precision_mode = KF_PRECISION_ROUTED;
-    o->cond_max = 1e6f;
+    o->cond_max = 1e4f;
     o->pt_lo = 0.25f;
     o->pt_hi = 200.0f;
     o->gain_max = 0.0f;

@@ -256,53 +256,137 @@ struct SlotRef {
     __device__ __forceinline__ float &chi2() const { return p[kSlotChi2 * stride]; }
 };
 
-// Update in FP64 on the slot: S^-1 by adjugate, each row of the gain
-// K = C[:, 0:3] S^-1 formed and applied at once (rows 5..3 read the untouched
-// rows 0..2; rows 2..0 use a copy of the 3x3 block), x += K r,
-// C -= K C[0:3, :] on the packed lower triangle (symmetric by construction),
-// chi2 = r^T S^-1 r; then the PSD repair: a variance that cancellation drove
-// to zero or below is clamped to 1e-12 of the trace (correlations are left
-// alone: on the cylinder the covariance has rank 5 and |rho| -> 1 is
-// legitimate).  Returns 2, 3 (repaired) or 1 (S not positive definite).
+// The slow paths work in the same local frame as the FP32 update (below):
+// n = (x, y)/|(x, y)| at the predicted position, t = z x n.  The slot holds
+// the Cartesian covariance, whose radial row is the FP32 rounding residue of
+// an exact zero; the local block over (t, z, px, py, pz) drops it, exactly as
+// the FP32 path does (in Cartesian form that residue, of order 1e-7 C_tt, can
+// rival a fine hit's V_nn and bias the update).  The slot's 21 covariance
+// floats are rewritten in place as the 15 of the local block (packed, local
+// index u = 0 t, 1 z, 2 px, 3 py, 4 pz) and back: every value is streamed
+// through the slot so that these out-of-line paths keep the register budget
+// of the FP32 main path.  After the update the Cartesian covariance is
+// rebuilt from the local block (x = -n_y t, y = n_x t), so its radial row is
+// exactly zero again.
+template <class R>
+__device__ __forceinline__ void slot_to_local(const SlotRef &sl, R nx, R ny)
+{
+    float *c = sl.p + kSlotC * sl.stride;
+    auto C = [&](int i, int j) -> float & { return c[pk(i, j) * sl.stride]; };
+    const float ltt = (float)(ny * ny * (R)C(0, 0) - 2 * nx * ny * (R)C(1, 0) + nx * nx * (R)C(1, 1));
+    float lkt[4];
+#pragma unroll
+    for (int k = 2; k < 6; ++k) lkt[k - 2] = (float)(nx * (R)C(k, 1) - ny * (R)C(k, 0));
+    // increasing local position: every source lies above its destination and
+    // is read before it is overwritten
+#pragma unroll 1
+    for (int u = 1; u < 5; ++u)
+#pragma unroll 1
+        for (int w = 1; w <= u; ++w) C(u, w) = C(u + 1, w + 1);
+    C(0, 0) = ltt;
+#pragma unroll
+    for (int u = 1; u < 5; ++u) C(u, 0) = lkt[u - 1];
+}
+
+template <class R>
+__device__ __forceinline__ void slot_to_cartesian(const SlotRef &sl, R nx, R ny)
+{
+    float *c = sl.p + kSlotC * sl.stride;
+    auto C = [&](int i, int j) -> float & { return c[pk(i, j) * sl.stride]; };
+    // decreasing Cartesian position: every source lies below its destination
+#pragma unroll 1
+    for (int i = 5; i >= 2; --i) {
+#pragma unroll 1
+        for (int j = i; j >= 2; --j) C(i, j) = C(i - 1, j - 1);
+        const R lt = (R)C(i - 1, 0);
+        C(i, 1) = (float)(nx * lt);
+        C(i, 0) = (float)(-ny * lt);
+    }
+    const R ltt = (R)C(0, 0);
+    C(1, 1) = (float)(nx * nx * ltt);
+    C(1, 0) = (float)(-nx * ny * ltt);
+    C(0, 0) = (float)(ny * ny * ltt);
+}
+
+// C_l -= K C_l[{t, z}, :] in place on the slot's local block, row u's gain
+// (kt[u], kz[u]) against the original t and z columns: rows and, within a
+// row, columns descending read only entries not yet rewritten, except the
+// original (z, t) entry, kept for row t.
+template <class R>
+__device__ __forceinline__ void slot_local_downdate(const SlotRef &sl, const R kt[5], const R kz[5])
+{
+    float *c = sl.p + kSlotC * sl.stride;
+    auto C = [&](int i, int j) -> float & { return c[pk(i, j) * sl.stride]; };
+    const R zt = (R)C(1, 0);
+#pragma unroll 1
+    for (int u = 4; u >= 0; --u)
+#pragma unroll 1
+        for (int w = u; w >= 0; --w) {
+            const R ctw = (R)C(w, 0);
+            const R czw = w > 0 ? (R)C(w, 1) : u > 0 ? (R)C(1, 0) : zt;
+            C(u, w) = (float)((R)C(u, w) - (kt[u] * ctw + kz[u] * czw));
+        }
+}
+
+// Update in FP64 on the slot, in the local frame: S (n, t, z) and S^-1 by
+// adjugate, the gain's five non-radial rows, x += K r, C -= K C[{t, z}, :]
+// on the local block, chi2 = r^T S^-1 r; then the PSD repair: a local
+// variance that cancellation drove to zero or below is clamped to 1e-12 of
+// the local trace (correlations are left alone).  Returns 2, 3 (repaired) or
+// 1 (S not positive definite).
 static __device__ __noinline__ int update_fp64(float *slot_p, int stride)
 {
     const SlotRef sl{slot_p, stride};
-    const double a = (double)sl.c(0, 0) + sl.v(0), b = (double)sl.c(1, 0) + sl.v(1);
-    const double cc = (double)sl.c(1, 1) + sl.v(2), d = (double)sl.c(2, 0) + sl.v(3);
-    const double e = (double)sl.c(2, 1) + sl.v(4), f = (double)sl.c(2, 2) + sl.v(5);
+    const double X0 = sl.x(0), X1 = sl.x(1);
+    const double ir = 1.0 / sqrt(X0 * X0 + X1 * X1);
+    const double nx = X0 * ir, ny = X1 * ir;
+    slot_to_local<double>(sl, nx, ny);
+    auto L = [&](int i, int j) -> float & { return sl.c(i, j); };  // the slot's local block
+    const double v0 = sl.v(0), v1 = sl.v(1), v2 = sl.v(2), v3 = sl.v(3), v4 = sl.v(4), v5 = sl.v(5);
+    const double a = nx * nx * v0 + 2.0 * nx * ny * v1 + ny * ny * v2;
+    const double b = nx * ny * (v2 - v0) + (nx * nx - ny * ny) * v1;
+    const double cc = (double)L(0, 0) + (ny * ny * v0 - 2.0 * nx * ny * v1 + nx * nx * v2);
+    const double d = nx * v3 + ny * v4, e = (double)L(1, 0) + (nx * v4 - ny * v3), f = (double)L(1, 1) + v5;
     const double i00 = cc * f - e * e, i10 = d * e - b * f, i11 = a * f - d * d;
     const double i20 = b * e - cc * d, i21 = b * d - a * e, i22 = a * cc - b * b;
     const double det = a * i00 + b * i10 + d * i20;
-    if (!(a > 0.0) || !(i22 > 0.0) || !(det > 0.0)) return 1;
+    if (!(a > 0.0) || !(i22 > 0.0) || !(det > 0.0)) {
+        slot_to_cartesian<double>(sl, nx, ny);
+        return 1;
+    }
     const double id = 1.0 / det;
     const double s00 = i00 * id, s10 = i10 * id, s11 = i11 * id, s20 = i20 * id, s21 = i21 * id, s22 = i22 * id;
-    const double r0 = (double)sl.m(0) - sl.x(0), r1 = (double)sl.m(1) - sl.x(1), r2 = (double)sl.m(2) - sl.x(2);
-    const double q0 = s00 * r0 + s10 * r1 + s20 * r2, q1 = s10 * r0 + s11 * r1 + s21 * r2;
-    const double q2 = s20 * r0 + s21 * r1 + s22 * r2;
-    sl.chi2() = (float)(r0 * q0 + r1 * q1 + r2 * q2);
-    // rows 5..3, then 2..0 from a copy of the 3x3 block; within a row the
-    // columns descend, so every C[0:3, j] read is still the original value
-    double h[6];
-    for (int i = 5; i >= 0; --i) {
-        if (i == 2)
-            for (int k = 0; k < 6; ++k) h[k] = sl.p[(kSlotC + k) * stride];
-        auto src = [&](int k, int j) -> double { return i >= 3 ? (double)sl.c(k, j) : h[pk(k, j)]; };
-        const double c0 = src(i, 0), c1 = src(i, 1), c2 = src(i, 2);
-        const double k0 = c0 * s00 + c1 * s10 + c2 * s20;
-        const double k1 = c0 * s10 + c1 * s11 + c2 * s21;
-        const double k2 = c0 * s20 + c1 * s21 + c2 * s22;
-        sl.x(i) = (float)((double)sl.x(i) + k0 * r0 + k1 * r1 + k2 * r2);
-        for (int j = i; j >= 0; --j)
-            sl.c(i, j) = (float)((double)sl.c(i, j) - (k0 * src(0, j) + k1 * src(1, j) + k2 * src(2, j)));
+    const double d0 = (double)sl.m(0) - X0, d1 = (double)sl.m(1) - X1;
+    const double rn = nx * d0 + ny * d1, rt = nx * d1 - ny * d0, rz = (double)sl.m(2) - sl.x(2);
+    const double q0 = s00 * rn + s10 * rt + s20 * rz, q1 = s10 * rn + s11 * rt + s21 * rz;
+    const double q2 = s20 * rn + s21 * rt + s22 * rz;
+    sl.chi2() = (float)(rn * q0 + rt * q1 + rz * q2);
+    double kt[5], kz[5];
+#pragma unroll 1
+    for (int u = 0; u < 5; ++u) {
+        const double ct = L(u, 0), cz = L(u, 1);
+        kt[u] = ct * s11 + cz * s21;
+        kz[u] = ct * s21 + cz * s22;
+        const double dx = (ct * s10 + cz * s20) * rn + kt[u] * rt + kz[u] * rz;
+        if (u == 0) {
+            sl.x(0) = (float)(X0 - ny * dx);
+            sl.x(1) = (float)(X1 + nx * dx);
+        } else {
+            sl.x(u + 1) = (float)((double)sl.x(u + 1) + dx);
+        }
     }
+    slot_local_downdate<double>(sl, kt, kz);
     double tr = 0.0;
-    for (int i = 0; i < 6; ++i) tr += fabs((double)sl.c(i, i));
+#pragma unroll 1
+    for (int u = 0; u < 5; ++u) tr += fabs((double)L(u, u));
     bool rep = false;
-    for (int i = 0; i < 6; ++i)
-        if (!(sl.c(i, i) > 0.0f)) {
-            sl.c(i, i) = (float)(1e-12 * tr);
+#pragma unroll 1
+    for (int u = 0; u < 5; ++u)
+        if (!(L(u, u) > 0.0f)) {
+            L(u, u) = (float)(1e-12 * tr);
             rep = true;
         }
+    slot_to_cartesian<double>(sl, nx, ny);
     return rep ? 3 : 2;
 }
 
@@ -353,48 +437,65 @@ __device__ __forceinline__ ff ff_dot3(ff s0, ff s1, ff s2, float c0, float c1, f
     return fast_two_sum(t1.hi, err);
 }
 
-// Update on the slot with the gain formed in float-float: S = C_xx + V and
-// S^-1 by adjugate / determinant, each row K_i = C[i, 0:3] S^-1 rounded to
-// FP32 and applied at once (same row order as update_fp64), x += K r and
-// C -= K C[0:3, :] in FP32; chi2 = r^T S^-1 r with r = m - x formed exactly.
-// Returns 2, or 1 if S is not positive definite.
+// Update on the slot with the gain formed in float-float, in the local frame
+// of update_fp64: S (n, t, z) from the FP32 local entries (the entries that
+// add C and V exact two-sums), S^-1 by adjugate / determinant, the gain's rows
+// (C_ut, C_uz) S^-1 rounded to FP32, x += K r and C -= K C[{t, z}, :] in FP32;
+// chi2 = r^T S^-1 r.  Returns 2, or 1 if S is not positive definite.
 static __device__ __noinline__ int update_ff(float *slot_p, int stride)
 {
     const SlotRef sl{slot_p, stride};
-    const ff a = two_sum(sl.c(0, 0), sl.v(0)), b = two_sum(sl.c(1, 0), sl.v(1));
-    const ff cc = two_sum(sl.c(1, 1), sl.v(2)), d = two_sum(sl.c(2, 0), sl.v(3));
-    const ff e = two_sum(sl.c(2, 1), sl.v(4)), f = two_sum(sl.c(2, 2), sl.v(5));
+    const float X0 = sl.x(0), X1 = sl.x(1);
+    const float ir = rsqrtf(X0 * X0 + X1 * X1);
+    const float nx = X0 * ir, ny = X1 * ir;
+    slot_to_local<float>(sl, nx, ny);
+    auto L = [&](int i, int j) -> float & { return sl.c(i, j); };
+    const float v0 = sl.v(0), v1 = sl.v(1), v2 = sl.v(2), v3 = sl.v(3), v4 = sl.v(4);
+    const ff a{fmaf(nx * nx, v0, fmaf(2.0f * nx * ny, v1, ny * ny * v2)), 0.0f};
+    const ff b{fmaf(nx * ny, v2 - v0, (nx * nx - ny * ny) * v1), 0.0f};
+    const ff d{fmaf(nx, v3, ny * v4), 0.0f};
+    const ff cc = two_sum(L(0, 0), fmaf(ny * ny, v0, fmaf(-2.0f * nx * ny, v1, nx * nx * v2)));
+    const ff e = two_sum(L(1, 0), fmaf(nx, v4, -ny * v3)), f = two_sum(L(1, 1), sl.v(5));
     const ff i00 = ff_det2(cc, f, e, e), i10 = ff_det2(d, e, b, f), i11 = ff_det2(a, f, d, d);
     const ff i20 = ff_det2(b, e, cc, d), i21 = ff_det2(b, d, a, e), i22 = ff_det2(a, cc, b, b);
     const ff det = ff_add(ff_mul(a, i00), ff_add(ff_mul(b, i10), ff_mul(d, i20)));
-    if (!(a.hi > 0.0f) || !(i22.hi > 0.0f) || !(det.hi > 0.0f)) return 1;
+    if (!(a.hi > 0.0f) || !(i22.hi > 0.0f) || !(det.hi > 0.0f)) {
+        slot_to_cartesian<float>(sl, nx, ny);
+        return 1;
+    }
     // 1/det: one Newton step on the FP32 reciprocal, r + r (1 - det r)
     const float rc = 1.0f / det.hi;
     const ff one_minus = ff_add(ff{1.0f, 0.0f}, ff_neg(ff_mul(det, ff{rc, 0.0f})));
     const ff id = ff_add(ff{rc, 0.0f}, ff_mul(one_minus, ff{rc, 0.0f}));
     const ff s00 = ff_mul(i00, id), s10 = ff_mul(i10, id), s11 = ff_mul(i11, id);
     const ff s20 = ff_mul(i20, id), s21 = ff_mul(i21, id), s22 = ff_mul(i22, id);
-    const ff r0 = two_sum(sl.m(0), -sl.x(0)), r1 = two_sum(sl.m(1), -sl.x(1)), r2 = two_sum(sl.m(2), -sl.x(2));
-    const ff q0 = ff_add(ff_mul(s00, r0), ff_add(ff_mul(s10, r1), ff_mul(s20, r2)));
-    const ff q1 = ff_add(ff_mul(s10, r0), ff_add(ff_mul(s11, r1), ff_mul(s21, r2)));
-    const ff q2 = ff_add(ff_mul(s20, r0), ff_add(ff_mul(s21, r1), ff_mul(s22, r2)));
-    const ff chi = ff_add(ff_mul(r0, q0), ff_add(ff_mul(r1, q1), ff_mul(r2, q2)));
+    const float d0 = sl.m(0) - X0, d1 = sl.m(1) - X1;
+    const ff rn = two_sum(nx * d0, ny * d1), rt = two_sum(nx * d1, -ny * d0), rz = two_sum(sl.m(2), -sl.x(2));
+    const ff q0 = ff_add(ff_mul(s00, rn), ff_add(ff_mul(s10, rt), ff_mul(s20, rz)));
+    const ff q1 = ff_add(ff_mul(s10, rn), ff_add(ff_mul(s11, rt), ff_mul(s21, rz)));
+    const ff q2 = ff_add(ff_mul(s20, rn), ff_add(ff_mul(s21, rt), ff_mul(s22, rz)));
+    const ff chi = ff_add(ff_mul(rn, q0), ff_add(ff_mul(rt, q1), ff_mul(rz, q2)));
     sl.chi2() = __fadd_rn(chi.hi, chi.lo);
-    const float rr0 = __fadd_rn(r0.hi, r0.lo), rr1 = __fadd_rn(r1.hi, r1.lo), rr2 = __fadd_rn(r2.hi, r2.lo);
-    float h[6];
-    for (int i = 5; i >= 0; --i) {
-        if (i == 2)
-            for (int k = 0; k < 6; ++k) h[k] = sl.p[(kSlotC + k) * stride];
-        auto src = [&](int k, int j) -> float { return i >= 3 ? sl.c(k, j) : h[pk(k, j)]; };
-        const float c0 = src(i, 0), c1 = src(i, 1), c2 = src(i, 2);
-        const ff k0f = ff_dot3(s00, s10, s20, c0, c1, c2);
-        const ff k1f = ff_dot3(s10, s11, s21, c0, c1, c2);
-        const ff k2f = ff_dot3(s20, s21, s22, c0, c1, c2);
-        const float k0 = __fadd_rn(k0f.hi, k0f.lo), k1 = __fadd_rn(k1f.hi, k1f.lo), k2 = __fadd_rn(k2f.hi, k2f.lo);
-        sl.x(i) = fmaf(k0, rr0, fmaf(k1, rr1, fmaf(k2, rr2, sl.x(i))));
-        for (int j = i; j >= 0; --j)
-            sl.c(i, j) = fmaf(-k0, src(0, j), fmaf(-k1, src(1, j), fmaf(-k2, src(2, j), sl.c(i, j))));
+    const float rrn = __fadd_rn(rn.hi, rn.lo), rrt = __fadd_rn(rt.hi, rt.lo), rrz = __fadd_rn(rz.hi, rz.lo);
+    const ff zero{0.0f, 0.0f};
+    float kt[5], kz[5];
+    for (int u = 0; u < 5; ++u) {
+        const float ct = L(u, 0), cz = L(u, 1);
+        const ff knf = ff_dot3(s10, s20, zero, ct, cz, 0.0f);
+        const ff ktf = ff_dot3(s11, s21, zero, ct, cz, 0.0f);
+        const ff kzf = ff_dot3(s21, s22, zero, ct, cz, 0.0f);
+        kt[u] = __fadd_rn(ktf.hi, ktf.lo);
+        kz[u] = __fadd_rn(kzf.hi, kzf.lo);
+        const float dx = fmaf(__fadd_rn(knf.hi, knf.lo), rrn, fmaf(kt[u], rrt, kz[u] * rrz));
+        if (u == 0) {
+            sl.x(0) = fmaf(-ny, dx, X0);
+            sl.x(1) = fmaf(nx, dx, X1);
+        } else {
+            sl.x(u + 1) += dx;
+        }
     }
+    slot_local_downdate<float>(sl, kt, kz);
+    slot_to_cartesian<float>(sl, nx, ny);
     return 2;
 }
 
@@ -405,7 +506,7 @@ static __device__ __noinline__ int update_ext(float *slot, int stride, int kind)
 
 struct Routing {
     int mode;        // 0 FP32, 1 routed
-    float cond2_max; // squared condition threshold
+    float det_min;   // 27 / (4 cond_max): the least det of S's correlation matrix done in FP32
     float pt_lo, pt_hi;
     float gain_max;  // information-gain threshold: C_ii / V_ii above it routes the gain
 };
@@ -427,9 +528,10 @@ struct Routing {
 // updated, each from the t and z columns.  dx and C are rotated back to x/y.
 // Routing (mode 1):
 //   * the whole update is redone in FP64 with a PSD repair (update_fp64) when
-//     S is not positive definite in FP32, when its Frobenius condition
-//     estimate ||S||_F ||S^-1||_F exceeds the threshold, or when pT lies
-//     outside [pt_lo, pt_hi];
+//     S is not positive definite in FP32, when the determinant of its
+//     correlation matrix R = D^-1/2 S D^-1/2 (D = diag S) is below
+//     27 / (4 cond_max), which keeps cond_2(R) <= cond_max on the FP32 path,
+//     or when pT lies outside [pt_lo, pt_hi];
 //   * with gain_max > 0, the gain is formed in float-float (update_ff) when
 //     C_ii > gain_max V_ii for some i.  Float-float runs on the FP32 pipe,
 //     which on this part is 64 times wider than the FP64 one.
@@ -458,10 +560,13 @@ __device__ __forceinline__ int update(float x[6], float c[21], const float m[3],
     const bool pd = a > 0.0f && i22 > 0.0f && det > 0.0f;
     int kind = 0;
     if (rt.mode == 1) {
-        const float sS = a * a + cc * cc + f * f + 2.0f * (b * b + d * d + e * e);
-        const float sI = i00 * i00 + i11 * i11 + i22 * i22 + 2.0f * (i10 * i10 + i20 * i20 + i21 * i21);
+        // S's correlation matrix R = D^-1/2 S D^-1/2 (D = diag S): the rounding
+        // of the adjugate's cofactors grows with its condition, not with the
+        // spread of S's diagonal (V_nn << C_zz is harmless).  With eigenvalues
+        // summing to 3, det R >= 27 / (4 cond_max) bounds cond_2(R) by cond_max.
+        const bool ill = !pd || det <= rt.det_min * (a * cc * f);
         const float pt2 = x[3] * x[3] + x[4] * x[4];
-        if (!pd || sS * sI > rt.cond2_max * det * det || pt2 < rt.pt_lo * rt.pt_lo || pt2 > rt.pt_hi * rt.pt_hi)
+        if (ill || pt2 < rt.pt_lo * rt.pt_lo || pt2 > rt.pt_hi * rt.pt_hi)
             kind = 2;
         else if (rt.gain_max > 0.0f &&
                  (c[0] > rt.gain_max * v[0] || c[2] > rt.gain_max * v[2] || c[5] > rt.gain_max * v[5]))
