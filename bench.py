@@ -186,9 +186,36 @@ def cpu_baseline(batch, n_sample: int):
                          batch.hit_pos[:, :, sub], batch.hit_cov[:, :, sub], batch.hit_mask[sub],
                          threads=threads)
     dt = time.perf_counter() - t0
+    n1 = min(n_sample, 200_000)  # one core on a smaller sample
+    sub1 = slice(0, n1)
+    t1 = time.perf_counter()
+    kf_oracle.fit_arrays(f32(g.radii), f32(g.x_over_x0), float(np.float32(g.z_half)), float(np.float32(g.bz)),
+                         batch.seed_state[:, sub1], batch.seed_cov[:, sub1], batch.charge[sub1],
+                         batch.hit_pos[:, :, sub1], batch.hit_cov[:, :, sub1], batch.hit_mask[sub1], threads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": n_sample / dt, "unit": "tracks/s", "cores": threads, "kind": "oracle",
             "sample": f"first {n_sample} tracks of the workload, FP64 C oracle split over {threads} threads "
-                      f"({dt:.2f} s wall)"}
+                      f"({dt:.2f} s wall)",
+            "single_core": {"value": n1 / dt1, "unit": "tracks/s", "sample": f"first {n1} tracks, 1 thread"},
+            "cpu_model": cpu_model()}
+
+
+def cpu_model() -> str | None:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
 
 
 def run_reference(args, rank, world):
