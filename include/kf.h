@@ -171,6 +171,29 @@ int kf_fit_tracks(kf_context *ctx, const kf_geometry *geom, int64_t n_tracks,
                   uint32_t *out_flags, const kf_options *opt, kf_stream stream);
 
 /*
+ * kf_fit_tracks from and to host memory (the paper's events live on the host;
+ * Section 4.2 streams several events to the GPU concurrently, and Section 4.3
+ * finds host-device transfers about half of the GPU build's wall time).  The
+ * batch is cut into chunks of chunk_tracks tracks (0: 262,144); each chunk is
+ * copied in, fitted (the persistent fit, all of the chunk's events in one
+ * launch) and copied out on one of three internal streams, so the transfers
+ * of one chunk overlap the fit of another.
+ *
+ * Arrays: the layouts of kf_fit_tracks, all in host memory owned by the
+ * caller, pinned (cudaMallocHost / cudaHostRegister) for full speed; pageable
+ * memory works through the driver's staging, slower.  The call returns when
+ * every output is in host memory.  Device staging (about 3 x 591 B x
+ * chunk_tracks at 10 layers) is kept by the context and grown on demand
+ * (KF_ERR_NOMEM).  opt->launch_mode is ignored; the shape is
+ * opt->tracks_per_block / opt->reg_cap when set, else 64 tracks per block and
+ * 128 registers (no tuning runs).
+ */
+int kf_fit_tracks_host(kf_context *ctx, const kf_geometry *geom, int64_t n_tracks, const float *seed_state,
+                       const float *seed_cov, const int8_t *charge, const float *hit_pos, const float *hit_cov,
+                       const uint32_t *hit_mask, float *out_state, float *out_cov, float *out_chi2,
+                       int16_t *out_ndof, uint32_t *out_flags, int64_t chunk_tracks, const kf_options *opt);
+
+/*
  * Combinatorial track building, the clone engine (Sections 3, 3.1 and 4.3):
  * starting from each seed, layer by layer, every candidate is propagated to
  * the layer (same steps as kf_fit_tracks: helix, transport, scattering) and

@@ -20,20 +20,6 @@ using namespace kf;
 
 namespace {
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 struct GraphEntry {
     FitGeom g;
     Routing rt;
@@ -59,6 +45,7 @@ struct kf_context {
     uint64_t clock = 0;
     kf::BuildState *build = nullptr;
     kf::MlpState *mlp = nullptr;
+    kf::HostPipe *host = nullptr;
 };
 
 namespace kf {
@@ -83,6 +70,7 @@ int context_device(const kf_context *ctx) { return ctx->device; }
 int context_sm_count(const kf_context *ctx) { return ctx->sm_count; }
 BuildState *&context_build_state(kf_context *ctx) { return ctx->build; }
 MlpState *&context_mlp_state(kf_context *ctx) { return ctx->mlp; }
+HostPipe *&context_host_state(kf_context *ctx) { return ctx->host; }
 
 int check_geometry(kf_context *ctx, const kf_geometry *geom, FitGeom *g)
 {
@@ -208,6 +196,7 @@ void kf_context_destroy(kf_context *ctx)
     for (auto &e : ctx->graphs) cudaGraphExecDestroy(e.exec);
     kf::destroy_build_state(ctx->build);
     kf::destroy_mlp_state(ctx->mlp);
+    kf::destroy_host_state(ctx->host);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     cudaFree(ctx->d_counter);
     delete ctx;

@@ -13,6 +13,8 @@ struct BuildState;  // device scratch of the build step (kf_build.cu)
 void destroy_build_state(BuildState *s);
 struct MlpState;  // proposal network scratch and weights (kf_mlp.cu)
 void destroy_mlp_state(MlpState *s);
+struct HostPipe;  // staging buffers and streams of the host-buffer fit (kf_host.cu)
+void destroy_host_state(HostPipe *s);
 bool proposal_loaded(kf_context *ctx);
 // device copies of the loaded weights (the layouts of kf_mlp.cuh)
 void proposal_weights(kf_context *ctx, const __nv_bfloat16 **W1, const __nv_bfloat16 **W2, const float **w32);
@@ -27,5 +29,22 @@ int context_device(const kf_context *ctx);
 int context_sm_count(const kf_context *ctx);
 BuildState *&context_build_state(kf_context *ctx);
 MlpState *&context_mlp_state(kf_context *ctx);
+HostPipe *&context_host_state(kf_context *ctx);
+
+// Make `dev` current for a scope, restoring the caller's device after.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 
 }  // namespace kf

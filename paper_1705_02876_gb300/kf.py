@@ -78,6 +78,8 @@ def load() -> ctypes.CDLL:
         L.kf_last_error.restype = ctypes.c_char_p
         L.kf_fit_tracks.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int64, _vp, ctypes.c_int] + \
             [_vp] * 11 + [ctypes.POINTER(Options), _vp]
+        L.kf_fit_tracks_host.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int64] + [_vp] * 11 + \
+            [ctypes.c_int64, ctypes.POINTER(Options)]
         L.kf_fit_tuned_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.kf_build_tracks.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int, _vp, _vp, _vp,
@@ -216,6 +218,59 @@ def fit_tracks(ctx: Context, geom: GeometryArgs, seed_state, seed_cov, charge, h
                               ctypes.byref(opt) if opt is not None else None, s.cuda_stream)
     ctx.check(rc, "kf_fit_tracks")
     return out
+
+
+def _host_ptr(t: torch.Tensor, dtype, shape, name=""):
+    if t.dtype != dtype or t.is_cuda or not t.is_contiguous():
+        raise KFError(f"{name}: expected a contiguous host {dtype} tensor, got {t.dtype} "
+                      f"{'cuda' if t.is_cuda else 'cpu'} contiguous={t.is_contiguous()}")
+    if tuple(t.shape) != tuple(shape):
+        raise KFError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
+    return t.data_ptr() if t.numel() else None
+
+
+def fit_outputs_host(n_tracks: int, pin: bool = True) -> dict:
+    e = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=pin)
+    return dict(state=e((6, n_tracks), torch.float32), cov=e((21, n_tracks), torch.float32),
+                chi2=e((n_tracks,), torch.float32), ndof=e((n_tracks,), torch.int16),
+                flags=e((n_tracks,), torch.int32))
+
+
+def fit_tracks_host(ctx: Context, geom: GeometryArgs, seed_state, seed_cov, charge, hit_pos, hit_cov, hit_mask,
+                    opt: Options | None = None, out: dict | None = None, chunk_tracks: int = 0) -> dict:
+    """kf_fit_tracks_host on host (CPU, ideally pinned) tensors: copies in,
+    fits and copies out in overlapping chunks; returns when the outputs are
+    filled."""
+    T = int(charge.shape[0])
+    L = geom.struct.n_layers
+    if out is None:
+        out = fit_outputs_host(T)
+    args = [
+        _host_ptr(seed_state, torch.float32, (6, T), "seed_state"),
+        _host_ptr(seed_cov, torch.float32, (21, T), "seed_cov"),
+        _host_ptr(charge, torch.int8, (T,), "charge"),
+        _host_ptr(hit_pos, torch.float32, (L, 3, T), "hit_pos"),
+        _host_ptr(hit_cov, torch.float32, (L, 6, T), "hit_cov"),
+        _host_ptr(hit_mask, torch.int32, (T,), "hit_mask"),
+        _host_ptr(out["state"], torch.float32, (6, T), "out_state"),
+        _host_ptr(out["cov"], torch.float32, (21, T), "out_cov"),
+        _host_ptr(out["chi2"], torch.float32, (T,), "out_chi2"),
+        _host_ptr(out["ndof"], torch.int16, (T,), "out_ndof"),
+        _host_ptr(out["flags"], torch.int32, (T,), "out_flags"),
+    ]
+    rc = load().kf_fit_tracks_host(ctx.handle, ctypes.byref(geom.struct), T, *args, int(chunk_tracks),
+                                   ctypes.byref(opt) if opt is not None else None)
+    ctx.check(rc, "kf_fit_tracks_host")
+    return out
+
+
+def to_host(batch, pin: bool = True) -> dict:
+    """A ``synth.FitBatch``'s input arrays as (pinned) host tensors."""
+    t = lambda a, dt: (torch.from_numpy(np.ascontiguousarray(a)).to(dtype=dt)).pin_memory() if pin else \
+        torch.from_numpy(np.ascontiguousarray(a)).to(dtype=dt)
+    return dict(seed_state=t(batch.seed_state, torch.float32), seed_cov=t(batch.seed_cov, torch.float32),
+                charge=t(batch.charge, torch.int8), hit_pos=t(batch.hit_pos, torch.float32),
+                hit_cov=t(batch.hit_cov, torch.float32), hit_mask=t(batch.hit_mask.view(np.int32), torch.int32))
 
 
 def build_tracks(ctx: Context, geom: GeometryArgs, hit_offsets, hit_pos, hit_cov, seed_event, seed_state,
