@@ -224,7 +224,7 @@ int kf_fit_tracks_host(kf_context *ctx, const kf_geometry *geom, int64_t n_track
  *   out_chi2 [S][N], out_nhits [S][N] (-1 for an empty slot),
  *   out_state [6][S*N], out_cov [21][S*N] packed, out_flags [S][N];
  *   N = opt->max_cands (1..8).
- * Scratch: 12 bytes per hit plus 4 (n_phi_bins n_z_bins + 1) bytes per
+ * Scratch: 16 bytes per hit plus 4 (n_phi_bins n_z_bins + 1) bytes per
  * (event, layer), kept by the context and grown on demand (KF_ERR_NOMEM).
  * The call copies hit_offsets to the device and waits for that copy.
  */

@@ -25,8 +25,7 @@ namespace kf {
 
 struct BuildState {
     size_t hit_capacity = 0, bin_capacity = 0, seg_capacity = 0;
-    float *bphi = nullptr, *bz = nullptr;
-    int32_t *bidx = nullptr;
+    float4 *bkey = nullptr;  // binned hits: (phi, z, index within the segment as bits, 0)
     int32_t *bin_off = nullptr;
     int64_t *seg_off = nullptr;  // device copy of the segment bounds [n_seg + 1]
     int64_t *ev_off = nullptr;   // device copy of hit_offsets [n_events][L + 1]
@@ -36,9 +35,7 @@ struct BuildState {
 void destroy_build_state(BuildState *s)
 {
     if (!s) return;
-    cudaFree(s->bphi);
-    cudaFree(s->bz);
-    cudaFree(s->bidx);
+    cudaFree(s->bkey);
     cudaFree(s->bin_off);
     cudaFree(s->seg_off);
     cudaFree(s->ev_off);
@@ -66,12 +63,13 @@ __device__ __forceinline__ int z_bin(float z, const BinGrid &bg)
 }
 
 // One block per (event, layer) segment: count hits per bin in shared memory,
-// scan, scatter phi, z and the hit's index within the segment into the same
-// positions of the binned arrays, bin by bin (bin = iz * n_phi + iphi).
+// scan, scatter each hit's key (phi, z, index within the segment) bin by bin
+// (bin = iz * n_phi + iphi).  A key is one 16-byte store here and one 16-byte
+// load in the window scan: the destinations are random at a few hits per bin,
+// so each key costs one memory sector, not three.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) bin_hits_kernel(const int64_t *seg_off, const float *hit_pos, int64_t H,
-                                                           BinGrid bg, float *bphi, float *bz, int32_t *bidx,
-                                                           int32_t *bin_off)
+                                                           BinGrid bg, float4 *bkey, int32_t *bin_off)
 {
     extern __shared__ int cnt[];
     __shared__ int warp_sums[THREADS / 32];
@@ -123,9 +121,7 @@ __global__ void __launch_bounds__(THREADS) bin_hits_kernel(const int64_t *seg_of
         const float x = hit_pos[h], y = hit_pos[H + h], z = hit_pos[2 * H + h];
         const float phi = atan2f(y, x);
         const int p = atomicAdd(&cnt[z_bin(z, bg) * bg.n_phi + phi_bin(phi, bg.n_phi)], 1);
-        bphi[lo + p] = phi;
-        bz[lo + p] = z;
-        bidx[lo + p] = (int32_t)(h - lo);
+        bkey[lo + p] = make_float4(phi, z, __int_as_float((int)(h - lo)), 0.0f);
     }
 }
 
@@ -139,8 +135,8 @@ struct BuildParams {
     int n_events;
     const int64_t *ev_off;  // [E][L + 1]
     const float *hit_pos, *hit_cov;
-    const float *bphi, *bz;
-    const int32_t *bidx, *bin_off;
+    const float4 *bkey;
+    const int32_t *bin_off;
     const int32_t *seed_event;
     const float *seed_state, *seed_cov;
     const int8_t *seed_charge;
@@ -221,8 +217,9 @@ struct WindowCursor {
         for (;;) {
             while (hb < h1) {
                 const int64_t q = w.seg_lo + hb++;
-                if (fabsf(wrap_pi(p.bphi[q] - w.phic)) <= w.dphi && fabsf(p.bz[q] - w.z) <= w.dz)
-                    return (uint32_t)p.bidx[q];
+                const float4 k = p.bkey[q];
+                if (fabsf(wrap_pi(k.x - w.phic)) <= w.dphi && fabsf(k.y - w.z) <= w.dz)
+                    return (uint32_t)__float_as_int(k.z);
             }
             if (iz > w.iz1) return kNoKey;
             if (++k >= w.nphi) {
@@ -736,13 +733,7 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
         cap = need;
         return true;
     };
-    size_t hcap = st->hit_capacity;
-    bool ok = grow((void **)&st->bphi, hcap, (size_t)n_hits, sizeof(float));
-    size_t hcap2 = st->hit_capacity;
-    ok = ok && grow((void **)&st->bz, hcap2, (size_t)n_hits, sizeof(float));
-    size_t hcap3 = st->hit_capacity;
-    ok = ok && grow((void **)&st->bidx, hcap3, (size_t)n_hits, sizeof(int32_t));
-    if (ok) st->hit_capacity = std::max(st->hit_capacity, (size_t)n_hits);
+    bool ok = grow((void **)&st->bkey, st->hit_capacity, (size_t)n_hits, sizeof(float4));
     ok = ok && grow((void **)&st->bin_off, st->bin_capacity, n_seg * (nb + 1), sizeof(int32_t));
     ok = ok && grow((void **)&st->seg_off, st->seg_capacity, n_seg + 1, sizeof(int64_t));
     ok = ok && grow((void **)&st->ev_off, st->ev_capacity, (size_t)n_events * (L + 1), sizeof(int64_t));
@@ -767,8 +758,8 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
         cudaFuncSetAttribute(bin_hits_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16385 * 4);
         attr_set = true;
     }
-    bin_hits_kernel<1024><<<(unsigned)n_seg, 1024, bin_smem, stream>>>(st->seg_off, hit_pos, n_hits, bg, st->bphi,
-                                                                        st->bz, st->bidx, st->bin_off);
+    bin_hits_kernel<1024><<<(unsigned)n_seg, 1024, bin_smem, stream>>>(st->seg_off, hit_pos, n_hits, bg, st->bkey,
+                                                                        st->bin_off);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(ctx, e, "binning launch");
 
     BuildParams p;
@@ -786,9 +777,7 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
     p.ev_off = st->ev_off;
     p.hit_pos = hit_pos;
     p.hit_cov = hit_cov;
-    p.bphi = st->bphi;
-    p.bz = st->bz;
-    p.bidx = st->bidx;
+    p.bkey = st->bkey;
     p.bin_off = st->bin_off;
     p.seed_event = seed_event;
     p.seed_state = seed_state;
