@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--build-events", type=int, default=64, help="events of the build workload (0: skip it)")
     p.add_argument("--build-steps", type=int, default=10)
     p.add_argument("--no-ragged", action="store_true", help="skip the ragged-batching comparison")
+    p.add_argument("--no-transport", action="store_true", help="skip the batched 6x6 transport comparison")
     p.add_argument("--train-events", type=int, default=3, help="events logged to train the proposal")
     p.add_argument("--train-epochs", type=int, default=4)
     return p.parse_args()
@@ -414,6 +415,47 @@ def bench_ragged(args, kf, ctx, dev, stream, rank):
     return res
 
 
+def bench_transport(args, kf, ctx, dev, stream):
+    """Batched 6x6 covariance transport C <- J C J^T (the paper's Section 4.1
+    study of many small matrix products): the library's one-thread-per-matrix
+    kernel on SoA data against two batched cuBLAS products (torch.bmm, FP32,
+    TF32 off) on [n][6][6] data, at growing batch sizes."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    rng = np.random.default_rng(11)
+    res = {"form": "ours: kf_transport_batch, J [36][n] + packed C [21][n] in registers, 312 B per matrix; "
+                   "cublas: bmm(bmm(J, C), J^T) on [n][6][6], 576 B per matrix", "sizes": {}}
+    for n in (10_000, 100_000, 1_000_000, 10_000_000):
+        J = torch.from_numpy((np.eye(6, dtype=np.float32).reshape(36, 1) +
+                              0.1 * rng.standard_normal((36, n), dtype=np.float32))).to(dev)
+        C0 = torch.from_numpy(rng.standard_normal((21, n), dtype=np.float32)).to(dev)
+        C = C0.clone()
+        Ja = J.T.reshape(n, 6, 6).contiguous()
+        Ca = torch.randn(n, 6, 6, device=dev)
+        Jt = Ja.transpose(1, 2)
+
+        def timed(fn, reps):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        reps = max(5, int(2e8 // (n * 312)))
+        ms = timed(lambda: kf.transport_batch(ctx, J, C, stream=stream), reps)
+        ms_cb = timed(lambda: torch.bmm(torch.bmm(Ja, Ca), Jt), reps)
+        res["sizes"][str(n)] = {
+            "ours": {"matrices_per_s": n / (ms * 1e-3), "ms": ms, "hbm_gbs": 312 * n / (ms * 1e-3) / 1e9},
+            "cublas": {"matrices_per_s": n / (ms_cb * 1e-3), "ms": ms_cb}}
+        del J, C0, C, Ja, Ca, Jt
+    return res
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
@@ -555,6 +597,8 @@ def main():
         line["build"] = bench_build(args, kf, ctx, dev, stream, rank, world)
     if not args.no_ragged:
         line["ragged"] = bench_ragged(args, kf, ctx, dev, stream, rank)
+    if not args.no_transport:
+        line["transport6x6"] = bench_transport(args, kf, ctx, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch, T)
     if rank == 0:

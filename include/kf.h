@@ -309,6 +309,19 @@ int kf_proposal_load(kf_context *ctx, const float *weights, kf_stream stream);
 int kf_proposal_score(kf_context *ctx, const float *features, int64_t n, float *logits, kf_stream stream);
 
 /*
+ * Batched covariance transport C <- J C J^T for n general (dense) 6x6
+ * Jacobians: the batched small-matrix product the paper measures on the GPU
+ * (Section 4.1, 6x6 products in a Matriplex-style layout against batched
+ * cuBLAS).  One thread per matrix, J and C in registers; no structure of J is
+ * assumed (the fit's own transport exploits it).
+ *
+ * J: device float [36][n], J[i][j] of matrix t at (6 i + j) n + t.
+ * C: device float [21][n], packed lower triangle, read and overwritten.
+ * n may be 0.  KF_ERR_ARG on a NULL or misaligned pointer.
+ */
+int kf_transport_batch(kf_context *ctx, int64_t n, const float *J, float *C, kf_stream stream);
+
+/*
  * Launch shape the autotuner picked for the persistent fit of n_layers layers
  * and a batch of n_tracks' size class (powers of two), once a KF_LAUNCH_AUTO
  * fit of that class has run on ctx.  Writes tracks per block and the register

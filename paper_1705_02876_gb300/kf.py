@@ -80,6 +80,7 @@ def load() -> ctypes.CDLL:
             [_vp] * 11 + [ctypes.POINTER(Options), _vp]
         L.kf_fit_tracks_host.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int64] + [_vp] * 11 + \
             [ctypes.c_int64, ctypes.POINTER(Options)]
+        L.kf_transport_batch.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp]
         L.kf_fit_tuned_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.kf_build_tracks.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int, _vp, _vp, _vp,
@@ -387,6 +388,15 @@ def proposal_score(ctx: Context, features, stream=None):
                                   logits.data_ptr() if n else None, _cur_stream(features, stream))
     ctx.check(rc, "kf_proposal_score")
     return logits
+
+
+def transport_batch(ctx: Context, J, C, stream=None):
+    """kf_transport_batch: C [21][n] <- J C J^T in place, J [36][n] (CUDA tensors)."""
+    n = int(C.shape[1])
+    rc = load().kf_transport_batch(ctx.handle, n, _ptr(J, torch.float32, (36, n), "J"),
+                                   _ptr(C, torch.float32, (21, n), "C"), _cur_stream(C, stream))
+    ctx.check(rc, "kf_transport_batch")
+    return C
 
 
 def to_device(batch, device="cuda") -> dict:
