@@ -76,6 +76,12 @@ def lib():
             _lib.orc_build_tracks_ex.restype = ctypes.c_int
             _lib.orc_build_tracks_ex.argtypes = _lib.orc_build_tracks.argtypes + \
                 [ctypes.c_void_p] * 3 + [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+            _lib.orc_smooth_tracks.restype = ctypes.c_int
+            _lib.orc_smooth_tracks.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_int64, ctypes.c_int64, ctypes.c_int64] + \
+                [ctypes.c_void_p] * 10
+            _lib.orc_propagate_back.restype = ctypes.c_int
+            _lib.orc_propagate_back.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
             _lib.orc_bf16_round.restype = ctypes.c_double
             _lib.orc_bf16_round.argtypes = [ctypes.c_double]
             _lib.orc_mlp_logit.restype = ctypes.c_double
@@ -209,6 +215,50 @@ def fit_batch_exact(batch, threads=None, per_layer=False):
     return fit_arrays(g.radii, g.x_over_x0, g.z_half, g.bz, e["seed_state"], e["seed_cov"],
                       batch.charge, e["hit_pos"], e["hit_cov"], batch.hit_mask, threads,
                       per_layer, None, double_inputs=True)
+
+
+def smooth_batch(batch, threads=None, track_range=None):
+    """Forward fit + Rauch-Tung-Striebel smoother of a ``synth.FitBatch`` in
+    FP64.  Returns state [L][6][T] and cov [L][21][T] (smoothed, NaN where the
+    fit did not reach), filt_state [L][6][T] (forward filter) and reached [T]."""
+    g = batch.geom
+    T = batch.n_tracks
+    L = g.n_layers
+    f32 = lambda v: np.asarray(v, dtype=np.float32).astype(np.float64)
+    arr = lambda a, dt: np.ascontiguousarray(a, dtype=dt)
+    ss, sc = arr(batch.seed_state, np.float32), arr(batch.seed_cov, np.float32)
+    ch, hm = arr(batch.charge, np.int8), arr(batch.hit_mask, np.uint32)
+    hp, hc = arr(batch.hit_pos, np.float32), arr(batch.hit_cov, np.float32)
+    out = dict(state=np.zeros((L, 6, T)), cov=np.zeros((L, 21, T)), filt_state=np.zeros((L, 6, T)),
+               reached=np.zeros(T, dtype=np.int32))
+    rad, xx0 = f32(g.radii), f32(g.x_over_x0)
+    t0, t1 = track_range if track_range is not None else (0, T)
+    threads = threads or os.cpu_count() or 1
+    chunk = max(1, -(-(t1 - t0) // (threads * 4)))
+    ranges = [(a, min(a + chunk, t1)) for a in range(t0, t1, chunk)]
+
+    def run(rg):
+        rc = lib().orc_smooth_tracks(L, _p(rad), _p(xx0), float(np.float32(g.z_half)), float(np.float32(g.bz)),
+                                     rg[0], rg[1], T, ss.ctypes.data, sc.ctypes.data, ch.ctypes.data,
+                                     hp.ctypes.data, hc.ctypes.data, hm.ctypes.data, out["state"].ctypes.data,
+                                     out["cov"].ctypes.data, out["filt_state"].ctypes.data,
+                                     out["reached"].ctypes.data)
+        assert rc == 0
+
+    if len(ranges) <= 1:
+        for rg in ranges:
+            run(rg)
+    else:
+        with cf.ThreadPoolExecutor(threads) as ex:
+            list(ex.map(run, ranges))
+    return out
+
+
+def propagate_back(state, q, bz, r):
+    """The crossing of radius r backwards along the helix (None if unreachable)."""
+    out = np.zeros(6)
+    rc = lib().orc_propagate_back(_p(_f64(state).copy()), int(q), float(bz), float(r), _p(out))
+    return None if rc else out
 
 
 # ---------------------------------------------------------------------------
