@@ -415,6 +415,38 @@ def bench_ragged(args, kf, ctx, dev, stream, rank):
     return res
 
 
+def bench_smoother(args, kf, ctx, dev, stream, batch, d_in):
+    """The fit followed by the Rauch-Tung-Striebel smoother on the fit
+    workload: smoothed state and covariance after every layer."""
+    import torch
+    geom = kf.GeometryArgs.of(batch.geom)
+    out = None
+
+    def step():
+        nonlocal out
+        out = kf.smooth_tracks(ctx, geom, **d_in, out=out, stream=stream)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    n = 10
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(n):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / n
+    T, L = batch.n_tracks, batch.geom.n_layers
+    # DRAM bytes per track: fit inputs 473, per layer 160 B of scratch written and
+    # read back, 108 B of filtered estimates written and read back, 108 B of
+    # smoothed estimates written
+    per_track = 113 + 36 * L + L * (2 * 160 + 2 * 108 + 108)
+    return {"value": T / (ms * 1e-3), "unit": "tracks/s", "ms_per_step": ms, "layers": L,
+            "hbm_gbs_algorithmic": per_track * T / (ms * 1e-3) / 1e9,
+            "form": "one thread per track: routed forward fit keeping every layer, then the backward pass"}
+
+
 def bench_transport(args, kf, ctx, dev, stream):
     """Batched 6x6 covariance transport C <- J C J^T (the paper's Section 4.1
     study of many small matrix products): the library's one-thread-per-matrix
@@ -599,6 +631,7 @@ def main():
         line["ragged"] = bench_ragged(args, kf, ctx, dev, stream, rank)
     if not args.no_transport:
         line["transport6x6"] = bench_transport(args, kf, ctx, dev, stream)
+    line["smoother"] = bench_smoother(args, kf, ctx, dev, stream, batch, d_in)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch, T)
     if rank == 0:

@@ -309,6 +309,32 @@ int kf_proposal_load(kf_context *ctx, const float *weights, kf_stream stream);
 int kf_proposal_score(kf_context *ctx, const float *features, int64_t n, float *logits, kf_stream stream);
 
 /*
+ * The fit followed by the Kalman smoother: at every layer the estimate that
+ * uses all of the track's hits (Section 2 names a final fit with a smoother,
+ * after building, as the step giving each track's best parameters).  The
+ * forward pass is kf_fit_tracks' per-track fit (routed precision as set in
+ * opt); the backward pass is the Rauch-Tung-Striebel recursion in each layer's
+ * local coordinates (t, z, px, py, pz), where the covariances are positive
+ * definite, with Cp^-1 from a Cholesky factorisation scaled to unit diagonal.
+ *
+ * Inputs: the layouts of kf_fit_tracks (device, caller-owned).
+ * Outputs (device, caller-owned): out_state [L][6][T] and out_cov [L][21][T]
+ *   packed, the smoothed estimate after every layer the fit reached, NaN on
+ *   the other layers and on every layer of a track with a non-finite input;
+ *   out_reached [T] (int16) the number of layers reached (0 for such a
+ *   track); out_flags [T] as kf_fit_tracks (INVERSION_FAILED also when a
+ *   predicted covariance could not be factorised, the layer then keeping its
+ *   filtered estimate).
+ * Scratch: 136 L bytes per track, kept by the context (KF_ERR_NOMEM).
+ * One thread per track, one launch; opt->launch_mode and the shape are
+ * ignored.
+ */
+int kf_smooth_tracks(kf_context *ctx, const kf_geometry *geom, int64_t n_tracks, const float *seed_state,
+                     const float *seed_cov, const int8_t *charge, const float *hit_pos, const float *hit_cov,
+                     const uint32_t *hit_mask, float *out_state, float *out_cov, int16_t *out_reached,
+                     uint32_t *out_flags, const kf_options *opt, kf_stream stream);
+
+/*
  * Batched covariance transport C <- J C J^T for n general (dense) 6x6
  * Jacobians: the batched small-matrix product the paper measures on the GPU
  * (Section 4.1, 6x6 products in a Matriplex-style layout against batched

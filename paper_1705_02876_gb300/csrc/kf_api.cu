@@ -46,6 +46,7 @@ struct kf_context {
     kf::BuildState *build = nullptr;
     kf::MlpState *mlp = nullptr;
     kf::HostPipe *host = nullptr;
+    kf::SmoothState *smooth = nullptr;
 };
 
 namespace kf {
@@ -71,6 +72,7 @@ int context_sm_count(const kf_context *ctx) { return ctx->sm_count; }
 BuildState *&context_build_state(kf_context *ctx) { return ctx->build; }
 MlpState *&context_mlp_state(kf_context *ctx) { return ctx->mlp; }
 HostPipe *&context_host_state(kf_context *ctx) { return ctx->host; }
+SmoothState *&context_smooth_state(kf_context *ctx) { return ctx->smooth; }
 
 int check_geometry(kf_context *ctx, const kf_geometry *geom, FitGeom *g)
 {
@@ -197,6 +199,7 @@ void kf_context_destroy(kf_context *ctx)
     kf::destroy_build_state(ctx->build);
     kf::destroy_mlp_state(ctx->mlp);
     kf::destroy_host_state(ctx->host);
+    kf::destroy_smooth_state(ctx->smooth);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     cudaFree(ctx->d_counter);
     delete ctx;

@@ -204,19 +204,28 @@ __device__ __forceinline__ void transport(const Jac &J, float c[21])
     for (int i = 0; i < 21; ++i) c[i] = nc[i];
 }
 
-// Multiple scattering of a thin layer at the crossing xn on radius 1/inv_r:
-// Q = theta0^2 (|p|^2 I3 - p p^T) on the momentum block; theta0 from the
-// Highland formula (beta = 1) for x_over_x0 / |cos(incidence)|.
-__device__ __forceinline__ void add_scattering(const float xn[6], float inv_r, float x_over_x0, float c[21])
+// theta0^2 of the Highland formula (beta = 1) for a thin layer of x_over_x0
+// radiation lengths crossed at xn on radius 1/inv_r (path x_over_x0 /
+// |cos(incidence)|); p2 receives |p|^2.
+__device__ __forceinline__ float scattering_theta2(const float xn[6], float inv_r, float x_over_x0, float &p2)
 {
-    if (!(x_over_x0 > 0.0f)) return;
     const float px = xn[3], py = xn[4], pz = xn[5];
-    const float p2 = px * px + py * py + pz * pz;
+    p2 = px * px + py * py + pz * pz;
     const float ip = rsqrtf(p2);
     const float cosi = fabsf(px * xn[0] + py * xn[1]) * ip * inv_r;
     const float xx0 = __fdividef(x_over_x0, cosi);
     const float th = 0.0136f * ip * sqrtf(xx0) * (1.0f + 0.038f * __logf(xx0));
-    const float t2 = th * th;
+    return th * th;
+}
+
+// Multiple scattering of a thin layer: Q = theta0^2 (|p|^2 I3 - p p^T) added
+// to the momentum block.
+__device__ __forceinline__ void add_scattering(const float xn[6], float inv_r, float x_over_x0, float c[21])
+{
+    if (!(x_over_x0 > 0.0f)) return;
+    const float px = xn[3], py = xn[4], pz = xn[5];
+    float p2;
+    const float t2 = scattering_theta2(xn, inv_r, x_over_x0, p2);
     c[pk(3, 3)] = fmaf(t2, p2 - px * px, c[pk(3, 3)]);
     c[pk(4, 3)] = fmaf(-t2, px * py, c[pk(4, 3)]);
     c[pk(4, 4)] = fmaf(t2, p2 - py * py, c[pk(4, 4)]);

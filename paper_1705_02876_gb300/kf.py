@@ -80,6 +80,8 @@ def load() -> ctypes.CDLL:
             [_vp] * 11 + [ctypes.POINTER(Options), _vp]
         L.kf_fit_tracks_host.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int64] + [_vp] * 11 + \
             [ctypes.c_int64, ctypes.POINTER(Options)]
+        L.kf_smooth_tracks.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int64] + [_vp] * 10 + \
+            [ctypes.POINTER(Options), _vp]
         L.kf_transport_batch.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp]
         L.kf_fit_tuned_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
@@ -388,6 +390,38 @@ def proposal_score(ctx: Context, features, stream=None):
                                   logits.data_ptr() if n else None, _cur_stream(features, stream))
     ctx.check(rc, "kf_proposal_score")
     return logits
+
+
+def smooth_tracks(ctx: Context, geom: GeometryArgs, seed_state, seed_cov, charge, hit_pos, hit_cov, hit_mask,
+                  opt: Options | None = None, out: dict | None = None,
+                  stream: torch.cuda.Stream | None = None) -> dict:
+    """kf_smooth_tracks on CUDA tensors: the smoothed state [L][6][T] and
+    covariance [L][21][T] after every layer, layers reached [T], flags [T]."""
+    T = int(charge.shape[0])
+    L = geom.struct.n_layers
+    dev = charge.device
+    if out is None:
+        out = dict(state=torch.empty((L, 6, T), dtype=torch.float32, device=dev),
+                   cov=torch.empty((L, 21, T), dtype=torch.float32, device=dev),
+                   reached=torch.empty(T, dtype=torch.int16, device=dev),
+                   flags=torch.empty(T, dtype=torch.int32, device=dev))
+    args = [
+        _ptr(seed_state, torch.float32, (6, T), "seed_state"),
+        _ptr(seed_cov, torch.float32, (21, T), "seed_cov"),
+        _ptr(charge, torch.int8, (T,), "charge"),
+        _ptr(hit_pos, torch.float32, (L, 3, T), "hit_pos"),
+        _ptr(hit_cov, torch.float32, (L, 6, T), "hit_cov"),
+        _ptr(hit_mask, torch.int32, (T,), "hit_mask"),
+        _ptr(out["state"], torch.float32, (L, 6, T), "out_state"),
+        _ptr(out["cov"], torch.float32, (L, 21, T), "out_cov"),
+        _ptr(out["reached"], torch.int16, (T,), "out_reached"),
+        _ptr(out["flags"], torch.int32, (T,), "out_flags"),
+    ]
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    rc = load().kf_smooth_tracks(ctx.handle, ctypes.byref(geom.struct), T, *args,
+                                 ctypes.byref(opt) if opt is not None else None, s.cuda_stream)
+    ctx.check(rc, "kf_smooth_tracks")
+    return out
 
 
 def transport_batch(ctx: Context, J, C, stream=None):

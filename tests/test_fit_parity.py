@@ -4,7 +4,9 @@ inputs, through the C interface.
 Tolerances (stated for the fit): positions |dx| / r_last <= 1e-4, momenta
 |dp_i| / |p| <= 1e-4, chi2 |d| <= 1e-3 max(chi2, ndof); ndof and the stop
 flags (unreachable, left barrel, NaN input) exact.  r_last is the radius of
-the last layer the track reached.
+the last layer the track reached.  Covariance (test_covariance_precision): in
+the layer's local frame (t, z, px, py, pz), every entry within 5e-3 of
+sqrt(C_ii C_jj) — the FP32 update's rounding accumulated over up to 17 layers.
 """
 import numpy as np
 import pytest
@@ -163,6 +165,37 @@ def test_argument_errors(kf, ctx):
         kf.fit_tracks(ctx, kf.GeometryArgs.of(b.geom), **dev, opt=kf.options(launch_mode=1))
     with pytest.raises(kf.KFError, match="precision_mode"):
         kf.fit_tracks(ctx, kf.GeometryArgs.of(b.geom), **dev, opt=kf.options(precision_mode=7))
+
+
+def _local_cov(state, cov):
+    r = np.hypot(state[0], state[1])
+    nx, ny = state[0] / r, state[1] / r
+    n = state.shape[1]
+    C = np.zeros((6, 6, n))
+    k = 0
+    for i in range(6):
+        for j in range(i + 1):
+            C[i, j] = C[j, i] = cov[k]
+            k += 1
+    P = np.zeros((5, 6, n))
+    P[0, 0], P[0, 1] = -ny, nx
+    for i in range(1, 5):
+        P[i, i + 1] = 1.0
+    return np.einsum("ian,abn,jbn->ijn", P, C, P)
+
+
+@pytest.mark.parametrize("name", ["parity", "ragged"])
+def test_covariance_precision(kf, ctx, oracle, name):
+    b = synth.workload(name, scale=1.0 if name == "parity" else 0.02)
+    gpu = run_gpu(kf, ctx, b)
+    ref = oracle.fit_batch(b)
+    ok = (ref["flags"] & 12) == 0
+    rs = ref["state"][:, ok]
+    Lg = _local_cov(rs, gpu["cov"][:, ok].astype(np.float64))
+    Lr = _local_cov(rs, ref["cov"][:, ok])
+    d = np.sqrt(np.abs(np.einsum("iin->in", Lr)))
+    err = np.abs(Lg - Lr) / (d[:, None] * d[None, :])
+    assert err.max() <= 5e-3, err.max()
 
 
 @pytest.mark.slow
