@@ -82,6 +82,12 @@ def lib():
                 [ctypes.c_void_p] * 10
             _lib.orc_propagate_back.restype = ctypes.c_int
             _lib.orc_propagate_back.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
+            _lib.orc_triplet_circle.restype = ctypes.c_int
+            _lib.orc_triplet_circle.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp]
+            _lib.orc_seed_triplets.restype = ctypes.c_int64
+            _lib.orc_seed_triplets.argtypes = [_dp] + [ctypes.c_double] * 5 + \
+                [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                 ctypes.c_void_p, ctypes.c_int64]
             _lib.orc_bf16_round.restype = ctypes.c_double
             _lib.orc_bf16_round.argtypes = [ctypes.c_double]
             _lib.orc_mlp_logit.restype = ctypes.c_double
@@ -252,6 +258,47 @@ def smooth_batch(batch, threads=None, track_range=None):
         with cf.ThreadPoolExecutor(threads) as ex:
             list(ex.map(run, ranges))
     return out
+
+
+SEED_DEFAULTS = dict(pt_min=0.3, d0_max=0.15, z0_max=4.0, dz_max=0.8, pt_both_charges=2.0)
+
+
+def triplet_circle(p0, p1, p2):
+    """(curvature, distance of the origin to the circle, orientation) of three
+    (x, y) points, or None if collinear."""
+    k, d0, o = (ctypes.c_double() for _ in range(3))
+    rc = lib().orc_triplet_circle(_p(_f64(p0).copy()), _p(_f64(p1).copy()), _p(_f64(p2).copy()),
+                                  ctypes.byref(k), ctypes.byref(d0), ctypes.byref(o))
+    return (k.value, d0.value, o.value) if rc else None
+
+
+def seed_triplets(events, **opt):
+    """Seeding triplets of a ``synth.BuildEvents`` with seed-layer hits:
+    int64 [n][4] (event, h0, h1, h2), sorted."""
+    o_ = dict(SEED_DEFAULTS, **opt)  # pt_both_charges only decides which charges a triplet seeds
+    g = events.geom
+    r = np.asarray(g.radii[:3], dtype=np.float32).astype(np.float64)
+    hp = np.ascontiguousarray(events.seed_hit_pos, dtype=np.float32)
+    off = np.ascontiguousarray(events.seed_hit_offsets, dtype=np.int64)
+    H = hp.shape[1]
+    E = off.shape[0]
+    bz = float(np.float32(g.bz))
+
+    def run(e0, e1, cap):
+        out = np.zeros((max(cap, 1), 4), dtype=np.int64)
+        n = lib().orc_seed_triplets(_p(r), bz, o_["pt_min"], o_["d0_max"], o_["z0_max"], o_["dz_max"],
+                                    hp.ctypes.data, H, off.ctypes.data, e0, e1, out.ctypes.data, cap)
+        assert n >= 0
+        return n, out
+
+    parts = []
+    for e in range(E):
+        n, _ = run(e, e + 1, 0)
+        n2, out = run(e, e + 1, n)
+        assert n2 == n
+        parts.append(out[:n])
+    t = np.concatenate(parts) if parts else np.zeros((0, 4), dtype=np.int64)
+    return t[np.lexsort((t[:, 3], t[:, 1], t[:, 2], t[:, 0]))]
 
 
 def propagate_back(state, q, bz, r):

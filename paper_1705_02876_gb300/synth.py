@@ -397,6 +397,13 @@ class BuildEvents:
     hit_track: np.ndarray          # [H] int64 global sim-track id, -1 for noise
     track_nhits: np.ndarray        # [n_sim] hits of each sim track over all layers
     n_events: int
+    # every hit of the seed layers (true hits and, for seeding from hits, noise),
+    # per (event, seed layer) segment; None unless requested
+    seed_hit_pos: np.ndarray | None = None      # [3, Hs] float32
+    seed_hit_cov: np.ndarray | None = None      # [6, Hs] float32
+    seed_hit_offsets: np.ndarray | None = None  # [E, n_seed_layers + 1] int64
+    seed_hit_track: np.ndarray | None = None    # [Hs] int64, -1 for noise
+    track_pt: np.ndarray | None = None          # [n_sim] generated pT
 
     @property
     def build_geom(self) -> Geometry:
@@ -410,10 +417,13 @@ class BuildEvents:
 def make_build_events(seed: int, n_events: int, tracks_per_event: int, geom: Geometry | None = None,
                       noise_factor: float = 10.0, n_seed_layers: int = 3, sigma_rphi=0.01,
                       sigma_z=0.1, ms=True, pt_lo=0.5, pt_hi=10.0, eta_max=1.0,
-                      noise_per_layer: int | None = None) -> BuildEvents:
+                      noise_per_layer: int | None = None, seed_layer_hits: bool = False) -> BuildEvents:
     """``n_events`` events of ``tracks_per_event`` simulated tracks each, plus
     ``noise_factor`` x tracks_per_event uniform noise hits per layer (or
-    ``noise_per_layer``), on the toy barrel (17 layers by default)."""
+    ``noise_per_layer``), on the toy barrel (17 layers by default).  With
+    ``seed_layer_hits`` the seed layers' hits (every track's true hits plus the
+    same density of noise, from a stream of their own) are stored too, for
+    seeding from hits."""
     geom = geom or toy_geometry(17)
     L = geom.n_layers
     r_kin, r_hit, r_ms, r_eff, r_seed, r_noise, r_perm = _streams(seed, 7)
@@ -468,8 +478,37 @@ def make_build_events(seed: int, n_events: int, tracks_per_event: int, geom: Geo
     hit_pos = f32(np.concatenate(pos_parts, axis=1)) if pos_parts else np.zeros((3, 0), np.float32)
     hit_cov = f32(np.concatenate(cov_parts, axis=1)) if cov_parts else np.zeros((6, 0), np.float32)
     hit_track = np.concatenate(trk_parts) if trk_parts else np.zeros(0, np.int64)
-    return BuildEvents(geom, n_seed_layers, seed_fit, event_of[sidx].astype(np.int32), sidx.astype(np.int64),
-                       hit_pos, hit_cov, offsets, hit_track, track_nhits, n_events)
+    ev = BuildEvents(geom, n_seed_layers, seed_fit, event_of[sidx].astype(np.int32), sidx.astype(np.int64),
+                     hit_pos, hit_cov, offsets, hit_track, track_nhits, n_events)
+    ev.track_pt = np.hypot(vertex[3], vertex[4])
+    if seed_layer_hits:
+        r_snoise, r_sperm = _streams(seed, 10)[8:10]
+        sp, sc, st = [], [], []
+        soff = np.zeros((n_events, n_seed_layers + 1), dtype=np.int64)
+        cur = 0
+        for e in range(n_events):
+            lo, hi = e * tracks_per_event, (e + 1) * tracks_per_event
+            for l in range(n_seed_layers):
+                has = ((sim["hit_mask"][lo:hi] >> np.uint32(l)) & np.uint32(1)).astype(bool)
+                phi = r_snoise.uniform(0.0, 2.0 * math.pi, n_noise)
+                zz = r_snoise.uniform(-geom.z_half, geom.z_half, n_noise)
+                nxp, nyp = geom.radii[l] * np.cos(phi), geom.radii[l] * np.sin(phi)
+                pos = np.concatenate([sim["hit_pos"][l][:, lo:hi][:, has], np.stack([nxp, nyp, zz])], axis=1)
+                cov = np.concatenate([sim["hit_cov"][l][:, lo:hi][:, has],
+                                      hit_covariance(nxp, nyp, sigma_rphi, sigma_rphi, sigma_z)], axis=1)
+                trk = np.concatenate([np.arange(lo, hi)[has], np.full(n_noise, -1, dtype=np.int64)])
+                perm = r_sperm.permutation(pos.shape[1])
+                sp.append(pos[:, perm])
+                sc.append(cov[:, perm])
+                st.append(trk[perm])
+                soff[e, l] = cur
+                cur += pos.shape[1]
+                soff[e, l + 1] = cur
+        ev.seed_hit_pos = f32(np.concatenate(sp, axis=1))
+        ev.seed_hit_cov = f32(np.concatenate(sc, axis=1))
+        ev.seed_hit_offsets = soff
+        ev.seed_hit_track = np.concatenate(st)
+    return ev
 
 
 def build_workload(scale_events: int | None = None, seed: int = 4, tracks_per_event: int = 5000):
