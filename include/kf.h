@@ -309,6 +309,70 @@ int kf_proposal_load(kf_context *ctx, const float *weights, kf_stream stream);
 int kf_proposal_score(kf_context *ctx, const float *features, int64_t n, float *logits, kf_stream stream);
 
 /*
+ * Seeding from hits (the paper seeds from the true hits of each simulated
+ * track and leaves realistic seeding for later, Section 2): triplets of hits
+ * on the three seed layers of every event that a track from the beam line
+ * above pt_min could have made, and the seed fit's inputs built from them.
+ *
+ * A triplet (h0, h1, h2) of one event, with the hits' own radii r_i, azimuths
+ * phi_i and z_i, is a seed when |phi_1 - phi_0| <= w01 and |phi_2 - phi_1| <=
+ * w12 (w_ab = asin(R_b / 2 R_min) - asin(R_a / 2 R_min) + d0_max (1/R_a +
+ * 1/R_b), R_a the layers' radii, R_min = pt_min / (0.0029979 |Bz|)); the line
+ * through (r_0, z_0), (r_1, z_1) meets r = 0 within z0_max and predicts z at
+ * r_2 within dz_max; and the circle through the three (x, y) points has pT >=
+ * pt_min and passes within d0_max of the beam line.  Its charge follows the
+ * turning sense (positive charges turn clockwise in Bz > 0); a triplet with
+ * pT above pt_both_charges, straighter than three hits resolve, is seeded
+ * with both charges.
+ */
+typedef struct {
+    float pt_min;           /* GeV */
+    float d0_max;           /* cm, distance of the circle to the beam line */
+    float z0_max;           /* cm, |z| where the (r, z) line meets the beam line */
+    float dz_max;           /* cm, |z_2 - the line's prediction| */
+    float pt_both_charges;  /* GeV */
+    float pt_unresolved;    /* GeV, the seed fit's starting pT of a two-charge triplet */
+    float p_sigma_resolved;    /* momentum sigma of the seed fit's start, relative */
+    float p_sigma_unresolved;  /* the same for a two-charge triplet */
+    int n_phi_bins, n_z_bins;  /* bins of the seed layers' hits */
+} kf_seeding;
+
+/* Defaults: pt_min 0.3, d0_max 0.15, z0_max 4, dz_max 0.8, pt_both_charges 2,
+ * pt_unresolved 6, p_sigma_resolved 0.3, p_sigma_unresolved 1, 256 x 64 bins. */
+void kf_seeding_default(kf_seeding *opt);
+
+/*
+ * Find the triplets.  geom: the three seed layers (host).  hit_offsets: host
+ * [n_events][4]; event e's hits of seed layer l are hit_offsets[e][l] ..
+ * hit_offsets[e][l+1]-1 of hit_pos [3][n_hits] (device), events back to back,
+ * n_hits < 2^31.  *n_seeds (host) receives the number of seeds (a triplet
+ * seeded with both charges counts twice); the call waits for the search.
+ * The seeds stay in the context until the next search, in no fixed order.
+ */
+int kf_seed_triplets(kf_context *ctx, const kf_geometry *geom, int n_events, const int64_t *hit_offsets,
+                     const float *hit_pos, int64_t n_hits, const kf_seeding *opt, int64_t *n_seeds,
+                     kf_stream stream);
+
+/*
+ * The first n (<= *n_seeds of the last search) seeds as the seed fit's inputs,
+ * in kf_fit_tracks' layouts with T = n (device, caller-owned): out_state
+ * [6][n] (1 cm before the first hit along the circle's tangent, pT from the
+ * circle, or pt_unresolved for a two-charge triplet, whose curvature the hits
+ * do not measure, pz from the first chord's slope), out_cov [21][n]
+ * (diagonal: sigma 10% of each position component and p_sigma_resolved, or
+ * p_sigma_unresolved for a two-charge triplet, of each momentum component,
+ * floors 1e-4 cm, 1e-3 GeV),
+ * out_charge [n], out_hit_pos [3][3][n], out_hit_cov [3][6][n] (the three
+ * hits, from hit_pos [3][H] / hit_cov [6][H] of the search), out_mask [n] (= 7);
+ * out_event [n] and out_hits [3][n] (indices into hit_pos) identify each
+ * seed.
+ */
+int kf_seed_fetch(kf_context *ctx, const kf_geometry *geom, const float *hit_pos, const float *hit_cov,
+                  const kf_seeding *opt, int64_t n, int32_t *out_event, int32_t *out_hits, float *out_state,
+                  float *out_cov, int8_t *out_charge, float *out_hit_pos, float *out_hit_cov, uint32_t *out_mask,
+                  kf_stream stream);
+
+/*
  * The fit followed by the Kalman smoother: at every layer the estimate that
  * uses all of the track's hits (Section 2 names a final fit with a smoother,
  * after building, as the step giving each track's best parameters).  The

@@ -301,6 +301,63 @@ def seed_triplets(events, **opt):
     return t[np.lexsort((t[:, 3], t[:, 1], t[:, 2], t[:, 0]))]
 
 
+def seed_fit_inputs(events, trip, pt_min=0.3, pt_both_charges=2.0, pt_unresolved=6.0, p_sigma_resolved=0.3,
+                    p_sigma_unresolved=1.0):
+    """The seed fit's inputs of seeding triplets [n][4] in FP64, from the
+    recipe's definition: one seed per charge the triplet seeds (its turning
+    sense's, and the other as well when the circle's pT is at least
+    pt_both_charges); the state 1 cm before the first hit along the circle's
+    tangent there, pT from the circle (pt_unresolved for a two-charge triplet,
+    whose curvature the three hits do not measure), pz from the first chord's
+    slope; a diagonal covariance with sigma 10% of each position component and
+    p_sigma_resolved (p_sigma_unresolved for a two-charge triplet) of each
+    momentum component, floors 1e-4 cm, 1e-3 GeV.  Returns arrays sorted by
+    the key (event, h0, h1, h2, charge)."""
+    hp = events.seed_hit_pos.astype(np.float64)
+    hc = events.seed_hit_cov.astype(np.float64)
+    bz = float(np.float32(events.geom.bz))
+    k_field = 0.00299792458
+    kamb = k_field * abs(bz) / pt_both_charges
+    keys, states, covs = [], [], []
+    for e, h0, h1, h2 in trip:
+        P = [hp[:2, h] for h in (h0, h1, h2)]
+        r = triplet_circle(*P)
+        k, orient = (r[0], r[2]) if r is not None else (0.0, 0.0)
+        both = abs(k) <= kamb
+        q0 = 1 if orient * bz < 0 else -1
+        for q in ((q0, -q0) if both else (q0,)):
+            pt = pt_unresolved if both else k_field * abs(bz) / abs(k)
+            ka = k_field * abs(bz) / pt
+            a = P[1] - P[0]
+            alen = np.hypot(*a)
+            turn = 1.0 if q * bz < 0 else -1.0
+            half = np.arcsin(min(1.0, 0.5 * alen * ka)) * turn
+            c, s_ = np.cos(-half), np.sin(-half)
+            cx, cy = a / alen
+            tx, ty = c * cx - s_ * cy, s_ * cx + c * cy
+            tanl = (hp[2, h1] - hp[2, h0]) / alen
+            st = np.array([P[0][0] - tx, P[0][1] - ty, hp[2, h0] - tanl, pt * tx, pt * ty, pt * tanl])
+            rel = np.array([0.1, 0.1, 0.1] + [p_sigma_unresolved if both else p_sigma_resolved] * 3)
+            fl = np.array([1e-4] * 3 + [1e-3] * 3)
+            cv = np.zeros(21)
+            for i in range(6):
+                cv[i * (i + 1) // 2 + i] = (rel[i] * st[i]) ** 2 + fl[i] ** 2
+            keys.append((e, h0, h1, h2, q))
+            states.append(st)
+            covs.append(cv)
+    key = np.array(keys, dtype=np.int64).reshape(-1, 5)
+    order = np.lexsort((key[:, 4], key[:, 3], key[:, 1], key[:, 2], key[:, 0])) if len(key) else np.zeros(0, int)
+    key = key[order]
+    n = len(key)
+    hits = key[:, 1:4].T
+    return dict(key=key, seed_state=np.array(states).reshape(-1, 6)[order].T if n else np.zeros((6, 0)),
+                seed_cov=np.array(covs).reshape(-1, 21)[order].T if n else np.zeros((21, 0)),
+                charge=key[:, 4].astype(np.int8), event=key[:, 0].astype(np.int32),
+                hit_pos=np.stack([hp[:, hits[l]] for l in range(3)]) if n else np.zeros((3, 3, 0)),
+                hit_cov=np.stack([hc[:, hits[l]] for l in range(3)]) if n else np.zeros((3, 6, 0)),
+                hit_mask=np.full(n, 7, dtype=np.uint32))
+
+
 def propagate_back(state, q, bz, r):
     """The crossing of radius r backwards along the helix (None if unreachable)."""
     out = np.zeros(6)

@@ -47,6 +47,7 @@ struct kf_context {
     kf::MlpState *mlp = nullptr;
     kf::HostPipe *host = nullptr;
     kf::SmoothState *smooth = nullptr;
+    kf::SeedState *seed = nullptr;
 };
 
 namespace kf {
@@ -73,6 +74,7 @@ BuildState *&context_build_state(kf_context *ctx) { return ctx->build; }
 MlpState *&context_mlp_state(kf_context *ctx) { return ctx->mlp; }
 HostPipe *&context_host_state(kf_context *ctx) { return ctx->host; }
 SmoothState *&context_smooth_state(kf_context *ctx) { return ctx->smooth; }
+SeedState *&context_seed_state(kf_context *ctx) { return ctx->seed; }
 
 int check_geometry(kf_context *ctx, const kf_geometry *geom, FitGeom *g)
 {
@@ -200,6 +202,7 @@ void kf_context_destroy(kf_context *ctx)
     kf::destroy_mlp_state(ctx->mlp);
     kf::destroy_host_state(ctx->host);
     kf::destroy_smooth_state(ctx->smooth);
+    kf::destroy_seed_state(ctx->seed);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     cudaFree(ctx->d_counter);
     delete ctx;

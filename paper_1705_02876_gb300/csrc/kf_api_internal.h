@@ -17,6 +17,8 @@ struct HostPipe;  // staging buffers and streams of the host-buffer fit (kf_host
 void destroy_host_state(HostPipe *s);
 struct SmoothState;  // per-layer scratch of the smoother (kf_smooth.cu)
 void destroy_smooth_state(SmoothState *s);
+struct SeedState;  // binned seed-layer hits and found triplets (kf_seed.cu)
+void destroy_seed_state(SeedState *s);
 bool proposal_loaded(kf_context *ctx);
 // device copies of the loaded weights (the layouts of kf_mlp.cuh)
 void proposal_weights(kf_context *ctx, const __nv_bfloat16 **W1, const __nv_bfloat16 **W2, const float **w32);
@@ -33,6 +35,7 @@ BuildState *&context_build_state(kf_context *ctx);
 MlpState *&context_mlp_state(kf_context *ctx);
 HostPipe *&context_host_state(kf_context *ctx);
 SmoothState *&context_smooth_state(kf_context *ctx);
+SeedState *&context_seed_state(kf_context *ctx);
 
 // Make `dev` current for a scope, restoring the caller's device after.
 struct DeviceGuard {

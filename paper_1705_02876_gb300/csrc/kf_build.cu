@@ -19,6 +19,7 @@
 #include "kf.h"
 #include "kf_api_internal.h"
 #include "kf_fit.cuh"
+#include "kf_bins.cuh"
 #include "kf_mlp.cuh"
 
 namespace kf {
@@ -43,87 +44,6 @@ void destroy_build_state(BuildState *s)
 }
 
 namespace {
-
-constexpr float kPi = 3.14159265358979f;
-
-struct BinGrid {
-    int n_phi, n_z;
-    float z_half;
-};
-
-__device__ __forceinline__ int phi_bin(float phi, int n_phi)
-{
-    const int b = (int)floorf((phi + kPi) * (float)n_phi * (1.0f / (2.0f * kPi)));
-    return min(max(b, 0), n_phi - 1);
-}
-__device__ __forceinline__ int z_bin(float z, const BinGrid &bg)
-{
-    const int b = (int)floorf((z + bg.z_half) * (float)bg.n_z / (2.0f * bg.z_half));
-    return min(max(b, 0), bg.n_z - 1);
-}
-
-// One block per (event, layer) segment: count hits per bin in shared memory,
-// scan, scatter each hit's key (phi, z, index within the segment) bin by bin
-// (bin = iz * n_phi + iphi).  A key is one 16-byte store here and one 16-byte
-// load in the window scan: the destinations are random at a few hits per bin,
-// so each key costs one memory sector, not three.
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) bin_hits_kernel(const int64_t *seg_off, const float *hit_pos, int64_t H,
-                                                           BinGrid bg, float4 *bkey, int32_t *bin_off)
-{
-    extern __shared__ int cnt[];
-    __shared__ int warp_sums[THREADS / 32];
-    const int seg = blockIdx.x;
-    const int64_t lo = seg_off[seg], hi = seg_off[seg + 1];
-    const int nb = bg.n_phi * bg.n_z;
-    for (int i = threadIdx.x; i < nb; i += THREADS) cnt[i] = 0;
-    __syncthreads();
-    for (int64_t h = lo + threadIdx.x; h < hi; h += THREADS) {
-        const float x = hit_pos[h], y = hit_pos[H + h], z = hit_pos[2 * H + h];
-        atomicAdd(&cnt[z_bin(z, bg) * bg.n_phi + phi_bin(atan2f(y, x), bg.n_phi)], 1);
-    }
-    __syncthreads();
-    // exclusive scan: each thread owns a contiguous run of bins
-    const int per = (nb + THREADS - 1) / THREADS;
-    const int b0 = min(nb, (int)threadIdx.x * per), b1 = min(nb, b0 + per);
-    int run = 0;
-    for (int b = b0; b < b1; ++b) run += cnt[b];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = run;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int o = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += o;
-    }
-    if (lane == 31) warp_sums[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        int w = lane < THREADS / 32 ? warp_sums[lane] : 0;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int o = __shfl_up_sync(0xffffffffu, w, d);
-            if (lane >= d) w += o;
-        }
-        if (lane < THREADS / 32) warp_sums[lane] = w;
-    }
-    __syncthreads();
-    int base = incl - run + (warp > 0 ? warp_sums[warp - 1] : 0);
-    int32_t *bo = bin_off + (int64_t)seg * (nb + 1);
-    for (int b = b0; b < b1; ++b) {
-        const int c = cnt[b];
-        cnt[b] = base;
-        bo[b] = base;
-        base += c;
-    }
-    if (threadIdx.x == 0) bo[nb] = (int)(hi - lo);
-    __syncthreads();
-    for (int64_t h = lo + threadIdx.x; h < hi; h += THREADS) {
-        const float x = hit_pos[h], y = hit_pos[H + h], z = hit_pos[2 * H + h];
-        const float phi = atan2f(y, x);
-        const int p = atomicAdd(&cnt[z_bin(z, bg) * bg.n_phi + phi_bin(phi, bg.n_phi)], 1);
-        bkey[lo + p] = make_float4(phi, z, __int_as_float((int)(h - lo)), 0.0f);
-    }
-}
 
 struct BuildParams {
     FitGeom g;
@@ -158,12 +78,6 @@ struct BuildParams {
 
 constexpr int kMaxN = 8;
 constexpr uint32_t kNoKey = 0xffffffffu;
-
-__device__ __forceinline__ float wrap_pi(float d)
-{
-    d = d > kPi ? d - 2.0f * kPi : d;
-    return d <= -kPi ? d + 2.0f * kPi : d;
-}
 
 // Chi2 increment of a hit (m, packed V) against the predicted candidate, in
 // the layer's local frame (n, t, z) with the radial row of C projected out

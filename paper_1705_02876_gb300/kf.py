@@ -80,6 +80,12 @@ def load() -> ctypes.CDLL:
             [_vp] * 11 + [ctypes.POINTER(Options), _vp]
         L.kf_fit_tracks_host.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int64] + [_vp] * 11 + \
             [ctypes.c_int64, ctypes.POINTER(Options)]
+        L.kf_seeding_default.argtypes = [ctypes.POINTER(Seeding)]
+        L.kf_seeding_default.restype = None
+        L.kf_seed_triplets.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int, _vp, _vp, ctypes.c_int64,
+                                       ctypes.POINTER(Seeding), ctypes.POINTER(ctypes.c_int64), _vp]
+        L.kf_seed_fetch.argtypes = [_vp, ctypes.POINTER(Geometry), _vp, _vp, ctypes.POINTER(Seeding),
+                                    ctypes.c_int64] + [_vp] * 8 + [_vp]
         L.kf_smooth_tracks.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int64] + [_vp] * 10 + \
             [ctypes.POINTER(Options), _vp]
         L.kf_transport_batch.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp]
@@ -107,6 +113,23 @@ def header_functions() -> list[str]:
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(kf_[a-z0-9_]+)\s*\(", text)))
+
+
+class Seeding(ctypes.Structure):
+    _fields_ = [("pt_min", ctypes.c_float), ("d0_max", ctypes.c_float), ("z0_max", ctypes.c_float),
+                ("dz_max", ctypes.c_float), ("pt_both_charges", ctypes.c_float), ("pt_unresolved", ctypes.c_float),
+                ("p_sigma_resolved", ctypes.c_float), ("p_sigma_unresolved", ctypes.c_float), ("n_phi_bins", ctypes.c_int),
+                ("n_z_bins", ctypes.c_int)]
+
+
+def seeding(**kw) -> Seeding:
+    o = Seeding()
+    load().kf_seeding_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
 
 
 def options(**kw) -> Options:
@@ -390,6 +413,36 @@ def proposal_score(ctx: Context, features, stream=None):
                                   logits.data_ptr() if n else None, _cur_stream(features, stream))
     ctx.check(rc, "kf_proposal_score")
     return logits
+
+
+def seed_triplets(ctx: Context, geom: GeometryArgs, hit_offsets, hit_pos, hit_cov, opt: Seeding | None = None,
+                  stream: torch.cuda.Stream | None = None) -> dict:
+    """kf_seed_triplets + kf_seed_fetch: the seeds of the seed layers' hits
+    (hit_offsets host int64 [E][4], hit_pos [3][H] and hit_cov [6][H] CUDA
+    tensors) as the seed fit's inputs (state, cov, charge, hit_pos, hit_cov,
+    hit_mask, laid out for fit_tracks) plus event [n] and hits [3][n]."""
+    off = np.ascontiguousarray(hit_offsets, dtype=np.int64)
+    H = int(hit_pos.shape[1])
+    dev = hit_pos.device
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    n = ctypes.c_int64()
+    optp = ctypes.byref(opt) if opt is not None else None
+    rc = load().kf_seed_triplets(ctx.handle, ctypes.byref(geom.struct), int(off.shape[0]),
+                                 off.ctypes.data if off.size else None, _ptr(hit_pos, torch.float32, (3, H), "hit_pos"),
+                                 H, optp, ctypes.byref(n), s.cuda_stream)
+    ctx.check(rc, "kf_seed_triplets")
+    n = int(n.value)
+    e = lambda shape, dt: torch.empty(shape, dtype=dt, device=dev)
+    out = dict(event=e((n,), torch.int32), hits=e((3, n), torch.int32), seed_state=e((6, n), torch.float32),
+               seed_cov=e((21, n), torch.float32), charge=e((n,), torch.int8), hit_pos=e((3, 3, n), torch.float32),
+               hit_cov=e((3, 6, n), torch.float32), hit_mask=e((n,), torch.int32))
+    rc = load().kf_seed_fetch(ctx.handle, ctypes.byref(geom.struct), _ptr(hit_pos, torch.float32, (3, H), "hit_pos"),
+                              _ptr(hit_cov, torch.float32, (6, H), "hit_cov"), optp, n,
+                              *[_ptr(out[k], out[k].dtype, tuple(out[k].shape), k) for k in
+                                ("event", "hits", "seed_state", "seed_cov", "charge", "hit_pos", "hit_cov",
+                                 "hit_mask")], s.cuda_stream)
+    ctx.check(rc, "kf_seed_fetch")
+    return out
 
 
 def smooth_tracks(ctx: Context, geom: GeometryArgs, seed_state, seed_cov, charge, hit_pos, hit_cov, hit_mask,

@@ -16,29 +16,39 @@ from __future__ import annotations
 import numpy as np
 
 
-def efficiency_fake_rate(best_hits, seed_track, hit_track, track_nhits, n_seed_hits=3, min_hits=7):
+def efficiency_fake_rate(best_hits, seed_track, hit_track, track_nhits, n_seed_hits=3, min_hits=7,
+                         eligible_tracks=None):
     """best_hits [S, L]: global hit index per build layer (-1 = none) of each
     seed's best candidate; seed_track [S]: the simulated track each seed came
-    from; hit_track [H]: owner of each hit (-1 = noise); track_nhits: hits of
-    every simulated track over all layers."""
+    from (-1: a seed whose hits are not all from one simulated track, whose
+    seed hits then count for no track); hit_track [H]: owner of each hit (-1 =
+    noise); track_nhits: hits of every simulated track over all layers;
+    eligible_tracks: the simulated tracks efficiency is measured on (default:
+    the seeds' tracks with at least min_hits hits)."""
     best_hits = np.asarray(best_hits)
+    seed_track = np.asarray(seed_track)
     S = best_hits.shape[0]
     owner = np.where(best_hits >= 0, np.asarray(hit_track)[np.maximum(best_hits, 0)], -2)
     n_build = (best_hits >= 0).sum(1)
     n_total = n_build + n_seed_hits
-    own = (owner == np.asarray(seed_track)[:, None]).sum(1) + n_seed_hits
+    own = (owner == seed_track[:, None]).sum(1) + np.where(seed_track >= 0, n_seed_hits, 0)
     # the majority owner of a candidate's hits is its seed's track whenever it
     # has at least half; otherwise look for another owner with half
     matched_track = np.full(S, -1, dtype=np.int64)
     ok = 2 * own >= n_total
-    matched_track[ok] = np.asarray(seed_track)[ok]
+    matched_track[ok] = seed_track[ok]
     for s in np.nonzero(~ok)[0]:
         vals, cnt = np.unique(owner[s][owner[s] >= 0], return_counts=True)
         if len(cnt) and 2 * cnt.max() >= n_total[s]:
             matched_track[s] = vals[np.argmax(cnt)]
     counted = n_total >= min_hits
     fake = counted & (matched_track < 0)
-    eligible = np.unique(np.asarray(seed_track)[np.asarray(track_nhits)[np.asarray(seed_track)] >= min_hits])
+    if eligible_tracks is None:
+        st = seed_track[seed_track >= 0]
+        eligible = np.unique(st[np.asarray(track_nhits)[st] >= min_hits])
+    else:
+        et = np.asarray(eligible_tracks)
+        eligible = np.unique(et[np.asarray(track_nhits)[et] >= min_hits])
     found = np.unique(matched_track[counted & (matched_track >= 0)])
     eff = np.isin(eligible, found).mean() if len(eligible) else float("nan")
     fake_rate = fake.sum() / max(counted.sum(), 1)

@@ -125,3 +125,75 @@ def test_every_seedable_track_found_with_its_charge(oracle):
             agree += q == charge[int(trk[row[1]])]
     assert agree >= 0.995 * true.sum(), (agree, true.sum(), both)
     assert both < 0.9 * true.sum()
+
+
+def _exact_triplets(pt_lo, pt_hi, n=64, seed=3):
+    """Noiseless helices (no smearing, no scattering) through the toy barrel's
+    three seed layers, with the seed layers' hits as the seeding input."""
+    from types import SimpleNamespace
+    geom = synth.toy_geometry(3, bz=3.75)  # exact in FP32, the precision the library takes Bz in
+    rng = np.random.default_rng(seed)
+    vertex, q = synth.draw_vertex_tracks(rng, n, pt_lo, pt_hi, "uniform", 1.0, vtx_sigma_xy=0.0)
+    sim = synth.simulate(rng, rng, rng, geom, vertex, q, smear=False, ms=False)
+    assert (sim["hit_mask"] == 7).all()
+    hp = np.concatenate([sim["hit_pos"][l] for l in range(3)], axis=1)
+    hc = np.concatenate([sim["hit_cov"][l] for l in range(3)], axis=1)
+    ev = SimpleNamespace(geom=geom, seed_hit_pos=hp, seed_hit_cov=hc)
+    trip = np.stack([np.zeros(n, np.int64), np.arange(n), n + np.arange(n), 2 * n + np.arange(n)], axis=1)
+    return ev, trip, q, sim["truth"][0]
+
+
+def test_seed_start_on_exact_helices(oracle):
+    """Three exact points of a helix fix its circle: the seed's pT is the
+    generated pT, its transverse direction the helix's tangent at the first
+    hit, its charge the generated one, and its tan(lambda) the helix's up to
+    the chord-to-arc ratio; the start lies 1 cm before the first hit along
+    that tangent and the covariance has the stated relative sigmas."""
+    o = dict(pt_min=0.3, pt_both_charges=2.0, pt_unresolved=6.0, p_sigma_resolved=0.3, p_sigma_unresolved=1.0)
+    ev, trip, q, t0 = _exact_triplets(0.5, 1.9)
+    r = oracle.seed_fit_inputs(ev, trip, **o)
+    assert len(r["key"]) == len(trip)  # resolved: one charge each
+    idx = r["key"][:, 1]
+    st = r["seed_state"]
+    pt_true = np.hypot(t0[3, idx], t0[4, idx])
+    pt = np.hypot(st[3], st[4])
+    np.testing.assert_allclose(pt, pt_true, rtol=1e-9)
+    np.testing.assert_array_equal(r["charge"], q[idx])
+    np.testing.assert_allclose(st[3] / pt, t0[3, idx] / pt_true, atol=1e-9)
+    np.testing.assert_allclose(st[4] / pt, t0[4, idx] / pt_true, atol=1e-9)
+    hp0 = ev.seed_hit_pos[:, idx]
+    np.testing.assert_allclose(st[0], hp0[0] - st[3] / pt, atol=1e-12)
+    np.testing.assert_allclose(st[1], hp0[1] - st[4] / pt, atol=1e-12)
+    tl_true = t0[5, idx] / pt_true
+    np.testing.assert_allclose(st[5] / pt, tl_true, rtol=2e-3)
+    assert (np.abs(st[5] / pt) >= np.abs(tl_true)).all()  # the chord is shorter than the arc
+    np.testing.assert_allclose(st[2], hp0[2] - st[5] / pt, atol=1e-12)
+    diag = r["seed_cov"][[0, 2, 5, 9, 14, 20]]
+    np.testing.assert_allclose(diag[3:], (0.3 * st[3:]) ** 2 + 1e-6, rtol=1e-12)
+    np.testing.assert_allclose(diag[:3], (0.1 * st[:3]) ** 2 + 1e-8, rtol=1e-12)
+    assert np.count_nonzero(r["seed_cov"]) == 6 * len(trip)
+
+
+def test_seed_start_of_straight_triplets(oracle):
+    """Above pt_both_charges the three hits do not resolve the curvature:
+    both charges are seeded, each starting at pt_unresolved with the
+    unresolved momentum sigma, and each turning its own way over the first
+    chord."""
+    ev, trip, q, t0 = _exact_triplets(20.0, 50.0, n=32)
+    r = oracle.seed_fit_inputs(ev, trip, pt_unresolved=5.0, p_sigma_unresolved=0.8)
+    assert len(r["key"]) == 2 * len(trip)
+    assert (r["key"][0::2, 1] == r["key"][1::2, 1]).all() and (r["key"][0::2, 4] == -1).all()
+    st = r["seed_state"]
+    pt = np.hypot(st[3], st[4])
+    np.testing.assert_allclose(pt, 5.0, rtol=1e-12)
+    np.testing.assert_allclose(r["seed_cov"][9], (0.8 * st[3]) ** 2 + 1e-6, rtol=1e-12)
+    # the two starts differ by twice the half turning angle of a 5 GeV circle over the chord
+    hp = ev.seed_hit_pos
+    idx = r["key"][0::2, 1]
+    chord = np.hypot(hp[0, trip[:, 2]] - hp[0, trip[:, 1]], hp[1, trip[:, 2]] - hp[1, trip[:, 1]])[idx]
+    half = np.arcsin(0.5 * chord * K * float(ev.geom.bz) / 5.0)
+    cosang = (st[3, 0::2] * st[3, 1::2] + st[4, 0::2] * st[4, 1::2]) / 25.0
+    np.testing.assert_allclose(np.arccos(np.clip(cosang, -1, 1)), 2 * half, rtol=1e-6)
+    # a negative charge turns counter-clockwise in Bz > 0: its start direction is clockwise of the chord's
+    cross = st[3, 0::2] * st[4, 1::2] - st[4, 0::2] * st[3, 1::2]
+    assert (cross > 0).all()
