@@ -17,7 +17,6 @@ from __future__ import annotations
 
 import argparse
 import hashlib
-import glob
 import json
 import math
 import os
@@ -64,6 +63,7 @@ def parse():
     p.add_argument("--no-ragged", action="store_true", help="skip the ragged-batching comparison")
     p.add_argument("--no-transport", action="store_true", help="skip the batched 6x6 transport comparison")
     p.add_argument("--train-events", type=int, default=3, help="events logged to train the proposal")
+    p.add_argument("--seed-events", type=int, default=4, help="build-workload events seeded from hits")
     p.add_argument("--train-epochs", type=int, default=4)
     return p.parse_args()
 
@@ -84,11 +84,24 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
-    """Hash of the kernel sources and of the build flags that compile them."""
+    """Hash of the fit kernel's sources (its translation unit and every header
+    it includes from the package or include/) and of the build script."""
+    import re
+    csrc = os.path.join(ROOT, "paper_1705_02876_gb300", "csrc")
+    inc = os.path.join(ROOT, "include")
+    todo, seen = [os.path.join(csrc, "kf_fit.cu")], []
+    while todo:
+        p = todo.pop()
+        if p in seen:
+            continue
+        seen.append(p)
+        for name in re.findall(r'#include\s+"([^"]+)"', open(p).read()):
+            for d in (csrc, inc):
+                if os.path.exists(os.path.join(d, name)):
+                    todo.append(os.path.join(d, name))
+                    break
     h = hashlib.sha256()
-    paths = sorted(glob.glob(os.path.join(ROOT, "paper_1705_02876_gb300", "csrc", "*")))
-    paths.append(os.path.join(ROOT, "paper_1705_02876_gb300", "build.py"))
-    for p in paths:
+    for p in sorted(seen) + [os.path.join(ROOT, "paper_1705_02876_gb300", "build.py")]:
         with open(p, "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -264,7 +277,10 @@ def bench_build(args, kf, ctx, dev, stream, rank, world):
     import torch
     from paper_1705_02876_gb300 import metrics, synth
     E = args.build_events
-    ev = synth.make_build_events(4 + 1000 * rank, E, 5000)
+    # the seed layers' hits (every track's hits, no added noise) feed the
+    # seeding-from-hits section; they come from streams of their own and leave
+    # the build's events unchanged
+    ev = synth.make_build_events(4 + 1000 * rank, E, 5000, seed_layer_hits=True, seed_noise_per_layer=0)
     sf = ev.seed_fit
     t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dtype=dt)
     d_sf = kf.to_device(sf, dev)
@@ -322,6 +338,7 @@ def bench_build(args, kf, ctx, dev, stream, rank, world):
                                       ev.seed_track, ev.hit_track, ev.track_nhits)
     learned = bench_learned(args, kf, ctx, dev, stream, rank, ev, seed_geom, d_sf, fit_out, build_geom, hp, hc, se,
                             sq, timed)
+    seeding = bench_seeding(args, kf, ctx, dev, stream, ev, build_geom, hp, hc, timed)
     out = {"value": S / (ms * 1e-3), "unit": "seeds/s", "ms_per_step": ms, "seeds": S,
            "workload": BUILD_WORKLOAD.format(E=E),
            "form": "seed fit + binning + build of all events in one launch each, routed precision, "
@@ -331,8 +348,56 @@ def bench_build(args, kf, ctx, dev, stream, rank, world):
            "plain": {"value": S / (ms_plain * 1e-3), "unit": "seeds/s", "ms_per_step": ms_plain,
                      "form": "FP32 only, one launch per event", "efficiency": qp["efficiency"],
                      "fake_rate": qp["fake_rate"]},
-           "learned": learned}
+           "learned": learned, "seeding": seeding}
     return out
+
+
+def bench_seeding(args, kf, ctx, dev, stream, ev, build_geom, hp, hc, timed):
+    """Seeding from hits on the first --seed-events events of the build
+    workload: the triplet search over the three seed layers' hits (every
+    track's hit, no added noise) with the seed fit's inputs, alone and followed
+    by the 3-layer seed fit and the build of every seed."""
+    import torch
+    from paper_1705_02876_gb300 import metrics
+    E = min(args.seed_events, ev.n_events)
+    g3 = kf.GeometryArgs.of(ev.geom.sub(0, 3))
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dtype=dt)
+    soff = ev.seed_hit_offsets[:E]
+    n_hits = int(soff[-1, -1] - soff[0, 0])
+    shp, shc = t(ev.seed_hit_pos, torch.float32), t(ev.seed_hit_cov, torch.float32)
+    seeds = None
+
+    def step_seed():
+        nonlocal seeds
+        seeds = kf.seed_triplets(ctx, g3, soff, shp, shc, stream=stream)
+
+    ms_seed = timed(step_seed, args.build_steps)
+    n = int(seeds["charge"].shape[0])
+    fit_out = kf.fit_outputs(n, dev)
+    b_out = None
+
+    def step_chain():
+        nonlocal seeds, b_out
+        seeds = kf.seed_triplets(ctx, g3, soff, shp, shc, stream=stream)
+        kf.fit_tracks(ctx, g3, seeds["seed_state"], seeds["seed_cov"], seeds["charge"], seeds["hit_pos"],
+                      seeds["hit_cov"], seeds["hit_mask"], out=fit_out, stream=stream)
+        b_out = kf.build_tracks(ctx, build_geom, ev.hit_offsets[:E], hp, hc, seeds["event"], fit_out["state"],
+                                fit_out["cov"], seeds["charge"], out=b_out, stream=stream)
+
+    ms_chain = timed(step_chain, max(2, args.build_steps // 2))
+    hits = seeds["hits"].cpu().numpy()
+    trk = ev.seed_hit_track[hits]
+    st = np.where((trk[0] >= 0) & (trk[0] == trk[1]) & (trk[1] == trk[2]), trk[0], -1)
+    q = metrics.efficiency_fake_rate(b_out["hit"][:, 0].cpu().numpy(), st, ev.hit_track, ev.track_nhits,
+                                     eligible_tracks=ev.seed_track[ev.seed_event < E])
+    return {"value": E / (ms_chain * 1e-3), "unit": "events/s", "ms_per_step": ms_chain, "events": E,
+            "seeds": n, "seeds_per_event": n / E, "true_seed_share": float((st >= 0).mean()),
+            "form": "triplet search + seed inputs + 3-layer seed fit + build of every seed, default cuts "
+                    "(pT > 0.3 GeV, d0 < 0.15 cm, |z0| < 4 cm, dz < 0.8 cm; both charges above 2 GeV)",
+            "efficiency": q["efficiency"], "fake_rate": q["fake_rate"], "hit_purity": q["hit_purity"],
+            "search": {"value": n_hits / (ms_seed * 1e-3), "unit": "seed-layer hits/s", "ms_per_step": ms_seed,
+                       "seed_layer_hits": n_hits, "events_per_s": E / (ms_seed * 1e-3),
+                       "form": "binning + triplet search + count read-back + seed inputs"}}
 
 
 def bench_learned(args, kf, ctx, dev, stream, rank, ev, seed_geom, d_sf, fit_out, build_geom, hp, hc, se, sq, timed):

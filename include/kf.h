@@ -113,6 +113,8 @@ typedef struct {
     float window_nsigma;     /* search window half-width in sigmas */
     float hit_sigma_rphi;    /* nominal hit resolution used for the window, cm */
     float hit_sigma_z;
+    float window_max_dphi;   /* cap of the window's phi half-width, rad */
+    float window_max_dz;     /* cap of its z half-width, cm */
     int n_phi_bins;          /* hit bins per layer, in phi ... */
     int n_z_bins;            /* ... and in z */
     int use_proposal;        /* 1: the learned proposal keeps the top-k in-window hits */
@@ -120,8 +122,9 @@ typedef struct {
 } kf_options;
 
 /* Fill *opt with the defaults: routed precision (cond_max 1e4, pT in
- * [0.25, 200], gain_max 0), automatic launch, N = 6, chi2 cut 30, 3-sigma window,
- * 0.01/0.1 cm nominal resolution, 256 x 64 bins, proposal off, top-k 4. */
+ * [0.25, 200], gain_max 0), automatic launch, N = 6, chi2 cut 30, 3-sigma window
+ * capped at 0.05 rad and 5 cm, 0.01/0.1 cm nominal resolution, 256 x 64 bins,
+ * proposal off, top-k 4. */
 void kf_options_default(kf_options *opt);
 
 /* Create a context on CUDA device `device` (requires compute capability
@@ -205,8 +208,10 @@ int kf_fit_tracks_host(kf_context *ctx, const kf_geometry *geom, int64_t n_track
  * if it lies within the window
  *   |dphi| <= window_nsigma sqrt(sigma_rphi,pred^2 + hit_sigma_rphi^2) / r,
  *   |dz|   <= window_nsigma sqrt(sigma_z,pred^2 + hit_sigma_z^2)
- * around the predicted crossing and its chi2 increment is at most chi2_cut.
- * A candidate that cannot reach a layer, or crosses it beyond |z| = z_half,
+ * around the predicted crossing, the half-widths capped at window_max_dphi and
+ * window_max_dz (a prediction that has lost its precision, as near a
+ * tangential crossing, does not search the whole layer), and its chi2
+ * increment is at most chi2_cut.  A candidate that cannot reach a layer, or crosses it beyond |z| = z_half,
  * stops and yields only its hole child from then on (its flags record why).
  * Hits are first sorted into n_phi_bins x n_z_bins bins per (event, layer)
  * in context scratch (Section 3: hits partitioned spatially).

@@ -15,7 +15,10 @@
  * numbers): a hit is compatible if it lies in the window
  *   |dphi| <= nsigma sqrt(sigma_rphi,pred^2 + sigma_rphi,hit^2) / r,
  *   |dz|   <= nsigma sqrt(sigma_z,pred^2 + sigma_z,hit^2)
- * around the predicted crossing and its chi2 increment is at most chi2_cut;
+ * around the predicted crossing (half-widths capped at dphi_max and dz_max:
+ * a candidate whose prediction has lost its precision, as near a tangential
+ * crossing, does not search the whole layer) and its chi2 increment is at
+ * most chi2_cut;
  * ties in (hits, chi2) go to the lower candidate index, then the lower hit
  * index within the layer (the hole first); a candidate that cannot reach a
  * layer or crosses it beyond |z| = z_half stops and yields only its hole child
@@ -271,7 +274,7 @@ int orc_build_tracks_ex(int n_layers, const double *radii, const double *x_over_
                      double sigma_rphi_hit, double sigma_z_hit, int32_t *out_hit, double *out_chi2,
                      int32_t *out_nhits, double *out_state, double *out_cov, int32_t *out_ncand, double *log_f,
                      double *log_y, int32_t *log_ref, int64_t log_cap, int64_t *log_n, const double *mlp,
-                     int topk, int mlp_bf16)
+                     int topk, int mlp_bf16, double dphi_max, double dz_max)
 {
     const int N = max_cands, L = n_layers;
     const int64_t S = n_seeds;
@@ -318,8 +321,9 @@ int orc_build_tracks_ex(int n_layers, const double *radii, const double *x_over_
                     const double rc = hypot(xp, yp);
                     const double tx = -yp / rc, ty = xp / rc;
                     const double var_rphi = tx * tx * k->Cp[0] + 2.0 * tx * ty * k->Cp[1] + ty * ty * k->Cp[7];
-                    const double dphi = nsigma * sqrt(var_rphi + sigma_rphi_hit * sigma_rphi_hit) / radii[l];
-                    const double dz = nsigma * sqrt(k->Cp[14] + sigma_z_hit * sigma_z_hit);
+                    const double dphi =
+                        fmin(nsigma * sqrt(var_rphi + sigma_rphi_hit * sigma_rphi_hit) / radii[l], dphi_max);
+                    const double dz = fmin(nsigma * sqrt(k->Cp[14] + sigma_z_hit * sigma_z_hit), dz_max);
                     const double phic = atan2(yp, xp);
                     /* phi intervals of the window, split at +-pi */
                     double lo_[3], hi_[3];
@@ -459,5 +463,6 @@ int orc_build_tracks(int n_layers, const double *radii, const double *x_over_x0,
     return orc_build_tracks_ex(n_layers, radii, x_over_x0, z_half, bz, hit_offsets, hit_pos, hit_cov, H, phi, order,
                                s_begin, s_end, n_seeds, seed_event, seed_state, seed_cov, seed_charge, max_cands,
                                chi2_cut, nsigma, sigma_rphi_hit, sigma_z_hit, out_hit, out_chi2, out_nhits,
-                               out_state, out_cov, out_ncand, NULL, NULL, NULL, 0, NULL, NULL, 1, 0);
+                               out_state, out_cov, out_ncand, NULL, NULL, NULL, 0, NULL, NULL, 1, 0, HUGE_VAL,
+                               HUGE_VAL);
 }

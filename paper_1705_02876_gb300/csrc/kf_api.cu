@@ -160,6 +160,8 @@ void kf_options_default(kf_options *o)
     o->window_nsigma = 3.0f;
     o->hit_sigma_rphi = 0.01f;
     o->hit_sigma_z = 0.1f;
+    o->window_max_dphi = 0.05f;
+    o->window_max_dz = 5.0f;
     o->n_phi_bins = 256;
     o->n_z_bins = 64;
     o->use_proposal = 0;

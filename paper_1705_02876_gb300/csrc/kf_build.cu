@@ -50,7 +50,7 @@ struct BuildParams {
     Routing rt;
     BinGrid bg;
     int N;
-    float chi2_cut, nsigma, sig_rphi2, sig_z2;
+    float chi2_cut, nsigma, sig_rphi2, sig_z2, max_dphi, max_dz;
     int64_t S, H;
     int n_events;
     const int64_t *ev_off;  // [E][L + 1]
@@ -270,8 +270,8 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
             ctt = fmaf(ny * ny, c[pk(0, 0)], fmaf(-2.0f * nx * ny, c[pk(1, 0)], nx * nx * c[pk(1, 1)]));
             ctz = fmaf(nx, c[pk(2, 1)], -ny * c[pk(2, 0)]);
             czz = c[pk(2, 2)];
-            win.dphi = p.nsigma * sqrtf(ctt + p.sig_rphi2) * p.g.inv_r[l];
-            win.dz = p.nsigma * sqrtf(czz + p.sig_z2);
+            win.dphi = fminf(p.nsigma * sqrtf(ctt + p.sig_rphi2) * p.g.inv_r[l], p.max_dphi);
+            win.dz = fminf(p.nsigma * sqrtf(czz + p.sig_z2), p.max_dz);
             win.phic = atan2f(x[1], x[0]);
             win.z = x[2];
             win.bo = p.bin_off + (((int64_t)ev * L + l) * (nbins + 1));
@@ -571,8 +571,10 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
     if ((rc = check_geometry(ctx, geom, &g))) return rc;
     if ((rc = check_options(ctx, o))) return rc;
     if (o.max_cands < 1 || o.max_cands > 8) return set_error(ctx, KF_ERR_ARG, "max_cands must be 1..8");
-    if (!(o.chi2_cut > 0.0f) || !(o.window_nsigma > 0.0f) || !(o.hit_sigma_rphi >= 0.0f) || !(o.hit_sigma_z >= 0.0f))
-        return set_error(ctx, KF_ERR_ARG, "chi2_cut and window_nsigma must be positive, hit sigmas non-negative");
+    if (!(o.chi2_cut > 0.0f) || !(o.window_nsigma > 0.0f) || !(o.hit_sigma_rphi >= 0.0f) || !(o.hit_sigma_z >= 0.0f) ||
+        !(o.window_max_dphi > 0.0f) || !(o.window_max_dz > 0.0f))
+        return set_error(ctx, KF_ERR_ARG,
+                         "chi2_cut, window_nsigma and the window caps must be positive, hit sigmas non-negative");
     if (o.n_phi_bins < 1 || o.n_z_bins < 1 || (int64_t)o.n_phi_bins * o.n_z_bins > 16384)
         return set_error(ctx, KF_ERR_ARG, "n_phi_bins x n_z_bins must be 1..16384");
     const __nv_bfloat16 *W1 = nullptr, *W2 = nullptr;
@@ -685,6 +687,8 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
     p.nsigma = o.window_nsigma;
     p.sig_rphi2 = o.hit_sigma_rphi * o.hit_sigma_rphi;
     p.sig_z2 = o.hit_sigma_z * o.hit_sigma_z;
+    p.max_dphi = o.window_max_dphi;
+    p.max_dz = o.window_max_dz;
     p.S = n_seeds;
     p.H = n_hits;
     p.n_events = n_events;

@@ -49,6 +49,7 @@ class Options(ctypes.Structure):
                 ("reg_cap", ctypes.c_int), ("max_cands", ctypes.c_int),
                 ("chi2_cut", ctypes.c_float), ("window_nsigma", ctypes.c_float),
                 ("hit_sigma_rphi", ctypes.c_float), ("hit_sigma_z", ctypes.c_float),
+                ("window_max_dphi", ctypes.c_float), ("window_max_dz", ctypes.c_float),
                 ("n_phi_bins", ctypes.c_int), ("n_z_bins", ctypes.c_int),
                 ("use_proposal", ctypes.c_int), ("topk", ctypes.c_int)]
 
@@ -118,8 +119,8 @@ def header_functions() -> list[str]:
 class Seeding(ctypes.Structure):
     _fields_ = [("pt_min", ctypes.c_float), ("d0_max", ctypes.c_float), ("z0_max", ctypes.c_float),
                 ("dz_max", ctypes.c_float), ("pt_both_charges", ctypes.c_float), ("pt_unresolved", ctypes.c_float),
-                ("p_sigma_resolved", ctypes.c_float), ("p_sigma_unresolved", ctypes.c_float), ("n_phi_bins", ctypes.c_int),
-                ("n_z_bins", ctypes.c_int)]
+                ("p_sigma_resolved", ctypes.c_float), ("p_sigma_unresolved", ctypes.c_float),
+                ("n_phi_bins", ctypes.c_int), ("n_z_bins", ctypes.c_int)]
 
 
 def seeding(**kw) -> Seeding:

@@ -37,10 +37,21 @@ def efficiency_fake_rate(best_hits, seed_track, hit_track, track_nhits, n_seed_h
     matched_track = np.full(S, -1, dtype=np.int64)
     ok = 2 * own >= n_total
     matched_track[ok] = seed_track[ok]
-    for s in np.nonzero(~ok)[0]:
-        vals, cnt = np.unique(owner[s][owner[s] >= 0], return_counts=True)
-        if len(cnt) and 2 * cnt.max() >= n_total[s]:
-            matched_track[s] = vals[np.argmax(cnt)]
+    rest = np.nonzero(~ok)[0]
+    if len(rest) and best_hits.shape[1]:
+        # most frequent owner per row: sort each row, run lengths from the
+        # start index of each run of equal values
+        o = np.sort(owner[rest], axis=1)
+        L = o.shape[1]
+        j = np.broadcast_to(np.arange(L), o.shape)
+        new_run = np.ones_like(o, dtype=bool)
+        new_run[:, 1:] = o[:, 1:] != o[:, :-1]
+        start = np.maximum.accumulate(np.where(new_run, j, 0), axis=1)
+        run = np.where(o >= 0, j - start + 1, 0)
+        arg = run.argmax(axis=1)
+        cnt = run[np.arange(len(rest)), arg]
+        hit = (cnt > 0) & (2 * cnt >= n_total[rest])
+        matched_track[rest[hit]] = o[np.arange(len(rest)), arg][hit]
     counted = n_total >= min_hits
     fake = counted & (matched_track < 0)
     if eligible_tracks is None:

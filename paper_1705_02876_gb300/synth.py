@@ -417,13 +417,14 @@ class BuildEvents:
 def make_build_events(seed: int, n_events: int, tracks_per_event: int, geom: Geometry | None = None,
                       noise_factor: float = 10.0, n_seed_layers: int = 3, sigma_rphi=0.01,
                       sigma_z=0.1, ms=True, pt_lo=0.5, pt_hi=10.0, eta_max=1.0,
-                      noise_per_layer: int | None = None, seed_layer_hits: bool = False) -> BuildEvents:
+                      noise_per_layer: int | None = None, seed_layer_hits: bool = False,
+                      seed_noise_per_layer: int | None = None) -> BuildEvents:
     """``n_events`` events of ``tracks_per_event`` simulated tracks each, plus
     ``noise_factor`` x tracks_per_event uniform noise hits per layer (or
     ``noise_per_layer``), on the toy barrel (17 layers by default).  With
     ``seed_layer_hits`` the seed layers' hits (every track's true hits plus the
-    same density of noise, from a stream of their own) are stored too, for
-    seeding from hits."""
+    same density of noise, or ``seed_noise_per_layer`` noise hits, from a
+    stream of their own) are stored too, for seeding from hits."""
     geom = geom or toy_geometry(17)
     L = geom.n_layers
     r_kin, r_hit, r_ms, r_eff, r_seed, r_noise, r_perm = _streams(seed, 7)
@@ -483,6 +484,7 @@ def make_build_events(seed: int, n_events: int, tracks_per_event: int, geom: Geo
     ev.track_pt = np.hypot(vertex[3], vertex[4])
     if seed_layer_hits:
         r_snoise, r_sperm = _streams(seed, 10)[8:10]
+        n_snoise = n_noise if seed_noise_per_layer is None else int(seed_noise_per_layer)
         sp, sc, st = [], [], []
         soff = np.zeros((n_events, n_seed_layers + 1), dtype=np.int64)
         cur = 0
@@ -490,13 +492,13 @@ def make_build_events(seed: int, n_events: int, tracks_per_event: int, geom: Geo
             lo, hi = e * tracks_per_event, (e + 1) * tracks_per_event
             for l in range(n_seed_layers):
                 has = ((sim["hit_mask"][lo:hi] >> np.uint32(l)) & np.uint32(1)).astype(bool)
-                phi = r_snoise.uniform(0.0, 2.0 * math.pi, n_noise)
-                zz = r_snoise.uniform(-geom.z_half, geom.z_half, n_noise)
+                phi = r_snoise.uniform(0.0, 2.0 * math.pi, n_snoise)
+                zz = r_snoise.uniform(-geom.z_half, geom.z_half, n_snoise)
                 nxp, nyp = geom.radii[l] * np.cos(phi), geom.radii[l] * np.sin(phi)
                 pos = np.concatenate([sim["hit_pos"][l][:, lo:hi][:, has], np.stack([nxp, nyp, zz])], axis=1)
                 cov = np.concatenate([sim["hit_cov"][l][:, lo:hi][:, has],
                                       hit_covariance(nxp, nyp, sigma_rphi, sigma_rphi, sigma_z)], axis=1)
-                trk = np.concatenate([np.arange(lo, hi)[has], np.full(n_noise, -1, dtype=np.int64)])
+                trk = np.concatenate([np.arange(lo, hi)[has], np.full(n_snoise, -1, dtype=np.int64)])
                 perm = r_sperm.permutation(pos.shape[1])
                 sp.append(pos[:, perm])
                 sc.append(cov[:, perm])

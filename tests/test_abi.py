@@ -1,6 +1,7 @@
 """The C library builds for sm_103a, loads, and exports every function the
 header declares; host-side argument checks need no GPU."""
 import ctypes
+import os
 import subprocess
 
 import pytest
@@ -26,8 +27,36 @@ def test_options_defaults_and_struct_size():
     o = kf.options()
     assert o.precision_mode == kf.PRECISION_ROUTED
     assert o.max_cands == 6 and abs(o.chi2_cut - 30.0) < 1e-6 and o.topk == 4
-    # the ctypes mirror has the C struct's size: 17 four-byte fields
-    assert ctypes.sizeof(kf.Options) == 17 * 4
+    assert abs(o.window_max_dphi - 0.05) < 1e-7 and abs(o.window_max_dz - 5.0) < 1e-6
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of kf_options, kf_seeding and kf_geometry have the C
+    structs' sizes and field offsets, as gcc lays them out from kf.h."""
+    pytest.importorskip("torch")
+    import shutil
+    from paper_1705_02876_gb300 import kf
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    mirrors = {"kf_options": kf.Options, "kf_seeding": kf.Seeding, "kf_geometry": kf.Geometry}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kf.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(kf.HEADER), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        c, f, v = line.split()
+        got[(c, f)] = int(v)
+    for cname, py in mirrors.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
 
 
 def test_context_create_fails_cleanly_without_gpu():

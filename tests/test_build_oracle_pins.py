@@ -56,7 +56,7 @@ def test_exhaustive_clone_engine_equals_fits_of_every_sequence(oracle):
     sc = _packed(C0).astype(np.float32)[:, None]
     r = oracle.build_arrays(geom.radii, geom.x_over_x0, geom.z_half, np.float32(geom.bz), off, hit_pos, hit_cov,
                             np.zeros(1, np.int32), ss, sc, np.ones(1, np.int8), max_cands=16, chi2_cut=1e9,
-                            nsigma=1e4, threads=1)
+                            nsigma=1e4, threads=1, dphi_max=None, dz_max=None)
     assert r["ncand"][0] == 16
     seen = set()
     prev = None
@@ -83,7 +83,7 @@ def test_exhaustive_clone_engine_equals_fits_of_every_sequence(oracle):
     assert len(seen) == 16
 
 
-def _best_hit_numpy(oracle, ev, seeds, nsigma=3.0, cut=30.0, s_rphi=0.01, s_z=0.1):
+def _best_hit_numpy(oracle, ev, seeds, nsigma=3.0, cut=30.0, s_rphi=0.01, s_z=0.1, dphi_max=0.05, dz_max=5.0):
     """Best-hit building written plainly: for each layer keep the compatible
     hit with the lowest chi2 increment (lowest index on a tie), else a hole."""
     g = ev.build_geom
@@ -107,8 +107,8 @@ def _best_hit_numpy(oracle, ev, seeds, nsigma=3.0, cut=30.0, s_rphi=0.01, s_z=0.
             lo, hi = ev.hit_offsets[e, l], ev.hit_offsets[e, l + 1]
             t = np.array([-xp[1], xp[0]]) / math.hypot(xp[0], xp[1])
             var_rphi = t @ Cp[:2, :2] @ t
-            dphi = nsigma * math.sqrt(var_rphi + s_rphi ** 2) / radii[l]
-            dz = nsigma * math.sqrt(Cp[2, 2] + s_z ** 2)
+            dphi = min(nsigma * math.sqrt(var_rphi + s_rphi ** 2) / radii[l], dphi_max)
+            dz = min(nsigma * math.sqrt(Cp[2, 2] + s_z ** 2), dz_max)
             d = phi_all[lo:hi] - math.atan2(xp[1], xp[0])
             d = (d + math.pi) % (2 * math.pi) - math.pi
             cand = np.nonzero((np.abs(d) <= dphi) & (np.abs(pos[2, lo:hi] - xp[2]) <= dz))[0]
@@ -136,12 +136,53 @@ def test_best_hit_is_clone_engine_with_one_candidate(oracle):
     assert np.array_equal(r["hit"][:, 0, :], ref)
 
 
+def test_window_caps(oracle):
+    """A candidate with a wide prediction: the hits it considers (the training
+    log lists every in-window hit) are those of a brute-force box of
+    half-widths min(nsigma sigma, cap) around the predicted crossing, with and
+    without caps."""
+    geom = synth.Geometry(np.array([16.0]), np.array([0.0]), 100.0, 3.8)
+    rng = np.random.default_rng(5)
+    n = 20000
+    phi = rng.uniform(-np.pi, np.pi, n)
+    z = rng.uniform(-100.0, 100.0, n)
+    hit_pos = np.stack([16.0 * np.cos(phi), 16.0 * np.sin(phi), z]).astype(np.float32)
+    hit_cov = synth.hit_covariance(hit_pos[0], hit_pos[1], 0.01, 0.01, 0.1).astype(np.float32)
+    seed = np.array([8.0, 1.0, 0.5, 2.0, 0.3, 0.4])
+    C0 = np.diag([0.25, 0.25, 16.0, 1e-3, 1e-3, 1e-3])
+    ss = seed.astype(np.float32)[:, None]
+    sc = _packed(C0).astype(np.float32)[:, None]
+    bz = float(np.float32(geom.bz))
+    ok, xp, J, _ = oracle.propagate(ss[:, 0].astype(np.float64), 1, bz, 16.0)
+    assert ok
+    Cp = J @ _unpack(sc[:, 0].astype(np.float64)) @ J.T
+    t = np.array([-xp[1], xp[0]]) / math.hypot(xp[0], xp[1])
+    w_phi = 3.0 * math.sqrt(t @ Cp[:2, :2] @ t + 0.01 ** 2) / 16.0
+    w_z = 3.0 * math.sqrt(Cp[2, 2] + 0.1 ** 2)
+    pos = hit_pos.astype(np.float64)
+    d = np.arctan2(pos[1], pos[0]) - math.atan2(xp[1], xp[0])
+    d = (d + math.pi) % (2 * math.pi) - math.pi
+    counts = []
+    for cap_phi, cap_z in ((None, None), (0.05, 5.0), (0.02, 1.0)):
+        wp = w_phi if cap_phi is None else min(w_phi, cap_phi)
+        wz = w_z if cap_z is None else min(w_z, cap_z)
+        box = np.nonzero((np.abs(d) <= wp) & (np.abs(pos[2] - xp[2]) <= wz))[0]
+        r = oracle.build_arrays(geom.radii, geom.x_over_x0, geom.z_half, bz, np.array([[0, n]], np.int64),
+                                hit_pos, hit_cov, np.zeros(1, np.int32), ss, sc, np.ones(1, np.int8), max_cands=1,
+                                chi2_cut=1e12, threads=1, log=True, dphi_max=cap_phi, dz_max=cap_z)
+        got = np.sort(r["log"]["ref"][:, 3])
+        assert np.array_equal(got, box), (cap_phi, len(got), len(box))
+        counts.append(len(box))
+    assert w_phi > 0.05 and w_z > 5.0  # both caps bind
+    assert counts[0] > counts[1] > counts[2] > 0
+
+
 def test_noise_free_events_recover_the_seed_tracks(oracle):
     """One track per event, no noise and a window and cut wide enough for any
     hit: the best candidate of every seed holds exactly the hits its track
     left on the build layers."""
     ev = synth.make_build_events(12, 300, 1, noise_per_layer=0)
-    r = oracle.build_events(ev, max_cands=6, nsigma=1e4, chi2_cut=1e12)
+    r = oracle.build_events(ev, max_cands=6, nsigma=1e4, chi2_cut=1e12, dphi_max=None, dz_max=None)
     best = r["hit"][:, 0, :]
     own = np.where(best >= 0, ev.hit_track[np.maximum(best, 0)], -1)
     assert np.all((best < 0) | (own == ev.seed_track[:, None]))
