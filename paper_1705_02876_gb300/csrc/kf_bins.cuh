@@ -28,8 +28,8 @@ __device__ __forceinline__ int z_bin(float z, const BinGrid &bg)
 }
 
 // One block per (event, layer) segment: count hits per bin in shared memory,
-// scan, scatter each hit's key (phi, z, index within the segment) bin by bin
-// (bin = iz * n_phi + iphi).  A key is one 16-byte store here and one 16-byte
+// scan, scatter each hit's key (phi, z, index within the segment, transverse
+// radius) bin by bin (bin = iz * n_phi + iphi).  A key is one 16-byte store here and one 16-byte
 // load in the window scan: the destinations are random at a few hits per bin,
 // so each key costs one memory sector, not three.
 template <int THREADS>
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(THREADS) bin_hits_kernel(const int64_t *seg_of
         const float x = hit_pos[h], y = hit_pos[H + h], z = hit_pos[2 * H + h];
         const float phi = atan2f(y, x);
         const int p = atomicAdd(&cnt[z_bin(z, bg) * bg.n_phi + phi_bin(phi, bg.n_phi)], 1);
-        bkey[lo + p] = make_float4(phi, z, __int_as_float((int)(h - lo)), 0.0f);
+        bkey[lo + p] = make_float4(phi, z, __int_as_float((int)(h - lo)), sqrtf(x * x + y * y));
     }
 }
 

@@ -20,7 +20,7 @@
 // Bz > 0); a triplet with pT above pt_both_charges (|kappa| the hits cannot
 // resolve) seeds both charges.
 //
-// One thread per hit of the middle layer scans the binned hits of layer 0 in
+// One warp per hit of the middle layer scans the binned hits of layer 0 in
 // its window, and for every doublet passing (a) and (b) the binned hits of
 // layer 2 in theirs; the windows' z ranges are widened for hit radii within
 // 0.1 cm of the layer radius, and every candidate is then tested exactly.
@@ -97,88 +97,166 @@ __device__ __forceinline__ bool triplet_circle(float x0, float y0, float x1, flo
     return true;
 }
 
-// Visit the binned keys of segment `seg` with phi within w of phic and z in
-// [zlo, zhi] (bin ranges only; the caller applies the exact tests).
-template <class F>
-__device__ __forceinline__ void scan_bins(const SeedParams &p, int64_t seg, float phic, float w, float zlo, float zhi,
-                                          F &&f)
+// The bins of a window as contiguous key runs: for each z row iz0..iz1 the
+// phi bins a0..b0-1, and a1..b1-1 when the window wraps past +-pi (keys are
+// stored bin by bin, bin = iz * n_phi + iphi, so each run is one key range).
+struct Runs {
+    int iz0, iz1, a0, b0, a1, b1;
+};
+
+__device__ __forceinline__ Runs window_runs(const BinGrid &bg, float phic, float w, float zlo, float zhi)
 {
-    const int nb = p.bg.n_phi * p.bg.n_z;
-    const int32_t *bo = p.bin_off + seg * (nb + 1);
-    const int64_t lo = p.seg_off[seg];
-    const int iz0 = z_bin(zlo, p.bg), iz1 = z_bin(zhi, p.bg);
-    int ip0, nphi;
+    Runs r;
+    r.iz0 = z_bin(zlo, bg);
+    r.iz1 = z_bin(zhi, bg);
+    r.a1 = r.b1 = 0;
     if (w >= kPi) {
-        ip0 = 0;
-        nphi = p.bg.n_phi;
-    } else {
-        const float pm = 1e-5f;
-        ip0 = (int)floorf((phic - w - pm + kPi) * (float)p.bg.n_phi * (1.0f / (2.0f * kPi)));
-        const int ip1 = (int)floorf((phic + w + pm + kPi) * (float)p.bg.n_phi * (1.0f / (2.0f * kPi)));
-        nphi = min(ip1 - ip0 + 1, p.bg.n_phi);
+        r.a0 = 0;
+        r.b0 = bg.n_phi;
+        return r;
     }
-    for (int iz = iz0; iz <= iz1; ++iz)
-        for (int k = 0; k < nphi; ++k) {
-            int ip = ip0 + k;
-            ip = ip < 0 ? ip + p.bg.n_phi : (ip >= p.bg.n_phi ? ip - p.bg.n_phi : ip);
-            const int b = iz * p.bg.n_phi + ip;
-            for (int q = bo[b]; q < bo[b + 1]; ++q) f(p.bkey[lo + q], lo);
-        }
+    const float pm = 1e-5f, scale = (float)bg.n_phi * (1.0f / (2.0f * kPi));
+    int ip0 = (int)floorf((phic - w - pm + kPi) * scale);
+    const int ip1 = (int)floorf((phic + w + pm + kPi) * scale);
+    const int nphi = min(ip1 - ip0 + 1, bg.n_phi);
+    if (ip0 < 0) ip0 += bg.n_phi;  // phic in [-pi, pi], w < pi: ip0 >= -n_phi
+    r.a0 = ip0;
+    if (ip0 + nphi <= bg.n_phi) {
+        r.b0 = ip0 + nphi;
+    } else {
+        r.b0 = bg.n_phi;
+        r.b1 = ip0 + nphi - bg.n_phi;
+    }
+    return r;
 }
 
-__global__ void __launch_bounds__(128) triplet_kernel(const SeedParams p)
+constexpr int kSeedWarps = 4;      // warps per block, one middle-layer hit each at a time
+constexpr int kDoubletQueue = 64;  // doublets a warp collects before scanning layer 2 for them
+
+// One warp per hit h1 of the middle layer: the lanes stride over the key runs
+// of h1's layer-0 window and queue the doublets passing (a) and (b) in shared
+// memory; for each queued doublet the lanes stride over the key runs of its
+// layer-2 window and apply (d), (e) and (c).  Triplets are appended with one
+// atomic per warp and ballot (a triplet seeded with both charges takes two
+// slots); the count keeps growing past the capacity so that the host can
+// size a rerun.
+__global__ void __launch_bounds__(32 * kSeedWarps) triplet_kernel(const SeedParams p)
 {
+    __shared__ int32_t queue[kSeedWarps][kDoubletQueue];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const int e = blockIdx.y;
-    const int64_t s1 = p.seg_off[3 * e + 1], s2 = p.seg_off[3 * e + 2];
-    const int64_t h1 = s1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (h1 >= s2) return;
+    const int64_t lo0 = p.seg_off[3 * e], s1 = p.seg_off[3 * e + 1], lo2 = p.seg_off[3 * e + 2];
+    const int n_phi = p.bg.n_phi, nb = n_phi * p.bg.n_z;
+    const int32_t *bo0 = p.bin_off + (int64_t)(3 * e) * (nb + 1);
+    const int32_t *bo2 = p.bin_off + (int64_t)(3 * e + 2) * (nb + 1);
     const int64_t H = p.H;
-    const float x1 = p.hit_pos[h1], y1 = p.hit_pos[H + h1], z1 = p.hit_pos[2 * H + h1];
-    const float r1 = sqrtf(x1 * x1 + y1 * y1), f1 = atan2f(y1, x1);
-    // layer 0: z0 = (z_0 r_1 - z_1 r_0) / (r_1 - r_0) within z0_max, for r_0 near R_0
-    float zlo = INFINITY, zhi = -INFINITY;
+    for (int64_t h1 = s1 + (int64_t)blockIdx.x * kSeedWarps + wq; h1 < lo2;
+         h1 += (int64_t)gridDim.x * kSeedWarps) {
+        const float x1 = p.hit_pos[h1], y1 = p.hit_pos[H + h1], z1 = p.hit_pos[2 * H + h1];
+        const float r1 = sqrtf(x1 * x1 + y1 * y1), f1 = atan2f(y1, x1);
+        // layer 0: z0 = (z_0 r_1 - z_1 r_0) / (r_1 - r_0) within z0_max, for r_0 near R_0
+        float zlo = INFINITY, zhi = -INFINITY;
 #pragma unroll
-    for (int s = -1; s <= 1; s += 2) {
-        const float r0 = p.R[0] + s * kRadialSlack;
-        zlo = fminf(zlo, (z1 * r0 - p.z0_max * (r1 - r0)) / r1);
-        zhi = fmaxf(zhi, (z1 * r0 + p.z0_max * (r1 - r0)) / r1);
-    }
-    const float zm = 1e-3f * (1.0f + fabsf(zlo) + fabsf(zhi));
-    scan_bins(p, 3 * e, f1, p.w01, zlo - zm, zhi + zm, [&](const float4 k0, int64_t lo0) {
-        if (!(fabsf(wrap_pi(f1 - k0.x)) <= p.w01)) return;
-        const int64_t h0 = lo0 + __float_as_int(k0.z);
-        const float x0 = p.hit_pos[h0], y0 = p.hit_pos[H + h0], z0 = p.hit_pos[2 * H + h0];
-        const float r0 = sqrtf(x0 * x0 + y0 * y0);
-        const float zv = (z0 * r1 - z1 * r0) / (r1 - r0);
-        if (!(fabsf(zv) <= p.z0_max)) return;
-        const float slope = (z1 - z0) / (r1 - r0);
-        const float zaa = fmaf(slope, p.R[2] - kRadialSlack - r1, z1), zbb = fmaf(slope, p.R[2] + kRadialSlack - r1, z1);
-        const float z2lo = fminf(zaa, zbb) - p.dz_max, z2hi = fmaxf(zaa, zbb) + p.dz_max;
-        const float zm2 = 1e-3f * (1.0f + fabsf(z2lo) + fabsf(z2hi));
-        scan_bins(p, 3 * e + 2, f1, p.w12, z2lo - zm2, z2hi + zm2, [&](const float4 k2, int64_t lo2) {
-            if (!(fabsf(wrap_pi(k2.x - f1)) <= p.w12)) return;
-            const int64_t h2 = lo2 + __float_as_int(k2.z);
-            const float x2 = p.hit_pos[h2], y2 = p.hit_pos[H + h2], z2 = p.hit_pos[2 * H + h2];
-            const float r2 = sqrtf(x2 * x2 + y2 * y2);
-            const float zp = z1 + (z1 - z0) * (r2 - r1) / (r1 - r0);
-            if (!(fabsf(z2 - zp) <= p.dz_max)) return;
-            Circle c;
-            if (!triplet_circle(x0, y0, x1, y1, x2, y2, &c)) return;
-            if (!(fabsf(c.kappa) <= p.kmax) || !(c.d0 <= p.d0_max)) return;
-            const int q = c.orient * p.bz < 0.0f ? 1 : -1;
-            const int nq = fabsf(c.kappa) <= p.kamb ? 2 : 1;
-            const unsigned long long i0 = atomicAdd(p.count, (unsigned long long)nq);
-            for (int j = 0; j < nq; ++j) {
-                const unsigned long long i = i0 + j;
-                if (i >= (unsigned long long)p.cap) break;
-                p.trip[0 * p.cap + i] = e;
-                p.trip[1 * p.cap + i] = (int32_t)h0;
-                p.trip[2 * p.cap + i] = (int32_t)h1;
-                p.trip[3 * p.cap + i] = (int32_t)h2;
-                p.trip[4 * p.cap + i] = j == 0 ? q : -q;
+        for (int sg = -1; sg <= 1; sg += 2) {
+            const float r0 = p.R[0] + sg * kRadialSlack;
+            zlo = fminf(zlo, (z1 * r0 - p.z0_max * (r1 - r0)) / r1);
+            zhi = fmaxf(zhi, (z1 * r0 + p.z0_max * (r1 - r0)) / r1);
+        }
+        const float zm = 1e-3f * (1.0f + fabsf(zlo) + fabsf(zhi));
+        const Runs w0 = window_runs(p.bg, f1, p.w01, zlo - zm, zhi + zm);
+        int nq = 0;  // queued doublets (warp-uniform)
+
+        auto drain = [&]() {
+            for (int d = 0; d < nq; ++d) {
+                const int64_t h0 = queue[wq][d];
+                const float x0 = p.hit_pos[h0], y0 = p.hit_pos[H + h0], z0 = p.hit_pos[2 * H + h0];
+                const float r0 = sqrtf(x0 * x0 + y0 * y0);
+                const float slope = (z1 - z0) / (r1 - r0);
+                const float zaa = fmaf(slope, p.R[2] - kRadialSlack - r1, z1);
+                const float zbb = fmaf(slope, p.R[2] + kRadialSlack - r1, z1);
+                const float z2lo = fminf(zaa, zbb) - p.dz_max, z2hi = fmaxf(zaa, zbb) + p.dz_max;
+                const float zm2 = 1e-3f * (1.0f + fabsf(z2lo) + fabsf(z2hi));
+                const Runs w2 = window_runs(p.bg, f1, p.w12, z2lo - zm2, z2hi + zm2);
+                for (int iz = w2.iz0; iz <= w2.iz1; ++iz)
+                    for (int run = 0; run < 2; ++run) {
+                        const int a = run ? w2.a1 : w2.a0, b = run ? w2.b1 : w2.b0;
+                        if (a >= b) continue;
+                        const int ka = bo2[iz * n_phi + a], kb = bo2[iz * n_phi + b];
+                        for (int base = ka; base < kb; base += 32) {
+                            const int j = base + lane;
+                            bool pass = false;
+                            int q = 0, nqq = 0;
+                            int32_t h2 = 0;
+                            if (j < kb) {
+                                const float4 k2 = p.bkey[lo2 + j];
+                                if (fabsf(wrap_pi(k2.x - f1)) <= p.w12) {
+                                    // the key holds z and r: x and y are read only for a
+                                    // candidate within dz_max
+                                    const float zp = z1 + (z1 - z0) * (k2.w - r1) / (r1 - r0);
+                                    Circle c;
+                                    if (fabsf(k2.y - zp) <= p.dz_max) {
+                                        h2 = (int32_t)(lo2 + __float_as_int(k2.z));
+                                        const float x2 = p.hit_pos[h2], y2 = p.hit_pos[H + h2];
+                                        pass = triplet_circle(x0, y0, x1, y1, x2, y2, &c) &&
+                                               fabsf(c.kappa) <= p.kmax && c.d0 <= p.d0_max;
+                                    }
+                                    if (pass) {
+                                        q = c.orient * p.bz < 0.0f ? 1 : -1;
+                                        nqq = fabsf(c.kappa) <= p.kamb ? 2 : 1;
+                                    }
+                                }
+                            }
+                            const unsigned m1 = __ballot_sync(~0u, pass), m2 = __ballot_sync(~0u, nqq == 2);
+                            if (m1) {
+                                unsigned long long i0 = 0;
+                                if (lane == 0)
+                                    i0 = atomicAdd(p.count, (unsigned long long)(__popc(m1) + __popc(m2)));
+                                i0 = __shfl_sync(~0u, i0, 0) + __popc(m1 & lt) + __popc(m2 & lt);
+                                for (int jj = 0; jj < nqq; ++jj) {
+                                    const unsigned long long i = i0 + jj;
+                                    if (i >= (unsigned long long)p.cap) break;
+                                    p.trip[0 * p.cap + i] = e;
+                                    p.trip[1 * p.cap + i] = (int32_t)h0;
+                                    p.trip[2 * p.cap + i] = (int32_t)h1;
+                                    p.trip[3 * p.cap + i] = h2;
+                                    p.trip[4 * p.cap + i] = jj == 0 ? q : -q;
+                                }
+                            }
+                        }
+                    }
             }
-        });
-    });
+            nq = 0;
+            __syncwarp();  // the queue is read before it is refilled
+        };
+
+        for (int iz = w0.iz0; iz <= w0.iz1; ++iz)
+            for (int run = 0; run < 2; ++run) {
+                const int a = run ? w0.a1 : w0.a0, b = run ? w0.b1 : w0.b0;
+                if (a >= b) continue;
+                const int ka = bo0[iz * n_phi + a], kb = bo0[iz * n_phi + b];
+                for (int base = ka; base < kb; base += 32) {
+                    const int j = base + lane;
+                    bool ok = false;
+                    int32_t h0 = 0;
+                    if (j < kb) {
+                        const float4 k0 = p.bkey[lo0 + j];
+                        if (fabsf(wrap_pi(f1 - k0.x)) <= p.w01) {
+                            h0 = (int32_t)(lo0 + __float_as_int(k0.z));
+                            const float zv = (k0.y * r1 - z1 * k0.w) / (r1 - k0.w);  // key: z_0, r_0
+                            ok = fabsf(zv) <= p.z0_max;
+                        }
+                    }
+                    const unsigned m = __ballot_sync(~0u, ok);
+                    const int c = __popc(m);
+                    if (nq + c > kDoubletQueue) drain();
+                    if (ok) queue[wq][nq + __popc(m & lt)] = h0;
+                    __syncwarp();
+                    nq += c;
+                }
+            }
+        drain();
+    }
 }
 
 struct FetchParams {
@@ -386,8 +464,8 @@ extern "C" int kf_seed_triplets(kf_context *ctx, const kf_geometry *geom, int n_
         if ((e = cudaMemsetAsync(st->count, 0, sizeof(unsigned long long), stream)) != cudaSuccess)
             return cuda_error(ctx, e, "seeding counter");
         if (max_l1 > 0) {
-            const dim3 grid((unsigned)((max_l1 + 127) / 128), (unsigned)n_events);
-            triplet_kernel<<<grid, 128, 0, stream>>>(p);
+            const dim3 grid((unsigned)((max_l1 + kSeedWarps - 1) / kSeedWarps), (unsigned)n_events);
+            triplet_kernel<<<grid, 32 * kSeedWarps, 0, stream>>>(p);
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(ctx, e, "triplet search");
         }
         unsigned long long cnt = 0;
