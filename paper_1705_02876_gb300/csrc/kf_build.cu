@@ -671,11 +671,11 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
     const size_t bin_smem = (size_t)(nb + 1) * sizeof(int);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(bin_hits_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16385 * 4);
+        cudaFuncSetAttribute(bin_hits_kernel<kBinThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16385 * 4);
         attr_set = true;
     }
-    bin_hits_kernel<1024><<<(unsigned)n_seg, 1024, bin_smem, stream>>>(st->seg_off, hit_pos, n_hits, bg, st->bkey,
-                                                                        st->bin_off);
+    bin_hits_kernel<kBinThreads><<<(unsigned)n_seg, kBinThreads, bin_smem, stream>>>(st->seg_off, hit_pos, n_hits,
+                                                                                    bg, st->bkey, st->bin_off);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(ctx, e, "binning launch");
 
     BuildParams p;

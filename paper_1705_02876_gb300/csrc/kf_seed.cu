@@ -426,10 +426,10 @@ extern "C" int kf_seed_triplets(kf_context *ctx, const kf_geometry *geom, int n_
     BinGrid bg{o.n_phi_bins, o.n_z_bins, g.z_half};
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(bin_hits_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16385 * 4);
+        cudaFuncSetAttribute(bin_hits_kernel<kBinThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16385 * 4);
         attr = true;
     }
-    bin_hits_kernel<1024><<<(unsigned)n_seg, 1024, (size_t)(nb + 1) * sizeof(int), stream>>>(
+    bin_hits_kernel<kBinThreads><<<(unsigned)n_seg, kBinThreads, (size_t)(nb + 1) * sizeof(int), stream>>>(
         st->seg_off, hit_pos, n_hits, bg, st->bkey, st->bin_off);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(ctx, e, "seeding binning");
 
