@@ -57,7 +57,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--precision", default="routed", choices=["routed", "fp32"],
                    help="precision of the timed fit (the chosen form is routed)")
-    p.add_argument("--shape", default=None, help="fixed fit launch shape TRACKS_PER_BLOCK:REG_CAP (no tuning)")
+    p.add_argument("--shape", default=None,
+                   help="fixed fit launch shape TRACKS_PER_BLOCK:REG_CAP[:HIT_PREFETCH] (no tuning; prefetch 1 if omitted)")
     p.add_argument("--build-events", type=int, default=64, help="events of the build workload (0: skip it)")
     p.add_argument("--build-steps", type=int, default=10)
     p.add_argument("--no-ragged", action="store_true", help="skip the ragged-batching comparison")
@@ -476,7 +477,8 @@ def bench_ragged(args, kf, ctx, dev, stream, rank):
         res[name] = {"value": T / (ms * 1e-3), "unit": "tracks/s", "ms_per_step": ms,
                      "launches_per_step": 1 if mode != kf.LAUNCH_PER_EVENT else len(b.event_offsets) - 1}
     shape = ctx.tuned_shape(b.geom.n_layers, T)
-    res["tuned_shape"] = {"tracks_per_block": shape[0], "reg_cap": shape[1]} if shape else None
+    res["tuned_shape"] = ({"tracks_per_block": shape[0], "reg_cap": shape[1], "hit_prefetch": shape[2]}
+                          if shape else None)
     return res
 
 
@@ -580,7 +582,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
     chosen = kf.options(precision_mode=kf.PRECISION_ROUTED if args.precision == "routed" else kf.PRECISION_FP32)
     if args.shape:
-        chosen.tracks_per_block, chosen.reg_cap = (int(v) for v in args.shape.split(":"))
+        parts = [int(v) for v in args.shape.split(":")]
+        chosen.tracks_per_block, chosen.reg_cap = parts[0], parts[1]
+        chosen.hit_prefetch = parts[2] if len(parts) > 2 else 1
 
     def step(opt=chosen, o=out):
         kf.fit_tracks(ctx, geom, **d_in, event_offsets=batch.event_offsets, opt=opt, out=o, stream=stream)
@@ -664,7 +668,8 @@ def main():
     traffic = recorded_traffic(src_hash)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
-    tuned = ctx.tuned_shape(N_LAYERS, T) if not args.shape else (chosen.tracks_per_block, chosen.reg_cap)
+    tuned = (ctx.tuned_shape(N_LAYERS, T) if not args.shape
+             else (chosen.tracks_per_block, chosen.reg_cap, chosen.hit_prefetch))
     line = {
         "metric": METRIC, "value": value, "unit": "tracks/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -672,6 +677,7 @@ def main():
         "config": {"workload": WORKLOAD, "tracks_per_gpu": T, "layers": N_LAYERS,
                    "l2": "inputs larger than L2 (1.18 GB per step), not flushed",
                    "tracks_per_block": tuned[0] if tuned else None, "reg_cap": tuned[1] if tuned else None,
+                   "hit_prefetch": tuned[2] if tuned else None,
                    "parallelism": f"replicas{world}"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": traffic,

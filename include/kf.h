@@ -107,6 +107,9 @@ typedef struct {
     int tracks_per_block;    /* 0 = autotuned, else 32, 64, 128 or 256 */
     int reg_cap;             /* registers per thread of the persistent fit: 0 = autotuned,
                                 -1 = uncapped, 168, 128, 96 or 80 */
+    int hit_prefetch;        /* layers of hits the persistent fit loads ahead of their
+                                update: 0 = autotuned, 1 = the next layer into registers,
+                                2 or 4 = through a ring in shared memory (cp.async) */
     /* building */
     int max_cands;           /* N candidates kept per seed, 1 (best hit) .. 8 */
     float chi2_cut;          /* hits with a larger chi2 increment are incompatible */
@@ -419,11 +422,12 @@ int kf_transport_batch(kf_context *ctx, int64_t n, const float *J, float *C, kf_
 /*
  * Launch shape the autotuner picked for the persistent fit of n_layers layers
  * and a batch of n_tracks' size class (powers of two), once a KF_LAUNCH_AUTO
- * fit of that class has run on ctx.  Writes tracks per block and the register
- * cap per thread (-1: uncapped).  KF_ERR_ARG if that class has not been tuned.
+ * fit of that class has run on ctx.  Writes tracks per block, the register
+ * cap per thread (-1: uncapped) and the hit prefetch depth (kf_options).
+ * KF_ERR_ARG if that class has not been tuned.
  */
 int kf_fit_tuned_shape(kf_context *ctx, int n_layers, int64_t n_tracks, int *tracks_per_block,
-                       int *reg_cap);
+                       int *reg_cap, int *hit_prefetch);
 
 /*
  * The fit for callers that cannot allocate device memory.  The paper has no

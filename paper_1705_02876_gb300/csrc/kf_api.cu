@@ -24,7 +24,8 @@ struct GraphEntry {
     FitGeom g;
     Routing rt;
     FitIO io;
-    int block, cap, grid;
+    FitShape shape;
+    int grid;
     cudaGraphExec_t exec;
     uint64_t last_use;
 };
@@ -39,8 +40,8 @@ struct kf_context {
     unsigned *d_counter = nullptr;  // persistent-kernel work counter
     cudaStream_t capture_stream = nullptr;
     std::string err;
-    // (L, log2 size, precision, fixed block, fixed cap) -> (block, cap)
-    std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> tuned;
+    // (L, log2 size, precision, fixed block, fixed cap, fixed depth) -> shape
+    std::map<std::tuple<int, int, int, int, int, int>, kf::FitShape> tuned;
     std::vector<GraphEntry> graphs;
     uint64_t clock = 0;
     kf::BuildState *build = nullptr;
@@ -136,6 +137,8 @@ int check_options(kf_context *ctx, const kf_options &o)
     if (o.reg_cap != 0 && o.reg_cap != -1 && o.reg_cap != 168 && o.reg_cap != 128 && o.reg_cap != 96 &&
         o.reg_cap != 80)
         return set_error(ctx, KF_ERR_ARG, "reg_cap must be 0, -1, 168, 128, 96 or 80");
+    if (o.hit_prefetch != 0 && o.hit_prefetch != 1 && o.hit_prefetch != 2 && o.hit_prefetch != 4)
+        return set_error(ctx, KF_ERR_ARG, "hit_prefetch must be 0, 1, 2 or 4");
     return KF_OK;
 }
 
@@ -155,6 +158,7 @@ void kf_options_default(kf_options *o)
     o->launch_mode = KF_LAUNCH_AUTO;
     o->tracks_per_block = 0;
     o->reg_cap = 0;
+    o->hit_prefetch = 0;
     o->max_cands = 6;
     o->chi2_cut = 30.0f;
     o->window_nsigma = 3.0f;
@@ -225,10 +229,11 @@ int size_class(int64_t n)
 
 // Enqueue the persistent fit: counter reset + kernel, replayed from a cached
 // CUDA graph when this exact launch was captured before.
-cudaError_t enqueue_persistent(kf_context *ctx, const FitGeom &g, const Routing &rt, const FitIO &io, int block,
-                               int cap, cudaStream_t stream, bool use_graph)
+cudaError_t enqueue_persistent(kf_context *ctx, const FitGeom &g, const Routing &rt, const FitIO &io,
+                               const FitShape &sh, cudaStream_t stream, bool use_graph)
 {
-    const int per_sm = persistent_blocks_per_sm(block, cap);
+    const int block = sh.block;
+    const int per_sm = persistent_blocks_per_sm(block, sh.cap, sh.depth);
     if (per_sm <= 0) return cudaErrorInvalidConfiguration;
     const int64_t units = (io.T + 31) / 32;
     const int64_t want = (units * 32 + block - 1) / block;
@@ -238,10 +243,11 @@ cudaError_t enqueue_persistent(kf_context *ctx, const FitGeom &g, const Routing 
     if (!use_graph || capst != cudaStreamCaptureStatusNone) {
         cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned), stream);
         if (e != cudaSuccess) return e;
-        return launch_fit_persistent(g, rt, io, block, cap, grid, ctx->d_counter, stream);
+        return launch_fit_persistent(g, rt, io, block, sh.cap, sh.depth, grid, ctx->d_counter, stream);
     }
     for (auto &e : ctx->graphs) {
-        if (e.block == block && e.cap == cap && e.grid == grid && same_bytes(&e.g, &g, sizeof g) &&
+        if (e.shape.block == block && e.shape.cap == sh.cap && e.shape.depth == sh.depth && e.grid == grid &&
+            same_bytes(&e.g, &g, sizeof g) &&
             same_bytes(&e.rt, &rt, sizeof rt) && same_bytes(&e.io, &io, sizeof io)) {
             e.last_use = ++ctx->clock;
             return cudaGraphLaunch(e.exec, stream);
@@ -252,7 +258,8 @@ cudaError_t enqueue_persistent(kf_context *ctx, const FitGeom &g, const Routing 
     if (e != cudaSuccess) return e;
     cudaError_t e1 = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned), ctx->capture_stream);
     cudaError_t e2 = e1 == cudaSuccess
-                         ? launch_fit_persistent(g, rt, io, block, cap, grid, ctx->d_counter, ctx->capture_stream)
+                         ? launch_fit_persistent(g, rt, io, block, sh.cap, sh.depth, grid, ctx->d_counter,
+                                                 ctx->capture_stream)
                          : e1;
     e = cudaStreamEndCapture(ctx->capture_stream, &graph);
     if (e2 != cudaSuccess) e = e2;
@@ -271,53 +278,54 @@ cudaError_t enqueue_persistent(kf_context *ctx, const FitGeom &g, const Routing 
         cudaGraphExecDestroy(ctx->graphs[lru].exec);
         ctx->graphs.erase(ctx->graphs.begin() + lru);
     }
-    ctx->graphs.push_back(GraphEntry{g, rt, io, block, cap, grid, exec, ++ctx->clock});
+    ctx->graphs.push_back(GraphEntry{g, rt, io, sh, grid, exec, ++ctx->clock});
     return cudaGraphLaunch(exec, stream);
 }
 
-// Time every compiled (tracks per block, register cap) shape on the caller's
-// own buffers (the fit is idempotent: it reads its inputs and overwrites its
-// outputs) and keep the fastest for this layer count, size class and
-// precision.  Skipped while the stream is being captured.
-// fixed_block / fixed_cap (0 = free) restrict the search to matching shapes.
-std::pair<int, int> tune_shape(kf_context *ctx, const FitGeom &g, const Routing &rt, const FitIO &io,
-                               cudaStream_t stream, int fixed_block, int fixed_cap)
+// Time every compiled (tracks per block, register cap, hit prefetch depth)
+// shape on the caller's own buffers (the fit is idempotent: it reads its
+// inputs and overwrites its outputs) and keep the fastest for this layer
+// count, size class and precision.  Skipped while the stream is being
+// captured.  fixed (fields 0 = free; cap -1 = uncapped) restricts the search
+// to matching shapes.
+FitShape tune_shape(kf_context *ctx, const FitGeom &g, const Routing &rt, const FitIO &io, cudaStream_t stream,
+                    const FitShape &fixed)
 {
-    const auto key = std::make_tuple(g.L, size_class(io.T), rt.mode, fixed_block, fixed_cap);
+    const auto key = std::make_tuple(g.L, size_class(io.T), rt.mode, fixed.block, fixed.cap, fixed.depth);
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) return it->second;
-    int blocks[32], caps[32];
+    FitShape cand[64];
     int n = 0;
     {
-        int all_b[32], all_c[32];
-        const int m = persistent_shapes(all_b, all_c, 32);
+        int all_b[64], all_c[64], all_d[64];
+        const int m = persistent_shapes(all_b, all_c, all_d, 64);
         for (int i = 0; i < m; ++i)
-            if ((!fixed_block || all_b[i] == fixed_block) && (!fixed_cap || all_c[i] == (fixed_cap < 0 ? 0 : fixed_cap))) {
-                blocks[n] = all_b[i];
-                caps[n] = all_c[i];
-                ++n;
-            }
+            if ((!fixed.block || all_b[i] == fixed.block) &&
+                (!fixed.cap || all_c[i] == (fixed.cap < 0 ? 0 : fixed.cap)) &&
+                (!fixed.depth || all_d[i] == fixed.depth))
+                cand[n++] = FitShape{all_b[i], all_c[i], all_d[i]};
     }
-    if (n == 0) return {fixed_block ? fixed_block : 128, fixed_cap > 0 ? fixed_cap : 0};
+    if (n == 0)
+        return FitShape{fixed.block ? fixed.block : 128, fixed.cap > 0 ? fixed.cap : 0, fixed.depth ? fixed.depth : 1};
     cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(stream, &capst);
-    if (capst != cudaStreamCaptureStatusNone) return {blocks[0], caps[0]};
+    if (capst != cudaStreamCaptureStatusNone) return cand[0];
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    std::pair<int, int> best{blocks[0], caps[0]};
+    FitShape best = cand[0];
     float best_ms = 1e30f;
     for (int i = 0; i < n; ++i) {
-        if (enqueue_persistent(ctx, g, rt, io, blocks[i], caps[i], stream, false) != cudaSuccess) continue;
+        if (enqueue_persistent(ctx, g, rt, io, cand[i], stream, false) != cudaSuccess) continue;
         cudaEventRecord(a, stream);
-        for (int rep = 0; rep < 3; ++rep) enqueue_persistent(ctx, g, rt, io, blocks[i], caps[i], stream, false);
+        for (int rep = 0; rep < 3; ++rep) enqueue_persistent(ctx, g, rt, io, cand[i], stream, false);
         cudaEventRecord(b, stream);
         if (cudaEventSynchronize(b) != cudaSuccess) break;
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, a, b);
         if (ms < best_ms) {
             best_ms = ms;
-            best = {blocks[i], caps[i]};
+            best = cand[i];
         }
     }
     cudaEventDestroy(a);
@@ -380,23 +388,26 @@ int kf_fit_tracks(kf_context *ctx, const kf_geometry *geom, int64_t n_tracks, co
             e = launch_fit_plain(g, rt, io, event_offsets[ev], event_offsets[ev + 1], block ? block : 128, stream);
         break;
     default: {
-        std::pair<int, int> shape{block, o.reg_cap < 0 ? 0 : o.reg_cap};
-        if (!block || !o.reg_cap) shape = tune_shape(ctx, g, rt, io, stream, block, o.reg_cap);
-        e = enqueue_persistent(ctx, g, rt, io, shape.first, shape.second, stream, true);
+        FitShape shape{block, o.reg_cap < 0 ? 0 : o.reg_cap, o.hit_prefetch};
+        if (!block || !o.reg_cap || !o.hit_prefetch)
+            shape = tune_shape(ctx, g, rt, io, stream, FitShape{block, o.reg_cap, o.hit_prefetch});
+        e = enqueue_persistent(ctx, g, rt, io, shape, stream, true);
     }
     }
     if (e != cudaSuccess) return cuda_error(ctx, e, "fit launch");
     return KF_OK;
 }
 
-int kf_fit_tuned_shape(kf_context *ctx, int n_layers, int64_t n_tracks, int *tracks_per_block, int *reg_cap)
+int kf_fit_tuned_shape(kf_context *ctx, int n_layers, int64_t n_tracks, int *tracks_per_block, int *reg_cap,
+                       int *hit_prefetch)
 {
-    if (!ctx || !tracks_per_block || !reg_cap) return KF_ERR_ARG;
+    if (!ctx || !tracks_per_block || !reg_cap || !hit_prefetch) return KF_ERR_ARG;
     for (int mode = 1; mode >= 0; --mode) {
-        auto it = ctx->tuned.find(std::make_tuple(n_layers, size_class(n_tracks), mode, 0, 0));
+        auto it = ctx->tuned.find(std::make_tuple(n_layers, size_class(n_tracks), mode, 0, 0, 0));
         if (it != ctx->tuned.end()) {
-            *tracks_per_block = it->second.first;
-            *reg_cap = it->second.second ? it->second.second : -1;
+            *tracks_per_block = it->second.block;
+            *reg_cap = it->second.cap ? it->second.cap : -1;
+            *hit_prefetch = it->second.depth;
             return KF_OK;
         }
     }

@@ -20,13 +20,27 @@ __device__ __forceinline__ bool all_finite(const float *v)
     return acc == 0.0f;
 }
 
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Fit track t over every layer in order (the steps and stop rules are those of
-// kf_fit_tracks in kf.h).  The next present hit is loaded one layer ahead,
-// through pointers advanced by one layer's stride.  A non-finite value in a
+// kf_fit_tracks in kf.h).  Hits are loaded DEPTH layers ahead of their update:
+// DEPTH = 1 into registers, through pointers advanced by one layer's stride;
+// DEPTH >= 2 by asynchronous copies (cp.async, one commit group per layer,
+// empty for a layer without a hit) into this thread's column of a ring of
+// DEPTH + 1 shared-memory stages of 9 floats each ([stage * 9 + i][stride]),
+// so that the loads in flight hold no registers.  A non-finite value in a
 // used hit makes the chi2 increment non-finite, or makes S fail its positive
 // definiteness test, so the hit is tested only then.
+template <int DEPTH>
 __device__ __forceinline__ void fit_track(const FitGeom &g, const Routing &rt, const FitIO &io, int64_t t,
-                                          float *slot, int stride)
+                                          float *slot, int stride, float *ring = nullptr)
 {
     const int64_t T = io.T;
     float x[6], c[21];
@@ -49,14 +63,49 @@ __device__ __forceinline__ void fit_track(const FitGeom &g, const Routing &rt, c
 #pragma unroll
         for (int i = 0; i < 6; ++i) vv[i] = __ldcs(hc + i * T);
     };
-    if (mask & 1u) load_hit(m, v);
+    // DEPTH >= 2: layer l's hit goes to stage l % (DEPTH + 1); stage_in is the
+    // stage of the next layer to issue, stage_out that of the next to use
+    int stage_in = 0, stage_out = 0, l_in = 0;
+    auto issue = [&]() {
+        if (l_in < g.L && ((mask >> l_in) & 1u)) {
+            const float *p = io.hit_pos + (int64_t)(3 * l_in) * T + t;
+            const float *q = io.hit_cov + (int64_t)(6 * l_in) * T + t;
+            float *st = ring + stage_in * 9 * stride;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) cp_async4(st + i * stride, p + i * T);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) cp_async4(st + (3 + i) * stride, q + i * T);
+        }
+        cp_async_commit();
+        ++l_in;
+        stage_in = stage_in == DEPTH ? 0 : stage_in + 1;
+    };
+    if constexpr (DEPTH == 1) {
+        if (mask & 1u) load_hit(m, v);
+    } else {
+#pragma unroll
+        for (int k = 0; k < DEPTH; ++k) issue();
+    }
     for (int l = 0; l < g.L && !(flags & kStop); ++l) {
         const bool has = (mask >> l) & 1u;
         const bool has_next = l + 1 < g.L && ((mask >> (l + 1)) & 1u);
-        hp += T3;
-        hc += T6;
         float mn[3], vn[6];
-        if (has_next) load_hit(mn, vn);
+        if constexpr (DEPTH == 1) {
+            hp += T3;
+            hc += T6;
+            if (has_next) load_hit(mn, vn);
+        } else {
+            issue();                      // layer l + DEPTH
+            cp_async_wait<DEPTH>();       // layer l's group has landed
+            if (has) {
+                const float *st = ring + stage_out * 9 * stride;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) m[i] = st[i * stride];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) v[i] = st[(3 + i) * stride];
+            }
+            stage_out = stage_out == DEPTH ? 0 : stage_out + 1;
+        }
         float xn[6], s;
         Jac J;
         if (!propagate(x, qkb, g.r[l], xn, s, &J)) {
@@ -89,13 +138,16 @@ __device__ __forceinline__ void fit_track(const FitGeom &g, const Routing &rt, c
                 if (st == 3) flags |= KF_FLAG_PSD_REPAIRED;
             }
         }
-        if (has_next) {
+        if constexpr (DEPTH == 1) {
+            if (has_next) {
 #pragma unroll
-            for (int i = 0; i < 3; ++i) m[i] = mn[i];
+                for (int i = 0; i < 3; ++i) m[i] = mn[i];
 #pragma unroll
-            for (int i = 0; i < 6; ++i) v[i] = vn[i];
+                for (int i = 0; i < 6; ++i) v[i] = vn[i];
+            }
         }
     }
+    if constexpr (DEPTH > 1) cp_async_wait<0>();  // no copy of this track may land in the next one's ring
     if (flags & KF_FLAG_NAN_INPUT) {  // a track with bad input returns its seed
 #pragma unroll
         for (int i = 0; i < 6; ++i) x[i] = io.seed_state[i * T + t];
@@ -119,7 +171,7 @@ __global__ void __launch_bounds__(256) fit_plain_kernel(const FitGeom g, const R
 {
     extern __shared__ float slots[];
     const int64_t t = t_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < t_end) fit_track(g, rt, io, t, slots + threadIdx.x, blockDim.x);
+    if (t < t_end) fit_track<1>(g, rt, io, t, slots + threadIdx.x, blockDim.x);
 }
 
 // Persistent kernel: each warp claims 32-track units from *counter until the
@@ -127,11 +179,13 @@ __global__ void __launch_bounds__(256) fit_plain_kernel(const FitGeom g, const R
 // in one launch).  Warps schedule themselves, so a warp slowed by an
 // extended-precision update does not hold the rest of its block.  MINB > 1
 // caps the registers per thread at 65536 / (BLOCK * MINB) to raise occupancy.
-template <int BLOCK, int MINB>
+// DEPTH >= 2 keeps the hit ring in dynamic shared memory (ring_floats(...)).
+template <int BLOCK, int MINB, int DEPTH>
 __global__ void __launch_bounds__(BLOCK, MINB) fit_persistent_kernel(const FitGeom g, const Routing rt,
                                                                       const FitIO io, unsigned *counter)
 {
     __shared__ float slots[kSlotSize * BLOCK];
+    extern __shared__ float ring[];
     const unsigned lane = threadIdx.x & 31u;
     const unsigned n_units = (unsigned)((io.T + 31) / 32);
     for (;;) {
@@ -140,35 +194,58 @@ __global__ void __launch_bounds__(BLOCK, MINB) fit_persistent_kernel(const FitGe
         u = __shfl_sync(0xffffffffu, u, 0);
         if (u >= n_units) break;
         const int64_t t = (int64_t)u * 32 + lane;
-        if (t < io.T) fit_track(g, rt, io, t, slots + threadIdx.x, BLOCK);
+        if (t < io.T) fit_track<DEPTH>(g, rt, io, t, slots + threadIdx.x, BLOCK, ring + threadIdx.x);
     }
 }
 
 using PersistentFn = void (*)(FitGeom, Routing, FitIO, unsigned *);
 
-// (block, register cap) shapes the autotuner chooses from; cap 0 = none.
-// A cap of R registers is __launch_bounds__(BLOCK, 65536 / (R * BLOCK)).
+// Dynamic shared memory of a shape: DEPTH + 1 stages of 9 floats per thread.
+constexpr size_t ring_bytes(int block, int depth) { return depth > 1 ? (size_t)(depth + 1) * 9 * block * 4 : 0; }
+
+// (block, register cap, hit prefetch depth) shapes the autotuner chooses
+// from; cap 0 = none.  A cap of R registers is
+// __launch_bounds__(BLOCK, 65536 / (R * BLOCK)).
 struct Shape {
-    int block, cap;
+    int block, cap, depth;
     PersistentFn fn;
 };
 const Shape kShapes[] = {
-    {32, 0, fit_persistent_kernel<32, 1>},     {64, 0, fit_persistent_kernel<64, 1>},
-    {128, 0, fit_persistent_kernel<128, 1>},   {256, 0, fit_persistent_kernel<256, 1>},
-    {32, 168, fit_persistent_kernel<32, 12>},  {64, 168, fit_persistent_kernel<64, 6>},
-    {128, 168, fit_persistent_kernel<128, 3>}, {32, 128, fit_persistent_kernel<32, 16>},
-    {64, 128, fit_persistent_kernel<64, 8>},   {128, 128, fit_persistent_kernel<128, 4>},
-    {256, 128, fit_persistent_kernel<256, 2>}, {32, 96, fit_persistent_kernel<32, 20>},
-    {64, 96, fit_persistent_kernel<64, 10>},   {128, 96, fit_persistent_kernel<128, 5>},
-    {32, 80, fit_persistent_kernel<32, 24>},   {64, 80, fit_persistent_kernel<64, 12>},
-    {128, 80, fit_persistent_kernel<128, 6>},  {256, 80, fit_persistent_kernel<256, 3>},
+    {32, 0, 1, fit_persistent_kernel<32, 1, 1>},     {64, 0, 1, fit_persistent_kernel<64, 1, 1>},
+    {128, 0, 1, fit_persistent_kernel<128, 1, 1>},   {256, 0, 1, fit_persistent_kernel<256, 1, 1>},
+    {32, 168, 1, fit_persistent_kernel<32, 12, 1>},  {64, 168, 1, fit_persistent_kernel<64, 6, 1>},
+    {128, 168, 1, fit_persistent_kernel<128, 3, 1>}, {32, 128, 1, fit_persistent_kernel<32, 16, 1>},
+    {64, 128, 1, fit_persistent_kernel<64, 8, 1>},   {128, 128, 1, fit_persistent_kernel<128, 4, 1>},
+    {256, 128, 1, fit_persistent_kernel<256, 2, 1>}, {32, 96, 1, fit_persistent_kernel<32, 20, 1>},
+    {64, 96, 1, fit_persistent_kernel<64, 10, 1>},   {128, 96, 1, fit_persistent_kernel<128, 5, 1>},
+    {32, 80, 1, fit_persistent_kernel<32, 24, 1>},   {64, 80, 1, fit_persistent_kernel<64, 12, 1>},
+    {128, 80, 1, fit_persistent_kernel<128, 6, 1>},  {256, 80, 1, fit_persistent_kernel<256, 3, 1>},
+    {32, 128, 2, fit_persistent_kernel<32, 16, 2>},  {64, 128, 2, fit_persistent_kernel<64, 8, 2>},
+    {128, 128, 2, fit_persistent_kernel<128, 4, 2>}, {256, 128, 2, fit_persistent_kernel<256, 2, 2>},
+    {32, 96, 2, fit_persistent_kernel<32, 20, 2>},   {64, 96, 2, fit_persistent_kernel<64, 10, 2>},
+    {128, 96, 2, fit_persistent_kernel<128, 5, 2>},  {32, 128, 4, fit_persistent_kernel<32, 16, 4>},
+    {64, 128, 4, fit_persistent_kernel<64, 8, 4>},   {128, 128, 4, fit_persistent_kernel<128, 4, 4>},
+    {256, 128, 4, fit_persistent_kernel<256, 2, 4>}, {32, 96, 4, fit_persistent_kernel<32, 20, 4>},
+    {64, 96, 4, fit_persistent_kernel<64, 10, 4>},   {128, 96, 4, fit_persistent_kernel<128, 5, 4>},
 };
 
-const Shape *find_shape(int block, int cap)
+const Shape *find_shape(int block, int cap, int depth)
 {
     for (const Shape &sh : kShapes)
-        if (sh.block == block && sh.cap == cap) return &sh;
+        if (sh.block == block && sh.cap == cap && sh.depth == depth) return &sh;
     return nullptr;
+}
+
+// Allow a shape's dynamic shared memory (once per process: one device each).
+bool prepare_shape(const Shape *sh)
+{
+    const size_t bytes = ring_bytes(sh->block, sh->depth);
+    if (!bytes) return true;
+    static bool done[sizeof(kShapes) / sizeof(kShapes[0])] = {};
+    const size_t i = (size_t)(sh - kShapes);
+    if (!done[i])
+        done[i] = cudaFuncSetAttribute(sh->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+    return done[i];
 }
 
 }  // namespace
@@ -183,32 +260,36 @@ cudaError_t launch_fit_plain(const FitGeom &g, const Routing &rt, const FitIO &i
     return cudaGetLastError();
 }
 
-int persistent_blocks_per_sm(int block, int cap)
+int persistent_blocks_per_sm(int block, int cap, int depth)
 {
-    const Shape *sh = find_shape(block, cap);
+    const Shape *sh = find_shape(block, cap, depth);
     int n = 0;
-    if (!sh || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sh->fn, block, 0) != cudaSuccess) return 0;
+    if (!sh || !prepare_shape(sh) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sh->fn, block, ring_bytes(block, depth)) != cudaSuccess)
+        return 0;
     return n;
 }
 
-int persistent_shapes(int *blocks, int *caps, int max_n)
+int persistent_shapes(int *blocks, int *caps, int *depths, int max_n)
 {
     int n = 0;
     for (const Shape &sh : kShapes)
         if (n < max_n) {
             blocks[n] = sh.block;
             caps[n] = sh.cap;
+            depths[n] = sh.depth;
             ++n;
         }
     return n;
 }
 
-cudaError_t launch_fit_persistent(const FitGeom &g, const Routing &rt, const FitIO &io, int block, int cap, int grid,
-                                  unsigned *counter, cudaStream_t stream)
+cudaError_t launch_fit_persistent(const FitGeom &g, const Routing &rt, const FitIO &io, int block, int cap, int depth,
+                                  int grid, unsigned *counter, cudaStream_t stream)
 {
-    const Shape *sh = find_shape(block, cap);
+    const Shape *sh = find_shape(block, cap, depth);
     if (!sh) return cudaErrorInvalidValue;
-    sh->fn<<<grid, block, 0, stream>>>(g, rt, io, counter);
+    if (!prepare_shape(sh)) return cudaErrorInvalidValue;
+    sh->fn<<<grid, block, ring_bytes(block, depth), stream>>>(g, rt, io, counter);
     return cudaGetLastError();
 }
 

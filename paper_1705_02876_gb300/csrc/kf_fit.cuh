@@ -34,6 +34,12 @@ struct FitIO {
     uint32_t *out_flags;
 };
 
+// A persistent-fit launch shape: threads per block, register cap (0 = none)
+// and hit prefetch depth (layers ahead).
+struct FitShape {
+    int block, cap, depth;
+};
+
 // status word bits written by the persistent kernels (device scratch)
 constexpr unsigned kStatusTimeout = 1u;
 
@@ -41,13 +47,15 @@ constexpr unsigned kStatusTimeout = 1u;
 cudaError_t launch_fit_plain(const FitGeom &g, const Routing &rt, const FitIO &io, int64_t t_begin,
                              int64_t t_end, int block, cudaStream_t stream);
 // Persistent kernel: grid = `grid` blocks of `block` threads with registers
-// capped at `cap` per thread (0 = no cap); warps claim 32-track units from
-// *counter, which must read 0 at launch.
+// capped at `cap` per thread (0 = no cap), hits loaded `depth` layers ahead
+// (1: registers; 2, 4: a cp.async ring in shared memory); warps claim 32-track
+// units from *counter, which must read 0 at launch.
 cudaError_t launch_fit_persistent(const FitGeom &g, const Routing &rt, const FitIO &io, int block, int cap,
-                                  int grid, unsigned *counter, cudaStream_t stream);
-// Blocks of the persistent kernel of this shape that fit on one SM at once.
-int persistent_blocks_per_sm(int block, int cap);
-// The (block, cap) shapes compiled in; returns how many were written.
-int persistent_shapes(int *blocks, int *caps, int max_n);
+                                  int depth, int grid, unsigned *counter, cudaStream_t stream);
+// Blocks of the persistent kernel of this shape that fit on one SM at once
+// (0 if the shape is not compiled in).
+int persistent_blocks_per_sm(int block, int cap, int depth);
+// The (block, cap, depth) shapes compiled in; returns how many were written.
+int persistent_shapes(int *blocks, int *caps, int *depths, int max_n);
 
 }  // namespace kf

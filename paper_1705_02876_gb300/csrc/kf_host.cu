@@ -93,8 +93,11 @@ extern "C" int kf_fit_tracks_host(kf_context *ctx, const kf_geometry *geom, int6
     const int block = o.tracks_per_block ? o.tracks_per_block : 64;
     const int cap = o.reg_cap < 0 ? 0 : (o.reg_cap ? o.reg_cap : 128);
     DeviceGuard dg(context_device(ctx));
-    const int per_sm = persistent_blocks_per_sm(block, cap);
-    if (per_sm < 1) return set_error(ctx, KF_ERR_ARG, "no persistent fit of %d tracks per block, cap %d", block, cap);
+    const int depth = o.hit_prefetch ? o.hit_prefetch : 1;
+    const int per_sm = persistent_blocks_per_sm(block, cap, depth);
+    if (per_sm < 1)
+        return set_error(ctx, KF_ERR_ARG, "no persistent fit of %d tracks per block, cap %d, hit prefetch %d", block,
+                         cap, depth);
     const int grid = per_sm * context_sm_count(ctx);
     int64_t C = chunk_tracks ? chunk_tracks : (int64_t(1) << 18);
     C = std::min<int64_t>(C, n_tracks);
@@ -168,7 +171,7 @@ extern "C" int kf_fit_tracks_host(kf_context *ctx, const kf_geometry *geom, int6
                      reinterpret_cast<float *>(b + lay.out_chi2),
                      reinterpret_cast<int16_t *>(b + lay.out_ndof),
                      reinterpret_cast<uint32_t *>(b + lay.out_flags)};
-            e = launch_fit_persistent(g, rt, io, block, cap, grid, hp->counter + k, s);
+            e = launch_fit_persistent(g, rt, io, block, cap, depth, grid, hp->counter + k, s);
         }
         out(out_state, lay.out_state, 4, 6);
         out(out_cov, lay.out_cov, 4, 21);

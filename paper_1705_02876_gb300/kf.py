@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision_mode", ctypes.c_int), ("cond_max", ctypes.c_float),
                 ("pt_lo", ctypes.c_float), ("pt_hi", ctypes.c_float), ("gain_max", ctypes.c_float),
                 ("launch_mode", ctypes.c_int), ("tracks_per_block", ctypes.c_int),
-                ("reg_cap", ctypes.c_int), ("max_cands", ctypes.c_int),
+                ("reg_cap", ctypes.c_int), ("hit_prefetch", ctypes.c_int), ("max_cands", ctypes.c_int),
                 ("chi2_cut", ctypes.c_float), ("window_nsigma", ctypes.c_float),
                 ("hit_sigma_rphi", ctypes.c_float), ("hit_sigma_z", ctypes.c_float),
                 ("window_max_dphi", ctypes.c_float), ("window_max_dz", ctypes.c_float),
@@ -90,7 +90,7 @@ def load() -> ctypes.CDLL:
         L.kf_smooth_tracks.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int64] + [_vp] * 10 + \
             [ctypes.POINTER(Options), _vp]
         L.kf_transport_batch.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp]
-        L.kf_fit_tuned_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int64,
+        L.kf_fit_tuned_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.kf_build_tracks.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int, _vp, _vp, _vp,
                                       ctypes.c_int64, ctypes.c_int64] + [_vp] * 10 + \
@@ -176,9 +176,11 @@ class Context:
             pass
 
     def tuned_shape(self, n_layers: int, n_tracks: int):
-        b, t = ctypes.c_int(), ctypes.c_int()
-        rc = load().kf_fit_tuned_shape(self._h, n_layers, n_tracks, ctypes.byref(b), ctypes.byref(t))
-        return (b.value, t.value) if rc == KF_OK else None
+        """(tracks per block, register cap, hit prefetch depth) the autotuner
+        picked, or None before a fit of that size class."""
+        b, t, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        rc = load().kf_fit_tuned_shape(self._h, n_layers, n_tracks, ctypes.byref(b), ctypes.byref(t), ctypes.byref(d))
+        return (b.value, t.value, d.value) if rc == KF_OK else None
 
 
 class GeometryArgs:

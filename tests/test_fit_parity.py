@@ -117,6 +117,28 @@ def test_register_caps(kf, ctx, oracle, cap):
         compare(gpu, ref)
 
 
+@pytest.mark.parametrize("block", [32, 64, 128, 256])
+def test_hit_prefetch_depths(kf, ctx, oracle, block):
+    """Hits loaded 2 or 4 layers ahead through the shared-memory ring give
+    the same bits as the one-layer register prefetch of the same shape, on
+    ragged events with missing hits and tracks that stop early (loopers, tracks
+    leaving the barrel), so that copies still in flight at a stop are drained
+    before the thread's next track; and they match the oracle."""
+    b = synth.make_fit_batch(37, [900, 1, 31, 2100, 65], geom=synth.toy_geometry(17), hit_eff=0.9,
+                             pt_lo=0.2, pt_hi=5.0, pt_dist="loguniform", eta_max=2.0)
+    ref = oracle.fit_batch(b)
+    base = run_gpu(kf, ctx, b, tracks_per_block=block, reg_cap=128, hit_prefetch=1)
+    compare(base, ref)
+    assert (base["flags"].view(np.uint32) & STOP).any()
+    for depth in (2, 4):
+        gpu = run_gpu(kf, ctx, b, tracks_per_block=block, reg_cap=128, hit_prefetch=depth)
+        for k in base:
+            assert np.array_equal(np.ascontiguousarray(gpu[k]).view(np.uint8),
+                                  np.ascontiguousarray(base[k]).view(np.uint8)), (depth, k)
+    with pytest.raises(kf.KFError, match="hit_prefetch"):
+        run_gpu(kf, ctx, b, hit_prefetch=3)
+
+
 def test_stops_flags_and_anisotropic_hits(kf, ctx, oracle):
     """Loopers that cannot reach the outer layers, tracks leaving the barrel,
     off-diagonal hit covariances (sigma_r != sigma_rphi), NaN inputs."""
