@@ -76,6 +76,24 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The maximum of x over all ranks of the default process group (x itself
+    on one rank): the timed region ends when the slowest rank ends."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(units_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput of a weak-scaling step: every rank processes its
+    own units_per_rank, and the step takes the slowest rank's time."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -612,13 +630,9 @@ def main():
     t_wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = starts[0].elapsed_time(ends[-1])
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(starts[0].elapsed_time(ends[-1]), world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * T / (ms_per_step * 1e-3)
+    value = weak_value(T, world, ms_per_step)
     kern_ms = statistics.mean(step_ms)
 
     # plain form: one FP32 launch per event, same data (outside the timed region)
@@ -655,11 +669,7 @@ def main():
     for _ in range(n_e2e):
         e2e_step()
     barrier()
-    e2e_ms = (time.perf_counter() - t_e) * 1e3 / n_e2e
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks((time.perf_counter() - t_e) * 1e3 / n_e2e, world, dev)
 
     routed_share = float(((out["flags"] & 16) != 0).float().mean().item())
     flops = FLOPS_PER_TRACK_LAYER * N_LAYERS * T
@@ -687,7 +697,7 @@ def main():
                      "hbm_frac_of_measured": (BYTES_PER_TRACK * T / (kern_ms * 1e-3) / 1e9 / hbm) if hbm else None},
         "plain": {"value": T / (plain_ms * 1e-3), "unit": "tracks/s", "ms_per_step": plain_ms,
                   "form": "FP32 only, one plain launch per event (100 launches)"},
-        "e2e": {"value": world * T / (e2e_ms * 1e-3), "unit": "tracks/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": weak_value(T, world, e2e_ms), "unit": "tracks/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                 "form": "kf_fit_tracks_host: pinned host buffers, 262,144-track chunks on 3 streams"},
         "fp64_routed_share": routed_share,
