@@ -649,9 +649,10 @@ def main():
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1) / n_plain
 
-    # end to end through the public host-buffer call: pinned host inputs are
-    # copied in, fitted and copied out in chunks that overlap on three streams;
-    # the call returns with every output in host memory
+    # end to end through the public host-buffer call: the fit reads the pinned
+    # host inputs and writes the pinned host outputs in place (every byte
+    # crosses the host link inside the timed region); the call returns with
+    # every output in host memory
     host_in = kf.to_host(batch)
     host_out = kf.fit_outputs_host(T)
     h2d = sum(v.numel() * v.element_size() for v in host_in.values())
@@ -699,7 +700,8 @@ def main():
                   "form": "FP32 only, one plain launch per event (100 launches)"},
         "e2e": {"value": weak_value(T, world, e2e_ms), "unit": "tracks/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-                "form": "kf_fit_tracks_host: pinned host buffers, 262,144-track chunks on 3 streams"},
+                "form": "kf_fit_tracks_host on pinned host buffers: one persistent launch reads the inputs and "
+                        "writes the outputs in host memory over the host link"},
         "fp64_routed_share": routed_share,
         "gpu_launches": args.steps,
         "clocks": clocks,

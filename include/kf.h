@@ -179,20 +179,25 @@ int kf_fit_tracks(kf_context *ctx, const kf_geometry *geom, int64_t n_tracks,
 /*
  * kf_fit_tracks from and to host memory (the paper's events live on the host;
  * Section 4.2 streams several events to the GPU concurrently, and Section 4.3
- * finds host-device transfers about half of the GPU build's wall time).  The
- * batch is cut into chunks of chunk_tracks tracks (0: 262,144); each chunk is
- * copied in, fitted (the persistent fit, all of the chunk's events in one
- * launch) and copied out on one of three internal streams, so the transfers
- * of one chunk overlap the fit of another.
+ * finds host-device transfers about half of the GPU build's wall time).
+ *
+ * chunk_tracks = 0 and every array page-locked memory the device can address
+ * (cudaMallocHost, cudaHostAlloc, cudaHostRegister): one persistent fit
+ * launch reads the inputs and writes the outputs where they are, over the
+ * host link; nothing is staged.  Otherwise the batch is cut into chunks of
+ * chunk_tracks tracks (0: 262,144); each chunk is copied in, fitted (the
+ * persistent fit, all of the chunk's events in one launch) and copied out on
+ * one of three internal streams, so the transfers of one chunk overlap the
+ * fit of another.
  *
  * Arrays: the layouts of kf_fit_tracks, all in host memory owned by the
- * caller, pinned (cudaMallocHost / cudaHostRegister) for full speed; pageable
- * memory works through the driver's staging, slower.  The call returns when
- * every output is in host memory.  Device staging (about 3 x 591 B x
- * chunk_tracks at 10 layers) is kept by the context and grown on demand
- * (KF_ERR_NOMEM).  opt->launch_mode is ignored; the shape is
- * opt->tracks_per_block / opt->reg_cap when set, else 64 tracks per block and
- * 128 registers (no tuning runs).
+ * caller; pageable memory takes the chunked path through the driver's
+ * staging, slower.  The call returns when every output is in host memory.
+ * Device staging (about 3 x 591 B x chunk_tracks at 10 layers) is kept by the
+ * context and grown on demand (KF_ERR_NOMEM).  opt->launch_mode is ignored;
+ * the shape is opt->tracks_per_block / opt->reg_cap / opt->hit_prefetch when
+ * set, else 64 tracks per block, 128 registers and the register prefetch (no
+ * tuning runs).
  */
 int kf_fit_tracks_host(kf_context *ctx, const kf_geometry *geom, int64_t n_tracks, const float *seed_state,
                        const float *seed_cov, const int8_t *charge, const float *hit_pos, const float *hit_cov,

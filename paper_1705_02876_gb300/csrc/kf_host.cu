@@ -1,7 +1,12 @@
-// The fit from host buffers: chunks of tracks copied in, fitted and copied out
-// on a ring of streams so that the copies of one chunk overlap the fit of the
-// next (the paper's multi-stream event transfers, Section 4.2; its builds
-// spent about half their wall time on host-device transfers, Section 4.3).
+// The fit from host buffers (the paper's multi-stream event transfers, Section
+// 4.2; its builds spent about half their wall time on host-device transfers,
+// Section 4.3).  Page-locked buffers the device can address are read and
+// written in place by one persistent launch: on this part the kernel's loads
+// over the host link run as fast as the copy engines (about 210 GB/s), and the
+// inputs' reads and the outputs' writes share the link in both directions
+// with no pipeline fill or drain.  Other buffers go through chunks copied in,
+// fitted and copied out on a ring of streams, so that the copies of one chunk
+// overlap the fit of the next.
 #include <algorithm>
 
 #include "kf.h"
@@ -117,6 +122,48 @@ extern "C" int kf_fit_tracks_host(kf_context *ctx, const kf_geometry *geom, int6
             return set_error(ctx, KF_ERR_NOMEM, "could not create the host pipeline's streams");
         }
     }
+    const Routing rt = make_routing(o);
+    // page-locked buffers the device addresses in place: one launch, the
+    // transfers happen inside the kernel's loads and stores
+    if (chunk_tracks == 0) {
+        const void *host[11] = {seed_state, seed_cov, charge, hit_pos, hit_cov, hit_mask,
+                                out_state, out_cov, out_chi2, out_ndof, out_flags};
+        void *dev[11] = {};
+        bool mapped = true;
+        for (int i = 0; i < 11 && mapped; ++i) {
+            cudaPointerAttributes a{};
+            if (cudaPointerGetAttributes(&a, host[i]) != cudaSuccess) {
+                cudaGetLastError();  // clear: an unknown pointer is an answer, not an error
+                mapped = false;
+            } else {
+                mapped = a.type == cudaMemoryTypeHost && a.devicePointer != nullptr;
+                dev[i] = a.devicePointer;
+            }
+        }
+        if (mapped) {
+            const FitIO io{n_tracks,
+                           static_cast<const float *>(dev[0]),
+                           static_cast<const float *>(dev[1]),
+                           static_cast<const int8_t *>(dev[2]),
+                           static_cast<const float *>(dev[3]),
+                           static_cast<const float *>(dev[4]),
+                           static_cast<const uint32_t *>(dev[5]),
+                           static_cast<float *>(dev[6]),
+                           static_cast<float *>(dev[7]),
+                           static_cast<float *>(dev[8]),
+                           static_cast<int16_t *>(dev[9]),
+                           static_cast<uint32_t *>(dev[10])};
+            cudaStream_t s = hp->stream[0];
+            const int64_t units = (n_tracks + 31) / 32;
+            const int grid_n = (int)std::min<int64_t>(grid, std::max<int64_t>((units * 32 + block - 1) / block, 1));
+            cudaError_t e = cudaMemsetAsync(hp->counter, 0, sizeof(unsigned), s);
+            if (e == cudaSuccess) e = launch_fit_persistent(g, rt, io, block, cap, depth, grid_n, hp->counter, s);
+            const cudaError_t e2 = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_error(ctx, e, "host-buffer fit");
+            if (e2 != cudaSuccess) return cuda_error(ctx, e2, "host-buffer fit");
+            return KF_OK;
+        }
+    }
     if (hp->buf_bytes < lay.total) {
         for (int i = 0; i < kHostStreams; ++i) {
             cudaStreamSynchronize(hp->stream[i]);
@@ -130,7 +177,6 @@ extern "C" int kf_fit_tracks_host(kf_context *ctx, const kf_geometry *geom, int6
         hp->buf_bytes = lay.total;
     }
 
-    const Routing rt = make_routing(o);
     const int64_t T = n_tracks;
     const int64_t n_chunks = (T + C - 1) / C;
     cudaError_t e = cudaSuccess;

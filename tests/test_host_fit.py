@@ -1,6 +1,7 @@
-"""kf_fit_tracks_host (host buffers, chunked copies overlapping the fit)
-against kf_fit_tracks on the same inputs: the same kernel on the same tracks,
-so the outputs agree bit for bit; and against the oracle."""
+"""kf_fit_tracks_host (host buffers: read and written in place when every
+buffer is page-locked, else chunked copies overlapping the fit) against
+kf_fit_tracks on the same inputs: the same kernel on the same tracks, so the
+outputs agree bit for bit; and against the oracle."""
 import numpy as np
 import pytest
 
@@ -28,12 +29,17 @@ def _device_fit(kf, ctx, b, opt):
     return {k: v.cpu().numpy() for k, v in r.items()}
 
 
-@pytest.mark.parametrize("chunk,pin", [(96, True), (0, True), (200, False)])
-def test_host_fit_equals_device_fit(kf, ctx, chunk, pin):
+@pytest.mark.parametrize("chunk,pin,pin_out", [(96, True, True), (0, True, True), (0, True, False),
+                                               (0, False, False), (200, False, False)])
+def test_host_fit_equals_device_fit(kf, ctx, chunk, pin, pin_out):
+    """chunk 0 with every buffer pinned is the in-place path; a pageable
+    buffer anywhere sends chunk 0 to the chunked copies."""
     b = synth.workload("ragged", scale=0.02)  # 17 layers, missing hits, uneven events
-    opt = kf.options(tracks_per_block=64, reg_cap=128)
+    opt = kf.options(tracks_per_block=64, reg_cap=128, hit_prefetch=1)
     ref = _device_fit(kf, ctx, b, opt)
-    out = kf.fit_tracks_host(ctx, kf.GeometryArgs.of(b.geom), **kf.to_host(b, pin=pin), opt=opt, chunk_tracks=chunk)
+    out = kf.fit_outputs_host(b.n_tracks, pin=pin_out)
+    kf.fit_tracks_host(ctx, kf.GeometryArgs.of(b.geom), **kf.to_host(b, pin=pin), opt=opt, chunk_tracks=chunk,
+                       out=out)
     for k in ref:
         assert np.array_equal(out[k].numpy(), ref[k], equal_nan=True), k
 
