@@ -160,3 +160,45 @@ def test_seeding_arguments(kf, ctx, events):
         kf.seed_triplets(ctx, kf.GeometryArgs.of(ev.geom.sub(0, 3)), ev.seed_hit_offsets,
                          _t(ev.seed_hit_pos, torch.float32), _t(ev.seed_hit_cov, torch.float32),
                          opt=kf.seeding(pt_min=0.0))
+
+
+def test_triplet_buffer_overflow_rerun(kf, ctx, oracle):
+    """A dense event (3,000 tracks, no noise) makes more triplets than the
+    first search's buffer holds (4 per hit): the search runs again with a
+    buffer sized by the count, and the set still matches the oracle's."""
+    ev = synth.make_build_events(61, 1, 3000, noise_per_layer=0, seed_layer_hits=True, seed_noise_per_layer=0)
+    opt = dict(oracle.SEED_DEFAULTS)
+    ctx2 = kf.Context(0)  # a fresh context: the first search starts from the smallest buffer
+    key, _, _, _ = gpu_seeds(kf, ctx2, ev)
+    assert len(key) > max(65536, 4 * ev.seed_hit_pos.shape[1])  # the first buffer's size
+    ref = oracle.seed_fit_inputs(ev, oracle.seed_triplets(ev), opt["pt_min"], opt["pt_both_charges"])
+    ig, io, only_g, only_o = _match(key, ref["key"])
+    for k in list(only_g) + list(only_o):
+        assert _margin(ev, np.array(k[1:4]), opt) < 1e-4, k
+    assert len(only_g) + len(only_o) <= 1e-3 * len(ig)
+    ctx2.close()
+
+
+def test_seeding_degenerate_inputs(kf, ctx, events):
+    """No events; events with an empty seed layer (no triplet can form); an
+    event with an empty middle layer next to a full one."""
+    ev = events
+    g3 = kf.GeometryArgs.of(ev.geom.sub(0, 3))
+    hp, hc = _t(ev.seed_hit_pos, torch.float32), _t(ev.seed_hit_cov, torch.float32)
+    out = kf.seed_triplets(ctx, g3, np.zeros((0, 4), np.int64), hp, hc)
+    assert out["charge"].shape == (0,)
+    # event 0 with its layer-2 hits cut off, event 1 with an empty middle layer
+    off = ev.seed_hit_offsets.copy()
+    a = off[0].copy()
+    b = off[1].copy()
+    rows = np.array([[a[0], a[1], a[2], a[2]], [a[2], a[2] + (b[1] - b[0]), a[2] + (b[1] - b[0]),
+                                                   a[2] + (b[1] - b[0])]], np.int64)
+    out = kf.seed_triplets(ctx, g3, rows, hp, hc)
+    torch.cuda.synchronize()
+    assert out["charge"].shape == (0,)
+    # only the first event, intact: the same seeds as that event alone in the full search
+    key_all, _, _, _ = gpu_seeds(kf, ctx, ev)
+    out = kf.seed_triplets(ctx, g3, off[:1], hp, hc)
+    torch.cuda.synchronize()
+    n0 = int(out["charge"].shape[0])
+    assert n0 == int((key_all[:, 0] == 0).sum()) and n0 > 0
