@@ -1,7 +1,8 @@
 // Combinatorial track building on sm_103a (Sections 3, 3.1 and 4.3):
-//   bin_hits_kernel   - counting sort of every (event, layer)'s hits into
+//   bin_hits          - counting sort of every (event, layer)'s hits into
 //                       phi x z bins (Section 3: hits partitioned spatially
-//                       for a fast look-up of the compatible ones);
+//                       for a fast look-up of the compatible ones), three
+//                       kernels over all segments (kf_bins.cuh);
 //   build_kernel      - the clone engine, all layers in one launch: each
 //                       seed's candidates occupy a group of G = 2^k >= N lanes
 //                       of a warp; every lane propagates its candidate, scans
@@ -25,9 +26,10 @@
 namespace kf {
 
 struct BuildState {
-    size_t hit_capacity = 0, bin_capacity = 0, seg_capacity = 0;
-    float4 *bkey = nullptr;  // binned hits: (phi, z, index within the segment as bits, 0)
+    size_t hit_capacity = 0, bin_capacity = 0, seg_capacity = 0, cnt_capacity = 0;
+    float4 *bkey = nullptr;  // binned hits: (phi, z, index within the segment as bits, radius)
     int32_t *bin_off = nullptr;
+    int32_t *bin_cnt = nullptr;  // per (segment, bin) counts, then cursors, of the binning
     int64_t *seg_off = nullptr;  // device copy of the segment bounds [n_seg + 1]
     int64_t *ev_off = nullptr;   // device copy of hit_offsets [n_events][L + 1]
     size_t ev_capacity = 0;
@@ -38,6 +40,7 @@ void destroy_build_state(BuildState *s)
     if (!s) return;
     cudaFree(s->bkey);
     cudaFree(s->bin_off);
+    cudaFree(s->bin_cnt);
     cudaFree(s->seg_off);
     cudaFree(s->ev_off);
     delete s;
@@ -651,6 +654,7 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
     };
     bool ok = grow((void **)&st->bkey, st->hit_capacity, (size_t)n_hits, sizeof(float4));
     ok = ok && grow((void **)&st->bin_off, st->bin_capacity, n_seg * (nb + 1), sizeof(int32_t));
+    ok = ok && grow((void **)&st->bin_cnt, st->cnt_capacity, n_seg * nb, sizeof(int32_t));
     ok = ok && grow((void **)&st->seg_off, st->seg_capacity, n_seg + 1, sizeof(int64_t));
     ok = ok && grow((void **)&st->ev_off, st->ev_capacity, (size_t)n_events * (L + 1), sizeof(int64_t));
     if (!ok) return set_error(ctx, KF_ERR_NOMEM, "could not allocate the build's scratch");
@@ -658,6 +662,8 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
     for (int e = 0; e < n_events; ++e)
         for (int l = 0; l < L; ++l) seg[(size_t)e * L + l] = hit_offsets[(int64_t)e * (L + 1) + l];
     seg[n_seg] = hit_offsets[(int64_t)(n_events - 1) * (L + 1) + L];
+    int64_t max_seg = 0;
+    for (size_t i = 0; i < n_seg; ++i) max_seg = std::max<int64_t>(max_seg, seg[i + 1] - seg[i]);
     cudaError_t e = cudaMemcpyAsync(st->seg_off, seg.data(), (n_seg + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
                                     stream);
     if (e == cudaSuccess)
@@ -668,15 +674,9 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(ctx, e, "offsets copy");
 
     BinGrid bg{o.n_phi_bins, o.n_z_bins, g.z_half};
-    const size_t bin_smem = (size_t)(nb + 1) * sizeof(int);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(bin_hits_kernel<kBinThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16385 * 4);
-        attr_set = true;
-    }
-    bin_hits_kernel<kBinThreads><<<(unsigned)n_seg, kBinThreads, bin_smem, stream>>>(st->seg_off, hit_pos, n_hits,
-                                                                                    bg, st->bkey, st->bin_off);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(ctx, e, "binning launch");
+    if ((e = bin_hits(st->seg_off, (int64_t)n_seg, max_seg, hit_pos, n_hits, bg, st->bkey, st->bin_off, st->bin_cnt,
+                      context_sm_count(ctx), stream)) != cudaSuccess)
+        return cuda_error(ctx, e, "binning launch");
 
     BuildParams p;
     p.g = g;
