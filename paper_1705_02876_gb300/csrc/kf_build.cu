@@ -321,16 +321,38 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
             int n_in = 0;
             WindowCursor cur;
             if (reached) {
-                cur.start(win);
-                for (uint32_t hl = cur.next(p, win); hl != kNoKey; hl = cur.next(p, win)) {
-                    if (n_in == cap) {
-                        ++n_in;
-                        break;
-                    }
+                // each z row's bins are one contiguous key run (two past the
+                // wrap at +-pi): one pair of bin-offset loads per run, then
+                // the keys four at a time with their loads issued together
+                const int nphi = p.bg.n_phi;
+                int a0 = win.ip0;
+                a0 = a0 < 0 ? a0 + nphi : (a0 >= nphi ? a0 - nphi : a0);
+                const int e0 = a0 + win.nphi;
+                const int b0 = min(e0, nphi), b1 = e0 > nphi ? e0 - nphi : 0;
+                for (int iz = win.iz0; iz <= win.iz1 && n_in <= cap; ++iz) {
+                    const int32_t *row = win.bo + iz * nphi;
+                    for (int r = 0; r < 2 && n_in <= cap; ++r) {
+                        const int ra = r ? 0 : a0, rb = r ? b1 : b0;
+                        if (ra >= rb) continue;
+                        const int ka = row[ra], kb = row[rb];
+                        for (int q = ka; q < kb && n_in <= cap; q += 4) {
+                            float4 kk[4];
 #pragma unroll
-                    for (int k = 0; k < kMaxN; ++k)
-                        if (k == n_in) hb[k] = hl;
-                    ++n_in;
+                            for (int j = 0; j < 4; ++j)
+                                if (q + j < kb) kk[j] = p.bkey[seg_lo + q + j];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                if (q + j < kb && n_in <= cap && fabsf(wrap_pi(kk[j].x - win.phic)) <= win.dphi &&
+                                    fabsf(kk[j].y - win.z) <= win.dz) {
+                                    const uint32_t hl = (uint32_t)__float_as_int(kk[j].z);
+#pragma unroll
+                                    for (int k = 0; k < kMaxN; ++k)
+                                        if (k == n_in && n_in < cap) hb[k] = hl;
+                                    ++n_in;
+                                }
+                            }
+                        }
+                    }
                 }
             }
             const bool wide = n_in > cap;
