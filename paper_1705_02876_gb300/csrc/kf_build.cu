@@ -167,6 +167,7 @@ __host__ __device__ constexpr size_t build_smem_base(int L) { return ((size_t)(L
 constexpr size_t kBuildSmemMlp = sizeof(MlpSmemWeights) + 4 * sizeof(MlpWarpStage);
 
 constexpr int kModePlain = 0, kModeLog = 1, kModeProposal = 2;
+constexpr int kKeyBatch = 4;  // window keys loaded together in the collecting scan (8 was slower)
 
 template <int G, int MODE>
 __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
             if (reached) {
                 // each z row's bins are one contiguous key run (two past the
                 // wrap at +-pi): one pair of bin-offset loads per run, then
-                // the keys four at a time with their loads issued together
+                // the keys kKeyBatch at a time with their loads issued together
                 const int nphi = p.bg.n_phi;
                 int a0 = win.ip0;
                 a0 = a0 < 0 ? a0 + nphi : (a0 >= nphi ? a0 - nphi : a0);
@@ -335,13 +336,13 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
                         const int ra = r ? 0 : a0, rb = r ? b1 : b0;
                         if (ra >= rb) continue;
                         const int ka = row[ra], kb = row[rb];
-                        for (int q = ka; q < kb && n_in <= cap; q += 4) {
-                            float4 kk[4];
+                        for (int q = ka; q < kb && n_in <= cap; q += kKeyBatch) {
+                            float4 kk[kKeyBatch];
 #pragma unroll
-                            for (int j = 0; j < 4; ++j)
+                            for (int j = 0; j < kKeyBatch; ++j)
                                 if (q + j < kb) kk[j] = p.bkey[seg_lo + q + j];
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
+                            for (int j = 0; j < kKeyBatch; ++j) {
                                 if (q + j < kb && n_in <= cap && fabsf(wrap_pi(kk[j].x - win.phic)) <= win.dphi &&
                                     fabsf(kk[j].y - win.z) <= win.dz) {
                                     const uint32_t hl = (uint32_t)__float_as_int(kk[j].z);
