@@ -202,3 +202,33 @@ def test_seeding_degenerate_inputs(kf, ctx, events):
     torch.cuda.synchronize()
     n0 = int(out["charge"].shape[0])
     assert n0 == int((key_all[:, 0] == 0).sum()) and n0 > 0
+
+
+def test_full_size_seeding_sampled(kf, ctx, oracle):
+    """One event of the build workload as the bench seeds it (5,000 tracks,
+    every track's hit on the seed layers, no added noise; about 360,000
+    seeds): the whole triplet set against the oracle's, the seed inputs on
+    3,000 sampled seeds."""
+    ev = synth.make_build_events(4, 1, 5000, seed_layer_hits=True, seed_noise_per_layer=0)
+    opt = dict(oracle.SEED_DEFAULTS)
+    key, g, _, _ = gpu_seeds(kf, ctx, ev)
+    trip = oracle.seed_triplets(ev)
+    tk = {tuple(r) for r in trip[:, :4]}
+    gk = {tuple(r) for r in key[:, :4]}
+    for k in (tk ^ gk):
+        assert _margin(ev, np.array(k[1:4]), opt) < 1e-4, k
+    assert len(tk ^ gk) <= 1e-3 * len(tk) and len(tk) > 300000 // 2
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(len(trip), 3000, replace=False))
+    ref = oracle.seed_fit_inputs(ev, trip[pick], opt["pt_min"], opt["pt_both_charges"])
+    ig, io, _, only_o = _match(key, ref["key"])
+    assert len(only_o) <= 1e-3 * len(ref["key"]) + 2
+    hp = ev.seed_hit_pos.astype(np.float64)
+    kamb = K * abs(float(np.float32(ev.geom.bz))) / opt["pt_both_charges"]
+    kap = np.array([oracle.triplet_circle(*(hp[:2, h] for h in ref["key"][j, 1:4]))[0] for j in io])
+    sel = np.abs(np.abs(kap) / kamb - 1) > 1e-4
+    ig, io = ig[sel], io[sel]
+    st_g, st_o = g["seed_state"][:, ig].astype(np.float64), ref["seed_state"][:, io]
+    scale = np.maximum(np.abs(st_o), np.array([1, 1, 1, 0.1, 0.1, 0.1])[:, None])
+    assert (np.abs(st_g - st_o) / scale).max() <= 5e-4
+    assert (np.abs(g["seed_cov"][:, ig] - ref["seed_cov"][:, io]) <= 1e-3 * np.abs(ref["seed_cov"][:, io]) + 1e-12).all()
