@@ -4,8 +4,8 @@
 //                       for a fast look-up of the compatible ones), three
 //                       kernels over all segments (kf_bins.cuh);
 //   build_kernel      - the clone engine, all layers in one launch: each
-//                       seed's candidates occupy a group of G = 2^k >= N lanes
-//                       of a warp; every lane propagates its candidate, scans
+//                       seed's candidates occupy a group of G >= N lanes of a
+//                       warp (G in 1, 2, 4, 6, 8); every lane propagates its candidate, scans
 //                       the bins its window overlaps and keeps its N best
 //                       compatible hits; the group merges its lanes' lists
 //                       into the N best children by warp shuffles (in place of
@@ -188,8 +188,10 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int slot = lane % G, gbase = lane - slot;
+    // G = 6: five groups per warp; lanes 30 and 31 form an idle group of two
+    const bool lane_ok = lane < SEEDS_PER_WARP * G;
     const int64_t s = ((int64_t)blockIdx.x * 4 + warp) * SEEDS_PER_WARP + lane / G;
-    const bool seed_ok = s < p.S;
+    const bool seed_ok = lane_ok && s < p.S;
     const int N = p.N;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << gbase);
 
@@ -473,8 +475,18 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
             uint32_t b32 = my32;
 #pragma unroll
             for (int d = 1; d < G; d <<= 1) {
-                const unsigned long long o64 = __shfl_xor_sync(gmask, b64, d, G);
-                const uint32_t o32 = __shfl_xor_sync(gmask, b32, d, G);
+                unsigned long long o64;
+                uint32_t o32;
+                if constexpr ((G & (G - 1)) == 0) {  // butterfly within a power-of-two group
+                    o64 = __shfl_xor_sync(gmask, b64, d, G);
+                    o32 = __shfl_xor_sync(gmask, b32, d, G);
+                } else {  // G = 6: pairs, then slots 0-3, then the two halves crossed
+                    const int ps = d == 1 ? (slot ^ 1) : d == 2 ? (slot < 4 ? slot ^ 2 : slot)
+                                                                : (slot < 4 ? 4 + (slot & 1) : slot - 4);
+                    const int src_lane = lane_ok ? gbase + ps : lane;
+                    o64 = __shfl_sync(gmask, b64, src_lane, 32);
+                    o32 = __shfl_sync(gmask, b32, src_lane, 32);
+                }
                 if (key_less(o64, o32, b64, b32)) {
                     b64 = o64;
                     b32 = o32;
@@ -741,7 +753,9 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
     p.mlp_w32 = w32;
     if (log && (e = cudaMemsetAsync(log->count, 0, sizeof(uint64_t), stream)) != cudaSuccess)
         return cuda_error(ctx, e, "log counter");
-    const int G = p.N == 1 ? 1 : p.N <= 2 ? 2 : p.N <= 4 ? 4 : 8;
+    // lanes per seed: the smallest group that holds N candidates (6 for N = 5
+    // or 6, so that a warp holds five seeds instead of four)
+    const int G = p.N == 1 ? 1 : p.N <= 2 ? 2 : p.N <= 4 ? 4 : p.N <= 6 ? 6 : 8;
     const int64_t seeds_per_block = 4 * (32 / G);
     const unsigned grid = (unsigned)((n_seeds + seeds_per_block - 1) / seeds_per_block);
     const int mode = o.use_proposal ? kModeProposal : log ? kModeLog : kModePlain;
@@ -754,16 +768,18 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
         cudaFuncSetAttribute(build_kernel<1, kModeProposal>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         cudaFuncSetAttribute(build_kernel<2, kModeProposal>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         cudaFuncSetAttribute(build_kernel<4, kModeProposal>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(build_kernel<6, kModeProposal>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         cudaFuncSetAttribute(build_kernel<8, kModeProposal>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         attr_prop = true;
     }
     using Kernel = void (*)(const BuildParams);
-    static const Kernel table[4][3] = {
+    static const Kernel table[5][3] = {
         {build_kernel<1, kModePlain>, build_kernel<1, kModeLog>, build_kernel<1, kModeProposal>},
         {build_kernel<2, kModePlain>, build_kernel<2, kModeLog>, build_kernel<2, kModeProposal>},
         {build_kernel<4, kModePlain>, build_kernel<4, kModeLog>, build_kernel<4, kModeProposal>},
+        {build_kernel<6, kModePlain>, build_kernel<6, kModeLog>, build_kernel<6, kModeProposal>},
         {build_kernel<8, kModePlain>, build_kernel<8, kModeLog>, build_kernel<8, kModeProposal>}};
-    const int gi = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : 3;
+    const int gi = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 6 ? 3 : 4;
     table[gi][mode]<<<grid, 128, smem, stream>>>(p);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(ctx, e, "build launch");
     return KF_OK;
