@@ -4,13 +4,14 @@
 //                       for a fast look-up of the compatible ones), three
 //                       kernels over all segments (kf_bins.cuh);
 //   build_kernel      - the clone engine, all layers in one launch: each
-//                       seed's candidates occupy a group of G >= N lanes of a
-//                       warp (G in 1, 2, 4, 6, 8); every lane propagates its candidate, scans
-//                       the bins its window overlaps and keeps its N best
-//                       compatible hits; the group merges its lanes' lists
-//                       into the N best children by warp shuffles (in place of
-//                       the paper's shared-memory heaps, Section 4.3) and each
-//                       lane takes over one child and updates it.
+//                       seed's candidates occupy a group of G >= N lanes of
+//                       a warp (G in 1, 2, 4, 6, 8); every lane propagates
+//                       its candidate, scans the bins its window overlaps
+//                       and keeps its N best compatible hits; the group
+//                       merges its lanes' lists into the N best children by
+//                       warp shuffles (in place of the paper's shared-memory
+//                       heaps, Section 4.3) and each lane takes over one
+//                       child and updates it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
