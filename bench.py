@@ -527,8 +527,11 @@ def bench_smoother(args, kf, ctx, dev, stream, batch, d_in):
     # read back, 108 B of filtered estimates written and read back, 108 B of
     # smoothed estimates written
     per_track = 113 + 36 * L + L * (2 * 160 + 2 * 108 + 108)
+    # inputs and the smoothed outputs alone (no scratch, no filtered round trip)
+    io_track = 113 + 36 * L + L * 108 + 2 + 4
     return {"value": T / (ms * 1e-3), "unit": "tracks/s", "ms_per_step": ms, "layers": L,
             "hbm_gbs_algorithmic": per_track * T / (ms * 1e-3) / 1e9,
+            "hbm_gbs_inputs_outputs": io_track * T / (ms * 1e-3) / 1e9,
             "form": "one thread per track: routed forward fit keeping every layer, then the backward pass"}
 
 
