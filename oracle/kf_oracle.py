@@ -50,6 +50,40 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def op_count_fit(batch) -> dict:
+    """Operations the FP64 oracle performs to fit a ``synth.FitBatch``: its
+    own source compiled with a counting scalar type (kf_opcount.cpp).  Returns
+    the counts by kind and the layers processed."""
+    src = os.path.join(_HERE, "kf_opcount.cpp")
+    so = os.path.join(_BUILD, "libkf_opcount.so")
+    os.makedirs(_BUILD, exist_ok=True)
+    deps = [src, _SRC]
+    if not os.path.exists(so) or any(os.path.getmtime(d) > os.path.getmtime(so) for d in deps):
+        tmp = so + f".{os.getpid()}.tmp"
+        subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+                        "-o", tmp, src], check=True)
+        os.replace(tmp, so)
+    cl = ctypes.CDLL(so)
+    cl.orc_count_fit.restype = ctypes.c_int
+    cl.orc_count_fit.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64] + \
+        [ctypes.c_void_p] * 7
+    g = batch.geom
+    f32 = lambda v: np.ascontiguousarray(np.asarray(v, dtype=np.float32).astype(np.float64))
+    r, xx0 = f32(g.radii), f32(g.x_over_x0)
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (batch.seed_state, batch.seed_cov)]
+    q = np.ascontiguousarray(batch.charge, dtype=np.int8)
+    hp = np.ascontiguousarray(batch.hit_pos, dtype=np.float32)
+    hc = np.ascontiguousarray(batch.hit_cov, dtype=np.float32)
+    mask = np.ascontiguousarray(batch.hit_mask, dtype=np.uint32)
+    counts = np.zeros(7, dtype=np.uint64)
+    rc = cl.orc_count_fit(len(r), _p(r), _p(xx0), float(np.float32(g.z_half)), float(np.float32(g.bz)),
+                          int(batch.n_tracks), arrs[0].ctypes.data, arrs[1].ctypes.data, q.ctypes.data,
+                          hp.ctypes.data, hc.ctypes.data, mask.ctypes.data, counts.ctypes.data)
+    assert rc == 0
+    names = ("add", "mul", "div", "sqrt", "call", "total", "layers")
+    return {k: int(v) for k, v in zip(names, counts)}
+
+
 def lib():
     global _lib
     with _lock:
