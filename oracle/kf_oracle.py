@@ -50,20 +50,25 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
-def op_count_fit(batch) -> dict:
-    """Operations the FP64 oracle performs to fit a ``synth.FitBatch``: its
-    own source compiled with a counting scalar type (kf_opcount.cpp).  Returns
-    the counts by kind and the layers processed."""
+def build_op_count(force: bool = False) -> str:
+    """Compile the operation-counting build of the oracle (kf_opcount.cpp,
+    which includes kf_oracle.c) with g++."""
     src = os.path.join(_HERE, "kf_opcount.cpp")
     so = os.path.join(_BUILD, "libkf_opcount.so")
     os.makedirs(_BUILD, exist_ok=True)
-    deps = [src, _SRC]
-    if not os.path.exists(so) or any(os.path.getmtime(d) > os.path.getmtime(so) for d in deps):
+    if force or not os.path.exists(so) or any(os.path.getmtime(d) > os.path.getmtime(so) for d in (src, _SRC)):
         tmp = so + f".{os.getpid()}.tmp"
         subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
                         "-o", tmp, src], check=True)
         os.replace(tmp, so)
-    cl = ctypes.CDLL(so)
+    return so
+
+
+def op_count_fit(batch) -> dict:
+    """Operations the FP64 oracle performs to fit a ``synth.FitBatch``: its
+    own source compiled with a counting scalar type (kf_opcount.cpp).  Returns
+    the counts by kind and the layers processed."""
+    cl = ctypes.CDLL(build_op_count())
     cl.orc_count_fit.restype = ctypes.c_int
     cl.orc_count_fit.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int64] + \
         [ctypes.c_void_p] * 7
