@@ -106,3 +106,37 @@ def test_smoother_nonfinite_input(kf, ctx, oracle):
         assert int(out["flags"][t]) & 8
     ref = oracle.smooth_batch(b)
     assert ref["reached"][3] == 0 and ref["reached"][7] == 0
+
+
+def test_smoother_full_size_sampled(kf, ctx, oracle):
+    """The fit workload (100 events x 20,000 tracks) smoothed in one launch, as
+    the benchmark runs it; 2,000 sampled tracks against the oracle's smoother
+    at every layer, with the bars above."""
+    b = synth.workload("fit")
+    out = kf.smooth_tracks(ctx, kf.GeometryArgs.of(b.geom), **kf.to_device(b))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3)
+    sel = np.sort(rng.choice(b.n_tracks, 2000, replace=False))
+    idx = torch.from_numpy(sel).cuda()
+    g = dict(state=out["state"][:, :, idx].cpu().numpy(), cov=out["cov"][:, :, idx].cpu().numpy(),
+             reached=out["reached"][idx].cpu().numpy())
+    sub = synth.FitBatch(b.geom, b.seed_state[:, sel], b.seed_cov[:, sel], b.charge[sel],
+                         b.hit_pos[:, :, sel], b.hit_cov[:, :, sel], b.hit_mask[sel],
+                         np.array([0, len(sel)]), b.truth[:, :, sel], b.crossed[:, sel], b.vertex[:, sel])
+    ref = oracle.smooth_batch(sub)
+    filt = oracle.fit_batch(sub, per_layer=True)
+    assert np.array_equal(g["reached"].astype(np.int32), ref["reached"])
+    for l in range(b.geom.n_layers):
+        ok = ref["reached"] > l
+        if not ok.any():
+            continue
+        gs, rs = g["state"][l][:, ok].astype(np.float64), ref["state"][l][:, ok]
+        r = np.maximum(np.hypot(rs[0], rs[1]), 1.0)
+        p = np.linalg.norm(rs[3:], axis=0)
+        assert (np.abs(gs[:3] - rs[:3]) / r).max() <= 1e-4
+        assert (np.abs(gs[3:] - rs[3:]) / p).max() <= 1e-4
+        Lg = _local_cov(rs, g["cov"][l][:, ok].astype(np.float64))
+        Lr = _local_cov(rs, ref["cov"][l][:, ok])
+        Lf = _local_cov(rs, filt["layer_cov"][l][:, ok])
+        df = np.sqrt(np.abs(np.einsum("iin->in", Lf)))
+        assert (np.abs(Lg - Lr) / (df[:, None] * df[None, :])).max() <= 5e-3

@@ -51,3 +51,38 @@ def test_transport_batch_empty_and_errors(kf):
     with pytest.raises(kf.KFError, match="shape"):
         kf.transport_batch(ctx, torch.zeros((36, 5), device="cuda"), torch.zeros((21, 4), device="cuda"))
     ctx.close()
+
+
+def test_transport_batch_full_size_sampled(kf, oracle):
+    """10 million matrices in one launch, as the benchmark times them (inputs
+    drawn on the device from a seeded generator, the same recipe as above);
+    2,000 sampled matrices against the oracle."""
+    n = 10_000_000
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    J = torch.eye(6, device="cuda")[None] + 0.5 * torch.randn((n, 6, 6), generator=gen, device="cuda")
+    scales = torch.logspace(-3, 1, 6, device="cuda")
+    B = torch.randn((n, 6, 6), generator=gen, device="cuda") * scales[None, None, :]
+    C = torch.bmm(B, B.transpose(1, 2))
+    del B
+    Jd = J.reshape(n, 36).T.contiguous()
+    Cd = torch.stack([C[:, i, j] for i, j in PK]).contiguous()
+    del C
+    rng = np.random.default_rng(12)
+    sel = np.sort(rng.choice(n, 2000, replace=False))
+    idx = torch.from_numpy(sel).cuda()
+    J_s = Jd[:, idx].cpu().numpy().astype(np.float64)
+    C_s = Cd[:, idx].cpu().numpy().astype(np.float64)
+    ctx = kf.Context(0)
+    kf.transport_batch(ctx, Jd, Cd)
+    torch.cuda.synchronize()
+    got = Cd[:, idx].cpu().numpy()
+    for k in range(len(sel)):
+        Jt = J_s[:, k].reshape(6, 6)
+        Ct = np.zeros((6, 6))
+        for q, (i, j) in enumerate(PK):
+            Ct[i, j] = Ct[j, i] = C_s[q, k]
+        ref = oracle.transport(Jt, Ct, np.zeros((6, 6)))
+        scale = np.abs(Jt) @ np.abs(Ct) @ np.abs(Jt).T
+        for q, (i, j) in enumerate(PK):
+            assert abs(got[q, k] - ref[i, j]) <= 2e-6 * scale[i, j], (k, i, j)
+    ctx.close()
