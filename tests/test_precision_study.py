@@ -26,7 +26,7 @@ torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
 
 PARAMS = ("t", "z", "px", "py", "pz")  # t: tangential position at the last crossing
-N_TRACKS = 200_000
+N_TRACKS = 1_000_000  # per resolution, the precision workload's size
 
 
 @pytest.fixture(scope="module")
