@@ -317,6 +317,11 @@ int kf_proposal_train(kf_context *ctx, float *weights, const float *features, co
  * for the tensor cores (biases and W3 stay FP32). */
 int kf_proposal_load(kf_context *ctx, const float *weights, kf_stream stream);
 
+/* kf_proposal_load with the weights given as bytes: weights (device) holds the
+ * 5,057 FP32 parameters in the order above, bytes must be 20,228
+ * (KF_ERR_ARG otherwise); enqueued on the legacy default stream. */
+int kf_load_proposal(kf_context *ctx, const void *weights, size_t bytes);
+
 /* Logits [n] of the loaded network for the pairs' features: BF16 inputs and
  * weights, FP32 accumulation, on the tensor cores. */
 int kf_proposal_score(kf_context *ctx, const float *features, int64_t n, float *logits, kf_stream stream);

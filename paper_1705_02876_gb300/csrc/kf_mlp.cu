@@ -362,6 +362,15 @@ int kf_proposal_load(kf_context *ctx, const float *weights, kf_stream stream_)
     return KF_OK;
 }
 
+int kf_load_proposal(kf_context *ctx, const void *weights, size_t bytes)
+{
+    if (!ctx) return KF_ERR_ARG;
+    if (bytes != kMlpParams * sizeof(float))
+        return set_error(ctx, KF_ERR_ARG, "weights must be %zu bytes (%d FP32 parameters), got %zu",
+                         (size_t)kMlpParams * sizeof(float), kMlpParams, bytes);
+    return kf_proposal_load(ctx, static_cast<const float *>(weights), nullptr);
+}
+
 int kf_proposal_score(kf_context *ctx, const float *features, int64_t n, float *logits, kf_stream stream_)
 {
     if (!ctx) return KF_ERR_ARG;

@@ -102,6 +102,7 @@ def load() -> ctypes.CDLL:
         L.kf_proposal_train.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                         ctypes.POINTER(ctypes.c_float), _vp]
         L.kf_proposal_load.argtypes = [_vp, _vp, _vp]
+        L.kf_load_proposal.argtypes = [_vp, _vp, ctypes.c_size_t]
         L.kf_proposal_score.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
         L.kf_fit_tracks_noalloc.argtypes = [ctypes.POINTER(Geometry), ctypes.c_int64] + [_vp] * 11 + \
             [ctypes.POINTER(Options), _vp]
@@ -407,6 +408,15 @@ def proposal_load(ctx: Context, weights, stream=None):
     rc = load().kf_proposal_load(ctx.handle, _ptr(weights, torch.float32, (PROPOSAL_PARAMS,), "weights"),
                                  _cur_stream(weights, stream))
     ctx.check(rc, "kf_proposal_load")
+
+
+def load_proposal(ctx: Context, weights):
+    """kf_load_proposal: the weights as bytes (a CUDA tensor of any dtype whose
+    storage holds the 5,057 FP32 parameters), on the default stream."""
+    if not weights.is_cuda or not weights.is_contiguous():
+        raise KFError("weights: expected a contiguous CUDA tensor")
+    rc = load().kf_load_proposal(ctx.handle, weights.data_ptr(), weights.numel() * weights.element_size())
+    ctx.check(rc, "kf_load_proposal")
 
 
 def proposal_score(ctx: Context, features, stream=None):

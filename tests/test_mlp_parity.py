@@ -93,3 +93,21 @@ def test_score_without_weights_fails(kf):
     with pytest.raises(kf.KFError, match="no proposal"):
         kf.proposal_score(c, cu(np.zeros((4, 12), np.float32)))
     c.close()
+
+
+def test_load_proposal_as_bytes(kf):
+    """kf_load_proposal (weights as bytes) loads the same network as
+    kf_proposal_load; a buffer of the wrong size is an argument error."""
+    X, _, w = data(5, 257)
+    c1, c2 = kf.Context(0), kf.Context(0)
+    kf.proposal_load(c1, cu(w))
+    torch.cuda.synchronize()
+    kf.load_proposal(c2, cu(w).view(torch.uint8))
+    torch.cuda.synchronize()
+    z1 = kf.proposal_score(c1, cu(X)).cpu().numpy()
+    z2 = kf.proposal_score(c2, cu(X)).cpu().numpy()
+    assert np.array_equal(z1, z2)
+    with pytest.raises(kf.KFError, match="bytes"):
+        kf.load_proposal(c2, cu(w[:-1]))
+    c1.close()
+    c2.close()
