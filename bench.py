@@ -126,6 +126,19 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def recorded_build_traffic():
+    """DRAM bytes of one W4 build call (the build kernel and the binning) from
+    the committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", "build_kernel_build_workload.txt")
+    try:
+        vals = dict(line.split(":", 1) for line in open(path).read().splitlines()
+                    if ":" in line and not line.startswith((" ", "#")))
+        return (float(vals["dram_bytes_read_per_launch"]) + float(vals["dram_bytes_write_per_launch"])
+                + float(vals["binning_dram_bytes_per_launch"]))
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def recorded_traffic(src_hash: str):
     """DRAM bytes per launch of the fit kernel from the committed ncu summary,
     if it was taken on the current kernel sources."""
@@ -351,6 +364,27 @@ def bench_build(args, kf, ctx, dev, stream, rank, world):
 
     ms = timed(step_chosen, args.build_steps)
     best = b_out["hit"][:, 0].cpu().numpy()
+
+    # the build call alone (binning + build kernel) for its roofline fractions
+    def step_build_only():
+        kf.build_tracks(ctx, build_geom, ev.hit_offsets, hp, hc, se, fit_out["state"], fit_out["cov"], sq,
+                        opt=chosen, out=b_out, stream=stream)
+
+    ms_call = timed(step_build_only, args.build_steps)
+    peaks = measured_peaks()
+    Lb = ev.build_geom.n_layers
+    flops = S * Lb * chosen.max_cands * FLOPS_PER_TRACK_LAYER  # every candidate slot live: an upper bound
+    dram = recorded_build_traffic() if E == 64 else None
+    hbm = peaks.get("hbm_gbs")
+    build_roofline = {
+        "bound": "latency", "call_ms": ms_call, "fp32_tflops": flops / (ms_call * 1e-3) / 1e12,
+        "fp32_frac": flops / (ms_call * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+        "fp32_flops_per_call": flops,
+        "fp32_flops_note": "seeds x build layers x N x 768: every candidate slot live at every layer (upper bound)",
+        "dram_gbs": dram / (ms_call * 1e-3) / 1e9 if dram else None,
+        "dram_frac": (dram / (ms_call * 1e-3) / 1e9 / hbm) if (dram and hbm) else None,
+        "dram_bytes_per_call": dram,
+        "dram_bytes_source": "ncu capture of the 64-event call (build kernel + binning), committed summary"}
     q = metrics.efficiency_fake_rate(best, ev.seed_track, ev.hit_track, ev.track_nhits)
     ms_plain = timed(step_plain, max(2, args.build_steps // 2))
     qp = metrics.efficiency_fake_rate(np.concatenate([o["hit"][:, 0].cpu().numpy() for o in plain_outs if o is not None]),
@@ -363,7 +397,7 @@ def bench_build(args, kf, ctx, dev, stream, rank, world):
            "form": "seed fit + binning + build of all events in one launch each, routed precision, "
                    "exhaustive chi2 in every window",
            "efficiency": q["efficiency"], "fake_rate": q["fake_rate"], "mean_hits": q["mean_hits"],
-           "hit_purity": q["hit_purity"],
+           "hit_purity": q["hit_purity"], "roofline": build_roofline,
            "plain": {"value": S / (ms_plain * 1e-3), "unit": "seeds/s", "ms_per_step": ms_plain,
                      "form": "FP32 only, one launch per event", "efficiency": qp["efficiency"],
                      "fake_rate": qp["fake_rate"]},
