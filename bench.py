@@ -102,13 +102,14 @@ def measured_peaks():
         return {}
 
 
-def kernel_source_hash() -> str:
-    """Hash of the fit kernel's sources (its translation unit and every header
-    it includes from the package or include/) and of the build script."""
+def kernel_source_hash(unit: str = "kf_fit.cu") -> str:
+    """Hash of a kernel's sources (its translation unit, by default the fit's,
+    and every header it includes from the package or include/) and of the
+    build script."""
     import re
     csrc = os.path.join(ROOT, "paper_1705_02876_gb300", "csrc")
     inc = os.path.join(ROOT, "include")
-    todo, seen = [os.path.join(csrc, "kf_fit.cu")], []
+    todo, seen = [os.path.join(csrc, unit)], []
     while todo:
         p = todo.pop()
         if p in seen:
@@ -126,13 +127,15 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_build_traffic():
+def recorded_build_traffic(src_hash: str):
     """DRAM bytes of one W4 build call (the build kernel and the binning) from
-    the committed ncu summary, or None."""
+    the committed ncu summary, if it was taken on the current build sources."""
     path = os.path.join(ROOT, "profiles", "build_kernel_build_workload.txt")
     try:
-        vals = dict(line.split(":", 1) for line in open(path).read().splitlines()
-                    if ":" in line and not line.startswith((" ", "#")))
+        vals = {k.strip(): v.strip() for k, v in (line.split(":", 1) for line in open(path).read().splitlines()
+                                                  if ":" in line and not line.startswith((" ", "#")))}
+        if vals.get("source_hash") != src_hash:
+            return None
         return (float(vals["dram_bytes_read_per_launch"]) + float(vals["dram_bytes_write_per_launch"])
                 + float(vals["binning_dram_bytes_per_launch"]))
     except (OSError, KeyError, ValueError):
@@ -374,7 +377,8 @@ def bench_build(args, kf, ctx, dev, stream, rank, world):
     peaks = measured_peaks()
     Lb = ev.build_geom.n_layers
     flops = S * Lb * chosen.max_cands * FLOPS_PER_TRACK_LAYER  # every candidate slot live: an upper bound
-    dram = recorded_build_traffic() if E == 64 else None
+    build_hash = kernel_source_hash("kf_build.cu")
+    dram = recorded_build_traffic(build_hash) if E == 64 else None
     hbm = peaks.get("hbm_gbs")
     build_roofline = {
         "bound": "latency", "call_ms": ms_call, "fp32_tflops": flops / (ms_call * 1e-3) / 1e12,
@@ -384,7 +388,8 @@ def bench_build(args, kf, ctx, dev, stream, rank, world):
         "dram_gbs": dram / (ms_call * 1e-3) / 1e9 if dram else None,
         "dram_frac": (dram / (ms_call * 1e-3) / 1e9 / hbm) if (dram and hbm) else None,
         "dram_bytes_per_call": dram,
-        "dram_bytes_source": "ncu capture of the 64-event call (build kernel + binning), committed summary"}
+        "dram_bytes_source": "ncu capture of the 64-event call (build kernel + binning), committed summary",
+        "kernel_source_hash": build_hash}
     q = metrics.efficiency_fake_rate(best, ev.seed_track, ev.hit_track, ev.track_nhits)
     ms_plain = timed(step_plain, max(2, args.build_steps // 2))
     qp = metrics.efficiency_fake_rate(np.concatenate([o["hit"][:, 0].cpu().numpy() for o in plain_outs if o is not None]),

@@ -40,7 +40,7 @@ constexpr int kBinPerThread = 8;                         // hits per thread
 constexpr int kBinChunk = kBinThreadsHP * kBinPerThread;  // hits per virtual block
 
 template <bool SCATTER>
-__global__ void __launch_bounds__(kBinThreadsHP) bin_chunk_kernel(const int64_t *seg_off, const float *hit_pos,
+__global__ void __launch_bounds__(kBinThreadsHP, 4) bin_chunk_kernel(const int64_t *seg_off, const float *hit_pos,
                                                                    int64_t H, BinGrid bg, int64_t chunks,
                                                                    int64_t n_virtual, int32_t *counts,
                                                                    float4 *bkey)
@@ -62,27 +62,45 @@ __global__ void __launch_bounds__(kBinThreadsHP) bin_chunk_kernel(const int64_t 
                 z[k] = hit_pos[2 * H + h];
             }
         }
+        if constexpr (SCATTER) {
+            // all of the thread's cursor claims are issued before the first
+            // key store, so that their round trips to L2 overlap
+            // (x and y are replaced by phi and the radius as they are used)
+            int p[kBinPerThread];
 #pragma unroll
-        for (int k = 0; k < kBinPerThread; ++k) {
-            const int64_t h = h0 + k * kBinThreadsHP;
-            if (h < hi) {
-                const float phi = atan2f(y[k], x[k]);
-                int32_t *slot = &cnt[z_bin(z[k], bg) * bg.n_phi + phi_bin(phi, bg.n_phi)];
-                if constexpr (SCATTER) {
-                    const int p = atomicAdd(slot, 1);
-                    bkey[lo + p] =
-                        make_float4(phi, z[k], __int_as_float((int)(h - lo)), sqrtf(x[k] * x[k] + y[k] * y[k]));
-                } else {
-                    atomicAdd(slot, 1);
+            for (int k = 0; k < kBinPerThread; ++k) {
+                if (h0 + k * kBinThreadsHP < hi) {
+                    const float phi = atan2f(y[k], x[k]), r = sqrtf(x[k] * x[k] + y[k] * y[k]);
+                    x[k] = phi;
+                    y[k] = r;
+                    p[k] = atomicAdd(&cnt[z_bin(z[k], bg) * bg.n_phi + phi_bin(phi, bg.n_phi)], 1);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kBinPerThread; ++k) {
+                const int64_t h = h0 + k * kBinThreadsHP;
+                if (h < hi) bkey[lo + p[k]] = make_float4(x[k], z[k], __int_as_float((int)(h - lo)), y[k]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kBinPerThread; ++k) {
+                if (h0 + k * kBinThreadsHP < hi) {
+                    const float phi = atan2f(y[k], x[k]);
+                    atomicAdd(&cnt[z_bin(z[k], bg) * bg.n_phi + phi_bin(phi, bg.n_phi)], 1);
                 }
             }
         }
     }
 }
 
-// One block per segment: exclusive scan of its bins' counts (each thread owns
-// a contiguous run of bins) into bin_off (the segment's [nb + 1] offsets) and
-// into counts, which become the scatter's cursors.
+// One block per segment: exclusive scan of its bins' counts into bin_off (the
+// segment's [nb + 1] offsets) and into counts, which become the scatter's
+// cursors.  Warp w owns bins [w * 32 kScanRun, (w + 1) * 32 kScanRun) and
+// walks them in kScanRun rounds of 32 consecutive bins, so that every load
+// and store of a warp is one contiguous run; a round is scanned with shuffles
+// and its total carried into the next.
+constexpr int kScanThreads = 1024, kScanRun = 16;
+constexpr int kMaxBins = kScanThreads * kScanRun;  // 16,384 bins per segment
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) bin_scan_kernel(const int64_t *seg_off, int nb, int32_t *counts,
                                                            int32_t *bin_off)
@@ -90,18 +108,24 @@ __global__ void __launch_bounds__(THREADS) bin_scan_kernel(const int64_t *seg_of
     __shared__ int warp_sums[THREADS / 32];
     const int64_t seg = blockIdx.x;
     int32_t *cnt = counts + seg * nb;
-    const int per = (nb + THREADS - 1) / THREADS;
-    const int b0 = min(nb, (int)threadIdx.x * per), b1 = min(nb, b0 + per);
-    int run = 0;
-    for (int b = b0; b < b1; ++b) run += cnt[b];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = run;
+    const int wb = warp * 32 * kScanRun + lane;  // this lane's bin in round 0
+    int v[kScanRun];
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int o = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += o;
+    for (int i = 0; i < kScanRun; ++i) v[i] = wb + 32 * i < nb ? cnt[wb + 32 * i] : 0;
+    int carry = 0;  // the warp's bins before this round
+#pragma unroll
+    for (int i = 0; i < kScanRun; ++i) {
+        int incl = v[i];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        v[i] = carry + incl - v[i];
+        carry += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (lane == 31) warp_sums[warp] = incl;
+    if (lane == 0) warp_sums[warp] = carry;
     __syncthreads();
     if (warp == 0) {
         int w = lane < THREADS / 32 ? warp_sums[lane] : 0;
@@ -113,14 +137,14 @@ __global__ void __launch_bounds__(THREADS) bin_scan_kernel(const int64_t *seg_of
         if (lane < THREADS / 32) warp_sums[lane] = w;
     }
     __syncthreads();
-    int base = incl - run + (warp > 0 ? warp_sums[warp - 1] : 0);
+    const int base = warp > 0 ? warp_sums[warp - 1] : 0;
     int32_t *bo = bin_off + seg * (nb + 1);
-    for (int b = b0; b < b1; ++b) {
-        const int c = cnt[b];
-        cnt[b] = base;
-        bo[b] = base;
-        base += c;
-    }
+#pragma unroll
+    for (int i = 0; i < kScanRun; ++i)
+        if (wb + 32 * i < nb) {
+            cnt[wb + 32 * i] = base + v[i];
+            bo[wb + 32 * i] = base + v[i];
+        }
     if (threadIdx.x == 0) bo[nb] = (int)(seg_off[seg + 1] - seg_off[seg]);
 }
 
@@ -133,6 +157,7 @@ inline cudaError_t bin_hits(const int64_t *seg_off, int64_t n_seg, int64_t max_s
 {
     if (n_seg <= 0) return cudaSuccess;
     const int nb = bg.n_phi * bg.n_z;
+    if (nb < 1 || nb > kMaxBins) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)n_seg * nb * sizeof(int32_t), stream);
     if (e != cudaSuccess) return e;
     const int64_t chunks = max_seg > 0 ? (max_seg + kBinChunk - 1) / kBinChunk : 1;
@@ -140,7 +165,7 @@ inline cudaError_t bin_hits(const int64_t *seg_off, int64_t n_seg, int64_t max_s
     const unsigned grid = (unsigned)(n_virtual < (int64_t)sm_count * 64 ? n_virtual : (int64_t)sm_count * 64);
     bin_chunk_kernel<false><<<grid, kBinThreadsHP, 0, stream>>>(seg_off, hit_pos, H, bg, chunks, n_virtual, counts,
                                                               bkey);
-    bin_scan_kernel<1024><<<(unsigned)n_seg, 1024, 0, stream>>>(seg_off, nb, counts, bin_off);
+    bin_scan_kernel<kScanThreads><<<(unsigned)n_seg, kScanThreads, 0, stream>>>(seg_off, nb, counts, bin_off);
     bin_chunk_kernel<true><<<grid, kBinThreadsHP, 0, stream>>>(seg_off, hit_pos, H, bg, chunks, n_virtual, counts,
                                                              bkey);
     return cudaGetLastError();
