@@ -11,7 +11,7 @@
  * the children are ranked by number of hits (more first) and chi2 (less
  * first) (Section 4.3), and only the best N survive, each updated with its
  * hit.  With N = 1 this is the best-hit approach (Section 3: the hit with the
- * lowest chi2 increment).  Readings of this build (the paper gives no
+ * lowest chi2 increment).  Readings taken here (the paper gives no
  * numbers): a hit is compatible if it lies in the window
  *   |dphi| <= nsigma sqrt(sigma_rphi,pred^2 + sigma_rphi,hit^2) / r,
  *   |dz|   <= nsigma sqrt(sigma_z,pred^2 + sigma_z,hit^2)

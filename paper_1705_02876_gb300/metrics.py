@@ -1,8 +1,8 @@
 """Track-finding efficiency and fake rate of built candidates (Section 3.2).
 
 The paper counts efficiency and fake rate with the rule that candidates
-matching fewer than 7 hits of a simulated track count as neither.  Reading of
-this build: per seed the best candidate (rank 0) is taken; it *matches* the
+matching fewer than 7 hits of a simulated track count as neither.  Reading
+taken here: per seed the best candidate (rank 0) is taken; it *matches* the
 simulated track that owns at least half of its hits (seed hits included); it
 is *counted* if it has at least 7 hits.  Efficiency = fraction of simulated
 tracks with at least 7 hits (and a seed) matched by a counted candidate; fake
