@@ -26,6 +26,17 @@
  * All linear algebra is dense and unblocked: full 6x6 products, a Cholesky
  * factorisation for S^-1.  Every function works in double precision on inputs
  * promoted from the float32 arrays the library sees.
+ *
+ * Pins (the CPU tests): the crossing against an RK4 integration of the
+ * equation of motion and against the line-cylinder root at Bz = 0; J against
+ * central differences; S^-1 against LU inversion; the update against the
+ * information form; the fit against exact hits, against a Gauss-Newton least
+ * squares fit when scattering is off, and against unit pulls and flat chi2
+ * p-values on simulated tracks.  The Highland constants (0.0136 GeV, 0.038)
+ * are a convention the generator and both implementations share: parity
+ * unpinned for those two constants.  Q's structure (no component along p,
+ * isotropic across it) and its size relative to the generator's kicks (the
+ * pull widths) are pinned.
  */
 #include <math.h>
 #include <stdint.h>
