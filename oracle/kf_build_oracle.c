@@ -6,6 +6,12 @@
  * and the CPU-baseline leg of the benchmark.  Shares no code with the CUDA
  * library.
  *
+ * Pins (the CPU tests): on tiny events the kept candidates equal the best N
+ * of fits of every hit sequence, enumerated by brute force; N = 1 is the
+ * best-hit search; the capped windows hold exactly the hits of a brute-force
+ * box; noise-free events give every seed its own track's hits; efficiency and
+ * fake rate land where the paper reports them for its toy detector.
+ *
  * The clone engine (Section 3.1): at each layer every candidate of a seed
  * yields one child per compatible hit plus one child without a hit (a hole);
  * the children are ranked by number of hits (more first) and chi2 (less

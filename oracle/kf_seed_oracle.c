@@ -8,6 +8,11 @@
  * TEST INFRASTRUCTURE ONLY: loaded by the test suite; shares no code with the
  * CUDA library.
  *
+ * Pins (the CPU tests): the triplet circle against exact helices; the
+ * triplets equal a brute force over every hit combination; every track that
+ * passes the cuts is found with its charge; the seed start on exact helices
+ * and on straight (two-charge) triplets.
+ *
  * A triplet (h0, h1, h2), h_i a hit of seed layer i of one event, with hit
  * radii r_i = |(x_i, y_i)|, azimuths phi_i and z_i, is a seed when
  *   (a) |phi_1 - phi_0| <= dphi_01 and (e) |phi_2 - phi_1| <= dphi_12 (wrapped),

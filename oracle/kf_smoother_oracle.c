@@ -9,6 +9,11 @@
  * TEST INFRASTRUCTURE ONLY: loaded by the test suite; shares no code with the
  * CUDA library.
  *
+ * Pins (the CPU tests): the last layer equals the forward fit; without
+ * scattering the smoothed states are one helix and equal a least-squares fit
+ * of all hits at every layer; smoothing never increases a variance; smoothed
+ * pulls have unit width.
+ *
  * Forward: the oracle's own propagation, transport, scattering and update
  * (kf_oracle.c), keeping at every layer reached the predicted state x_p and
  * covariance C_p, the filtered x_f and C_f, and the transport Jacobian F from

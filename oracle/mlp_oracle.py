@@ -8,6 +8,10 @@ the network, its inputs and its training follow the task's specification of
 the proposal (12 inputs, two hidden layers of width 64, one logit, top-k of the
 in-window hits).
 
+Pins (the CPU tests): the parameter count; BCE against its closed forms;
+gradients against central differences; a network reduced to one layer against
+logistic regression; Adam's first steps against their closed forms.
+
 Parameter layout (shared with the library's weight buffer, float32 there):
 W1 [12][64] (input-major), b1 [64], W2 [64][64], b2 [64], W3 [64], b3 [1] --
 5,057 values in that order.
