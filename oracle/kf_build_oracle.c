@@ -10,7 +10,12 @@
  * of fits of every hit sequence, enumerated by brute force; N = 1 is the
  * best-hit search; the capped windows hold exactly the hits of a brute-force
  * box; noise-free events give every seed its own track's hits; efficiency and
- * fake rate land where the paper reports them for its toy detector.
+ * fake rate land where the paper reports them for its toy detector.  For the
+ * proposal: BF16 rounding against hand-worked ties; the logit against the
+ * perceptron's definition in mlp_oracle.py; the training log against the
+ * plain build it records (build unchanged, labels on the surviving hits, rows
+ * inside the windows); a proposal wider than every window is the exhaustive
+ * build.
  *
  * The clone engine (Section 3.1): at each layer every candidate of a seed
  * yields one child per compatible hit plus one child without a hit (a hole);

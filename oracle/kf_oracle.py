@@ -3,11 +3,6 @@
 TEST INFRASTRUCTURE ONLY: imported by the tests, by the package smoke check and
 by the CPU-baseline leg of the benchmark.  Nothing in the library imports it.
 
-Pins of what this module adds to the C code (the CPU tests): BF16 rounding
-against hand-worked ties; the build's proposal logit against the perceptron's
-definition in mlp_oracle; the training log against the plain build it records
-(unchanged build, labels on the surviving hits, rows inside the windows).
-
 The C code processes a contiguous range of tracks; ``fit_tracks`` splits a
 batch into ranges and runs them on a thread pool (ctypes releases the GIL
 during the call), so the oracle uses the host's cores without any threading
