@@ -66,3 +66,34 @@ def test_context_create_fails_cleanly_without_gpu():
     from paper_1705_02876_gb300 import kf
     with pytest.raises(kf.KFError):
         kf.Context(0)
+
+
+def _header_arity():
+    """Parameter count of every function declared in kf.h, from the header text."""
+    import re
+    from paper_1705_02876_gb300 import kf
+    text = re.sub(r"/\*.*?\*/", "", open(kf.HEADER).read(), flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    out = {}
+    for m in re.finditer(r"\b(kf_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text):
+        args = m.group(2).strip()
+        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_declares_every_header_function_with_its_arity():
+    """The ctypes binding gives every function of kf.h argument types, as many
+    as the header's declaration has parameters (a missing or extra argument
+    would be passed silently otherwise)."""
+    pytest.importorskip("torch")
+    from paper_1705_02876_gb300 import build, kf
+    build.build()
+    L = kf.load()
+    arity = _header_arity()
+    assert set(arity) == set(kf.header_functions())
+    wrong = {}
+    for name, n in arity.items():
+        f = getattr(L, name)
+        if f.argtypes is None or len(f.argtypes) != n:
+            wrong[name] = (n, None if f.argtypes is None else len(f.argtypes))
+    assert not wrong, wrong
