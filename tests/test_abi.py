@@ -68,17 +68,43 @@ def test_context_create_fails_cleanly_without_gpu():
         kf.Context(0)
 
 
-def _header_arity():
-    """Parameter count of every function declared in kf.h, from the header text."""
+def _header_params():
+    """Parameter declarations of every function declared in kf.h, from the
+    header text."""
     import re
     from paper_1705_02876_gb300 import kf
     text = re.sub(r"/\*.*?\*/", "", open(kf.HEADER).read(), flags=re.S)
     text = re.sub(r"//[^\n]*", "", text)
     out = {}
     for m in re.finditer(r"\b(kf_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text):
-        args = m.group(2).strip()
-        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+        args = " ".join(m.group(2).split())
+        out[m.group(1)] = [] if args in ("", "void") else [a.strip() for a in args.split(",")]
     return out
+
+
+def _header_arity():
+    return {k: len(v) for k, v in _header_params().items()}
+
+
+# C parameter type (without its name) -> (kind, size in bytes) as the calling
+# convention sees it; every pointer, kf_stream included, is one kind
+_SCALARS = {"int": ("int", 4), "int32_t": ("int", 4), "unsigned": ("int", 4), "uint32_t": ("int", 4),
+            "int64_t": ("int", 8), "size_t": ("int", 8), "float": ("float", 4), "double": ("float", 8)}
+
+
+def _c_kind(decl):
+    if "*" in decl or decl.split()[0] == "kf_stream":
+        return ("ptr", 8)
+    t = " ".join(w for w in decl.split()[:-1] if w != "const")
+    return _SCALARS[t]
+
+
+def _ctypes_kind(t):
+    if t in (ctypes.c_float, ctypes.c_double):
+        return ("float", ctypes.sizeof(t))
+    if t is ctypes.c_void_p or t is ctypes.c_char_p or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return ("ptr", 8)
+    return ("int", ctypes.sizeof(t))
 
 
 def test_binding_declares_every_header_function_with_its_arity():
@@ -96,4 +122,20 @@ def test_binding_declares_every_header_function_with_its_arity():
         f = getattr(L, name)
         if f.argtypes is None or len(f.argtypes) != n:
             wrong[name] = (n, None if f.argtypes is None else len(f.argtypes))
+    assert not wrong, wrong
+
+
+def test_binding_argument_types_match_the_header():
+    """Each argument's ctypes type has the kind (pointer, integer, floating)
+    and width of the header's parameter: an int passed where the header takes
+    an int64_t, or a float for a double, would be read wrongly by the callee."""
+    pytest.importorskip("torch")
+    from paper_1705_02876_gb300 import build, kf
+    build.build()
+    L = kf.load()
+    wrong = []
+    for name, params in _header_params().items():
+        for i, (decl, t) in enumerate(zip(params, getattr(L, name).argtypes)):
+            if _c_kind(decl) != _ctypes_kind(t):
+                wrong.append((name, i, decl, t.__name__))
     assert not wrong, wrong
