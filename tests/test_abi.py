@@ -139,3 +139,27 @@ def test_binding_argument_types_match_the_header():
             if _c_kind(decl) != _ctypes_kind(t):
                 wrong.append((name, i, decl, t.__name__))
     assert not wrong, wrong
+
+
+def test_library_defaults_equal_the_oracle_defaults():
+    """kf_options_default and kf_seeding_default give the settings the
+    oracle's build and seeding functions default to, so that a test calling
+    both sides with defaults compares like with like (float32 on the library
+    side)."""
+    import inspect
+
+    import numpy as np
+    pytest.importorskip("torch")
+    from oracle import kf_oracle as orc
+    from paper_1705_02876_gb300 import kf
+    o, s = kf.options(), kf.seeding()
+    b = {k: v.default for k, v in inspect.signature(orc.build_arrays).parameters.items()}
+    pairs = [(o.max_cands, b["max_cands"]), (o.chi2_cut, b["chi2_cut"]), (o.window_nsigma, b["nsigma"]),
+             (o.hit_sigma_rphi, b["sigma_rphi"]), (o.hit_sigma_z, b["sigma_z"]), (o.topk, b["topk"]),
+             (o.window_max_dphi, b["dphi_max"]), (o.window_max_dz, b["dz_max"])]
+    f = {k: v.default for k, v in inspect.signature(orc.seed_fit_inputs).parameters.items()}
+    pairs += [(getattr(s, k), v) for k, v in orc.SEED_DEFAULTS.items()]
+    pairs += [(getattr(s, k), f[k]) for k in ("pt_min", "pt_both_charges", "pt_unresolved", "p_sigma_resolved",
+                                              "p_sigma_unresolved")]
+    for lib_value, oracle_value in pairs:
+        assert lib_value == np.float32(oracle_value), (lib_value, oracle_value)
