@@ -163,3 +163,78 @@ def test_library_defaults_equal_the_oracle_defaults():
                                               "p_sigma_unresolved")]
     for lib_value, oracle_value in pairs:
         assert lib_value == np.float32(oracle_value), (lib_value, oracle_value)
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include "kf.h"
+
+#define EXPECT(cond, code) do { if (!(cond)) { printf("failed %d\n", code); return code; } } while (0)
+
+int main(void)
+{
+    kf_options o;
+    kf_seeding s;
+    kf_context *ctx = (kf_context *)&o;
+    float r[3] = {4.0f, 8.0f, 12.0f}, xx0[3] = {0.01f, 0.01f, 0.01f};
+    kf_geometry g;
+    float f[8];
+    kf_options_default(&o);
+    kf_seeding_default(&s);
+    EXPECT(o.max_cands == 6 && o.topk == 4 && o.precision_mode == 1, 1);
+    EXPECT(s.n_phi_bins == 256 && s.n_z_bins == 64, 2);
+    /* no sm_103a device here: a clean error, no context */
+    EXPECT(kf_context_create(&ctx, 0) == KF_ERR_UNSUPPORTED && ctx == NULL, 3);
+    EXPECT(kf_context_create(NULL, 0) == KF_ERR_ARG, 4);
+    EXPECT(kf_last_error(NULL) != NULL && kf_last_error(NULL)[0] != 0, 5);
+    kf_context_destroy(NULL);
+    EXPECT(kf_fit_tracks(NULL, NULL, 0, NULL, 0, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL,
+                         &o, NULL) == KF_ERR_ARG, 6);
+    EXPECT(kf_transport_batch(NULL, 0, NULL, NULL, NULL) == KF_ERR_ARG, 7);
+    /* the context-free fit checks its arguments on the host first */
+    g.n_layers = 3;
+    g.r = r;
+    g.x_over_x0 = xx0;
+    g.z_half = 100.0f;
+    g.bz_tesla = 3.8f;
+    EXPECT(kf_fit_tracks_noalloc(NULL, 1, f, f, NULL, f, f, NULL, f, f, f, NULL, NULL, &o, NULL) == KF_ERR_ARG, 8);
+    EXPECT(kf_fit_tracks_noalloc(&g, 0, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, &o, NULL)
+           == KF_OK, 9);
+    EXPECT(kf_fit_tracks_noalloc(&g, -1, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, &o, NULL)
+           == KF_ERR_ARG, 10);
+    EXPECT(kf_fit_tracks_noalloc(&g, KF_NOALLOC_MAX_TRACKS + 1, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL,
+                                 NULL, NULL, &o, NULL) == KF_ERR_TOO_LARGE, 11);
+    EXPECT(kf_fit_tracks_noalloc(&g, 1, NULL, f, NULL, f, f, NULL, f, f, f, NULL, NULL, &o, NULL) == KF_ERR_ARG, 12);
+    EXPECT(kf_fit_tracks_noalloc(&g, 1, (const float *)((const char *)f + 2), f, (const int8_t *)f, f, f,
+                                 (const uint32_t *)f, f, f, f, (int16_t *)f, (uint32_t *)f, &o, NULL) == KF_ERR_ARG, 13);
+    g.n_layers = 0;
+    EXPECT(kf_fit_tracks_noalloc(&g, 1, f, f, (const int8_t *)f, f, f, (const uint32_t *)f, f, f, f, (int16_t *)f,
+                                 (uint32_t *)f, &o, NULL) == KF_ERR_ARG, 14);
+    printf("ok\n");
+    return 0;
+}
+"""
+
+
+def test_c_client_without_a_gpu(tmp_path):
+    """kf.h compiles as strict C99 and a C program linked against the library
+    gets the documented error codes, without a GPU and without a crash: no
+    context on a machine without an sm_103a device, KF_ERR_ARG for null
+    arguments, and the context-free fit's host-side checks (empty batch,
+    negative or too large sizes, null and misaligned pointers, bad geometry)."""
+    torch = pytest.importorskip("torch")
+    import shutil
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    from paper_1705_02876_gb300 import build, kf
+    build.build()
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    lib = kf.library_path()
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.dirname(kf.HEADER),
+                    str(src), "-o", str(exe), lib, "-Wl,-rpath," + os.path.dirname(lib)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
