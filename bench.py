@@ -739,6 +739,8 @@ def main():
                      "algorithmic_flops_per_launch": flops,
                      "hbm_gbs": BYTES_PER_TRACK * T / (kern_ms * 1e-3) / 1e9,
                      "hbm_frac_of_measured": (BYTES_PER_TRACK * T / (kern_ms * 1e-3) / 1e9 / hbm) if hbm else None},
+        # the build's headline fields, filled in below, near the front of the line
+        "build_summary": None,
         "plain": {"value": T / (plain_ms * 1e-3), "unit": "tracks/s", "ms_per_step": plain_ms,
                   "form": "FP32 only, one plain launch per event (100 launches)"},
         "e2e": {"value": weak_value(T, world, e2e_ms), "unit": "tracks/s", "h2d_bytes_per_step": h2d,
@@ -752,7 +754,16 @@ def main():
         "wall_s_timed": t_wall,
     }
     if args.build_events > 0:
-        line["build"] = bench_build(args, kf, ctx, dev, stream, rank, world)
+        b = line["build"] = bench_build(args, kf, ctx, dev, stream, rank, world)
+        r = b["roofline"]
+        line["build_summary"] = {
+            "seeds_per_s": b["value"], "plain_seeds_per_s": b["plain"]["value"],
+            "learned_seeds_per_s": b["learned"]["value"], "efficiency": b["efficiency"],
+            "fake_rate": b["fake_rate"], "learned_efficiency": b["learned"]["efficiency"],
+            "call_ms": r["call_ms"], "fp32_frac": r["fp32_frac"], "dram_frac": r["dram_frac"],
+            "dram_bytes_per_call": r["dram_bytes_per_call"]}
+    else:
+        del line["build_summary"]
     if not args.no_ragged:
         line["ragged"] = bench_ragged(args, kf, ctx, dev, stream, rank)
     if not args.no_transport:

@@ -460,15 +460,25 @@ int kf_fit_tuned_shape(kf_context *ctx, int n_layers, int64_t n_tracks, int *tra
  *     on a device share the counter, so calls whose work overlaps on the GPU
  *     (different streams, not ordered) race and give wrong results: order
  *     them on one stream or synchronise.
- *   - n_tracks must be at most KF_NOALLOC_MAX_TRACKS (the 32-bit counter
- *     must not wrap while every resident warp makes its last claim);
- *     larger batches return KF_ERR_TOO_LARGE.
- *   - No tuning runs: the shape is opt->tracks_per_block / opt->reg_cap when
- *     set, else 64 tracks per block with no register cap.  opt->launch_mode
- *     is ignored.  There is no context, so failures are reported by the
- *     return code only (KF_ERR_ARG, KF_ERR_TOO_LARGE, KF_ERR_CUDA).
+ *   - n_tracks must be at most KF_NOALLOC_MAX_TRACKS (2^36, the limit of
+ *     kf_fit_tracks too); larger batches return KF_ERR_TOO_LARGE, and so does
+ *     a launch that would hold more than 16,384 resident warps (the 32-bit
+ *     counter must not wrap while every warp makes its last claim; a GB300
+ *     holds at most 152 x 64 = 9,728).
+ *   - No tuning runs.  The shape is opt->tracks_per_block, opt->reg_cap and
+ *     opt->hit_prefetch where set, else 64 tracks per block, no register cap
+ *     and the register prefetch (depth 1).  Only the (block, cap, depth)
+ *     combinations the autotuner of kf_fit_tracks chooses from are compiled
+ *     in: blocks 32/64/128/256 with cap none/168/128/96/80 at depth 1 (cap
+ *     168 only below 256 threads, cap 96 only below 256), and at depths 2
+ *     and 4 the caps 128 (all blocks) and 96 (below 256); another combination
+ *     returns KF_ERR_ARG.  opt->launch_mode is ignored.  There is no context,
+ *     so failures are reported by the return code only: KF_ERR_ARG (a bad
+ *     argument or an uncompiled shape), KF_ERR_TOO_LARGE, KF_ERR_CUDA (a CUDA
+ *     call failed, including the shape's shared-memory opt-in or occupancy
+ *     query).
  */
-#define KF_NOALLOC_MAX_TRACKS (32LL * (4294967296LL - 16384LL))
+#define KF_NOALLOC_MAX_TRACKS (68719476736LL)
 int kf_fit_tracks_noalloc(const kf_geometry *geom, int64_t n_tracks, const float *seed_state,
                           const float *seed_cov, const int8_t *charge, const float *hit_pos,
                           const float *hit_cov, const uint32_t *hit_mask, float *out_state,

@@ -1,6 +1,10 @@
 // Kalman-filter track fit on sm_103a: one thread per track (Section 4.2),
 // state and packed covariance in registers, structure-of-arrays inputs read
 // coalesced (Section 4.1: element (i, j) of consecutive tracks is contiguous).
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "kf.h"
 #include "kf_fit.cuh"
 
@@ -236,16 +240,23 @@ const Shape *find_shape(int block, int cap, int depth)
     return nullptr;
 }
 
-// Allow a shape's dynamic shared memory (once per process: one device each).
-bool prepare_shape(const Shape *sh)
+// Allow a shape's dynamic shared memory on the current device.  The opt-in
+// is a per-device function attribute, so it is remembered per (device,
+// shape), under a lock: several host threads may launch at once.
+cudaError_t prepare_shape(const Shape *sh)
 {
     const size_t bytes = ring_bytes(sh->block, sh->depth);
-    if (!bytes) return true;
-    static bool done[sizeof(kShapes) / sizeof(kShapes[0])] = {};
-    const size_t i = (size_t)(sh - kShapes);
-    if (!done[i])
-        done[i] = cudaFuncSetAttribute(sh->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
-    return done[i];
+    if (!bytes) return cudaSuccess;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static std::mutex mu;
+    static std::set<std::pair<int, const Shape *>> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({dev, sh})) return cudaSuccess;
+    e = cudaFuncSetAttribute(sh->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done.insert({dev, sh});
+    return e;
 }
 
 }  // namespace
@@ -263,10 +274,11 @@ cudaError_t launch_fit_plain(const FitGeom &g, const Routing &rt, const FitIO &i
 int persistent_blocks_per_sm(int block, int cap, int depth)
 {
     const Shape *sh = find_shape(block, cap, depth);
+    if (!sh) return 0;
     int n = 0;
-    if (!sh || !prepare_shape(sh) ||
+    if (prepare_shape(sh) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sh->fn, block, ring_bytes(block, depth)) != cudaSuccess)
-        return 0;
+        return -1;
     return n;
 }
 
@@ -288,7 +300,8 @@ cudaError_t launch_fit_persistent(const FitGeom &g, const Routing &rt, const Fit
 {
     const Shape *sh = find_shape(block, cap, depth);
     if (!sh) return cudaErrorInvalidValue;
-    if (!prepare_shape(sh)) return cudaErrorInvalidValue;
+    const cudaError_t e = prepare_shape(sh);
+    if (e != cudaSuccess) return e;
     sh->fn<<<grid, block, ring_bytes(block, depth), stream>>>(g, rt, io, counter);
     return cudaGetLastError();
 }

@@ -52,8 +52,9 @@ cudaError_t launch_fit_plain(const FitGeom &g, const Routing &rt, const FitIO &i
 // units from *counter, which must read 0 at launch.
 cudaError_t launch_fit_persistent(const FitGeom &g, const Routing &rt, const FitIO &io, int block, int cap,
                                   int depth, int grid, unsigned *counter, cudaStream_t stream);
-// Blocks of the persistent kernel of this shape that fit on one SM at once
-// (0 if the shape is not compiled in).
+// Blocks of the persistent kernel of this shape that fit on one SM at once on
+// the current device: 0 if the shape is not compiled in, -1 if a CUDA call
+// (the shared-memory opt-in or the occupancy query) failed.
 int persistent_blocks_per_sm(int block, int cap, int depth);
 // The (block, cap, depth) shapes compiled in; returns how many were written.
 int persistent_shapes(int *blocks, int *caps, int *depths, int max_n);

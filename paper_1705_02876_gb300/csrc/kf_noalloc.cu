@@ -27,6 +27,10 @@ static __device__ __align__(256) unsigned g_noalloc_scratch[1];
 namespace {
 
 constexpr int kMaxDevices = 64;
+// resident warps a launch may hold so that the work counter cannot wrap:
+// KF_NOALLOC_MAX_TRACKS / 32 units plus this many final claims stay below 2^32
+constexpr int64_t kNoallocMaxWarps = 16384;
+static_assert(KF_NOALLOC_MAX_TRACKS / 32 + kNoallocMaxWarps < (int64_t(1) << 32), "counter margin");
 unsigned *g_scratch_address[kMaxDevices];  // device address of g_noalloc_scratch, per device
 std::mutex g_setup_mutex;
 
@@ -79,15 +83,19 @@ extern "C" int kf_fit_tracks_noalloc(const kf_geometry *geom, int64_t n_tracks, 
     if (scratch_address(device, &counter) != cudaSuccess) return KF_ERR_CUDA;
 
     // fixed launch shape (no tuning runs here): the caller's choice, else 64
-    // tracks per block without a register cap
+    // tracks per block without a register cap, hits prefetched into registers
     const int block = o.tracks_per_block ? o.tracks_per_block : 64;
     const int cap = o.reg_cap > 0 ? o.reg_cap : 0;
     const int depth = o.hit_prefetch ? o.hit_prefetch : 1;
     const int per_sm = persistent_blocks_per_sm(block, cap, depth);
-    if (per_sm <= 0) return KF_ERR_ARG;
+    if (per_sm == 0) return KF_ERR_ARG;  // this (block, cap, depth) combination is not compiled in
+    if (per_sm < 0) return KF_ERR_CUDA;
     const int64_t units = (n_tracks + 31) / 32;
     const int64_t want = (units * 32 + block - 1) / block;
     const int grid = (int)std::min<int64_t>((int64_t)sms * per_sm, want);
+    // every resident warp makes one claim past the last unit before it stops:
+    // the counter stays below 2^32 while units + resident warps do
+    if ((int64_t)grid * (block / 32) > kNoallocMaxWarps) return KF_ERR_TOO_LARGE;
     const FitIO io{n_tracks, seed_state, seed_cov, charge, hit_pos, hit_cov, hit_mask,
                    out_state, out_cov, out_chi2, out_ndof, out_flags};
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
