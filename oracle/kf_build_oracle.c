@@ -263,6 +263,33 @@ static int cmp_scored(const void *a, const void *b)
     return (x->h > y->h) - (x->h < y->h);
 }
 
+/* The phi intervals [lo, hi] of a window of half-width dphi around phic,
+ * split at +-pi (one interval covering everything when dphi >= pi). */
+static int window_intervals(double phic, double dphi, double lo_[3], double hi_[3])
+{
+    int nint = 0;
+    const double a = phic - dphi, b = phic + dphi;
+    if (dphi >= ORC_PI) {
+        lo_[0] = -ORC_PI - 1.0;
+        hi_[0] = ORC_PI + 1.0;
+        return 1;
+    }
+    lo_[nint] = a < -ORC_PI ? -ORC_PI - 1.0 : a;
+    hi_[nint] = b > ORC_PI ? ORC_PI + 1.0 : b;
+    ++nint;
+    if (a < -ORC_PI) {
+        lo_[nint] = a + 2.0 * ORC_PI;
+        hi_[nint] = ORC_PI + 1.0;
+        ++nint;
+    }
+    if (b > ORC_PI) {
+        lo_[nint] = -ORC_PI - 1.0;
+        hi_[nint] = b - 2.0 * ORC_PI;
+        ++nint;
+    }
+    return nint;
+}
+
 /*
  * Build seeds [s_begin, s_end).  Geometry: the build layers only.  Hits: all
  * layers of all events in hit_pos [3][H], hit_cov [6][H]; hit_offsets
@@ -276,6 +303,20 @@ static int cmp_scored(const void *a, const void *b)
  * rows past log_cap are dropped; log_n NULL = no log) and the proposal (mlp
  * the 5,057 weights, NULL = exhaustive search; topk >= 1; mlp_bf16 as in
  * mlp_logit).
+ *
+ * out_margin [S][4] (NULL = none) is a diagnostic for parity tests: for each
+ * seed, over all its layers and candidates, how close each kind of decision
+ * came to going the other way, as a relative distance (0 = on the edge):
+ *   [0] a hit's window test, max(|dphi| / dphi_w, |dz| / dz_w) against 1 for
+ *       the hits of a window 1.05 times wider, and a crossing's |z| against
+ *       z_half;
+ *   [1] a tested hit's chi2 increment against the cut, |dchi2 - cut| / cut;
+ *   [2] the ranking: two children next to each other among the first N + 1,
+ *       with the same number of hits, |chi2_a - chi2_b| / max(1, chi2_a);
+ *   [3] the proposal's top-k: the logits at ranks topk and topk + 1,
+ *       (z_k - z_k+1) / (1 + |z_k|).
+ * Infinity where the seed met no such decision.  It takes no part in the
+ * build.
  */
 int orc_build_tracks_ex(int n_layers, const double *radii, const double *x_over_x0, double z_half, double bz,
                      const int64_t *hit_offsets, const float *hit_pos, const float *hit_cov, int64_t H,
@@ -285,7 +326,7 @@ int orc_build_tracks_ex(int n_layers, const double *radii, const double *x_over_
                      double sigma_rphi_hit, double sigma_z_hit, int32_t *out_hit, double *out_chi2,
                      int32_t *out_nhits, double *out_state, double *out_cov, int32_t *out_ncand, double *log_f,
                      double *log_y, int32_t *log_ref, int64_t log_cap, int64_t *log_n, const double *mlp,
-                     int topk, int mlp_bf16, double dphi_max, double dz_max)
+                     int topk, int mlp_bf16, double dphi_max, double dz_max, double *out_margin)
 {
     const int N = max_cands, L = n_layers;
     const int64_t S = n_seeds;
@@ -297,6 +338,7 @@ int orc_build_tracks_ex(int n_layers, const double *radii, const double *x_over_
     child_t hits_of[MAXN][MAXN], all[MAXN * (MAXN + 1)];
     int nh[MAXN];
     for (int64_t s = s_begin; s < s_end; ++s) {
+        double mg[4] = {HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL};
         const int q = seed_charge[s];
         const int64_t *off = hit_offsets + (int64_t)seed_event[s] * (L + 1);
         int nc = 1;
@@ -318,7 +360,9 @@ int orc_build_tracks_ex(int n_layers, const double *radii, const double *x_over_
                 k->reached = 0;
                 if (!k->stopped) {
                     double J[36], Q[36], sd;
-                    if (orc_propagate(k->x, q, bz, radii[l], k->xp, J, &sd) || fabs(k->xp[2]) > z_half) {
+                    const int unreachable = orc_propagate(k->x, q, bz, radii[l], k->xp, J, &sd);
+                    if (!unreachable) mg[0] = fmin(mg[0], fabs(fabs(k->xp[2]) - z_half) / z_half);
+                    if (unreachable || fabs(k->xp[2]) > z_half) {
                         k->stopped = 1;
                     } else {
                         memcpy(k->Cp, k->C, sizeof k->C);
@@ -338,26 +382,20 @@ int orc_build_tracks_ex(int n_layers, const double *radii, const double *x_over_
                     const double phic = atan2(yp, xp);
                     /* phi intervals of the window, split at +-pi */
                     double lo_[3], hi_[3];
-                    int nint = 0;
-                    double a = phic - dphi, b = phic + dphi;
-                    if (dphi >= ORC_PI) {
-                        lo_[0] = -ORC_PI - 1.0;
-                        hi_[0] = ORC_PI + 1.0;
-                        nint = 1;
-                    } else {
-                        lo_[nint] = a < -ORC_PI ? -ORC_PI - 1.0 : a;
-                        hi_[nint] = b > ORC_PI ? ORC_PI + 1.0 : b;
-                        ++nint;
-                        if (a < -ORC_PI) {
-                            lo_[nint] = a + 2.0 * ORC_PI;
-                            hi_[nint] = ORC_PI + 1.0;
-                            ++nint;
-                        }
-                        if (b > ORC_PI) {
-                            lo_[nint] = -ORC_PI - 1.0;
-                            hi_[nint] = b - 2.0 * ORC_PI;
-                            ++nint;
-                        }
+                    const int nint = window_intervals(phic, dphi, lo_, hi_);
+                    if (out_margin) {
+                        /* window edges: every hit of the window 1.05 times wider */
+                        double mlo[3], mhi[3];
+                        const int mint = window_intervals(phic, 1.05 * dphi, mlo, mhi);
+                        for (int iv = 0; iv < mint; ++iv)
+                            for (int64_t p = lower_phi(phi, order, seg_lo, seg_hi, mlo[iv]);
+                                 p < seg_hi && phi[order[p]] <= mhi[iv]; ++p) {
+                                const int64_t h = order[p];
+                                const double ep = fabs(wrap_phi(phi[h] - phic)) / dphi;
+                                const double ez = fabs((double)hit_pos[2 * H + h] - zp) / dz;
+                                if (ep > 1.05 || ez > 1.05) continue;
+                                mg[0] = fmin(mg[0], fabs((ep > ez ? ep : ez) - 1.0));
+                            }
                     }
                     /* the in-window hits */
                     int64_t n_in = 0;
@@ -390,6 +428,7 @@ int orc_build_tracks_ex(int n_layers, const double *radii, const double *x_over_
                         }
                         qsort(win, (size_t)n_in, sizeof(scored_t), cmp_scored);
                         n_test = topk;
+                        mg[3] = fmin(mg[3], (win[topk - 1].z - win[topk].z) / (1.0 + fabs(win[topk - 1].z)));
                     }
                     for (int64_t i = 0; i < n_test; ++i) {
                         const int64_t h = win[i].h;
@@ -410,6 +449,7 @@ int orc_build_tracks_ex(int n_layers, const double *radii, const double *x_over_
                         }
                         double dc;
                         if (!hit_chi2(k->xp, k->Cp, hit_pos, hit_cov, H, h, &dc)) continue;
+                        mg[1] = fmin(mg[1], fabs(dc - chi2_cut) / chi2_cut);
                         if (!(dc <= chi2_cut)) continue;
                         child_t ch = {c, k->nhits + 1, h - seg_lo, h, k->chi2 + dc, dc, row};
                         insert_child(hits_of[c], &nh[c], N, &ch);
@@ -421,6 +461,9 @@ int orc_build_tracks_ex(int n_layers, const double *radii, const double *x_over_
             }
             qsort(all, (size_t)n_all, sizeof(child_t), cmp_child);
             const int nn = n_all < N ? n_all : N;
+            for (int j = 0; j + 1 < n_all && j < N; ++j)
+                if (all[j].nhits == all[j + 1].nhits)
+                    mg[2] = fmin(mg[2], fabs(all[j].chi2 - all[j + 1].chi2) / fmax(1.0, all[j].chi2));
             for (int j = 0; j < nn; ++j) {
                 const child_t *ch = &all[j];
                 const cand_t *par = &cand[ch->cand];
@@ -448,6 +491,8 @@ int orc_build_tracks_ex(int n_layers, const double *radii, const double *x_over_
             nc = nn;
         }
         out_ncand[s] = nc;
+        if (out_margin)
+            for (int i = 0; i < 4; ++i) out_margin[s * 4 + i] = mg[i];
         for (int j = 0; j < N; ++j) {
             const int64_t sj = s * N + j;
             for (int l = 0; l < L; ++l) out_hit[sj * L + l] = j < nc ? cand[j].hits[l] : -1;
@@ -475,5 +520,5 @@ int orc_build_tracks(int n_layers, const double *radii, const double *x_over_x0,
                                s_begin, s_end, n_seeds, seed_event, seed_state, seed_cov, seed_charge, max_cands,
                                chi2_cut, nsigma, sigma_rphi_hit, sigma_z_hit, out_hit, out_chi2, out_nhits,
                                out_state, out_cov, out_ncand, NULL, NULL, NULL, 0, NULL, NULL, 1, 0, HUGE_VAL,
-                               HUGE_VAL);
+                               HUGE_VAL, NULL);
 }

@@ -116,7 +116,7 @@ def lib():
             _lib.orc_build_tracks_ex.restype = ctypes.c_int
             _lib.orc_build_tracks_ex.argtypes = _lib.orc_build_tracks.argtypes + \
                 [ctypes.c_void_p] * 3 + [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
-                                         ctypes.c_double, ctypes.c_double]
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_void_p]
             _lib.orc_smooth_tracks.restype = ctypes.c_int
             _lib.orc_smooth_tracks.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_int64, ctypes.c_int64, ctypes.c_int64] + \
@@ -413,7 +413,7 @@ def propagate_back(state, q, bz, r):
 def build_arrays(radii, x_over_x0, z_half, bz, hit_offsets, hit_pos, hit_cov, seed_event, seed_state,
                  seed_cov, seed_charge, max_cands=6, chi2_cut=30.0, nsigma=3.0, sigma_rphi=0.01,
                  sigma_z=0.1, threads: int | None = None, seed_range=None, log=False, mlp=None, topk=4,
-                 mlp_bf16=False, dphi_max=0.05, dz_max=5.0):
+                 mlp_bf16=False, dphi_max=0.05, dz_max=5.0, margins=False):
     """Clone-engine build with the FP64 oracle over the given layers.  Arrays
     in the library's layout (float32 hits [3][H] / [6][H], offsets
     [E][L+1], seeds [6][S] / [21][S]).  Returns a dict of results.
@@ -423,7 +423,10 @@ def build_arrays(radii, x_over_x0, z_half, bz, hit_offsets, hit_pos, hit_cov, se
     rows in seed order.  mlp (5,057 float64 weights) turns on the learned
     proposal with the given topk; mlp_bf16 ranks with BF16 inputs, W1, W2 and
     first hidden layer (the tensor-core scoring's precision).  dphi_max (rad)
-    and dz_max (cm) cap the window's half-widths (None: no cap)."""
+    and dz_max (cm) cap the window's half-widths (None: no cap).  margins=True
+    adds out["margin"] [S][4]: per seed, how close its window tests, chi2 cuts,
+    rankings and top-k choices came to going the other way (the C oracle's
+    out_margin), for tracing a parity mismatch to a near-tie."""
     if log and mlp is not None:
         raise ValueError("the training log records the plain build")
     L = int(len(radii))
@@ -445,6 +448,8 @@ def build_arrays(radii, x_over_x0, z_half, bz, hit_offsets, hit_pos, hit_cov, se
     out = dict(hit=np.zeros((S, N, L), dtype=np.int32), chi2=np.zeros((S, N)),
                nhits=np.zeros((S, N), dtype=np.int32), state=np.zeros((6, S * N)),
                cov=np.zeros((21, S * N)), ncand=np.zeros(S, dtype=np.int32))
+    if margins:
+        out["margin"] = np.full((S, 4), np.inf)
     rad, xx0 = _f64(radii), _f64(x_over_x0)
     s0, s1 = seed_range if seed_range is not None else (0, S)
     threads = threads or os.cpu_count() or 1
@@ -467,7 +472,8 @@ def build_arrays(radii, x_over_x0, z_half, bz, hit_offsets, hit_pos, hit_cov, se
             None if lg is None else lg["features"].ctypes.data, None if lg is None else lg["labels"].ctypes.data,
             None if lg is None else lg["ref"].ctypes.data, cap, n.ctypes.data if log else None,
             None if w is None else w.ctypes.data, int(topk), int(bool(mlp_bf16)),
-            math.inf if dphi_max is None else float(dphi_max), math.inf if dz_max is None else float(dz_max))
+            math.inf if dphi_max is None else float(dphi_max), math.inf if dz_max is None else float(dz_max),
+            out["margin"].ctypes.data if margins else None)
         assert rc == 0, rc
         return int(n[0])
 

@@ -3,15 +3,14 @@
 //                       phi x z bins (Section 3: hits partitioned spatially
 //                       for a fast look-up of the compatible ones), three
 //                       kernels over all segments (kf_bins.cuh);
-//   build_kernel      - the clone engine, all layers in one launch: each
-//                       seed's candidates occupy a group of G >= N lanes of
-//                       a warp (G in 1, 2, 4, 6, 8); every lane propagates
-//                       its candidate, scans the bins its window overlaps
-//                       and keeps its N best compatible hits; the group
-//                       merges its lanes' lists into the N best children by
-//                       warp shuffles (in place of the paper's shared-memory
-//                       heaps, Section 4.3) and each lane takes over one
-//                       child and updates it.
+//   clone_kernel      - the clone engine, all layers in one launch: a block
+//                       holds 32 seeds, warp w candidate slot w of each; per
+//                       layer every candidate is propagated and its window's
+//                       hits are tested, one lane per seed merges the
+//                       candidates' children into the seed's N best (in place
+//                       of the paper's per-seed heaps, Section 4.3), and every
+//                       slot takes over its new child from shared memory and
+//                       updates it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,6 +48,33 @@ void destroy_build_state(BuildState *s)
 
 namespace {
 
+constexpr int kModePlain = 0, kModeLog = 1, kModeProposal = 2;
+constexpr int kKeyBatch = 4;  // window keys loaded together in the collecting scan (8 was slower)
+
+// Shared memory of the clone-engine kernel: for N candidate slots (one warp
+// each) of 32 seeds (one lane each) and L layers.  Every array is [..][32],
+// the seed's lane fastest, so a warp's accesses fall in distinct banks.
+// Offsets in bytes from the start of the dynamic shared memory.
+struct CloneLayout {
+    int st;        // float [N][kSlotSize][32]: slot w's predicted state (x: 0..5, c: 6..26) for the
+                   // merge and the hand-over, then the update's slot of the extended-precision paths
+    int flags;     // uint32 [N][32]: the candidate's flags, kStoppedBit = stopped
+    int nh;        // int [N][32]: its hits
+    int chi2;      // float [N][32]: its chi2
+    int ncand;     // int [32]: candidates of each seed
+    int bp;        // int32 [L][N][32]: back-pointers, parent slot << 27 | (hit index + 1)
+    // union: the merge's inputs and outputs, or the proposal's staged input rows
+    int lcnt;      // int [N][32]: hit children listed by slot w (at most N)
+    int lc;        // float [N][N][32]: their summed chi2, ascending (then hit index)
+    int lh;        // uint32 [N][N][32]: their hit indices within the (event, layer)
+    int lr;        // uint32 [N][N][32]: their rows of the training log (logging only)
+    int sel;       // uint32 [N][32]: child of new slot j, parent << 27 | (hit index + 1)
+    int sel_chi2;  // float [N][32]
+    int sel_nh;    // int [N][32]
+    int stage;     // float [N][32][kStageLd]: input rows of the proposal (proposal only)
+    int total;
+};
+
 struct BuildParams {
     FitGeom g;
     Routing rt;
@@ -78,6 +104,7 @@ struct BuildParams {
     int topk;
     const __nv_bfloat16 *mlp_W1, *mlp_W2;
     const float *mlp_w32;
+    CloneLayout lay;
 };
 
 constexpr int kMaxN = 8;
@@ -153,60 +180,100 @@ struct WindowCursor {
     }
 };
 
-// Order of children: (hits desc, chi2 asc, candidate asc, hit index asc) as
-// a two-word key compared lexicographically: k64 = (63 - hits) << 32 | the
-// bits of chi2 (non-negative floats order as their bit patterns), k32 =
-// candidate slot << 27 | (hit index within the layer + 1), 0 for the hole.
-__device__ __forceinline__ bool key_less(unsigned long long a64, uint32_t a32, unsigned long long b64, uint32_t b32)
+constexpr int kStageLd = 12;
+constexpr uint32_t kStoppedBit = 0x80000000u;
+
+CloneLayout clone_layout(int N, int L, int mode)
 {
-    return a64 < b64 || (a64 == b64 && a32 < b32);
+    CloneLayout o{};
+    int off = 0;
+    auto take = [&](int bytes) {
+        const int at = off;
+        off += (bytes + 15) / 16 * 16;
+        return at;
+    };
+    const int col = 32 * 4;  // one [32] array of 4-byte words
+    o.st = take(N * kSlotSize * col);
+    o.flags = take(N * col);
+    o.nh = take(N * col);
+    o.chi2 = take(N * col);
+    o.ncand = take(col);
+    o.bp = take(L * N * col);
+    const int base = off;
+    o.lcnt = take(N * col);
+    o.lc = take(N * N * col);
+    o.lh = take(N * N * col);
+    o.lr = mode == kModeLog ? take(N * N * col) : 0;
+    o.sel = take(N * col);
+    o.sel_chi2 = take(N * col);
+    o.sel_nh = take(N * col);
+    const int lists_end = off;
+    o.stage = base;
+    const int stage_end = mode == kModeProposal ? base + N * 32 * kStageLd * 4 : base;
+    o.total = std::max(lists_end, stage_end);
+    return o;
 }
 
-// Shared memory: back-pointers [L][128], update slots [kSlotSize][128], then
-// (proposal only) the network's weights and one staging area per warp.
-__host__ __device__ constexpr size_t build_smem_base(int L) { return ((size_t)(L + kSlotSize) * 128 * 4 + 127) / 128 * 128; }
-constexpr size_t kBuildSmemMlp = sizeof(MlpSmemWeights) + 4 * sizeof(MlpWarpStage);
-
-constexpr int kModePlain = 0, kModeLog = 1, kModeProposal = 2;
-constexpr int kKeyBatch = 4;  // window keys loaded together in the collecting scan (8 was slower)
-
-template <int G, int MODE>
-__global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
+template <class T>
+__device__ __forceinline__ T *sm_at(unsigned char *sm, int off)
 {
-    constexpr int SEEDS_PER_WARP = 32 / G;
-    extern __shared__ __align__(128) int32_t smem[];
-    const int L = p.g.L;
-    int32_t *bp = smem;                                   // [L][128] back-pointers
-    float *slots = reinterpret_cast<float *>(smem + L * 128);  // [kSlotSize][128]
-    MlpSmemWeights *mw = nullptr;
-    MlpWarpStage *mst = nullptr;
-    if (MODE == kModeProposal) {
-        unsigned char *base = reinterpret_cast<unsigned char *>(smem) + build_smem_base(L);
-        mw = reinterpret_cast<MlpSmemWeights *>(base);
-        mst = reinterpret_cast<MlpWarpStage *>(base + sizeof(MlpSmemWeights)) + (threadIdx.x >> 5);
-        mlp_load_weights(mw, p.mlp_W1, p.mlp_W2, p.mlp_w32);
-        __syncthreads();
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int slot = lane % G, gbase = lane - slot;
-    // G = 6: five groups per warp; lanes 30 and 31 form an idle group of two
-    const bool lane_ok = lane < SEEDS_PER_WARP * G;
-    const int64_t s = ((int64_t)blockIdx.x * 4 + warp) * SEEDS_PER_WARP + lane / G;
-    const bool seed_ok = lane_ok && s < p.S;
-    const int N = p.N;
-    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << gbase);
+    return reinterpret_cast<T *>(sm + off);
+}
+
+// The clone engine, all build layers in one launch.  Block = 32 seeds x N
+// candidate slots: warp w holds slot w of the 32 seeds, lane i seed i, so every
+// lane of every warp owns one candidate.  Per layer:
+//   P  every live candidate is propagated, transported and scattered (fit
+//      code); its predicted state goes to shared memory; its window is
+//      scanned and the chi2 of its in-window hits taken; its N best hit
+//      children (by chi2, then hit index) are listed in shared memory;
+//      [proposal: windows holding more than topk hits are ranked first, the
+//      warps scoring their rows on the tensor cores, and only the topk best
+//      by logit get a chi2]
+//   S  one lane per seed (warp 0) merges its candidates' lists and holes into
+//      the seed's N best children (hits desc, chi2 asc, parent slot asc, hit
+//      index asc, the hole first): N rounds of a minimum over at most N list
+//      heads held in registers;
+//   U  the thread of new slot j reads its child's parent state from shared
+//      memory and applies the update with the child's hit; a back-pointer
+//      (parent slot, hit) per (layer, slot) goes to shared memory.
+// After the last layer each slot walks its back-pointers to write its hits.
+template <int MODE>
+__global__ void __launch_bounds__(256) clone_kernel(const BuildParams p)
+{
+    extern __shared__ __align__(128) unsigned char sm[];
+    const CloneLayout &ly = p.lay;
+    const int N = p.N, L = p.g.L;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float *st = sm_at<float>(sm, ly.st);
+    uint32_t *s_flags = sm_at<uint32_t>(sm, ly.flags);
+    int *s_nh = sm_at<int>(sm, ly.nh);
+    float *s_chi2 = sm_at<float>(sm, ly.chi2);
+    int *s_ncand = sm_at<int>(sm, ly.ncand);
+    int32_t *s_bp = sm_at<int32_t>(sm, ly.bp);
+    int *s_lcnt = sm_at<int>(sm, ly.lcnt);
+    float *s_lc = sm_at<float>(sm, ly.lc);
+    uint32_t *s_lh = sm_at<uint32_t>(sm, ly.lh);
+    uint32_t *s_lr = sm_at<uint32_t>(sm, ly.lr);
+    uint32_t *s_sel = sm_at<uint32_t>(sm, ly.sel);
+    float *s_sel_chi2 = sm_at<float>(sm, ly.sel_chi2);
+    int *s_sel_nh = sm_at<int>(sm, ly.sel_nh);
+    const int me = w * 32 + lane;  // [w][lane] in the [N][32] arrays
+    float *col = st + w * kSlotSize * 32 + lane;  // this slot's column: [k][32]
+
+    const int64_t s = (int64_t)blockIdx.x * 32 + lane;
+    const bool seed_ok = s < p.S;
+    const int ev_in = seed_ok ? p.seed_event[s] : -1;
+    const bool ev_ok = seed_ok && ev_in >= 0 && ev_in < p.n_events;  // a seed of an unknown event builds nothing
+    const int ev = ev_ok ? ev_in : 0;
+    const float qkb = ev_ok ? (float)p.seed_charge[s] * p.g.qk : 0.0f;
 
     float x[6], c[21];
     float chi2 = 0.0f;
     int nhits = 0;
-    bool stopped = false;
     uint32_t flags = 0;
-    int nc = 1;
-    const int ev_in = seed_ok ? p.seed_event[s] : 0;
-    const bool ev_ok = ev_in >= 0 && ev_in < p.n_events;  // a seed of an unknown event builds nothing
-    const int ev = ev_ok ? ev_in : 0;
-    const float qkb = seed_ok ? (float)p.seed_charge[s] * p.g.qk : 0.0f;
-    if (seed_ok && ev_ok) {
+    int nc = ev_ok ? 1 : 0;
+    if (ev_ok && w == 0) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) x[i] = p.seed_state[i * p.S + s];
 #pragma unroll
@@ -216,21 +283,19 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
         for (int i = 0; i < 6; ++i) x[i] = 0.0f;
 #pragma unroll
         for (int i = 0; i < 21; ++i) c[i] = 0.0f;
-        nc = 0;
     }
     const int nbins = p.bg.n_phi * p.bg.n_z;
     for (int l = 0; l < L; ++l) {
-        const bool valid = slot < nc;
+        // ---------------------------------------------------------------- P
+        const bool valid = w < nc;
         bool reached = false;
-        if (valid && !stopped) {
+        if (valid && !(flags & kStoppedBit)) {
             float xn[6], sd;
             Jac J;
             if (!propagate(x, qkb, p.g.r[l], xn, sd, &J)) {
-                stopped = true;
-                flags |= KF_FLAG_UNREACHABLE;
+                flags |= kStoppedBit | KF_FLAG_UNREACHABLE;
             } else if (fabsf(xn[2]) > p.g.z_half) {
-                stopped = true;
-                flags |= KF_FLAG_LEFT_BARREL;
+                flags |= kStoppedBit | KF_FLAG_LEFT_BARREL;
             } else {
                 transport(J, c);
                 add_scattering(xn, p.g.inv_r[l], p.g.xx0[l], c);
@@ -239,37 +304,19 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
                 reached = true;
             }
         }
-        // this candidate's best compatible hits, sorted by (chi2, hit index);
-        // lr = each entry's row in the training log (logging only)
-        float lc[kMaxN];
-        uint32_t lh[kMaxN], lr[kMaxN];
+        if (valid) {  // the candidate (its predicted state) for the merge and the hand-over
 #pragma unroll
-        for (int k = 0; k < kMaxN; ++k) {
-            lc[k] = INFINITY;
-            lh[k] = kNoKey;
-            lr[k] = kNoKey;
+            for (int i = 0; i < 6; ++i) col[(kSlotX + i) * 32] = x[i];
+#pragma unroll
+            for (int i = 0; i < 21; ++i) col[(kSlotC + i) * 32] = c[i];
+            s_flags[me] = flags;
+            s_nh[me] = nhits;
+            s_chi2[me] = chi2;
         }
-        auto insert = [&](float dc, uint32_t hl, uint32_t row) {
-            if (!(dc < lc[kMaxN - 1] || (dc == lc[kMaxN - 1] && hl < lh[kMaxN - 1]))) return;
-            float cv = dc;
-            uint32_t hv = hl, rv = row;
-#pragma unroll
-            for (int k2 = 0; k2 < kMaxN; ++k2) {
-                const bool before = cv < lc[k2] || (cv == lc[k2] && hv < lh[k2]);
-                const float tc = lc[k2];
-                const uint32_t th = lh[k2], tr = lr[k2];
-                lc[k2] = before ? cv : tc;
-                lh[k2] = before ? hv : th;
-                lr[k2] = before ? rv : tr;
-                cv = before ? tc : cv;
-                hv = before ? th : hv;
-                rv = before ? tr : rv;
-            }
-        };
-        const int64_t seg = (int64_t)ev * (L + 1) + l;
-        const int64_t seg_lo = seed_ok ? p.ev_off[seg] : 0;
+        const int64_t seg_lo = ev_ok ? p.ev_off[(int64_t)ev * (L + 1) + l] : 0;
         Window win{};
         float nx = 0.0f, ny = 0.0f, ctt = 0.0f, ctz = 0.0f, czz = 0.0f;
+        float cf[kMlpIn];  // the proposal's inputs shared by every hit of this candidate (3..11)
         if (reached) {
             const float ir = rsqrtf(x[0] * x[0] + x[1] * x[1]);
             nx = x[0] * ir;
@@ -298,7 +345,15 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
             }
             win.ip0 = ip0;
             win.nphi = min(ip1 - ip0 + 1, p.bg.n_phi);
+            if (MODE != kModePlain) {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) cf[3 + i] = log10f(fmaxf(c[pk(i, i)], 1e-30f));
+                cf[9] = copysignf(rsqrtf(x[3] * x[3] + x[4] * x[4]), qkb);
+                cf[10] = __fdiv_rn((float)l, (float)L);  // correctly rounded, whatever the division flags
+                cf[11] = (float)(l - nhits);
+            }
         }
+        const float xp0 = x[0], xp1 = x[1], xp2 = x[2];  // the prediction the hits are tested against
         auto load_hit = [&](uint32_t hl, float m[3], float v[6]) {
             const int64_t hg = seg_lo + hl;
 #pragma unroll
@@ -306,13 +361,41 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
 #pragma unroll
             for (int i = 0; i < 6; ++i) v[i] = p.hit_cov[i * p.H + hg];
         };
-        // inputs of the proposal shared by every hit of this candidate
-        auto cand_features = [&](float f[kMlpIn]) {
+        auto eval = [&](uint32_t hl, float *dc, float f3[3]) {
+            float m[3], v[6];
+            load_hit(hl, m, v);
+            const float xp[3] = {xp0, xp1, xp2};
+            return hit_eval(xp, nx, ny, ctt, ctz, czz, m, v, dc, f3);
+        };
+        // this candidate's best hit children, sorted by (summed chi2, hit
+        // index); lr = each entry's row in the training log (logging only)
+        float lc[kMaxN];
+        uint32_t lh[kMaxN], lr[kMaxN];
 #pragma unroll
-            for (int i = 0; i < 6; ++i) f[3 + i] = log10f(fmaxf(c[pk(i, i)], 1e-30f));
-            f[9] = copysignf(rsqrtf(x[3] * x[3] + x[4] * x[4]), qkb);
-            f[10] = __fdiv_rn((float)l, (float)L);  // correctly rounded, whatever the division flags
-            f[11] = (float)(l - nhits);
+        for (int k = 0; k < kMaxN; ++k) {
+            lc[k] = INFINITY;
+            lh[k] = kNoKey;
+            lr[k] = kNoKey;
+        }
+        int n_list = 0;
+        auto insert = [&](float dc, uint32_t hl, uint32_t row) {
+            const float cv0 = chi2 + dc;
+            if (!(cv0 < lc[kMaxN - 1] || (cv0 == lc[kMaxN - 1] && hl < lh[kMaxN - 1]))) return;
+            float cv = cv0;
+            uint32_t hv = hl, rv = row;
+#pragma unroll
+            for (int k2 = 0; k2 < kMaxN; ++k2) {
+                const bool before = cv < lc[k2] || (cv == lc[k2] && hv < lh[k2]);
+                const float tc = lc[k2];
+                const uint32_t th = lh[k2], tr = lr[k2];
+                lc[k2] = before ? cv : tc;
+                lh[k2] = before ? hv : th;
+                lr[k2] = before ? rv : tr;
+                cv = before ? tc : cv;
+                hv = before ? th : hv;
+                rv = before ? tr : rv;
+            }
+            n_list = min(n_list + 1, kMaxN);
         };
         if (MODE != kModeLog) {
             // first pass: the window's hits are collected (cheap bin reads
@@ -323,7 +406,6 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
 #pragma unroll
             for (int k = 0; k < kMaxN; ++k) hb[k] = kNoKey;
             int n_in = 0;
-            WindowCursor cur;
             if (reached) {
                 // each z row's bins are one contiguous key run (two past the
                 // wrap at +-pi): one pair of bin-offset loads per run, then
@@ -360,47 +442,57 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
                 }
             }
             const bool wide = n_in > cap;
-            if (MODE == kModeProposal && __any_sync(0xffffffffu, wide)) {
-                // a wide window keeps its topk best hits by logit (logit desc,
-                // hit index asc); one hit per ranking lane per round, scored
-                // by the warp
-                float tz[kMaxN];
+            if (MODE == kModeProposal) {
+                // windows holding more than topk hits keep their topk best by
+                // logit (logit desc, hit index asc): the warps score one hit
+                // per ranking lane per round.  Their input rows are staged over
+                // the merge's lists, which are free until the lists are written
+                if (__syncthreads_or(wide)) {
+                    float *xs = sm_at<float>(sm, ly.stage) + w * 32 * kStageLd;
+                    const MlpWeightsRef mw{reinterpret_cast<const uint32_t *>(p.mlp_W1),
+                                           reinterpret_cast<const uint32_t *>(p.mlp_W2), p.mlp_w32 + kOffB1,
+                                           p.mlp_w32 + kOffB2, p.mlp_w32 + kOffW3, p.mlp_w32[kOffB3]};
+                    float tz[kMaxN];
 #pragma unroll
-                for (int k = 0; k < kMaxN; ++k) tz[k] = -INFINITY;
-                if (wide) {
+                    for (int k = 0; k < kMaxN; ++k) tz[k] = -INFINITY;
+                    WindowCursor cur;
+                    if (wide) {
 #pragma unroll
-                    for (int k = 0; k < kMaxN; ++k) hb[k] = kNoKey;
-                    cur.start(win);
-                }
-                bool more = wide;
-                while (__any_sync(0xffffffffu, more)) {
-                    const uint32_t hr = more ? cur.next(p, win) : kNoKey;
-                    more = hr != kNoKey;
-                    float feat[kMlpIn];
-#pragma unroll
-                    for (int i = 0; i < kMlpIn; ++i) feat[i] = 0.0f;
-                    if (more) {
-                        float m[3], v[6], dc;
-                        load_hit(hr, m, v);
-                        hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, feat);
-                        cand_features(feat);
+                        for (int k = 0; k < kMaxN; ++k) hb[k] = kNoKey;
+                        cur.start(win);
                     }
-                    mlp_stage_row(mst, feat);
-                    const float z = mlp_score_warp(mw, mst);
-                    if (more) {
-                        float cv = z;
-                        uint32_t hv = hr;
+                    bool more = wide;
+                    while (__any_sync(0xffffffffu, more)) {
+                        const uint32_t hr = more ? cur.next(p, win) : kNoKey;
+                        more = hr != kNoKey;
+                        float feat[kMlpIn];
 #pragma unroll
-                        for (int k2 = 0; k2 < kMaxN; ++k2) {
-                            const bool before = k2 < p.topk && (cv > tz[k2] || (cv == tz[k2] && hv < hb[k2]));
-                            const float t1 = tz[k2];
-                            const uint32_t t2 = hb[k2];
-                            tz[k2] = before ? cv : t1;
-                            hb[k2] = before ? hv : t2;
-                            cv = before ? t1 : cv;
-                            hv = before ? t2 : hv;
+                        for (int i = 0; i < kMlpIn; ++i) feat[i] = 0.0f;
+                        if (more) {
+                            float dc;
+                            eval(hr, &dc, feat);
+#pragma unroll
+                            for (int i = 3; i < kMlpIn; ++i) feat[i] = cf[i];
+                        }
+#pragma unroll
+                        for (int i = 0; i < kMlpIn; ++i) xs[lane * kStageLd + i] = feat[i];
+                        const float z = mlp_score_warp_split(mw, xs, kStageLd);
+                        if (more) {
+                            float cv = z;
+                            uint32_t hv = hr;
+#pragma unroll
+                            for (int k2 = 0; k2 < kMaxN; ++k2) {
+                                const bool before = k2 < p.topk && (cv > tz[k2] || (cv == tz[k2] && hv < hb[k2]));
+                                const float t1 = tz[k2];
+                                const uint32_t t2 = hb[k2];
+                                tz[k2] = before ? cv : t1;
+                                hb[k2] = before ? hv : t2;
+                                cv = before ? t1 : cv;
+                                hv = before ? t2 : hv;
+                            }
                         }
                     }
+                    __syncthreads();  // every row is scored before the lists overwrite the staging
                 }
             }
             if (MODE == kModeProposal || !wide) {
@@ -409,18 +501,16 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
 #pragma unroll
                 for (int k2 = 0; k2 < kMaxN; ++k2) {
                     if (hb[k2] == kNoKey) continue;
-                    float m[3], v[6], dc, f3[3];
-                    load_hit(hb[k2], m, v);
-                    if (hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, f3) && dc <= p.chi2_cut)
-                        insert(dc, hb[k2], kNoKey);
+                    float dc, f3[3];
+                    if (eval(hb[k2], &dc, f3) && dc <= p.chi2_cut) insert(dc, hb[k2], kNoKey);
                 }
             } else {
                 // exhaustive search of a window wider than the buffer
+                WindowCursor cur;
                 cur.start(win);
                 for (uint32_t hl = cur.next(p, win); hl != kNoKey; hl = cur.next(p, win)) {
-                    float m[3], v[6], dc, f3[3];
-                    load_hit(hl, m, v);
-                    if (hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, f3) && dc <= p.chi2_cut) insert(dc, hl, kNoKey);
+                    float dc, f3[3];
+                    if (eval(hl, &dc, f3) && dc <= p.chi2_cut) insert(dc, hl, kNoKey);
                 }
             }
         } else if (reached) {
@@ -429,155 +519,153 @@ __global__ void __launch_bounds__(128) build_kernel(const BuildParams p)
             WindowCursor cur;
             cur.start(win);
             for (uint32_t hl = cur.next(p, win); hl != kNoKey; hl = cur.next(p, win)) {
-                float m[3], v[6], dc, feat[kMlpIn];
-                load_hit(hl, m, v);
-                const bool ok = hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, feat);
+                float dc, feat[kMlpIn];
+                const bool ok = eval(hl, &dc, feat);
                 uint32_t row = kNoKey;
                 const unsigned long long r = atomicAdd(p.log_n, 1ull);
                 if (r < p.log_cap) {
-                    cand_features(feat);
+#pragma unroll
+                    for (int i = 3; i < kMlpIn; ++i) feat[i] = cf[i];
                     row = (uint32_t)r;
 #pragma unroll
                     for (int i = 0; i < kMlpIn; ++i) p.log_f[(int64_t)r * kMlpIn + i] = feat[i];
                     p.log_y[r] = 0.0f;
                     int32_t *ref = p.log_ref + (int64_t)r * 4;
                     ref[0] = (int32_t)s;
-                    ref[1] = slot;
+                    ref[1] = w;
                     ref[2] = l;
                     ref[3] = (int32_t)(seg_lo + hl);
                 }
                 if (ok && dc <= p.chi2_cut) insert(dc, hl, row);
             }
         }
-        // merge the group's lists: N rounds of a group arg-min; the head of a
-        // lane is its best hit child, then its hole child
-        int taken = 0;  // hit children of this lane already selected
-        bool hole_taken = false;
-        unsigned long long my64 = 0;
-        uint32_t my32 = kNoKey;
-        int new_parent = -1;
-        uint32_t new_hit = 0;  // hit index + 1, 0 = hole
-        float new_chi2 = 0.0f;
-        int new_nhits = 0;
-        int n_new = 0;
-        for (int r = 0; r < N; ++r) {
-            // head of this lane
-            if (valid && taken < N && lh[0] != kNoKey) {
-                my64 = ((unsigned long long)(63 - (nhits + 1)) << 32) | __float_as_uint(chi2 + lc[0]);
-                my32 = ((uint32_t)slot << 27) | (lh[0] + 1u);
-            } else if (valid && !hole_taken) {
-                my64 = ((unsigned long long)(63 - nhits) << 32) | __float_as_uint(chi2);
-                my32 = (uint32_t)slot << 27;
-            } else {
-                my64 = ~0ull;
-                my32 = kNoKey;
-            }
-            unsigned long long b64 = my64;
-            uint32_t b32 = my32;
+        if (valid) {  // the N best hit children for the merge
+            const int cnt = min(n_list, N);
+            s_lcnt[me] = cnt;
 #pragma unroll
-            for (int d = 1; d < G; d <<= 1) {
-                unsigned long long o64;
-                uint32_t o32;
-                if constexpr ((G & (G - 1)) == 0) {  // butterfly within a power-of-two group
-                    o64 = __shfl_xor_sync(gmask, b64, d, G);
-                    o32 = __shfl_xor_sync(gmask, b32, d, G);
-                } else {  // G = 6: pairs, then slots 0-3, then the two halves crossed
-                    const int ps = d == 1 ? (slot ^ 1) : d == 2 ? (slot < 4 ? slot ^ 2 : slot)
-                                                                : (slot < 4 ? 4 + (slot & 1) : slot - 4);
-                    const int src_lane = lane_ok ? gbase + ps : lane;
-                    o64 = __shfl_sync(gmask, b64, src_lane, 32);
-                    o32 = __shfl_sync(gmask, b32, src_lane, 32);
+            for (int k = 0; k < kMaxN; ++k)
+                if (k < cnt) {
+                    s_lc[(w * N + k) * 32 + lane] = lc[k];
+                    s_lh[(w * N + k) * 32 + lane] = lh[k];
+                    if (MODE == kModeLog) s_lr[(w * N + k) * 32 + lane] = lr[k];
                 }
-                if (key_less(o64, o32, b64, b32)) {
-                    b64 = o64;
-                    b32 = o32;
-                }
-            }
-            if (b32 == kNoKey) break;
-            const int win_slot = (int)(b32 >> 27);
-            if (slot == r) {
-                new_parent = win_slot;
-                new_hit = b32 & 0x7ffffffu;
-                new_nhits = 63 - (int)(b64 >> 32);
-                new_chi2 = __uint_as_float((uint32_t)(b64 & 0xffffffffu));
-            }
-            if (slot == win_slot) {
-                if ((b32 & 0x7ffffffu) != 0u) {  // pop the head of the list
-                    if (MODE == kModeLog && lr[0] != kNoKey) p.log_y[lr[0]] = 1.0f;  // the pair survives
-#pragma unroll
-                    for (int k = 0; k < kMaxN - 1; ++k) {
-                        lc[k] = lc[k + 1];
-                        lh[k] = lh[k + 1];
-                        lr[k] = lr[k + 1];
-                    }
-                    lc[kMaxN - 1] = INFINITY;
-                    lh[kMaxN - 1] = kNoKey;
-                    lr[kMaxN - 1] = kNoKey;
-                    ++taken;
+        }
+        __syncthreads();
+        // ---------------------------------------------------------------- S
+        if (w == 0) {
+            // children keys: k64 = (63 - hits) << 32 | chi2 bits (non-negative
+            // floats order as their bit patterns), k32 = parent slot << 27 |
+            // (hit index + 1), 0 for the hole; the head of slot q is its best
+            // listed hit child, then its hole child
+            uint32_t khi[kMaxN], klo[kMaxN], k32[kMaxN];
+            int head[kMaxN];
+            auto head_key = [&](int q, int h, uint32_t &hi, uint32_t &lo, uint32_t &kk) {
+                const int cnt = s_lcnt[q * 32 + lane];
+                const int nh = s_nh[q * 32 + lane];
+                if (h < cnt) {
+                    hi = (uint32_t)(63 - (nh + 1));
+                    lo = __float_as_uint(s_lc[(q * N + h) * 32 + lane]);
+                    kk = ((uint32_t)q << 27) | (s_lh[(q * N + h) * 32 + lane] + 1u);
+                } else if (h == cnt) {
+                    hi = (uint32_t)(63 - nh);
+                    lo = __float_as_uint(s_chi2[q * 32 + lane]);
+                    kk = (uint32_t)q << 27;
                 } else {
-                    hole_taken = true;
+                    hi = lo = kk = kNoKey;
                 }
+            };
+#pragma unroll
+            for (int q = 0; q < kMaxN; ++q) {
+                head[q] = 0;
+                khi[q] = klo[q] = k32[q] = kNoKey;
+                if (q < nc) head_key(q, 0, khi[q], klo[q], k32[q]);
             }
-            ++n_new;
+            int r = 0;
+            for (; r < N; ++r) {
+                uint32_t bhi = khi[0], blo = klo[0], b32 = k32[0];
+#pragma unroll
+                for (int q = 1; q < kMaxN; ++q) {
+                    const bool less = khi[q] < bhi || (khi[q] == bhi && (klo[q] < blo || (klo[q] == blo && k32[q] < b32)));
+                    bhi = less ? khi[q] : bhi;
+                    blo = less ? klo[q] : blo;
+                    b32 = less ? k32[q] : b32;
+                }
+                if (b32 == kNoKey) break;
+                s_sel[r * 32 + lane] = b32;
+                s_sel_chi2[r * 32 + lane] = __uint_as_float(blo);
+                s_sel_nh[r * 32 + lane] = 63 - (int)bhi;
+                const int q = (int)(b32 >> 27);
+                int hq = 0;
+#pragma unroll
+                for (int k = 0; k < kMaxN; ++k) hq = k == q ? head[k] : hq;
+                if (MODE == kModeLog && (b32 & 0x7ffffffu)) {
+                    const uint32_t row = s_lr[(q * N + hq) * 32 + lane];
+                    if (row != kNoKey) p.log_y[row] = 1.0f;  // the pair survives
+                }
+                uint32_t nhi, nlo, n32;
+                head_key(q, hq + 1, nhi, nlo, n32);
+#pragma unroll
+                for (int k = 0; k < kMaxN; ++k)
+                    if (k == q) {
+                        head[k] = hq + 1;
+                        khi[k] = nhi;
+                        klo[k] = nlo;
+                        k32[k] = n32;
+                    }
+            }
+            s_ncand[lane] = r;
         }
-        // each lane takes over child `slot` from its parent lane
-        const int src = gbase + (new_parent >= 0 ? new_parent : slot);
-        float px[6], pc[21];
+        __syncthreads();
+        // ---------------------------------------------------------------- U
+        const int nn = s_ncand[lane];
+        const uint32_t e = w < nn ? s_sel[me] : 0u;
+        const int par = w < nn ? (int)(e >> 27) : w;
+        {
+            const float *pcol = st + par * kSlotSize * 32 + lane;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) px[i] = __shfl_sync(gmask, x[i], src, 32);
+            for (int i = 0; i < 6; ++i) x[i] = pcol[(kSlotX + i) * 32];
 #pragma unroll
-        for (int i = 0; i < 21; ++i) pc[i] = __shfl_sync(gmask, c[i], src, 32);
-        const int pstop = __shfl_sync(gmask, (int)stopped, src, 32);
-        const uint32_t pflags = __shfl_sync(gmask, flags, src, 32);
-        nc = n_new;
-        if (slot < nc) {
-#pragma unroll
-            for (int i = 0; i < 6; ++i) x[i] = px[i];
-#pragma unroll
-            for (int i = 0; i < 21; ++i) c[i] = pc[i];
-            stopped = pstop != 0;
-            flags = pflags;
-            chi2 = new_chi2;
-            nhits = new_nhits;
-            if (new_hit) {
-                const int64_t hg = seg_lo + (new_hit - 1u);
+            for (int i = 0; i < 21; ++i) c[i] = pcol[(kSlotC + i) * 32];
+            flags = s_flags[par * 32 + lane];
+            chi2 = s_sel_chi2[me];
+            nhits = s_sel_nh[me];
+        }
+        __syncthreads();  // every parent state is read before a slot becomes an update's scratch
+        if (w < nn) {
+            const uint32_t h = e & 0x7ffffffu;
+            if (h) {
                 float m[3], v[6], d;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) m[i] = p.hit_pos[i * p.H + hg];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) v[i] = p.hit_cov[i * p.H + hg];
-                const int st = update(x, c, m, v, p.rt, &d, slots + threadIdx.x, 128);
-                if (st == 1) flags |= KF_FLAG_INVERSION_FAILED;
-                if (st >= 2) flags |= KF_FLAG_FP64_PATH;
-                if (st == 3) flags |= KF_FLAG_PSD_REPAIRED;
+                load_hit(h - 1u, m, v);
+                const int stt = update(x, c, m, v, p.rt, &d, col, 32);
+                if (stt == 1) flags |= KF_FLAG_INVERSION_FAILED;
+                if (stt >= 2) flags |= KF_FLAG_FP64_PATH;
+                if (stt == 3) flags |= KF_FLAG_PSD_REPAIRED;
             }
-            bp[l * 128 + threadIdx.x] = (int32_t)(((uint32_t)new_parent << 27) | new_hit);
+            s_bp[(l * N + w) * 32 + lane] = (int32_t)e;
         }
-        __syncwarp();
+        nc = nn;
     }
+    __syncthreads();
     if (!seed_ok) return;
-    const int N_ = p.N;
-    const int64_t sj = s * N_ + slot;
-    if (slot < N_) {
-        const bool have = slot < nc;
+    const int64_t sj = s * N + w;
+    const bool have = w < nc;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) p.out_state[i * p.S * N_ + sj] = have ? x[i] : 0.0f;
+    for (int i = 0; i < 6; ++i) p.out_state[i * p.S * N + sj] = have ? x[i] : 0.0f;
 #pragma unroll
-        for (int i = 0; i < 21; ++i) p.out_cov[i * p.S * N_ + sj] = have ? c[i] : 0.0f;
-        p.out_chi2[sj] = have ? chi2 : 0.0f;
-        p.out_nhits[sj] = (int16_t)(have ? nhits : -1);
-        p.out_flags[sj] = have ? flags : 0u;
-        int cur = slot;
-        for (int l = L - 1; l >= 0; --l) {
-            int32_t out = -1;
-            if (have) {
-                const uint32_t e = (uint32_t)bp[l * 128 + (threadIdx.x - slot) + cur];
-                const uint32_t h = e & 0x7ffffffu;
-                if (h) out = (int32_t)(p.ev_off[(int64_t)ev * (L + 1) + l] + (h - 1u));
-                cur = (int)(e >> 27);
-            }
-            p.out_hit[sj * L + l] = out;
+    for (int i = 0; i < 21; ++i) p.out_cov[i * p.S * N + sj] = have ? c[i] : 0.0f;
+    p.out_chi2[sj] = have ? chi2 : 0.0f;
+    p.out_nhits[sj] = (int16_t)(have ? nhits : -1);
+    p.out_flags[sj] = have ? (flags & ~kStoppedBit) : 0u;
+    int cur = w;
+    for (int l = L - 1; l >= 0; --l) {
+        int32_t out = -1;
+        if (have) {
+            const uint32_t e = (uint32_t)s_bp[(l * N + cur) * 32 + lane];
+            const uint32_t h = e & 0x7ffffffu;
+            if (h) out = (int32_t)(p.ev_off[(int64_t)ev * (L + 1) + l] + (h - 1u));
+            cur = (int)(e >> 27);
         }
+        p.out_hit[sj * L + l] = out;
     }
 }
 
@@ -754,34 +842,18 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
     p.mlp_w32 = w32;
     if (log && (e = cudaMemsetAsync(log->count, 0, sizeof(uint64_t), stream)) != cudaSuccess)
         return cuda_error(ctx, e, "log counter");
-    // lanes per seed: the smallest group that holds N candidates (6 for N = 5
-    // or 6, so that a warp holds five seeds instead of four)
-    const int G = p.N == 1 ? 1 : p.N <= 2 ? 2 : p.N <= 4 ? 4 : p.N <= 6 ? 6 : 8;
-    const int64_t seeds_per_block = 4 * (32 / G);
-    const unsigned grid = (unsigned)((n_seeds + seeds_per_block - 1) / seeds_per_block);
+    // one block per 32 seeds, one warp per candidate slot
     const int mode = o.use_proposal ? kModeProposal : log ? kModeLog : kModePlain;
-    const size_t smem = mode == kModeProposal
-                            ? build_smem_base(L) + kBuildSmemMlp
-                            : (size_t)L * 128 * sizeof(int32_t) + (size_t)kSlotSize * 128 * sizeof(float);
-    static bool attr_prop = false;
-    if (mode == kModeProposal && !attr_prop) {
-        const int mx = (int)(build_smem_base(KF_MAX_LAYERS) + kBuildSmemMlp);
-        cudaFuncSetAttribute(build_kernel<1, kModeProposal>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(build_kernel<2, kModeProposal>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(build_kernel<4, kModeProposal>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(build_kernel<6, kModeProposal>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(build_kernel<8, kModeProposal>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        attr_prop = true;
-    }
+    p.lay = clone_layout(p.N, L, mode);
+    const unsigned grid = (unsigned)((n_seeds + 31) / 32);
     using Kernel = void (*)(const BuildParams);
-    static const Kernel table[5][3] = {
-        {build_kernel<1, kModePlain>, build_kernel<1, kModeLog>, build_kernel<1, kModeProposal>},
-        {build_kernel<2, kModePlain>, build_kernel<2, kModeLog>, build_kernel<2, kModeProposal>},
-        {build_kernel<4, kModePlain>, build_kernel<4, kModeLog>, build_kernel<4, kModeProposal>},
-        {build_kernel<6, kModePlain>, build_kernel<6, kModeLog>, build_kernel<6, kModeProposal>},
-        {build_kernel<8, kModePlain>, build_kernel<8, kModeLog>, build_kernel<8, kModeProposal>}};
-    const int gi = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 6 ? 3 : 4;
-    table[gi][mode]<<<grid, 128, smem, stream>>>(p);
+    static const Kernel table[3] = {clone_kernel<kModePlain>, clone_kernel<kModeLog>, clone_kernel<kModeProposal>};
+    // the dynamic shared memory opt-in is a per-device attribute: set it on
+    // every call (a host-side attribute write, no stream work)
+    if ((e = cudaFuncSetAttribute(table[mode], cudaFuncAttributeMaxDynamicSharedMemorySize, p.lay.total)) !=
+        cudaSuccess)
+        return cuda_error(ctx, e, "build kernel shared memory");
+    table[mode]<<<grid, 32 * p.N, p.lay.total, stream>>>(p);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(ctx, e, "build launch");
     return KF_OK;
 }

@@ -189,27 +189,34 @@ __global__ void adam_kernel(float *w, float *grad, float *m, float *v, int t, fl
     grad[i] = 0.0f;
 }
 
-// FP32 master weights -> the transposed, padded BF16 copies the scoring reads.
-__global__ void to_bf16_kernel(const float *w, __nv_bfloat16 *W1t, __nv_bfloat16 *W2t)
+// FP32 master weights -> the network inference uses: W1 and W2 as the
+// transposed, padded BF16 copies the tensor cores read, W3 rounded to BF16 in
+// place in the FP32 copy (w32), the biases left in FP32.
+__global__ void to_bf16_kernel(float *w32, __nv_bfloat16 *W1t, __nv_bfloat16 *W2t)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kW1Elems; i += gridDim.x * blockDim.x) {
         const int n = i / kW1Ld, k = i % kW1Ld;
-        W1t[i] = __float2bfloat16(k < kMlpIn ? w[kOffW1 + k * kMlpHid + n] : 0.0f);
+        W1t[i] = __float2bfloat16(k < kMlpIn ? w32[kOffW1 + k * kMlpHid + n] : 0.0f);
     }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kW2Elems; i += gridDim.x * blockDim.x) {
         const int n = i / kW2Ld, k = i % kW2Ld;
-        W2t[i] = __float2bfloat16(k < kMlpHid ? w[kOffW2 + k * kMlpHid + n] : 0.0f);
+        W2t[i] = __float2bfloat16(k < kMlpHid ? w32[kOffW2 + k * kMlpHid + n] : 0.0f);
     }
+    __syncthreads();  // every W1/W2 read above precedes this block's W3 writes (disjoint ranges anyway)
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < kMlpHid; i += blockDim.x)
+            w32[kOffW3 + i] = __bfloat162float(__float2bfloat16(w32[kOffW3 + i]));
 }
 
-constexpr int kScoreWarps = 4;
+constexpr int kScoreWarps = 4, kScoreLd = 12;
 
 struct ScoreSmem {
     MlpSmemWeights w;
-    MlpWarpStage st[kScoreWarps];
+    float X[kScoreWarps][32 * kScoreLd];
 };
 
-// Each warp scores 32 rows at a time on the tensor cores.
+// Each warp scores 32 rows at a time on the tensor cores (mma.sync, split
+// activations).
 __global__ void __launch_bounds__(32 * kScoreWarps) mlp_score_kernel(const __nv_bfloat16 *W1, const __nv_bfloat16 *W2,
                                                                      const float *w32, const float *X, int64_t n,
                                                                      float *logits)
@@ -218,16 +225,16 @@ __global__ void __launch_bounds__(32 * kScoreWarps) mlp_score_kernel(const __nv_
     ScoreSmem &s = *reinterpret_cast<ScoreSmem *>(smem_raw);
     mlp_load_weights(&s.w, W1, W2, w32);
     __syncthreads();
+    const MlpWeightsRef mw{reinterpret_cast<const uint32_t *>(s.w.W1t), reinterpret_cast<const uint32_t *>(s.w.W2t),
+                           s.w.b1, s.w.b2, s.w.W3, s.w.b3};
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    MlpWarpStage *st = &s.st[warp];
+    float *xs = s.X[warp];
     const int64_t n_chunks = (n + 31) / 32;
     for (int64_t ch = (int64_t)blockIdx.x * kScoreWarps + warp; ch < n_chunks; ch += (int64_t)gridDim.x * kScoreWarps) {
         const int64_t row = ch * 32 + lane;
-        float f[kMlpIn];
 #pragma unroll
-        for (int i = 0; i < kMlpIn; ++i) f[i] = row < n ? X[row * kMlpIn + i] : 0.0f;
-        mlp_stage_row(st, f);
-        const float z = mlp_score_warp(&s.w, st);
+        for (int i = 0; i < kMlpIn; ++i) xs[lane * kScoreLd + i] = row < n ? X[row * kMlpIn + i] : 0.0f;
+        const float z = mlp_score_warp_split(mw, xs, kScoreLd);
         if (row < n) logits[row] = z;
     }
 }

@@ -3,14 +3,21 @@
 // the proposal the build step can use to rank a candidate's in-window hits so
 // that only the best k get the full Kalman chi2.
 //
-// Inference runs on the tensor cores in BF16 with FP32 accumulation, one warp
-// scoring 32 rows at a time with mma.sync.m16n8k16 (inline PTX): the build
-// kernel scores a few in-window hits per lane inside its per-warp layer loop,
-// where CTA-wide tcgen05 tiles do not fit.  The layer-1 accumulators are
-// turned into the layer-2 A fragments in registers (the m16n8 accumulator
-// layout of two adjacent n-tiles is the m16k16 A layout), and the last layer
-// (64 -> 1) is a dot product in FP32 reduced over the four lanes of a group,
-// so a call touches shared memory only for its inputs and the weights.
+// The network's weights are BF16 (W1, W2 and W3, rounded from the FP32 master
+// weights when they are loaded), its biases FP32.  Inference runs on the
+// tensor cores with FP32 accumulation.  Activations (the inputs and the first
+// hidden layer) are carried as a pair of BF16 numbers, hi = bf16(a) and lo =
+// bf16(a - hi), and each product is issued twice, once per part: the result
+// is the FP32 evaluation of the BF16-weight network to about 2^-16 of each
+// activation, so the ranking a build takes from the logits is that of the
+// network itself, not of a rounding of its inputs.
+//
+// One warp scores 32 rows at a time with mma.sync.m16n8k16 (inline PTX).  The
+// layer-1 accumulators are turned into the layer-2 A fragments in registers
+// (the m16n8 accumulator layout of two adjacent n-tiles is the m16k16 A
+// layout), and the last layer (64 -> 1) is a dot product in FP32 reduced over
+// the four lanes of a group, so a call touches memory only for its FP32 input
+// rows and the weights.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -28,7 +35,7 @@ constexpr int kMlpParams = kOffB3 + 1;  // 5057
 // transposed ([n][k], k contiguous, as the col-major B fragment reads them)
 // with rows padded so that the eight rows a fragment load touches fall in
 // distinct banks.
-constexpr int kW1Ld = 24, kW2Ld = 72, kXLd = 24;
+constexpr int kW1Ld = 24, kW2Ld = 72;
 constexpr int kW1Elems = kMlpHid * kW1Ld, kW2Elems = kMlpHid * kW2Ld;
 
 // Weights as the tensor cores read them (shared memory, per block).
@@ -36,11 +43,6 @@ struct __align__(16) MlpSmemWeights {
     __nv_bfloat16 W1t[kW1Elems];  // [64][24]: W1t[n][k] = W1[k][n], k >= 12 zero
     __nv_bfloat16 W2t[kW2Elems];  // [64][72]: W2t[n][k] = W2[k][n], k >= 64 zero
     float b1[kMlpHid], b2[kMlpHid], W3[kMlpHid], b3;
-};
-
-// Per-warp staging of the 32 input rows.
-struct __align__(16) MlpWarpStage {
-    __nv_bfloat16 X[32 * kXLd];  // [32][24], columns 12..15 zero, 16..23 unused
 };
 
 // Load the BF16 device copies (prepared by kf_proposal_load in the layout
@@ -61,22 +63,6 @@ __device__ __forceinline__ void mlp_load_weights(MlpSmemWeights *w, const __nv_b
     if (threadIdx.x == 0) w->b3 = f32[kOffB3];
 }
 
-// Write the calling lane's input row (12 features, rounded to BF16).
-__device__ __forceinline__ void mlp_stage_row(MlpWarpStage *st, const float f[kMlpIn])
-{
-    const int lane = threadIdx.x & 31;
-    uint32_t u[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(2 * i < kMlpIn ? f[2 * i] : 0.0f,
-                                                       2 * i + 1 < kMlpIn ? f[2 * i + 1] : 0.0f);
-        u[i] = *reinterpret_cast<const uint32_t *>(&h);
-    }
-    uint4 *d = reinterpret_cast<uint4 *>(st->X + lane * kXLd);
-    d[0] = make_uint4(u[0], u[1], u[2], u[3]);
-    d[1] = make_uint4(u[4], u[5], u[6], u[7]);
-}
-
 __device__ __forceinline__ void mma_bf16_m16n8k16(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                                   uint32_t b0, uint32_t b1)
 {
@@ -87,42 +73,64 @@ __device__ __forceinline__ void mma_bf16_m16n8k16(float c[4], uint32_t a0, uint3
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi)
+// A float pair as a BF16 pair (hi) and the BF16 rounding of what hi leaves
+// over (lo): hi + lo carries 16 significant bits of each value.
+__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t &hi, uint32_t &lo)
 {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(lo, 0.0f), fmaxf(hi, 0.0f));
-    return *reinterpret_cast<const uint32_t *>(&h);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
-// Score the 32 rows of st->X (row r belongs to lane r; rows a lane does not
-// use may hold anything: rows do not mix).  Warp-collective: every lane of the warp
-// calls it converged.  Returns the logit of the calling lane's row.
+// Where the scorer reads the network: W1t and W2t in the padded transposed
+// BF16 layouts of MlpSmemWeights (as 32-bit pairs), the FP32 biases, the
+// BF16-valued W3 (as floats) and b3.  Shared or global memory.
+struct MlpWeightsRef {
+    const uint32_t *W1, *W2;
+    const float *b1, *b2, *W3;
+    float b3;
+};
+
+// Score 32 input rows X [32][ldx] (FP32, row r belongs to lane r; columns
+// 0..11 used) with split activations.  Warp-collective: every lane calls it
+// converged.  Returns the logit of the calling lane's row.
 //
 // Fragment layouts (PTX ISA, mma.m16n8k16 with .bf16): g = lane / 4,
 // t = lane % 4; A (16x16, row-major) registers hold rows {g, g+8} x columns
 // {2t, 2t+1} and {2t+8, 2t+9}; B (16x8, col-major) rows {2t, 2t+1} and
 // {2t+8, 2t+9} of column g; the accumulator rows {g, g+8} x columns {2t, 2t+1}.
-__device__ __forceinline__ float mlp_score_warp(const MlpSmemWeights *w, const MlpWarpStage *st)
+__device__ __forceinline__ float mlp_score_warp_split(const MlpWeightsRef &w, const float *X, int ldx)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const uint32_t *X32 = reinterpret_cast<const uint32_t *>(st->X);
-    const uint32_t *W1 = reinterpret_cast<const uint32_t *>(w->W1t);
-    const uint32_t *W2 = reinterpret_cast<const uint32_t *>(w->W2t);
     __syncwarp();
     float zr[2][2];  // [m-tile][row g, row g+8]
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
-        const int r0 = (mt * 16 + g) * (kXLd / 2), r1 = r0 + 8 * (kXLd / 2);
-        const uint32_t x0 = X32[r0 + t], x1 = X32[r1 + t], x2 = X32[r0 + t + 4], x3 = X32[r1 + t + 4];
+        const float *x0 = X + (mt * 16 + g) * ldx, *x1 = x0 + 8 * ldx;
+        uint32_t ah[4], al[4];  // layer-1 A fragment, hi and lo
+        split_bf16x2(x0[2 * t], x0[2 * t + 1], ah[0], al[0]);
+        split_bf16x2(x1[2 * t], x1[2 * t + 1], ah[1], al[1]);
+        if (2 * t + 8 < kMlpIn) {
+            split_bf16x2(x0[2 * t + 8], x0[2 * t + 9], ah[2], al[2]);
+            split_bf16x2(x1[2 * t + 8], x1[2 * t + 9], ah[3], al[3]);
+        } else {
+            ah[2] = al[2] = ah[3] = al[3] = 0u;
+        }
         // layer 1 -> A fragments of layer 2 (k-step ks = n-tiles 2ks, 2ks+1)
-        uint32_t a[4][4];
+        uint32_t a[4][4], b[4][4];  // hi, lo
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt) {
             const int n = nt * 8 + g, j = nt * 8 + 2 * t;
+            const uint32_t w0 = w.W1[n * (kW1Ld / 2) + t], w1 = w.W1[n * (kW1Ld / 2) + t + 4];
             float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            mma_bf16_m16n8k16(c, x0, x1, x2, x3, W1[n * (kW1Ld / 2) + t], W1[n * (kW1Ld / 2) + t + 4]);
-            const float2 bb = *reinterpret_cast<const float2 *>(w->b1 + j);
-            a[nt >> 1][(nt & 1) * 2 + 0] = pack_relu_bf16(c[0] + bb.x, c[1] + bb.y);
-            a[nt >> 1][(nt & 1) * 2 + 1] = pack_relu_bf16(c[2] + bb.x, c[3] + bb.y);
+            mma_bf16_m16n8k16(c, ah[0], ah[1], ah[2], ah[3], w0, w1);
+            mma_bf16_m16n8k16(c, al[0], al[1], al[2], al[3], w0, w1);
+            const float2 bb = *reinterpret_cast<const float2 *>(w.b1 + j);
+            split_bf16x2(fmaxf(c[0] + bb.x, 0.0f), fmaxf(c[1] + bb.y, 0.0f), a[nt >> 1][(nt & 1) * 2 + 0],
+                         b[nt >> 1][(nt & 1) * 2 + 0]);
+            split_bf16x2(fmaxf(c[2] + bb.x, 0.0f), fmaxf(c[3] + bb.y, 0.0f), a[nt >> 1][(nt & 1) * 2 + 1],
+                         b[nt >> 1][(nt & 1) * 2 + 1]);
         }
         // layer 2, one n-tile at a time, folded into the 64 -> 1 dot product
         float z0 = 0.0f, z1 = 0.0f;
@@ -131,11 +139,13 @@ __device__ __forceinline__ float mlp_score_warp(const MlpSmemWeights *w, const M
             const int n = nt * 8 + g, j = nt * 8 + 2 * t;
             float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-                mma_bf16_m16n8k16(c, a[ks][0], a[ks][1], a[ks][2], a[ks][3], W2[n * (kW2Ld / 2) + ks * 8 + t],
-                                  W2[n * (kW2Ld / 2) + ks * 8 + t + 4]);
-            const float2 bb = *reinterpret_cast<const float2 *>(w->b2 + j);
-            const float2 ww = *reinterpret_cast<const float2 *>(w->W3 + j);
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint32_t w0 = w.W2[n * (kW2Ld / 2) + ks * 8 + t], w1 = w.W2[n * (kW2Ld / 2) + ks * 8 + t + 4];
+                mma_bf16_m16n8k16(c, a[ks][0], a[ks][1], a[ks][2], a[ks][3], w0, w1);
+                mma_bf16_m16n8k16(c, b[ks][0], b[ks][1], b[ks][2], b[ks][3], w0, w1);
+            }
+            const float2 bb = *reinterpret_cast<const float2 *>(w.b2 + j);
+            const float2 ww = *reinterpret_cast<const float2 *>(w.W3 + j);
             z0 = fmaf(ww.x, fmaxf(c[0] + bb.x, 0.0f), fmaf(ww.y, fmaxf(c[1] + bb.y, 0.0f), z0));
             z1 = fmaf(ww.x, fmaxf(c[2] + bb.x, 0.0f), fmaf(ww.y, fmaxf(c[3] + bb.y, 0.0f), z1));
         }
@@ -153,7 +163,7 @@ __device__ __forceinline__ float mlp_score_warp(const MlpSmemWeights *w, const M
     const int mt = lane >> 4, half = (lane >> 3) & 1;
     const float z = mt ? (half ? v11 : v10) : (half ? v01 : v00);
     __syncwarp();
-    return z + w->b3;
+    return z + w.b3;
 }
 
 }  // namespace kf
