@@ -41,6 +41,26 @@ def flatten(p):
     return np.concatenate([np.asarray(p[name], dtype=np.float64).reshape(-1) for name, _ in SHAPES])
 
 
+def bf16(v):
+    """Round to float32, then to bfloat16 (8-bit significand, nearest, ties to
+    even), returned as float64."""
+    u = np.ascontiguousarray(v, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return u.view(np.float32).astype(np.float64)
+
+
+def inference_weights(flat):
+    """The network the build ranks with: the weights W1, W2 and W3 in
+    bfloat16 (the configuration's "BF16 weights"), the biases in float32 (the
+    library keeps them so), from the float32 or float64 master weights."""
+    p = unflatten(flat)
+    for k in ("W1", "W2", "W3"):
+        p[k] = bf16(p[k])
+    for k in ("b1", "b2", "b3"):
+        p[k] = np.asarray(p[k], dtype=np.float32).astype(np.float64)
+    return flatten(p)
+
+
 def init_params(rng):
     """He-normal weights, zero biases."""
     p = {"W1": rng.normal(0, np.sqrt(2.0 / N_IN), (N_IN, N_HID)), "b1": np.zeros(N_HID),
