@@ -118,16 +118,16 @@ typedef struct {
     float hit_sigma_z;
     float window_max_dphi;   /* cap of the window's phi half-width, rad */
     float window_max_dz;     /* cap of its z half-width, cm */
-    int n_phi_bins;          /* hit bins per layer, in phi ... */
-    int n_z_bins;            /* ... and in z */
+    int n_phi_bins;          /* hit bins per layer, in phi ... (0 = autotuned) */
+    int n_z_bins;            /* ... and in z (0 = autotuned); at most 16,384 bins */
     int use_proposal;        /* 1: the learned proposal keeps the top-k in-window hits */
     int topk;
 } kf_options;
 
 /* Fill *opt with the defaults: routed precision (cond_max 1e4, pT in
  * [0.25, 200], gain_max 0), automatic launch, N = 6, chi2 cut 30, 3-sigma window
- * capped at 0.05 rad and 5 cm, 0.01/0.1 cm nominal resolution, 256 x 64 bins,
- * proposal off, top-k 4. */
+ * capped at 0.05 rad and 5 cm, 0.01/0.1 cm nominal resolution, autotuned hit
+ * bins, proposal off, top-k 4. */
 void kf_options_default(kf_options *opt);
 
 /* Create a context on CUDA device `device` (requires compute capability
@@ -222,7 +222,12 @@ int kf_fit_tracks_host(kf_context *ctx, const kf_geometry *geom, int64_t n_track
  * increment is at most chi2_cut.  A candidate that cannot reach a layer, or crosses it beyond |z| = z_half,
  * stops and yields only its hole child from then on (its flags record why).
  * Hits are first sorted into n_phi_bins x n_z_bins bins per (event, layer)
- * in context scratch (Section 3: hits partitioned spatially).
+ * in context scratch (Section 3: hits partitioned spatially).  Where opt
+ * leaves the bin grid 0 an autotuner chooses it: the first call of a workload
+ * class (layers, N, mode, the seed and hit counts' sizes in powers of two)
+ * times five grids of up to 16,384 bins on the caller's buffers and keeps the
+ * fastest (kf_build_tuned_shape reports it); the results do not depend on the
+ * grid.
  *
  * geom: the layers to build over (host).
  * hit_offsets: host, [n_events][L + 1]; the hits of event e on layer l are
@@ -238,7 +243,8 @@ int kf_fit_tracks_host(kf_context *ctx, const kf_geometry *geom, int64_t n_track
  *   out_state [6][S*N], out_cov [21][S*N] packed, out_flags [S][N];
  *   N = opt->max_cands (1..8).
  * Scratch: 16 bytes per hit plus 4 (n_phi_bins n_z_bins + 1) bytes per
- * (event, layer), kept by the context and grown on demand (KF_ERR_NOMEM).
+ * (event, layer) (16,384 bins when tuned), kept by the context and grown on
+ * demand (KF_ERR_NOMEM).
  * The call copies hit_offsets to the device and waits for that copy.
  */
 int kf_build_tracks(kf_context *ctx, const kf_geometry *geom, int n_events, const int64_t *hit_offsets,
@@ -247,6 +253,44 @@ int kf_build_tracks(kf_context *ctx, const kf_geometry *geom, int n_events, cons
                     const int8_t *seed_charge, int32_t *out_hit_idx, float *out_chi2, int16_t *out_nhits,
                     float *out_state, float *out_cov, uint32_t *out_flags, const kf_options *opt,
                     kf_stream stream);
+
+/*
+ * kf_build_tracks from and to host memory.  The paper's GPU build spent about
+ * half of its wall time moving events between host and device (Section 4.3)
+ * and fed the device from several CPU threads at once (Section 4.2).  Here the
+ * events are cut into batches of events_per_batch events (0: 16), and a
+ * pipeline of three streams overlaps the upload of one batch's hits and
+ * seeds, the build of the previous one and the download of the outputs of the
+ * one before that, through three rings of device buffers kept by the context.
+ *
+ * Arguments: those of kf_build_tracks, with every array in host memory owned
+ * by the caller (page-locked memory -- cudaMallocHost, cudaHostAlloc,
+ * cudaHostRegister -- lets the copies run asynchronously; pageable memory
+ * works through the driver's staging, without the overlap).  Seeds must be
+ * grouped by event: seed_event non-decreasing, every value in 0..n_events-1.
+ * out_hit_idx holds indices into the caller's hit_pos, as kf_build_tracks
+ * writes them.  The outputs equal kf_build_tracks' for the same inputs and
+ * options (the build does not depend on how the events are batched).  The
+ * call returns when every output is in host memory.  Device memory: three
+ * batches' inputs and outputs plus the binning scratch of one batch, kept by
+ * the context and grown on demand (KF_ERR_NOMEM).
+ */
+int kf_build_tracks_host(kf_context *ctx, const kf_geometry *geom, int n_events, const int64_t *hit_offsets,
+                         const float *hit_pos, const float *hit_cov, int64_t n_hits, int64_t n_seeds,
+                         const int32_t *seed_event, const float *seed_state, const float *seed_cov,
+                         const int8_t *seed_charge, int32_t *out_hit_idx, float *out_chi2, int16_t *out_nhits,
+                         float *out_state, float *out_cov, uint32_t *out_flags, int events_per_batch,
+                         const kf_options *opt);
+
+/*
+ * The hit-bin grid the build autotuner picked for builds of n_layers layers,
+ * N = max_cands, mode (0 plain, 1 logged, 2 learned proposal), n_seeds seeds
+ * and n_hits hits (their size classes, powers of two), with the grid left to
+ * the tuner (opt->n_phi_bins = opt->n_z_bins = 0).  KF_ERR_ARG if no such
+ * build has run on ctx.
+ */
+int kf_build_tuned_shape(kf_context *ctx, int n_layers, int max_cands, int mode, int64_t n_seeds, int64_t n_hits,
+                         int *n_phi_bins, int *n_z_bins);
 
 /*
  * kf_build_tracks that also records the training set of the learned proposal
@@ -313,8 +357,9 @@ int kf_proposal_gradient(kf_context *ctx, const float *weights, const float *fea
 int kf_proposal_train(kf_context *ctx, float *weights, const float *features, const float *labels, int64_t n,
                       int epochs, int batch, float learning_rate, float *epoch_loss, kf_stream stream);
 
-/* Load weights into the context for inference: copied, and rounded to BF16
- * for the tensor cores (biases and W3 stay FP32). */
+/* Load weights into the context for inference: copied, with W1, W2 and W3
+ * rounded to BF16 (the network's inference weights) and the biases kept in
+ * FP32. */
 int kf_proposal_load(kf_context *ctx, const float *weights, kf_stream stream);
 
 /* kf_proposal_load with the weights given as bytes: weights (device) holds the
@@ -322,9 +367,33 @@ int kf_proposal_load(kf_context *ctx, const float *weights, kf_stream stream);
  * (KF_ERR_ARG otherwise); enqueued on the legacy default stream. */
 int kf_load_proposal(kf_context *ctx, const void *weights, size_t bytes);
 
-/* Logits [n] of the loaded network for the pairs' features: BF16 inputs and
- * weights, FP32 accumulation, on the tensor cores. */
+/* Logits [n] of the loaded network for the pairs' features [n][12] (device),
+ * on the tensor cores: the network's BF16 weights, each activation carried as
+ * a pair of BF16 numbers (hi, and the rounding of what hi leaves over), FP32
+ * accumulation; the result is the FP32 evaluation of the BF16-weight network
+ * to about 2^-16 of each activation.  Uses the engine chosen by measurement
+ * (KF_SCORE_AUTO of kf_proposal_score_with). */
 int kf_proposal_score(kf_context *ctx, const float *features, int64_t n, float *logits, kf_stream stream);
+
+/* kf_proposal_score with the tensor-core instruction family named:
+ *   KF_SCORE_MMA_SYNC: warp-level mma.sync.m16n8k16, each warp scoring 32 rows
+ *     with the weights in shared memory and the accumulators in registers;
+ *   KF_SCORE_TCGEN05: tcgen05.mma, each CTA scoring 128-row tiles with the
+ *     weights staged once in shared memory and both layers' accumulators in
+ *     tensor memory.  Its waits for the tensor cores are bounded: a wait that
+ *     expires leaves that CTA's remaining rows unwritten and sets the flag
+ *     kf_proposal_status reports;
+ *   KF_SCORE_AUTO: the one kf_proposal_score uses.
+ * Both give the same logits within FP32 rounding. */
+#define KF_SCORE_AUTO 0
+#define KF_SCORE_MMA_SYNC 1
+#define KF_SCORE_TCGEN05 2
+int kf_proposal_score_with(kf_context *ctx, const float *features, int64_t n, float *logits, int engine,
+                           kf_stream stream);
+
+/* *expired = 1 if a bounded device-side wait of the scoring has expired on
+ * this context since it was created, else 0.  Synchronises with the device. */
+int kf_proposal_status(kf_context *ctx, int *expired);
 
 /*
  * Seeding from hits (the paper seeds from the true hits of each simulated

@@ -311,8 +311,10 @@ static int window_intervals(double phic, double dphi, double lo_[3], double hi_[
  *       the hits of a window 1.05 times wider, and a crossing's |z| against
  *       z_half;
  *   [1] a tested hit's chi2 increment against the cut, |dchi2 - cut| / cut;
- *   [2] the ranking: two children next to each other among the first N + 1,
- *       with the same number of hits, |chi2_a - chi2_b| / max(1, chi2_a);
+ *   [2] the ranking: two children next to each other among a seed's first
+ *       N + 1, or among a candidate's best N + 1 hit children (its list is
+ *       cut at N), with the same number of hits, |chi2_a - chi2_b| /
+ *       max(1, chi2_a);
  *   [3] the proposal's top-k: the logits at ranks topk and topk + 1,
  *       (z_k - z_k+1) / (1 + |z_k|).
  * Infinity where the seed met no such decision.  It takes no part in the
@@ -336,6 +338,7 @@ int orc_build_tracks_ex(int n_layers, const double *radii, const double *x_over_
     if (!win) return -2;
     cand_t cand[MAXN], next[MAXN];
     child_t hits_of[MAXN][MAXN], all[MAXN * (MAXN + 1)];
+    child_t hits_m[MAXN + 1]; /* margins: a candidate's best N + 1 hit children */
     int nh[MAXN];
     for (int64_t s = s_begin; s < s_end; ++s) {
         double mg[4] = {HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL};
@@ -357,6 +360,7 @@ int orc_build_tracks_ex(int n_layers, const double *radii, const double *x_over_
             for (int c = 0; c < nc; ++c) {
                 cand_t *k = &cand[c];
                 nh[c] = 0;
+                int nhm = 0;
                 k->reached = 0;
                 if (!k->stopped) {
                     double J[36], Q[36], sd;
@@ -453,7 +457,11 @@ int orc_build_tracks_ex(int n_layers, const double *radii, const double *x_over_
                         if (!(dc <= chi2_cut)) continue;
                         child_t ch = {c, k->nhits + 1, h - seg_lo, h, k->chi2 + dc, dc, row};
                         insert_child(hits_of[c], &nh[c], N, &ch);
+                        if (out_margin) insert_child(hits_m, &nhm, N + 1, &ch);
                     }
+                    /* the cap of a candidate's list at N children is a ranking too */
+                    for (int j = 0; j + 1 < nhm; ++j)
+                        mg[2] = fmin(mg[2], fabs(hits_m[j].chi2 - hits_m[j + 1].chi2) / fmax(1.0, hits_m[j].chi2));
                 }
                 for (int i = 0; i < nh[c]; ++i) all[n_all++] = hits_of[c][i];
                 child_t hole = {c, k->nhits, -1, -1, k->chi2, 0.0, -1};

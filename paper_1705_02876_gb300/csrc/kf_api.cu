@@ -166,8 +166,8 @@ void kf_options_default(kf_options *o)
     o->hit_sigma_z = 0.1f;
     o->window_max_dphi = 0.05f;
     o->window_max_dz = 5.0f;
-    o->n_phi_bins = 256;
-    o->n_z_bins = 64;
+    o->n_phi_bins = 0;
+    o->n_z_bins = 0;
     o->use_proposal = 0;
     o->topk = 4;
 }

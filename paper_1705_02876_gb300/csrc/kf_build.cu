@@ -3,18 +3,21 @@
 //                       phi x z bins (Section 3: hits partitioned spatially
 //                       for a fast look-up of the compatible ones), three
 //                       kernels over all segments (kf_bins.cuh);
-//   clone_kernel      - the clone engine, all layers in one launch: a block
-//                       holds 32 seeds, warp w candidate slot w of each; per
-//                       layer every candidate is propagated and its window's
-//                       hits are tested, one lane per seed merges the
-//                       candidates' children into the seed's N best (in place
-//                       of the paper's per-seed heaps, Section 4.3), and every
-//                       slot takes over its new child from shared memory and
-//                       updates it.
+//   build_kernel      - the clone engine, all layers in one launch: each
+//                       seed's candidates occupy a group of G >= N lanes of
+//                       a warp (G in 1, 2, 4, 6, 8); every lane propagates
+//                       its candidate, scans the bins its window overlaps
+//                       and keeps its N best compatible hits; the group
+//                       merges its lanes' lists into the N best children by
+//                       warp shuffles (in place of the paper's shared-memory
+//                       heaps, Section 4.3) and each lane takes over one
+//                       child and updates it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "kf.h"
@@ -33,11 +36,34 @@ struct BuildState {
     int64_t *seg_off = nullptr;  // device copy of the segment bounds [n_seg + 1]
     int64_t *ev_off = nullptr;   // device copy of hit_offsets [n_events][L + 1]
     size_t ev_capacity = 0;
+    // the host-buffer build's pipeline: streams, and per ring slot the batch's device buffers,
+    // its pinned offset staging and the events that order the slot's reuse
+    cudaStream_t hs_in = nullptr, hs_run = nullptr, hs_out = nullptr;
+    struct Slot {
+        char *dev = nullptr;
+        size_t dev_bytes = 0;
+        int64_t *pin = nullptr;  // pinned: segment bounds, then the batch's offsets rows
+        size_t pin_elems = 0;
+        cudaEvent_t in_done = nullptr, built = nullptr, out_done = nullptr;
+        bool used = false;
+    } slot[3];
+    // autotuned bin grids: (L, N, mode, seeds' size class, hits' size class, fixed n_phi, fixed n_z)
+    // -> (n_phi, n_z)
+    std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<int, int>> tuned;
 };
 
 void destroy_build_state(BuildState *s)
 {
     if (!s) return;
+    for (auto &sl : s->slot) {
+        cudaFree(sl.dev);
+        cudaFreeHost(sl.pin);
+        if (sl.in_done) cudaEventDestroy(sl.in_done);
+        if (sl.built) cudaEventDestroy(sl.built);
+        if (sl.out_done) cudaEventDestroy(sl.out_done);
+    }
+    for (cudaStream_t h : {s->hs_in, s->hs_run, s->hs_out})
+        if (h) cudaStreamDestroy(h);
     cudaFree(s->bkey);
     cudaFree(s->bin_off);
     cudaFree(s->bin_cnt);
@@ -51,30 +77,6 @@ namespace {
 constexpr int kModePlain = 0, kModeLog = 1, kModeProposal = 2;
 constexpr int kKeyBatch = 4;  // window keys loaded together in the collecting scan (8 was slower)
 
-// Shared memory of the clone-engine kernel: for N candidate slots (one warp
-// each) of 32 seeds (one lane each) and L layers.  Every array is [..][32],
-// the seed's lane fastest, so a warp's accesses fall in distinct banks.
-// Offsets in bytes from the start of the dynamic shared memory.
-struct CloneLayout {
-    int st;        // float [N][kSlotSize][32]: slot w's predicted state (x: 0..5, c: 6..26) for the
-                   // merge and the hand-over, then the update's slot of the extended-precision paths
-    int flags;     // uint32 [N][32]: the candidate's flags, kStoppedBit = stopped
-    int nh;        // int [N][32]: its hits
-    int chi2;      // float [N][32]: its chi2
-    int ncand;     // int [32]: candidates of each seed
-    int bp;        // int32 [L][N][32]: back-pointers, parent slot << 27 | (hit index + 1)
-    // union: the merge's inputs and outputs, or the proposal's staged input rows
-    int lcnt;      // int [N][32]: hit children listed by slot w (at most N)
-    int lc;        // float [N][N][32]: their summed chi2, ascending (then hit index)
-    int lh;        // uint32 [N][N][32]: their hit indices within the (event, layer)
-    int lr;        // uint32 [N][N][32]: their rows of the training log (logging only)
-    int sel;       // uint32 [N][32]: child of new slot j, parent << 27 | (hit index + 1)
-    int sel_chi2;  // float [N][32]
-    int sel_nh;    // int [N][32]
-    int stage;     // float [N][32][kStageLd]: input rows of the proposal (proposal only)
-    int total;
-};
-
 struct BuildParams {
     FitGeom g;
     Routing rt;
@@ -83,6 +85,8 @@ struct BuildParams {
     float chi2_cut, nsigma, sig_rphi2, sig_z2, max_dphi, max_dz;
     int64_t S, H;
     int n_events;
+    int event_base;    // seed_event values are event_base + the event's index in ev_off
+    int64_t hit_base;  // added to the written hit indices (ev_off holds batch-local offsets)
     const int64_t *ev_off;  // [E][L + 1]
     const float *hit_pos, *hit_cov;
     const float4 *bkey;
@@ -104,7 +108,6 @@ struct BuildParams {
     int topk;
     const __nv_bfloat16 *mlp_W1, *mlp_W2;
     const float *mlp_w32;
-    CloneLayout lay;
 };
 
 constexpr int kMaxN = 8;
@@ -180,100 +183,64 @@ struct WindowCursor {
     }
 };
 
+// Order of children: (hits desc, chi2 asc, candidate asc, hit index asc) as
+// a two-word key compared lexicographically: k64 = (63 - hits) << 32 | the
+// bits of chi2 (non-negative floats order as their bit patterns), k32 =
+// candidate slot << 27 | (hit index within the layer + 1), 0 for the hole.
+__device__ __forceinline__ bool key_less(unsigned long long a64, uint32_t a32, unsigned long long b64, uint32_t b32)
+{
+    return a64 < b64 || (a64 == b64 && a32 < b32);
+}
+
+// Shared memory: back-pointers [L][128], update slots [kSlotSize][128], then
+// (proposal only) the network's weights and each warp's 32 staged input rows
+// (FP32, kStageLd floats each).
 constexpr int kStageLd = 12;
-constexpr uint32_t kStoppedBit = 0x80000000u;
+__host__ __device__ constexpr size_t build_smem_base(int L) { return ((size_t)(L + kSlotSize) * 128 * 4 + 127) / 128 * 128; }
+constexpr size_t kBuildSmemMlp = sizeof(MlpSmemWeights) + 4 * 32 * kStageLd * sizeof(float);
 
-CloneLayout clone_layout(int N, int L, int mode)
+// At most 128 registers (four blocks per SM) in every mode: the proposal's
+// scoring path, rare where windows hold few hits, spills rather than taking
+// registers from the common path.
+template <int G, int MODE>
+__global__ void __launch_bounds__(128, 4) build_kernel(const BuildParams p)
 {
-    CloneLayout o{};
-    int off = 0;
-    auto take = [&](int bytes) {
-        const int at = off;
-        off += (bytes + 15) / 16 * 16;
-        return at;
-    };
-    const int col = 32 * 4;  // one [32] array of 4-byte words
-    o.st = take(N * kSlotSize * col);
-    o.flags = take(N * col);
-    o.nh = take(N * col);
-    o.chi2 = take(N * col);
-    o.ncand = take(col);
-    o.bp = take(L * N * col);
-    const int base = off;
-    o.lcnt = take(N * col);
-    o.lc = take(N * N * col);
-    o.lh = take(N * N * col);
-    o.lr = mode == kModeLog ? take(N * N * col) : 0;
-    o.sel = take(N * col);
-    o.sel_chi2 = take(N * col);
-    o.sel_nh = take(N * col);
-    const int lists_end = off;
-    o.stage = base;
-    const int stage_end = mode == kModeProposal ? base + N * 32 * kStageLd * 4 : base;
-    o.total = std::max(lists_end, stage_end);
-    return o;
-}
-
-template <class T>
-__device__ __forceinline__ T *sm_at(unsigned char *sm, int off)
-{
-    return reinterpret_cast<T *>(sm + off);
-}
-
-// The clone engine, all build layers in one launch.  Block = 32 seeds x N
-// candidate slots: warp w holds slot w of the 32 seeds, lane i seed i, so every
-// lane of every warp owns one candidate.  Per layer:
-//   P  every live candidate is propagated, transported and scattered (fit
-//      code); its predicted state goes to shared memory; its window is
-//      scanned and the chi2 of its in-window hits taken; its N best hit
-//      children (by chi2, then hit index) are listed in shared memory;
-//      [proposal: windows holding more than topk hits are ranked first, the
-//      warps scoring their rows on the tensor cores, and only the topk best
-//      by logit get a chi2]
-//   S  one lane per seed (warp 0) merges its candidates' lists and holes into
-//      the seed's N best children (hits desc, chi2 asc, parent slot asc, hit
-//      index asc, the hole first): N rounds of a minimum over at most N list
-//      heads held in registers;
-//   U  the thread of new slot j reads its child's parent state from shared
-//      memory and applies the update with the child's hit; a back-pointer
-//      (parent slot, hit) per (layer, slot) goes to shared memory.
-// After the last layer each slot walks its back-pointers to write its hits.
-template <int MODE>
-__global__ void __launch_bounds__(256) clone_kernel(const BuildParams p)
-{
-    extern __shared__ __align__(128) unsigned char sm[];
-    const CloneLayout &ly = p.lay;
-    const int N = p.N, L = p.g.L;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    float *st = sm_at<float>(sm, ly.st);
-    uint32_t *s_flags = sm_at<uint32_t>(sm, ly.flags);
-    int *s_nh = sm_at<int>(sm, ly.nh);
-    float *s_chi2 = sm_at<float>(sm, ly.chi2);
-    int *s_ncand = sm_at<int>(sm, ly.ncand);
-    int32_t *s_bp = sm_at<int32_t>(sm, ly.bp);
-    int *s_lcnt = sm_at<int>(sm, ly.lcnt);
-    float *s_lc = sm_at<float>(sm, ly.lc);
-    uint32_t *s_lh = sm_at<uint32_t>(sm, ly.lh);
-    uint32_t *s_lr = sm_at<uint32_t>(sm, ly.lr);
-    uint32_t *s_sel = sm_at<uint32_t>(sm, ly.sel);
-    float *s_sel_chi2 = sm_at<float>(sm, ly.sel_chi2);
-    int *s_sel_nh = sm_at<int>(sm, ly.sel_nh);
-    const int me = w * 32 + lane;  // [w][lane] in the [N][32] arrays
-    float *col = st + w * kSlotSize * 32 + lane;  // this slot's column: [k][32]
-
-    const int64_t s = (int64_t)blockIdx.x * 32 + lane;
-    const bool seed_ok = s < p.S;
-    const int ev_in = seed_ok ? p.seed_event[s] : -1;
-    const bool ev_ok = seed_ok && ev_in >= 0 && ev_in < p.n_events;  // a seed of an unknown event builds nothing
-    const int ev = ev_ok ? ev_in : 0;
-    const float qkb = ev_ok ? (float)p.seed_charge[s] * p.g.qk : 0.0f;
+    constexpr int SEEDS_PER_WARP = 32 / G;
+    extern __shared__ __align__(128) int32_t smem[];
+    const int L = p.g.L;
+    int32_t *bp = smem;                                   // [L][128] back-pointers
+    float *slots = reinterpret_cast<float *>(smem + L * 128);  // [kSlotSize][128]
+    MlpWeightsRef mref{};
+    float *xs = nullptr;  // this warp's staged input rows [32][kStageLd]
+    if (MODE == kModeProposal) {
+        unsigned char *base = reinterpret_cast<unsigned char *>(smem) + build_smem_base(L);
+        MlpSmemWeights *mw = reinterpret_cast<MlpSmemWeights *>(base);
+        xs = reinterpret_cast<float *>(base + sizeof(MlpSmemWeights)) + (threadIdx.x >> 5) * 32 * kStageLd;
+        mlp_load_weights(mw, p.mlp_W1, p.mlp_W2, p.mlp_w32);
+        __syncthreads();
+        mref = MlpWeightsRef{reinterpret_cast<const uint32_t *>(mw->W1t), reinterpret_cast<const uint32_t *>(mw->W2t),
+                             mw->b1, mw->b2, mw->W3, mw->b3};
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int slot = lane % G, gbase = lane - slot;
+    // G = 6: five groups per warp; lanes 30 and 31 form an idle group of two
+    const bool lane_ok = lane < SEEDS_PER_WARP * G;
+    const int64_t s = ((int64_t)blockIdx.x * 4 + warp) * SEEDS_PER_WARP + lane / G;
+    const bool seed_ok = lane_ok && s < p.S;
+    const int N = p.N;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << gbase);
 
     float x[6], c[21];
     float chi2 = 0.0f;
     int nhits = 0;
+    bool stopped = false;
     uint32_t flags = 0;
-    int nc = ev_ok ? 1 : 0;
-    if (ev_ok && w == 0) {
+    int nc = 1;
+    const int ev_in = seed_ok ? p.seed_event[s] - p.event_base : 0;
+    const bool ev_ok = ev_in >= 0 && ev_in < p.n_events;  // a seed of an unknown event builds nothing
+    const int ev = ev_ok ? ev_in : 0;
+    const float qkb = seed_ok ? (float)p.seed_charge[s] * p.g.qk : 0.0f;
+    if (seed_ok && ev_ok) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) x[i] = p.seed_state[i * p.S + s];
 #pragma unroll
@@ -283,19 +250,21 @@ __global__ void __launch_bounds__(256) clone_kernel(const BuildParams p)
         for (int i = 0; i < 6; ++i) x[i] = 0.0f;
 #pragma unroll
         for (int i = 0; i < 21; ++i) c[i] = 0.0f;
+        nc = 0;
     }
     const int nbins = p.bg.n_phi * p.bg.n_z;
     for (int l = 0; l < L; ++l) {
-        // ---------------------------------------------------------------- P
-        const bool valid = w < nc;
+        const bool valid = slot < nc;
         bool reached = false;
-        if (valid && !(flags & kStoppedBit)) {
+        if (valid && !stopped) {
             float xn[6], sd;
             Jac J;
             if (!propagate(x, qkb, p.g.r[l], xn, sd, &J)) {
-                flags |= kStoppedBit | KF_FLAG_UNREACHABLE;
+                stopped = true;
+                flags |= KF_FLAG_UNREACHABLE;
             } else if (fabsf(xn[2]) > p.g.z_half) {
-                flags |= kStoppedBit | KF_FLAG_LEFT_BARREL;
+                stopped = true;
+                flags |= KF_FLAG_LEFT_BARREL;
             } else {
                 transport(J, c);
                 add_scattering(xn, p.g.inv_r[l], p.g.xx0[l], c);
@@ -304,19 +273,37 @@ __global__ void __launch_bounds__(256) clone_kernel(const BuildParams p)
                 reached = true;
             }
         }
-        if (valid) {  // the candidate (its predicted state) for the merge and the hand-over
+        // this candidate's best compatible hits, sorted by (chi2, hit index);
+        // lr = each entry's row in the training log (logging only)
+        float lc[kMaxN];
+        uint32_t lh[kMaxN], lr[kMaxN];
 #pragma unroll
-            for (int i = 0; i < 6; ++i) col[(kSlotX + i) * 32] = x[i];
-#pragma unroll
-            for (int i = 0; i < 21; ++i) col[(kSlotC + i) * 32] = c[i];
-            s_flags[me] = flags;
-            s_nh[me] = nhits;
-            s_chi2[me] = chi2;
+        for (int k = 0; k < kMaxN; ++k) {
+            lc[k] = INFINITY;
+            lh[k] = kNoKey;
+            lr[k] = kNoKey;
         }
-        const int64_t seg_lo = ev_ok ? p.ev_off[(int64_t)ev * (L + 1) + l] : 0;
+        auto insert = [&](float dc, uint32_t hl, uint32_t row) {
+            if (!(dc < lc[kMaxN - 1] || (dc == lc[kMaxN - 1] && hl < lh[kMaxN - 1]))) return;
+            float cv = dc;
+            uint32_t hv = hl, rv = row;
+#pragma unroll
+            for (int k2 = 0; k2 < kMaxN; ++k2) {
+                const bool before = cv < lc[k2] || (cv == lc[k2] && hv < lh[k2]);
+                const float tc = lc[k2];
+                const uint32_t th = lh[k2], tr = lr[k2];
+                lc[k2] = before ? cv : tc;
+                lh[k2] = before ? hv : th;
+                lr[k2] = before ? rv : tr;
+                cv = before ? tc : cv;
+                hv = before ? th : hv;
+                rv = before ? tr : rv;
+            }
+        };
+        const int64_t seg = (int64_t)ev * (L + 1) + l;
+        const int64_t seg_lo = seed_ok ? p.ev_off[seg] : 0;
         Window win{};
         float nx = 0.0f, ny = 0.0f, ctt = 0.0f, ctz = 0.0f, czz = 0.0f;
-        float cf[kMlpIn];  // the proposal's inputs shared by every hit of this candidate (3..11)
         if (reached) {
             const float ir = rsqrtf(x[0] * x[0] + x[1] * x[1]);
             nx = x[0] * ir;
@@ -345,15 +332,7 @@ __global__ void __launch_bounds__(256) clone_kernel(const BuildParams p)
             }
             win.ip0 = ip0;
             win.nphi = min(ip1 - ip0 + 1, p.bg.n_phi);
-            if (MODE != kModePlain) {
-#pragma unroll
-                for (int i = 0; i < 6; ++i) cf[3 + i] = log10f(fmaxf(c[pk(i, i)], 1e-30f));
-                cf[9] = copysignf(rsqrtf(x[3] * x[3] + x[4] * x[4]), qkb);
-                cf[10] = __fdiv_rn((float)l, (float)L);  // correctly rounded, whatever the division flags
-                cf[11] = (float)(l - nhits);
-            }
         }
-        const float xp0 = x[0], xp1 = x[1], xp2 = x[2];  // the prediction the hits are tested against
         auto load_hit = [&](uint32_t hl, float m[3], float v[6]) {
             const int64_t hg = seg_lo + hl;
 #pragma unroll
@@ -361,41 +340,13 @@ __global__ void __launch_bounds__(256) clone_kernel(const BuildParams p)
 #pragma unroll
             for (int i = 0; i < 6; ++i) v[i] = p.hit_cov[i * p.H + hg];
         };
-        auto eval = [&](uint32_t hl, float *dc, float f3[3]) {
-            float m[3], v[6];
-            load_hit(hl, m, v);
-            const float xp[3] = {xp0, xp1, xp2};
-            return hit_eval(xp, nx, ny, ctt, ctz, czz, m, v, dc, f3);
-        };
-        // this candidate's best hit children, sorted by (summed chi2, hit
-        // index); lr = each entry's row in the training log (logging only)
-        float lc[kMaxN];
-        uint32_t lh[kMaxN], lr[kMaxN];
+        // inputs of the proposal shared by every hit of this candidate
+        auto cand_features = [&](float f[kMlpIn]) {
 #pragma unroll
-        for (int k = 0; k < kMaxN; ++k) {
-            lc[k] = INFINITY;
-            lh[k] = kNoKey;
-            lr[k] = kNoKey;
-        }
-        int n_list = 0;
-        auto insert = [&](float dc, uint32_t hl, uint32_t row) {
-            const float cv0 = chi2 + dc;
-            if (!(cv0 < lc[kMaxN - 1] || (cv0 == lc[kMaxN - 1] && hl < lh[kMaxN - 1]))) return;
-            float cv = cv0;
-            uint32_t hv = hl, rv = row;
-#pragma unroll
-            for (int k2 = 0; k2 < kMaxN; ++k2) {
-                const bool before = cv < lc[k2] || (cv == lc[k2] && hv < lh[k2]);
-                const float tc = lc[k2];
-                const uint32_t th = lh[k2], tr = lr[k2];
-                lc[k2] = before ? cv : tc;
-                lh[k2] = before ? hv : th;
-                lr[k2] = before ? rv : tr;
-                cv = before ? tc : cv;
-                hv = before ? th : hv;
-                rv = before ? tr : rv;
-            }
-            n_list = min(n_list + 1, kMaxN);
+            for (int i = 0; i < 6; ++i) f[3 + i] = log10f(fmaxf(c[pk(i, i)], 1e-30f));
+            f[9] = copysignf(rsqrtf(x[3] * x[3] + x[4] * x[4]), qkb);
+            f[10] = __fdiv_rn((float)l, (float)L);  // correctly rounded, whatever the division flags
+            f[11] = (float)(l - nhits);
         };
         if (MODE != kModeLog) {
             // first pass: the window's hits are collected (cheap bin reads
@@ -406,6 +357,7 @@ __global__ void __launch_bounds__(256) clone_kernel(const BuildParams p)
 #pragma unroll
             for (int k = 0; k < kMaxN; ++k) hb[k] = kNoKey;
             int n_in = 0;
+            WindowCursor cur;
             if (reached) {
                 // each z row's bins are one contiguous key run (two past the
                 // wrap at +-pi): one pair of bin-offset loads per run, then
@@ -442,57 +394,49 @@ __global__ void __launch_bounds__(256) clone_kernel(const BuildParams p)
                 }
             }
             const bool wide = n_in > cap;
-            if (MODE == kModeProposal) {
-                // windows holding more than topk hits keep their topk best by
-                // logit (logit desc, hit index asc): the warps score one hit
-                // per ranking lane per round.  Their input rows are staged over
-                // the merge's lists, which are free until the lists are written
-                if (__syncthreads_or(wide)) {
-                    float *xs = sm_at<float>(sm, ly.stage) + w * 32 * kStageLd;
-                    const MlpWeightsRef mw{reinterpret_cast<const uint32_t *>(p.mlp_W1),
-                                           reinterpret_cast<const uint32_t *>(p.mlp_W2), p.mlp_w32 + kOffB1,
-                                           p.mlp_w32 + kOffB2, p.mlp_w32 + kOffW3, p.mlp_w32[kOffB3]};
-                    float tz[kMaxN];
+            if (MODE == kModeProposal && __any_sync(0xffffffffu, wide)) {
+                // a wide window keeps its topk best hits by logit (logit desc,
+                // hit index asc); one hit per ranking lane per round, scored
+                // by the warp
+                float tz[kMaxN];
 #pragma unroll
-                    for (int k = 0; k < kMaxN; ++k) tz[k] = -INFINITY;
-                    WindowCursor cur;
-                    if (wide) {
+                for (int k = 0; k < kMaxN; ++k) tz[k] = -INFINITY;
+                if (wide) {
 #pragma unroll
-                        for (int k = 0; k < kMaxN; ++k) hb[k] = kNoKey;
-                        cur.start(win);
+                    for (int k = 0; k < kMaxN; ++k) hb[k] = kNoKey;
+                    cur.start(win);
+                }
+                bool more = wide;
+                while (__any_sync(0xffffffffu, more)) {
+                    const uint32_t hr = more ? cur.next(p, win) : kNoKey;
+                    more = hr != kNoKey;
+                    float feat[kMlpIn];
+#pragma unroll
+                    for (int i = 0; i < kMlpIn; ++i) feat[i] = 0.0f;
+                    if (more) {
+                        float m[3], v[6], dc;
+                        load_hit(hr, m, v);
+                        hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, feat);
+                        cand_features(feat);
                     }
-                    bool more = wide;
-                    while (__any_sync(0xffffffffu, more)) {
-                        const uint32_t hr = more ? cur.next(p, win) : kNoKey;
-                        more = hr != kNoKey;
-                        float feat[kMlpIn];
+                    __syncwarp();  // the previous round's rows are read
 #pragma unroll
-                        for (int i = 0; i < kMlpIn; ++i) feat[i] = 0.0f;
-                        if (more) {
-                            float dc;
-                            eval(hr, &dc, feat);
+                    for (int i = 0; i < kMlpIn; ++i) xs[lane * kStageLd + i] = feat[i];
+                    const float z = mlp_score_warp_split(mref, xs, kStageLd);
+                    if (more) {
+                        float cv = z;
+                        uint32_t hv = hr;
 #pragma unroll
-                            for (int i = 3; i < kMlpIn; ++i) feat[i] = cf[i];
-                        }
-#pragma unroll
-                        for (int i = 0; i < kMlpIn; ++i) xs[lane * kStageLd + i] = feat[i];
-                        const float z = mlp_score_warp_split(mw, xs, kStageLd);
-                        if (more) {
-                            float cv = z;
-                            uint32_t hv = hr;
-#pragma unroll
-                            for (int k2 = 0; k2 < kMaxN; ++k2) {
-                                const bool before = k2 < p.topk && (cv > tz[k2] || (cv == tz[k2] && hv < hb[k2]));
-                                const float t1 = tz[k2];
-                                const uint32_t t2 = hb[k2];
-                                tz[k2] = before ? cv : t1;
-                                hb[k2] = before ? hv : t2;
-                                cv = before ? t1 : cv;
-                                hv = before ? t2 : hv;
-                            }
+                        for (int k2 = 0; k2 < kMaxN; ++k2) {
+                            const bool before = k2 < p.topk && (cv > tz[k2] || (cv == tz[k2] && hv < hb[k2]));
+                            const float t1 = tz[k2];
+                            const uint32_t t2 = hb[k2];
+                            tz[k2] = before ? cv : t1;
+                            hb[k2] = before ? hv : t2;
+                            cv = before ? t1 : cv;
+                            hv = before ? t2 : hv;
                         }
                     }
-                    __syncthreads();  // every row is scored before the lists overwrite the staging
                 }
             }
             if (MODE == kModeProposal || !wide) {
@@ -501,16 +445,18 @@ __global__ void __launch_bounds__(256) clone_kernel(const BuildParams p)
 #pragma unroll
                 for (int k2 = 0; k2 < kMaxN; ++k2) {
                     if (hb[k2] == kNoKey) continue;
-                    float dc, f3[3];
-                    if (eval(hb[k2], &dc, f3) && dc <= p.chi2_cut) insert(dc, hb[k2], kNoKey);
+                    float m[3], v[6], dc, f3[3];
+                    load_hit(hb[k2], m, v);
+                    if (hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, f3) && dc <= p.chi2_cut)
+                        insert(dc, hb[k2], kNoKey);
                 }
             } else {
                 // exhaustive search of a window wider than the buffer
-                WindowCursor cur;
                 cur.start(win);
                 for (uint32_t hl = cur.next(p, win); hl != kNoKey; hl = cur.next(p, win)) {
-                    float dc, f3[3];
-                    if (eval(hl, &dc, f3) && dc <= p.chi2_cut) insert(dc, hl, kNoKey);
+                    float m[3], v[6], dc, f3[3];
+                    load_hit(hl, m, v);
+                    if (hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, f3) && dc <= p.chi2_cut) insert(dc, hl, kNoKey);
                 }
             }
         } else if (reached) {
@@ -519,153 +465,155 @@ __global__ void __launch_bounds__(256) clone_kernel(const BuildParams p)
             WindowCursor cur;
             cur.start(win);
             for (uint32_t hl = cur.next(p, win); hl != kNoKey; hl = cur.next(p, win)) {
-                float dc, feat[kMlpIn];
-                const bool ok = eval(hl, &dc, feat);
+                float m[3], v[6], dc, feat[kMlpIn];
+                load_hit(hl, m, v);
+                const bool ok = hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, feat);
                 uint32_t row = kNoKey;
                 const unsigned long long r = atomicAdd(p.log_n, 1ull);
                 if (r < p.log_cap) {
-#pragma unroll
-                    for (int i = 3; i < kMlpIn; ++i) feat[i] = cf[i];
+                    cand_features(feat);
                     row = (uint32_t)r;
 #pragma unroll
                     for (int i = 0; i < kMlpIn; ++i) p.log_f[(int64_t)r * kMlpIn + i] = feat[i];
                     p.log_y[r] = 0.0f;
                     int32_t *ref = p.log_ref + (int64_t)r * 4;
                     ref[0] = (int32_t)s;
-                    ref[1] = w;
+                    ref[1] = slot;
                     ref[2] = l;
                     ref[3] = (int32_t)(seg_lo + hl);
                 }
                 if (ok && dc <= p.chi2_cut) insert(dc, hl, row);
             }
         }
-        if (valid) {  // the N best hit children for the merge
-            const int cnt = min(n_list, N);
-            s_lcnt[me] = cnt;
-#pragma unroll
-            for (int k = 0; k < kMaxN; ++k)
-                if (k < cnt) {
-                    s_lc[(w * N + k) * 32 + lane] = lc[k];
-                    s_lh[(w * N + k) * 32 + lane] = lh[k];
-                    if (MODE == kModeLog) s_lr[(w * N + k) * 32 + lane] = lr[k];
-                }
-        }
-        __syncthreads();
-        // ---------------------------------------------------------------- S
-        if (w == 0) {
-            // children keys: k64 = (63 - hits) << 32 | chi2 bits (non-negative
-            // floats order as their bit patterns), k32 = parent slot << 27 |
-            // (hit index + 1), 0 for the hole; the head of slot q is its best
-            // listed hit child, then its hole child
-            uint32_t khi[kMaxN], klo[kMaxN], k32[kMaxN];
-            int head[kMaxN];
-            auto head_key = [&](int q, int h, uint32_t &hi, uint32_t &lo, uint32_t &kk) {
-                const int cnt = s_lcnt[q * 32 + lane];
-                const int nh = s_nh[q * 32 + lane];
-                if (h < cnt) {
-                    hi = (uint32_t)(63 - (nh + 1));
-                    lo = __float_as_uint(s_lc[(q * N + h) * 32 + lane]);
-                    kk = ((uint32_t)q << 27) | (s_lh[(q * N + h) * 32 + lane] + 1u);
-                } else if (h == cnt) {
-                    hi = (uint32_t)(63 - nh);
-                    lo = __float_as_uint(s_chi2[q * 32 + lane]);
-                    kk = (uint32_t)q << 27;
-                } else {
-                    hi = lo = kk = kNoKey;
-                }
-            };
-#pragma unroll
-            for (int q = 0; q < kMaxN; ++q) {
-                head[q] = 0;
-                khi[q] = klo[q] = k32[q] = kNoKey;
-                if (q < nc) head_key(q, 0, khi[q], klo[q], k32[q]);
+        // merge the group's lists: N rounds of a group arg-min; the head of a
+        // lane is its best hit child, then its hole child
+        int taken = 0;  // hit children of this lane already selected
+        bool hole_taken = false;
+        unsigned long long my64 = 0;
+        uint32_t my32 = kNoKey;
+        int new_parent = -1;
+        uint32_t new_hit = 0;  // hit index + 1, 0 = hole
+        float new_chi2 = 0.0f;
+        int new_nhits = 0;
+        int n_new = 0;
+        for (int r = 0; r < N; ++r) {
+            // head of this lane
+            if (valid && taken < N && lh[0] != kNoKey) {
+                my64 = ((unsigned long long)(63 - (nhits + 1)) << 32) | __float_as_uint(chi2 + lc[0]);
+                my32 = ((uint32_t)slot << 27) | (lh[0] + 1u);
+            } else if (valid && !hole_taken) {
+                my64 = ((unsigned long long)(63 - nhits) << 32) | __float_as_uint(chi2);
+                my32 = (uint32_t)slot << 27;
+            } else {
+                my64 = ~0ull;
+                my32 = kNoKey;
             }
-            int r = 0;
-            for (; r < N; ++r) {
-                uint32_t bhi = khi[0], blo = klo[0], b32 = k32[0];
+            unsigned long long b64 = my64;
+            uint32_t b32 = my32;
 #pragma unroll
-                for (int q = 1; q < kMaxN; ++q) {
-                    const bool less = khi[q] < bhi || (khi[q] == bhi && (klo[q] < blo || (klo[q] == blo && k32[q] < b32)));
-                    bhi = less ? khi[q] : bhi;
-                    blo = less ? klo[q] : blo;
-                    b32 = less ? k32[q] : b32;
+            for (int d = 1; d < G; d <<= 1) {
+                unsigned long long o64;
+                uint32_t o32;
+                if constexpr ((G & (G - 1)) == 0) {  // butterfly within a power-of-two group
+                    o64 = __shfl_xor_sync(gmask, b64, d, G);
+                    o32 = __shfl_xor_sync(gmask, b32, d, G);
+                } else {  // G = 6: pairs, then slots 0-3, then the two halves crossed
+                    const int ps = d == 1 ? (slot ^ 1) : d == 2 ? (slot < 4 ? slot ^ 2 : slot)
+                                                                : (slot < 4 ? 4 + (slot & 1) : slot - 4);
+                    const int src_lane = lane_ok ? gbase + ps : lane;
+                    o64 = __shfl_sync(gmask, b64, src_lane, 32);
+                    o32 = __shfl_sync(gmask, b32, src_lane, 32);
                 }
-                if (b32 == kNoKey) break;
-                s_sel[r * 32 + lane] = b32;
-                s_sel_chi2[r * 32 + lane] = __uint_as_float(blo);
-                s_sel_nh[r * 32 + lane] = 63 - (int)bhi;
-                const int q = (int)(b32 >> 27);
-                int hq = 0;
-#pragma unroll
-                for (int k = 0; k < kMaxN; ++k) hq = k == q ? head[k] : hq;
-                if (MODE == kModeLog && (b32 & 0x7ffffffu)) {
-                    const uint32_t row = s_lr[(q * N + hq) * 32 + lane];
-                    if (row != kNoKey) p.log_y[row] = 1.0f;  // the pair survives
+                if (key_less(o64, o32, b64, b32)) {
+                    b64 = o64;
+                    b32 = o32;
                 }
-                uint32_t nhi, nlo, n32;
-                head_key(q, hq + 1, nhi, nlo, n32);
+            }
+            if (b32 == kNoKey) break;
+            const int win_slot = (int)(b32 >> 27);
+            if (slot == r) {
+                new_parent = win_slot;
+                new_hit = b32 & 0x7ffffffu;
+                new_nhits = 63 - (int)(b64 >> 32);
+                new_chi2 = __uint_as_float((uint32_t)(b64 & 0xffffffffu));
+            }
+            if (slot == win_slot) {
+                if ((b32 & 0x7ffffffu) != 0u) {  // pop the head of the list
+                    if (MODE == kModeLog && lr[0] != kNoKey) p.log_y[lr[0]] = 1.0f;  // the pair survives
 #pragma unroll
-                for (int k = 0; k < kMaxN; ++k)
-                    if (k == q) {
-                        head[k] = hq + 1;
-                        khi[k] = nhi;
-                        klo[k] = nlo;
-                        k32[k] = n32;
+                    for (int k = 0; k < kMaxN - 1; ++k) {
+                        lc[k] = lc[k + 1];
+                        lh[k] = lh[k + 1];
+                        lr[k] = lr[k + 1];
                     }
+                    lc[kMaxN - 1] = INFINITY;
+                    lh[kMaxN - 1] = kNoKey;
+                    lr[kMaxN - 1] = kNoKey;
+                    ++taken;
+                } else {
+                    hole_taken = true;
+                }
             }
-            s_ncand[lane] = r;
+            ++n_new;
         }
-        __syncthreads();
-        // ---------------------------------------------------------------- U
-        const int nn = s_ncand[lane];
-        const uint32_t e = w < nn ? s_sel[me] : 0u;
-        const int par = w < nn ? (int)(e >> 27) : w;
-        {
-            const float *pcol = st + par * kSlotSize * 32 + lane;
+        // each lane takes over child `slot` from its parent lane
+        const int src = gbase + (new_parent >= 0 ? new_parent : slot);
+        float px[6], pc[21];
 #pragma unroll
-            for (int i = 0; i < 6; ++i) x[i] = pcol[(kSlotX + i) * 32];
+        for (int i = 0; i < 6; ++i) px[i] = __shfl_sync(gmask, x[i], src, 32);
 #pragma unroll
-            for (int i = 0; i < 21; ++i) c[i] = pcol[(kSlotC + i) * 32];
-            flags = s_flags[par * 32 + lane];
-            chi2 = s_sel_chi2[me];
-            nhits = s_sel_nh[me];
-        }
-        __syncthreads();  // every parent state is read before a slot becomes an update's scratch
-        if (w < nn) {
-            const uint32_t h = e & 0x7ffffffu;
-            if (h) {
+        for (int i = 0; i < 21; ++i) pc[i] = __shfl_sync(gmask, c[i], src, 32);
+        const int pstop = __shfl_sync(gmask, (int)stopped, src, 32);
+        const uint32_t pflags = __shfl_sync(gmask, flags, src, 32);
+        nc = n_new;
+        if (slot < nc) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) x[i] = px[i];
+#pragma unroll
+            for (int i = 0; i < 21; ++i) c[i] = pc[i];
+            stopped = pstop != 0;
+            flags = pflags;
+            chi2 = new_chi2;
+            nhits = new_nhits;
+            if (new_hit) {
+                const int64_t hg = seg_lo + (new_hit - 1u);
                 float m[3], v[6], d;
-                load_hit(h - 1u, m, v);
-                const int stt = update(x, c, m, v, p.rt, &d, col, 32);
-                if (stt == 1) flags |= KF_FLAG_INVERSION_FAILED;
-                if (stt >= 2) flags |= KF_FLAG_FP64_PATH;
-                if (stt == 3) flags |= KF_FLAG_PSD_REPAIRED;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) m[i] = p.hit_pos[i * p.H + hg];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) v[i] = p.hit_cov[i * p.H + hg];
+                const int st = update(x, c, m, v, p.rt, &d, slots + threadIdx.x, 128);
+                if (st == 1) flags |= KF_FLAG_INVERSION_FAILED;
+                if (st >= 2) flags |= KF_FLAG_FP64_PATH;
+                if (st == 3) flags |= KF_FLAG_PSD_REPAIRED;
             }
-            s_bp[(l * N + w) * 32 + lane] = (int32_t)e;
+            bp[l * 128 + threadIdx.x] = (int32_t)(((uint32_t)new_parent << 27) | new_hit);
         }
-        nc = nn;
+        __syncwarp();
     }
-    __syncthreads();
     if (!seed_ok) return;
-    const int64_t sj = s * N + w;
-    const bool have = w < nc;
+    const int N_ = p.N;
+    const int64_t sj = s * N_ + slot;
+    if (slot < N_) {
+        const bool have = slot < nc;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) p.out_state[i * p.S * N + sj] = have ? x[i] : 0.0f;
+        for (int i = 0; i < 6; ++i) p.out_state[i * p.S * N_ + sj] = have ? x[i] : 0.0f;
 #pragma unroll
-    for (int i = 0; i < 21; ++i) p.out_cov[i * p.S * N + sj] = have ? c[i] : 0.0f;
-    p.out_chi2[sj] = have ? chi2 : 0.0f;
-    p.out_nhits[sj] = (int16_t)(have ? nhits : -1);
-    p.out_flags[sj] = have ? (flags & ~kStoppedBit) : 0u;
-    int cur = w;
-    for (int l = L - 1; l >= 0; --l) {
-        int32_t out = -1;
-        if (have) {
-            const uint32_t e = (uint32_t)s_bp[(l * N + cur) * 32 + lane];
-            const uint32_t h = e & 0x7ffffffu;
-            if (h) out = (int32_t)(p.ev_off[(int64_t)ev * (L + 1) + l] + (h - 1u));
-            cur = (int)(e >> 27);
+        for (int i = 0; i < 21; ++i) p.out_cov[i * p.S * N_ + sj] = have ? c[i] : 0.0f;
+        p.out_chi2[sj] = have ? chi2 : 0.0f;
+        p.out_nhits[sj] = (int16_t)(have ? nhits : -1);
+        p.out_flags[sj] = have ? flags : 0u;
+        int cur = slot;
+        for (int l = L - 1; l >= 0; --l) {
+            int32_t out = -1;
+            if (have) {
+                const uint32_t e = (uint32_t)bp[l * 128 + (threadIdx.x - slot) + cur];
+                const uint32_t h = e & 0x7ffffffu;
+                if (h) out = (int32_t)(p.hit_base + p.ev_off[(int64_t)ev * (L + 1) + l] + (h - 1u));
+                cur = (int)(e >> 27);
+            }
+            p.out_hit[sj * L + l] = out;
         }
-        p.out_hit[sj * L + l] = out;
     }
 }
 
@@ -676,12 +624,264 @@ using namespace kf;
 
 namespace {
 
+// (n_phi, n_z) bin grids the build autotuner tries (at most 16,384 bins)
+constexpr int kBinGrids[][2] = {{256, 64}, {512, 32}, {128, 64}, {256, 32}, {128, 128}};
+
+int size_class(int64_t n)
+{
+    int c = 0;
+    while ((int64_t(1) << (c + 1)) <= n && c < 40) ++c;
+    return c;
+}
+
 struct BuildLog {
     float *features, *labels;
     int32_t *ref;
     int64_t capacity;
     uint64_t *count;
 };
+
+template <class T>
+bool grow(T **ptr, size_t &cap, size_t need)
+{
+    if (need <= cap) return true;
+    cudaFree(*ptr);
+    *ptr = nullptr;
+    cap = 0;
+    if (cudaMalloc((void **)ptr, std::max<size_t>(need, 1) * sizeof(T)) != cudaSuccess) return false;
+    cap = need;
+    return true;
+}
+
+// Segment bounds of the n_events rows of hit_offsets [n_events][L + 1], less
+// `shift`: out [n_events L + 1].  Returns the largest segment.
+int64_t segment_bounds(const int64_t *hit_offsets, int n_events, int L, int64_t shift, int64_t *out)
+{
+    const size_t n_seg = (size_t)n_events * L;
+    for (int e = 0; e < n_events; ++e)
+        for (int l = 0; l < L; ++l) out[(size_t)e * L + l] = hit_offsets[(int64_t)e * (L + 1) + l] - shift;
+    out[n_seg] = hit_offsets[(int64_t)(n_events - 1) * (L + 1) + L] - shift;
+    int64_t m = 0;
+    for (size_t i = 0; i < n_seg; ++i) m = std::max<int64_t>(m, out[i + 1] - out[i]);
+    return m;
+}
+
+// Bins per (event, layer) the build needs room for: the grid asked for, else
+// the largest the tuner tries.
+int bins_needed(const kf_options &o)
+{
+    int nb = 0;
+    for (const auto &gr : kBinGrids)
+        if ((!o.n_phi_bins || o.n_phi_bins == gr[0]) && (!o.n_z_bins || o.n_z_bins == gr[1]))
+            nb = std::max(nb, gr[0] * gr[1]);
+    return std::max(nb, std::max(o.n_phi_bins, 1) * std::max(o.n_z_bins, 1));
+}
+
+// Grow the binning scratch for n_events events of L layers and n_hits hits.
+bool reserve_bins(BuildState *st, const kf_options &o, int n_events, int L, int64_t n_hits)
+{
+    const size_t n_seg = (size_t)n_events * L;
+    const int nb = bins_needed(o);
+    return grow(&st->bkey, st->hit_capacity, (size_t)n_hits) &&
+           grow(&st->bin_off, st->bin_capacity, n_seg * (nb + 1)) && grow(&st->bin_cnt, st->cnt_capacity, n_seg * nb);
+}
+
+// One build on device buffers: events [0, n_events) of the batch (ev_off, the
+// batch's rows of hit_offsets less its first hit, and their segment bounds,
+// both on the device), its hits and seeds; written hit indices gain hit_base.
+struct BuildBatch {
+    int n_events;
+    const int64_t *ev_off, *seg_off;
+    int64_t max_seg;
+    const float *hit_pos, *hit_cov;
+    int64_t n_hits, n_seeds;
+    const int32_t *seed_event;
+    const float *seed_state, *seed_cov;
+    const int8_t *seed_charge;
+    int32_t *out_hit;
+    float *out_chi2;
+    int16_t *out_nhits;
+    float *out_state, *out_cov;
+    uint32_t *out_flags;
+    int event_base;
+    int64_t hit_base;
+};
+
+// Binning and the clone engine for one batch, in the tuned shape (tuned now,
+// synchronously, for a new workload class).
+int build_run(kf_context *ctx, const FitGeom &g, const kf_options &o, const BuildBatch &b, const BuildLog *log,
+              cudaStream_t stream)
+{
+    BuildState *st = context_build_state(ctx);
+    const int L = g.L;
+    const size_t n_seg = (size_t)b.n_events * L;
+    if (!reserve_bins(st, o, b.n_events, L, b.n_hits))
+        return set_error(ctx, KF_ERR_NOMEM, "could not allocate the build's scratch");
+    const __nv_bfloat16 *W1 = nullptr, *W2 = nullptr;
+    const float *w32 = nullptr;
+    if (o.use_proposal) proposal_weights(ctx, &W1, &W2, &w32);
+    BuildParams p;
+    p.g = g;
+    p.rt = make_routing(o);
+    p.N = o.max_cands;
+    p.chi2_cut = o.chi2_cut;
+    p.nsigma = o.window_nsigma;
+    p.sig_rphi2 = o.hit_sigma_rphi * o.hit_sigma_rphi;
+    p.sig_z2 = o.hit_sigma_z * o.hit_sigma_z;
+    p.max_dphi = o.window_max_dphi;
+    p.max_dz = o.window_max_dz;
+    p.S = b.n_seeds;
+    p.H = b.n_hits;
+    p.n_events = b.n_events;
+    p.event_base = b.event_base;
+    p.hit_base = b.hit_base;
+    p.ev_off = b.ev_off;
+    p.hit_pos = b.hit_pos;
+    p.hit_cov = b.hit_cov;
+    p.bkey = st->bkey;
+    p.bin_off = st->bin_off;
+    p.seed_event = b.seed_event;
+    p.seed_state = b.seed_state;
+    p.seed_cov = b.seed_cov;
+    p.seed_charge = b.seed_charge;
+    p.out_hit = b.out_hit;
+    p.out_chi2 = b.out_chi2;
+    p.out_nhits = b.out_nhits;
+    p.out_state = b.out_state;
+    p.out_cov = b.out_cov;
+    p.out_flags = b.out_flags;
+    p.log_f = log ? log->features : nullptr;
+    p.log_y = log ? log->labels : nullptr;
+    p.log_ref = log ? log->ref : nullptr;
+    p.log_n = log ? reinterpret_cast<unsigned long long *>(log->count) : nullptr;
+    p.log_cap = log ? (unsigned long long)log->capacity : 0ull;
+    p.topk = o.topk;
+    p.mlp_W1 = W1;
+    p.mlp_W2 = W2;
+    p.mlp_w32 = w32;
+    // lanes per seed: the smallest group that holds N candidates (6 for N = 5
+    // or 6, so that a warp holds five seeds instead of four)
+    const int G = p.N == 1 ? 1 : p.N <= 2 ? 2 : p.N <= 4 ? 4 : p.N <= 6 ? 6 : 8;
+    const int64_t seeds_per_block = 4 * (32 / G);
+    const unsigned grid = (unsigned)((b.n_seeds + seeds_per_block - 1) / seeds_per_block);
+    const int mode = o.use_proposal ? kModeProposal : log ? kModeLog : kModePlain;
+    const int smem = (int)(mode == kModeProposal ? build_smem_base(L) + kBuildSmemMlp
+                                                 : (size_t)L * 128 * sizeof(int32_t) + (size_t)kSlotSize * 128 * sizeof(float));
+    using Kernel = void (*)(const BuildParams);
+    static const Kernel table[5][3] = {
+        {build_kernel<1, kModePlain>, build_kernel<1, kModeLog>, build_kernel<1, kModeProposal>},
+        {build_kernel<2, kModePlain>, build_kernel<2, kModeLog>, build_kernel<2, kModeProposal>},
+        {build_kernel<4, kModePlain>, build_kernel<4, kModeLog>, build_kernel<4, kModeProposal>},
+        {build_kernel<6, kModePlain>, build_kernel<6, kModeLog>, build_kernel<6, kModeProposal>},
+        {build_kernel<8, kModePlain>, build_kernel<8, kModeLog>, build_kernel<8, kModeProposal>}};
+    const Kernel kern = table[G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 6 ? 3 : 4][mode];
+    // one build: the binning for the grid (n_phi, n_z), then the kernel
+    auto enqueue = [&](int nphi, int nz) -> cudaError_t {
+        const BinGrid bgr{nphi, nz, g.z_half};
+        cudaError_t e1 = bin_hits(b.seg_off, (int64_t)n_seg, b.max_seg, b.hit_pos, b.n_hits, bgr, st->bkey,
+                                  st->bin_off, st->bin_cnt, context_sm_count(ctx), stream);
+        if (e1 != cudaSuccess) return e1;
+        BuildParams q = p;
+        q.bg = bgr;
+        // the dynamic shared memory opt-in is a per-device attribute: set it
+        // on every call (a host-side attribute write, no stream work)
+        if ((e1 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+            return e1;
+        if (log && (e1 = cudaMemsetAsync(log->count, 0, sizeof(uint64_t), stream)) != cudaSuccess) return e1;
+        if (b.n_seeds > 0) kern<<<grid, 128, smem, stream>>>(q);
+        return cudaGetLastError();
+    };
+    // the shape: the one tuned for this workload class, or tuned now on the
+    // caller's own buffers (a build only reads its inputs and overwrites its
+    // outputs; the training log restarts its count)
+    const auto key = std::make_tuple(L, p.N, mode, size_class(b.n_seeds), size_class(b.n_hits), o.n_phi_bins, o.n_z_bins);
+    std::pair<int, int> shape;
+    cudaError_t e = cudaSuccess;
+    auto it = st->tuned.find(key);
+    if (it != st->tuned.end()) {
+        shape = it->second;
+    } else {
+        std::vector<std::pair<int, int>> cand;
+        for (const auto &gr : kBinGrids)
+            if ((!o.n_phi_bins || o.n_phi_bins == gr[0]) && (!o.n_z_bins || o.n_z_bins == gr[1]))
+                cand.emplace_back(gr[0], gr[1]);
+        if (cand.empty())  // a fixed grid outside the tuner's list
+            cand.emplace_back(o.n_phi_bins ? o.n_phi_bins : 256, o.n_z_bins ? o.n_z_bins : 64);
+        shape = cand[0];
+        if (cand.size() > 1) {
+            cudaEvent_t ta, tb;
+            cudaEventCreate(&ta);
+            cudaEventCreate(&tb);
+            float best = 1e30f;
+            for (const auto &c : cand) {
+                if ((e = enqueue(c.first, c.second)) != cudaSuccess) break;
+                cudaEventRecord(ta, stream);
+                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = enqueue(c.first, c.second);
+                cudaEventRecord(tb, stream);
+                if (e != cudaSuccess || (e = cudaEventSynchronize(tb)) != cudaSuccess) break;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, ta, tb);
+                if (ms < best) {
+                    best = ms;
+                    shape = c;
+                }
+            }
+            cudaEventDestroy(ta);
+            cudaEventDestroy(tb);
+            if (e != cudaSuccess) return cuda_error(ctx, e, "build tuning");
+        }
+        st->tuned[key] = shape;
+    }
+    if ((e = enqueue(shape.first, shape.second)) != cudaSuccess) return cuda_error(ctx, e, "build launch");
+    return KF_OK;
+}
+
+// Argument checks shared by the build entry points (pointers apart): the
+// geometry into *g, the options, the log, the sizes and, when there are
+// seeds, the offsets table (host).
+int check_build_args(kf_context *ctx, const kf_geometry *geom, const kf_options &o, int n_events,
+                     const int64_t *hit_offsets, int64_t n_hits, int64_t n_seeds, const BuildLog *log, FitGeom *g)
+{
+    int rc;
+    if ((rc = check_geometry(ctx, geom, g))) return rc;
+    if ((rc = check_options(ctx, o))) return rc;
+    if (o.max_cands < 1 || o.max_cands > 8) return set_error(ctx, KF_ERR_ARG, "max_cands must be 1..8");
+    if (!(o.chi2_cut > 0.0f) || !(o.window_nsigma > 0.0f) || !(o.hit_sigma_rphi >= 0.0f) || !(o.hit_sigma_z >= 0.0f) ||
+        !(o.window_max_dphi > 0.0f) || !(o.window_max_dz > 0.0f))
+        return set_error(ctx, KF_ERR_ARG,
+                         "chi2_cut, window_nsigma and the window caps must be positive, hit sigmas non-negative");
+    if (o.n_phi_bins < 0 || o.n_z_bins < 0 || (int64_t)o.n_phi_bins * o.n_z_bins > 16384)
+        return set_error(ctx, KF_ERR_ARG, "n_phi_bins x n_z_bins must be 1..16384 (0: tuned)");
+    if (o.use_proposal) {
+        if (log) return set_error(ctx, KF_ERR_ARG, "the training log records the plain build: use_proposal must be 0");
+        if (o.topk < 1 || o.topk > kMaxN) return set_error(ctx, KF_ERR_ARG, "topk must be 1..8");
+        if (!proposal_loaded(ctx)) return set_error(ctx, KF_ERR_ARG, "use_proposal needs weights (kf_proposal_load)");
+    }
+    if (log) {
+        if (log->capacity < 0) return set_error(ctx, KF_ERR_ARG, "log capacity must be >= 0");
+        if ((rc = check_ptr(ctx, log->count, 8, "log_count"))) return rc;
+        if (log->capacity > 0 && ((rc = check_ptr(ctx, log->features, 4, "log_features")) ||
+                                  (rc = check_ptr(ctx, log->labels, 4, "log_labels")) ||
+                                  (rc = check_ptr(ctx, log->ref, 4, "log_ref"))))
+            return rc;
+    }
+    if (n_events < 0 || n_seeds < 0 || n_hits < 0 || n_hits >= (int64_t(1) << 31))
+        return set_error(ctx, KF_ERR_ARG, "n_events, n_seeds must be >= 0 and n_hits < 2^31");
+    if (n_seeds == 0) return KF_OK;
+    if (n_events < 1 || !hit_offsets) return set_error(ctx, KF_ERR_ARG, "hit_offsets (host) needs n_events >= 1 rows");
+    const int L = g->L;
+    for (int e = 0; e < n_events; ++e) {
+        const int64_t *row = hit_offsets + (int64_t)e * (L + 1);
+        if (e > 0 && row[0] != hit_offsets[(int64_t)(e - 1) * (L + 1) + L])
+            return set_error(ctx, KF_ERR_ARG, "events must be stored back to back (event %d)", e);
+        for (int l = 0; l < L; ++l)
+            if (row[l] < 0 || row[l + 1] < row[l] || row[l + 1] > n_hits)
+                return set_error(ctx, KF_ERR_ARG, "hit_offsets row %d is not a non-decreasing run within n_hits", e);
+        if (row[L] - row[0] >= (int64_t(1) << 27))
+            return set_error(ctx, KF_ERR_ARG, "event %d holds 2^27 or more hits", e);
+    }
+    return KF_OK;
+}
 
 int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int64_t *hit_offsets,
                const float *hit_pos, const float *hit_cov, int64_t n_hits, int64_t n_seeds, const int32_t *seed_event,
@@ -695,33 +895,7 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
     else kf_options_default(&o);
     int rc;
     FitGeom g;
-    if ((rc = check_geometry(ctx, geom, &g))) return rc;
-    if ((rc = check_options(ctx, o))) return rc;
-    if (o.max_cands < 1 || o.max_cands > 8) return set_error(ctx, KF_ERR_ARG, "max_cands must be 1..8");
-    if (!(o.chi2_cut > 0.0f) || !(o.window_nsigma > 0.0f) || !(o.hit_sigma_rphi >= 0.0f) || !(o.hit_sigma_z >= 0.0f) ||
-        !(o.window_max_dphi > 0.0f) || !(o.window_max_dz > 0.0f))
-        return set_error(ctx, KF_ERR_ARG,
-                         "chi2_cut, window_nsigma and the window caps must be positive, hit sigmas non-negative");
-    if (o.n_phi_bins < 1 || o.n_z_bins < 1 || (int64_t)o.n_phi_bins * o.n_z_bins > 16384)
-        return set_error(ctx, KF_ERR_ARG, "n_phi_bins x n_z_bins must be 1..16384");
-    const __nv_bfloat16 *W1 = nullptr, *W2 = nullptr;
-    const float *w32 = nullptr;
-    if (o.use_proposal) {
-        if (log) return set_error(ctx, KF_ERR_ARG, "the training log records the plain build: use_proposal must be 0");
-        if (o.topk < 1 || o.topk > kMaxN) return set_error(ctx, KF_ERR_ARG, "topk must be 1..8");
-        if (!proposal_loaded(ctx)) return set_error(ctx, KF_ERR_ARG, "use_proposal needs weights (kf_proposal_load)");
-        proposal_weights(ctx, &W1, &W2, &w32);
-    }
-    if (log) {
-        if (log->capacity < 0) return set_error(ctx, KF_ERR_ARG, "log capacity must be >= 0");
-        if ((rc = check_ptr(ctx, log->count, 8, "log_count"))) return rc;
-        if (log->capacity > 0 && ((rc = check_ptr(ctx, log->features, 4, "log_features")) ||
-                                  (rc = check_ptr(ctx, log->labels, 4, "log_labels")) ||
-                                  (rc = check_ptr(ctx, log->ref, 4, "log_ref"))))
-            return rc;
-    }
-    if (n_events < 0 || n_seeds < 0 || n_hits < 0 || n_hits >= (int64_t(1) << 31))
-        return set_error(ctx, KF_ERR_ARG, "n_events, n_seeds must be >= 0 and n_hits < 2^31");
+    if ((rc = check_build_args(ctx, geom, o, n_events, hit_offsets, n_hits, n_seeds, log, &g))) return rc;
     if (n_seeds == 0) {
         if (log) {
             const cudaError_t e0 = cudaMemsetAsync(log->count, 0, sizeof(uint64_t), reinterpret_cast<cudaStream_t>(stream_));
@@ -729,18 +903,7 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
         }
         return KF_OK;
     }
-    if (n_events < 1 || !hit_offsets) return set_error(ctx, KF_ERR_ARG, "hit_offsets (host) needs n_events >= 1 rows");
     const int L = g.L;
-    for (int e = 0; e < n_events; ++e) {
-        const int64_t *row = hit_offsets + (int64_t)e * (L + 1);
-        if (e > 0 && row[0] != hit_offsets[(int64_t)(e - 1) * (L + 1) + L])
-            return set_error(ctx, KF_ERR_ARG, "events must be stored back to back (event %d)", e);
-        for (int l = 0; l < L; ++l)
-            if (row[l] < 0 || row[l + 1] < row[l] || row[l + 1] > n_hits)
-                return set_error(ctx, KF_ERR_ARG, "hit_offsets row %d is not a non-decreasing run within n_hits", e);
-        if (row[L] - row[0] >= (int64_t(1) << 27))
-            return set_error(ctx, KF_ERR_ARG, "event %d holds 2^27 or more hits", e);
-    }
     if (n_hits > 0 && ((rc = check_ptr(ctx, hit_pos, 4, "hit_pos")) || (rc = check_ptr(ctx, hit_cov, 4, "hit_cov"))))
         return rc;
     if ((rc = check_ptr(ctx, seed_event, 4, "seed_event")) || (rc = check_ptr(ctx, seed_state, 4, "seed_state")) ||
@@ -749,45 +912,15 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
         (rc = check_ptr(ctx, out_nhits, 2, "out_nhits")) || (rc = check_ptr(ctx, out_state, 4, "out_state")) ||
         (rc = check_ptr(ctx, out_cov, 4, "out_cov")) || (rc = check_ptr(ctx, out_flags, 4, "out_flags")))
         return rc;
-    int prev = -1;
-    cudaGetDevice(&prev);
-    if (prev != context_device(ctx)) cudaSetDevice(context_device(ctx));
-    struct Restore {
-        int prev;
-        ~Restore()
-        {
-            int cur = -1;
-            if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-        }
-    } restore{prev};
+    DeviceGuard dg(context_device(ctx));
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-
-    // scratch: binned hits, bin offsets, segment and event offsets
     BuildState *&st = context_build_state(ctx);
     if (!st) st = new BuildState;
-    const int nb = o.n_phi_bins * o.n_z_bins;
     const size_t n_seg = (size_t)n_events * L;
-    auto grow = [&](void **ptr, size_t &cap, size_t need, size_t elem) -> bool {
-        if (need <= cap) return true;
-        cudaFree(*ptr);
-        *ptr = nullptr;
-        cap = 0;
-        if (cudaMalloc(ptr, std::max<size_t>(need, 1) * elem) != cudaSuccess) return false;
-        cap = need;
-        return true;
-    };
-    bool ok = grow((void **)&st->bkey, st->hit_capacity, (size_t)n_hits, sizeof(float4));
-    ok = ok && grow((void **)&st->bin_off, st->bin_capacity, n_seg * (nb + 1), sizeof(int32_t));
-    ok = ok && grow((void **)&st->bin_cnt, st->cnt_capacity, n_seg * nb, sizeof(int32_t));
-    ok = ok && grow((void **)&st->seg_off, st->seg_capacity, n_seg + 1, sizeof(int64_t));
-    ok = ok && grow((void **)&st->ev_off, st->ev_capacity, (size_t)n_events * (L + 1), sizeof(int64_t));
-    if (!ok) return set_error(ctx, KF_ERR_NOMEM, "could not allocate the build's scratch");
+    if (!grow(&st->seg_off, st->seg_capacity, n_seg + 1) || !grow(&st->ev_off, st->ev_capacity, (size_t)n_events * (L + 1)))
+        return set_error(ctx, KF_ERR_NOMEM, "could not allocate the build's scratch");
     std::vector<int64_t> seg(n_seg + 1);
-    for (int e = 0; e < n_events; ++e)
-        for (int l = 0; l < L; ++l) seg[(size_t)e * L + l] = hit_offsets[(int64_t)e * (L + 1) + l];
-    seg[n_seg] = hit_offsets[(int64_t)(n_events - 1) * (L + 1) + L];
-    int64_t max_seg = 0;
-    for (size_t i = 0; i < n_seg; ++i) max_seg = std::max<int64_t>(max_seg, seg[i + 1] - seg[i]);
+    const int64_t max_seg = segment_bounds(hit_offsets, n_events, L, 0, seg.data());
     cudaError_t e = cudaMemcpyAsync(st->seg_off, seg.data(), (n_seg + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
                                     stream);
     if (e == cudaSuccess)
@@ -796,66 +929,10 @@ int build_impl(kf_context *ctx, const kf_geometry *geom, int n_events, const int
     if (e != cudaSuccess) return cuda_error(ctx, e, "offsets copy");
     // the host vector must outlive the asynchronous copy
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(ctx, e, "offsets copy");
-
-    BinGrid bg{o.n_phi_bins, o.n_z_bins, g.z_half};
-    if ((e = bin_hits(st->seg_off, (int64_t)n_seg, max_seg, hit_pos, n_hits, bg, st->bkey, st->bin_off, st->bin_cnt,
-                      context_sm_count(ctx), stream)) != cudaSuccess)
-        return cuda_error(ctx, e, "binning launch");
-
-    BuildParams p;
-    p.g = g;
-    p.rt = make_routing(o);
-    p.bg = bg;
-    p.N = o.max_cands;
-    p.chi2_cut = o.chi2_cut;
-    p.nsigma = o.window_nsigma;
-    p.sig_rphi2 = o.hit_sigma_rphi * o.hit_sigma_rphi;
-    p.sig_z2 = o.hit_sigma_z * o.hit_sigma_z;
-    p.max_dphi = o.window_max_dphi;
-    p.max_dz = o.window_max_dz;
-    p.S = n_seeds;
-    p.H = n_hits;
-    p.n_events = n_events;
-    p.ev_off = st->ev_off;
-    p.hit_pos = hit_pos;
-    p.hit_cov = hit_cov;
-    p.bkey = st->bkey;
-    p.bin_off = st->bin_off;
-    p.seed_event = seed_event;
-    p.seed_state = seed_state;
-    p.seed_cov = seed_cov;
-    p.seed_charge = seed_charge;
-    p.out_hit = out_hit_idx;
-    p.out_chi2 = out_chi2;
-    p.out_nhits = out_nhits;
-    p.out_state = out_state;
-    p.out_cov = out_cov;
-    p.out_flags = out_flags;
-    p.log_f = log ? log->features : nullptr;
-    p.log_y = log ? log->labels : nullptr;
-    p.log_ref = log ? log->ref : nullptr;
-    p.log_n = log ? reinterpret_cast<unsigned long long *>(log->count) : nullptr;
-    p.log_cap = log ? (unsigned long long)log->capacity : 0ull;
-    p.topk = o.topk;
-    p.mlp_W1 = W1;
-    p.mlp_W2 = W2;
-    p.mlp_w32 = w32;
-    if (log && (e = cudaMemsetAsync(log->count, 0, sizeof(uint64_t), stream)) != cudaSuccess)
-        return cuda_error(ctx, e, "log counter");
-    // one block per 32 seeds, one warp per candidate slot
-    const int mode = o.use_proposal ? kModeProposal : log ? kModeLog : kModePlain;
-    p.lay = clone_layout(p.N, L, mode);
-    const unsigned grid = (unsigned)((n_seeds + 31) / 32);
-    using Kernel = void (*)(const BuildParams);
-    static const Kernel table[3] = {clone_kernel<kModePlain>, clone_kernel<kModeLog>, clone_kernel<kModeProposal>};
-    // the dynamic shared memory opt-in is a per-device attribute: set it on
-    // every call (a host-side attribute write, no stream work)
-    if ((e = cudaFuncSetAttribute(table[mode], cudaFuncAttributeMaxDynamicSharedMemorySize, p.lay.total)) !=
-        cudaSuccess)
-        return cuda_error(ctx, e, "build kernel shared memory");
-    table[mode]<<<grid, 32 * p.N, p.lay.total, stream>>>(p);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(ctx, e, "build launch");
-    return KF_OK;
+    const BuildBatch bt{n_events, st->ev_off, st->seg_off, max_seg, hit_pos, hit_cov, n_hits, n_seeds, seed_event,
+                        seed_state, seed_cov, seed_charge, out_hit_idx, out_chi2, out_nhits, out_state, out_cov,
+                        out_flags, 0, 0};
+    return build_run(ctx, g, o, bt, log, stream);
 }
 
 }  // namespace
@@ -886,4 +963,231 @@ extern "C" int kf_build_tracks_logged(kf_context *ctx, const kf_geometry *geom, 
     return build_impl(ctx, geom, n_events, hit_offsets, hit_pos, hit_cov, n_hits, n_seeds, seed_event, seed_state,
                       seed_cov, seed_charge, out_hit_idx, out_chi2, out_nhits, out_state, out_cov, out_flags, opt,
                       stream, &log);
+}
+
+extern "C" int kf_build_tuned_shape(kf_context *ctx, int n_layers, int max_cands, int mode, int64_t n_seeds,
+                                    int64_t n_hits, int *n_phi_bins, int *n_z_bins)
+{
+    if (!ctx || !n_phi_bins || !n_z_bins) return KF_ERR_ARG;
+    BuildState *st = context_build_state(ctx);
+    if (st) {
+        auto it = st->tuned.find(std::make_tuple(n_layers, max_cands, mode, size_class(n_seeds), size_class(n_hits), 0, 0));
+        if (it != st->tuned.end()) {
+            *n_phi_bins = it->second.first;
+            *n_z_bins = it->second.second;
+            return KF_OK;
+        }
+    }
+    return set_error(ctx, KF_ERR_ARG, "no build of this class has been tuned yet");
+}
+
+namespace {
+
+// Byte offsets of one batch's device buffers (hits, seeds, outputs), each
+// array aligned to 256 bytes.
+struct HostBatchLayout {
+    size_t hit_pos, hit_cov, seed_event, seed_state, seed_cov, seed_charge, ev_off, seg_off, out_hit, out_chi2,
+        out_nhits, out_state, out_cov, out_flags, total;
+    HostBatchLayout(int64_t H, int64_t S, int E, int L, int N)
+    {
+        size_t o = 0;
+        auto take = [&](size_t bytes) {
+            const size_t at = o;
+            o += (bytes + 255) / 256 * 256;
+            return at;
+        };
+        hit_pos = take(3 * H * 4);
+        hit_cov = take(6 * H * 4);
+        seed_event = take(S * 4);
+        seed_state = take(6 * S * 4);
+        seed_cov = take(21 * S * 4);
+        seed_charge = take(S);
+        ev_off = take((size_t)E * (L + 1) * 8);
+        seg_off = take(((size_t)E * L + 1) * 8);
+        out_hit = take((size_t)S * N * L * 4);
+        out_chi2 = take((size_t)S * N * 4);
+        out_nhits = take((size_t)S * N * 2);
+        out_state = take((size_t)6 * S * N * 4);
+        out_cov = take((size_t)21 * S * N * 4);
+        out_flags = take((size_t)S * N * 4);
+        total = o;
+    }
+};
+
+// rows [r0, r0 + n) of `rows` arrays of row length `pitch` elements, between
+// host and device (dst pitch n); one strided copy
+template <class T>
+cudaError_t copy_rows(T *dst, size_t dpitch, const T *src, size_t spitch, int64_t n, int rows, cudaMemcpyKind kind,
+                      cudaStream_t stream)
+{
+    if (n <= 0) return cudaSuccess;
+    return cudaMemcpy2DAsync(dst, dpitch * sizeof(T), src, spitch * sizeof(T), (size_t)n * sizeof(T), rows, kind,
+                             stream);
+}
+
+}  // namespace
+
+extern "C" int kf_build_tracks_host(kf_context *ctx, const kf_geometry *geom, int n_events, const int64_t *hit_offsets,
+                                    const float *hit_pos, const float *hit_cov, int64_t n_hits, int64_t n_seeds,
+                                    const int32_t *seed_event, const float *seed_state, const float *seed_cov,
+                                    const int8_t *seed_charge, int32_t *out_hit_idx, float *out_chi2,
+                                    int16_t *out_nhits, float *out_state, float *out_cov, uint32_t *out_flags,
+                                    int events_per_batch, const kf_options *opt)
+{
+    if (!ctx) return KF_ERR_ARG;
+    kf_options o;
+    if (opt) o = *opt;
+    else kf_options_default(&o);
+    int rc;
+    FitGeom g;
+    if ((rc = check_build_args(ctx, geom, o, n_events, hit_offsets, n_hits, n_seeds, nullptr, &g))) return rc;
+    if (events_per_batch < 0) return set_error(ctx, KF_ERR_ARG, "events_per_batch must be >= 0");
+    if (n_seeds == 0) return KF_OK;
+    if (n_hits > 0 && ((rc = check_ptr(ctx, hit_pos, 4, "hit_pos")) || (rc = check_ptr(ctx, hit_cov, 4, "hit_cov"))))
+        return rc;
+    if ((rc = check_ptr(ctx, seed_event, 4, "seed_event")) || (rc = check_ptr(ctx, seed_state, 4, "seed_state")) ||
+        (rc = check_ptr(ctx, seed_cov, 4, "seed_cov")) || (rc = check_ptr(ctx, seed_charge, 1, "seed_charge")) ||
+        (rc = check_ptr(ctx, out_hit_idx, 4, "out_hit_idx")) || (rc = check_ptr(ctx, out_chi2, 4, "out_chi2")) ||
+        (rc = check_ptr(ctx, out_nhits, 2, "out_nhits")) || (rc = check_ptr(ctx, out_state, 4, "out_state")) ||
+        (rc = check_ptr(ctx, out_cov, 4, "out_cov")) || (rc = check_ptr(ctx, out_flags, 4, "out_flags")))
+        return rc;
+    for (int64_t i = 0; i < n_seeds; ++i)
+        if (seed_event[i] < 0 || seed_event[i] >= n_events || (i > 0 && seed_event[i] < seed_event[i - 1]))
+            return set_error(ctx, KF_ERR_ARG, "seed_event must be non-decreasing within 0..n_events-1 (seed %lld)",
+                             (long long)i);
+    const int L = g.L, N = o.max_cands;
+    const int B = events_per_batch ? events_per_batch : 16;
+    // batches of B events: their seed and hit ranges
+    struct Batch {
+        int e0, e1;
+        int64_t s0, s1, h0, h1;
+    };
+    std::vector<Batch> batches;
+    int64_t max_h = 0, max_s = 0;
+    for (int e0 = 0, si = 0; e0 < n_events; e0 += B) {
+        Batch bt;
+        bt.e0 = e0;
+        bt.e1 = std::min(e0 + B, n_events);
+        bt.s0 = si;
+        while (si < n_seeds && seed_event[si] < bt.e1) ++si;
+        bt.s1 = si;
+        bt.h0 = hit_offsets[(int64_t)bt.e0 * (L + 1)];
+        bt.h1 = hit_offsets[(int64_t)(bt.e1 - 1) * (L + 1) + L];
+        max_h = std::max(max_h, bt.h1 - bt.h0);
+        max_s = std::max(max_s, bt.s1 - bt.s0);
+        if (bt.s1 > bt.s0) batches.push_back(bt);
+    }
+    DeviceGuard dg(context_device(ctx));
+    BuildState *&st = context_build_state(ctx);
+    if (!st) st = new BuildState;
+    const HostBatchLayout lay(std::max<int64_t>(max_h, 1), std::max<int64_t>(max_s, 1), B, L, N);
+    const size_t pin_elems = ((size_t)B * L + 1) + (size_t)B * (L + 1);
+    bool ok = reserve_bins(st, o, B, L, max_h);
+    for (cudaStream_t *h : {&st->hs_in, &st->hs_run, &st->hs_out})
+        if (ok && !*h) ok = cudaStreamCreateWithFlags(h, cudaStreamNonBlocking) == cudaSuccess;
+    for (auto &sl : st->slot) {
+        if (!ok) break;
+        if (sl.dev_bytes < lay.total) {
+            cudaFree(sl.dev);
+            sl.dev = nullptr;
+            sl.dev_bytes = 0;
+            ok = cudaMalloc(&sl.dev, lay.total) == cudaSuccess;
+            if (ok) sl.dev_bytes = lay.total;
+        }
+        if (ok && sl.pin_elems < pin_elems) {
+            cudaFreeHost(sl.pin);
+            sl.pin = nullptr;
+            sl.pin_elems = 0;
+            ok = cudaMallocHost(&sl.pin, pin_elems * sizeof(int64_t)) == cudaSuccess;
+            if (ok) sl.pin_elems = pin_elems;
+        }
+        for (cudaEvent_t *ev : {&sl.in_done, &sl.built, &sl.out_done})
+            if (ok && !*ev) ok = cudaEventCreateWithFlags(ev, cudaEventDisableTiming) == cudaSuccess;
+        sl.used = false;
+    }
+    if (!ok) return set_error(ctx, KF_ERR_NOMEM, "could not allocate the host-buffer build's staging");
+    cudaError_t e = cudaSuccess;
+    for (size_t bi = 0; bi < batches.size() && e == cudaSuccess; ++bi) {
+        const Batch &bt = batches[bi];
+        BuildState::Slot &sl = st->slot[bi % 3];
+        const int E = bt.e1 - bt.e0;
+        const int64_t H = bt.h1 - bt.h0, S = bt.s1 - bt.s0;
+        char *d = sl.dev;
+        if (sl.used) {
+            // the slot's pinned offsets may be rewritten once their copy is done;
+            // its device buffers once the previous batch in it is built and read out
+            if ((e = cudaEventSynchronize(sl.in_done)) != cudaSuccess) break;
+            if ((e = cudaStreamWaitEvent(st->hs_in, sl.built, 0)) != cudaSuccess) break;
+            if ((e = cudaStreamWaitEvent(st->hs_run, sl.out_done, 0)) != cudaSuccess) break;
+        }
+        // host -> device: the batch's offsets (batch-local), hits and seeds
+        int64_t *seg = sl.pin, *evo = sl.pin + ((size_t)E * L + 1);
+        const int64_t max_seg = segment_bounds(hit_offsets + (int64_t)bt.e0 * (L + 1), E, L, bt.h0, seg);
+        for (int64_t i = 0; i < (int64_t)E * (L + 1); ++i) evo[i] = hit_offsets[(int64_t)bt.e0 * (L + 1) + i] - bt.h0;
+        cudaStream_t in = st->hs_in;
+        e = cudaMemcpyAsync(d + lay.seg_off, seg, ((size_t)E * L + 1) * 8, cudaMemcpyHostToDevice, in);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d + lay.ev_off, evo, (size_t)E * (L + 1) * 8, cudaMemcpyHostToDevice, in);
+        if (e == cudaSuccess)
+            e = copy_rows((float *)(d + lay.hit_pos), H, hit_pos + bt.h0, n_hits, H, 3, cudaMemcpyHostToDevice, in);
+        if (e == cudaSuccess)
+            e = copy_rows((float *)(d + lay.hit_cov), H, hit_cov + bt.h0, n_hits, H, 6, cudaMemcpyHostToDevice, in);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d + lay.seed_event, seed_event + bt.s0, S * 4, cudaMemcpyHostToDevice, in);
+        if (e == cudaSuccess)
+            e = copy_rows((float *)(d + lay.seed_state), S, seed_state + bt.s0, n_seeds, S, 6, cudaMemcpyHostToDevice,
+                          in);
+        if (e == cudaSuccess)
+            e = copy_rows((float *)(d + lay.seed_cov), S, seed_cov + bt.s0, n_seeds, S, 21, cudaMemcpyHostToDevice, in);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d + lay.seed_charge, seed_charge + bt.s0, S, cudaMemcpyHostToDevice, in);
+        if (e == cudaSuccess) e = cudaEventRecord(sl.in_done, in);
+        if (e != cudaSuccess) break;
+        // the build, on the run stream (the binning scratch is shared: builds run in order)
+        if ((e = cudaStreamWaitEvent(st->hs_run, sl.in_done, 0)) != cudaSuccess) break;
+        const BuildBatch b{E,
+                           (const int64_t *)(d + lay.ev_off),
+                           (const int64_t *)(d + lay.seg_off),
+                           max_seg,
+                           (const float *)(d + lay.hit_pos),
+                           (const float *)(d + lay.hit_cov),
+                           H,
+                           S,
+                           (const int32_t *)(d + lay.seed_event),
+                           (const float *)(d + lay.seed_state),
+                           (const float *)(d + lay.seed_cov),
+                           (const int8_t *)(d + lay.seed_charge),
+                           (int32_t *)(d + lay.out_hit),
+                           (float *)(d + lay.out_chi2),
+                           (int16_t *)(d + lay.out_nhits),
+                           (float *)(d + lay.out_state),
+                           (float *)(d + lay.out_cov),
+                           (uint32_t *)(d + lay.out_flags),
+                           bt.e0,
+                           bt.h0};
+        if ((rc = build_run(ctx, g, o, b, nullptr, st->hs_run))) return rc;
+        if ((e = cudaEventRecord(sl.built, st->hs_run)) != cudaSuccess) break;
+        // device -> host: the batch's outputs into the caller's rows
+        cudaStream_t out = st->hs_out;
+        if ((e = cudaStreamWaitEvent(out, sl.built, 0)) != cudaSuccess) break;
+        const int64_t SN = S * N, TN = n_seeds * N, s0N = bt.s0 * N;
+        e = cudaMemcpyAsync(out_hit_idx + s0N * L, d + lay.out_hit, (size_t)SN * L * 4, cudaMemcpyDeviceToHost, out);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out_chi2 + s0N, d + lay.out_chi2, (size_t)SN * 4, cudaMemcpyDeviceToHost, out);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out_nhits + s0N, d + lay.out_nhits, (size_t)SN * 2, cudaMemcpyDeviceToHost, out);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out_flags + s0N, d + lay.out_flags, (size_t)SN * 4, cudaMemcpyDeviceToHost, out);
+        if (e == cudaSuccess)
+            e = copy_rows(out_state + s0N, TN, (const float *)(d + lay.out_state), SN, SN, 6, cudaMemcpyDeviceToHost,
+                          out);
+        if (e == cudaSuccess)
+            e = copy_rows(out_cov + s0N, TN, (const float *)(d + lay.out_cov), SN, SN, 21, cudaMemcpyDeviceToHost, out);
+        if (e == cudaSuccess) e = cudaEventRecord(sl.out_done, out);
+        sl.used = true;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st->hs_out);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st->hs_run);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "host-buffer build");
+    return KF_OK;
 }

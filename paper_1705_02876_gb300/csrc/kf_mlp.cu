@@ -23,6 +23,7 @@ struct MlpState {
     float *loss = nullptr;                              // one accumulator
     float *w32 = nullptr;                               // loaded weights, FP32
     __nv_bfloat16 *W1 = nullptr, *W2 = nullptr;         // loaded weights, BF16, transposed and padded
+    unsigned *status = nullptr;                         // set by a tcgen05 scoring wait that expired
     bool loaded = false;
 };
 
@@ -36,6 +37,7 @@ void destroy_mlp_state(MlpState *s)
     cudaFree(s->w32);
     cudaFree(s->W1);
     cudaFree(s->W2);
+    cudaFree(s->status);
     delete s;
 }
 
@@ -209,6 +211,10 @@ __global__ void to_bf16_kernel(float *w32, __nv_bfloat16 *W1t, __nv_bfloat16 *W2
 }
 
 constexpr int kScoreWarps = 4, kScoreLd = 12;
+// kf_proposal_score's engine (KF_SCORE_AUTO), chosen by measurement on one
+// GB300: mma.sync below this many rows (at 65,536 rows 0.015 against 0.025
+// ms), tcgen05 from it on (1.24x faster at 2^20 rows, 1.68x at 2^24)
+constexpr int64_t kScoreTcMinRows = 262144;
 
 struct ScoreSmem {
     MlpSmemWeights w;
@@ -221,8 +227,8 @@ __global__ void __launch_bounds__(32 * kScoreWarps) mlp_score_kernel(const __nv_
                                                                      const float *w32, const float *X, int64_t n,
                                                                      float *logits)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    ScoreSmem &s = *reinterpret_cast<ScoreSmem *>(smem_raw);
+    extern __shared__ __align__(128) unsigned char score_smem_raw[];
+    ScoreSmem &s = *reinterpret_cast<ScoreSmem *>(score_smem_raw);
     mlp_load_weights(&s.w, W1, W2, w32);
     __syncthreads();
     const MlpWeightsRef mw{reinterpret_cast<const uint32_t *>(s.w.W1t), reinterpret_cast<const uint32_t *>(s.w.W2t),
@@ -239,6 +245,253 @@ __global__ void __launch_bounds__(32 * kScoreWarps) mlp_score_kernel(const __nv_
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same scoring on the fifth-generation tensor cores (tcgen05): one CTA of
+// 128 threads scores 128-row tiles.  The weights are staged once per CTA in
+// shared memory; per tile the rows' split inputs go to shared memory, one
+// thread issues the layer-1 products (hi and lo parts into one TMEM
+// accumulator, M = 128, N = 64, K = 16), the four warps read the accumulator
+// back from TMEM (warp w owns TMEM lanes 32w..32w+31, thread t row t), add the
+// bias, apply the ReLU, split the result and write it as the layer-2 A operand;
+// the layer-2 products (4 K-steps x hi/lo) accumulate into a second TMEM
+// region, which the warps read back for the 64 -> 1 dot product.
+//
+// Operands are K-major without swizzle, in core matrices of 8 rows x 16 bytes
+// (8 BF16 values): element (r, k) of a tile with K columns is at byte
+// ((r / 8) (K / 8) + k / 8) 128 + (r % 8) 16 + (k % 8) 2.  In the shared
+// memory descriptor the leading-dimension offset is the distance between core
+// matrices adjacent in K (128 B) and the stride-dimension offset the distance
+// between 8-row groups ((K / 8) 128 B).
+
+constexpr int kTcRows = 128, kTcCols = 128;  // rows per tile; TMEM columns (two 64-column accumulators)
+constexpr int kTcCtasPerSm = 4;               // 4 x 128 = the SM's 512 TMEM columns (and ~52 KB of
+                                              // shared memory each: a fifth cannot be resident)
+constexpr uint32_t kTcWaitLimit = 1u << 24;   // mbarrier polls before a wait gives up
+
+struct __align__(128) TcSmem {
+    uint8_t A1h[kTcRows * 32], A1l[kTcRows * 32];    // inputs, K = 16 (12 used)
+    uint8_t A2h[kTcRows * 128], A2l[kTcRows * 128];  // first hidden layer, K = 64
+    uint8_t B1[kMlpHid * 32];                         // W1^T: N = 64 x K = 16
+    uint8_t B2[kMlpHid * 128];                        // W2^T: N = 64 x K = 64
+    float b1[kMlpHid], b2[kMlpHid], W3[kMlpHid], b3;
+    unsigned long long mbar;
+    uint32_t taddr;
+};
+
+__device__ __forceinline__ uint32_t core_offset(int r, int k, int K)
+{
+    return (uint32_t)(((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Shared memory matrix descriptor (tcgen05): start address, leading- and
+// stride-dimension byte offsets (all >> 4), the fixed version bits 46..48 =
+// 0b001, base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t lbo, uint32_t sbo)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A
+// and B BF16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at
+// bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kMlpHid >> 3) << 17) |
+                              ((uint32_t)(kTcRows >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kTcIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tc_commit(unsigned long long *mbar)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(mbar);
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(a) : "memory");
+}
+
+// Wait for the mbarrier's phase `parity` to complete, polling at most
+// kTcWaitLimit times; false if it did not.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *mbar, uint32_t parity)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(mbar);
+    for (uint32_t i = 0; i < kTcWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void st_shared_v4(uint8_t *p, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
+{
+    *reinterpret_cast<uint4 *>(p) = make_uint4(a, b, c, d);
+}
+
+__global__ void __launch_bounds__(kTcRows) mlp_score_tc_kernel(const float *w32, const float *X, int64_t n,
+                                                               float *logits, unsigned *status)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    TcSmem &s = *reinterpret_cast<TcSmem *>(tc_smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // weights: W1^T and W2^T in BF16, K-major core matrices
+    for (int i = tid; i < kMlpHid * 16; i += kTcRows) {
+        const int nn = i >> 4, k = i & 15;
+        const __nv_bfloat16 v = __float2bfloat16(k < kMlpIn ? w32[kOffW1 + k * kMlpHid + nn] : 0.0f);
+        *reinterpret_cast<__nv_bfloat16 *>(s.B1 + core_offset(nn, k, 16)) = v;
+    }
+    for (int i = tid; i < kMlpHid * kMlpHid; i += kTcRows) {
+        const int nn = i >> 6, k = i & 63;
+        *reinterpret_cast<__nv_bfloat16 *>(s.B2 + core_offset(nn, k, 64)) =
+            __float2bfloat16(w32[kOffW2 + k * kMlpHid + nn]);
+    }
+    for (int i = tid; i < kMlpHid; i += kTcRows) {
+        s.b1[i] = w32[kOffB1 + i];
+        s.b2[i] = w32[kOffB2 + i];
+        s.W3[i] = w32[kOffW3 + i];
+    }
+    if (tid == 0) {
+        s.b3 = w32[kOffB3];
+        const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&s.mbar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        const uint32_t a = (uint32_t)__cvta_generic_to_shared(&s.taddr);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(a), "n"(kTcCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the staged weights, for the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s.taddr;
+    const uint32_t d1 = tmem, d2 = tmem + kMlpHid;      // accumulators: columns 0..63 and 64..127
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lanes
+    uint32_t parity = 0;
+    bool failed = false;
+    const int64_t tiles = (n + kTcRows - 1) / kTcRows;
+    // row `tid` of a tile's inputs; the next tile's are loaded while the
+    // current tile's products run
+    auto load_row = [&](int64_t tile, float f[kMlpIn]) {
+        const int64_t row = tile * kTcRows + tid;
+#pragma unroll
+        for (int i = 0; i < kMlpIn; ++i) f[i] = (tile < tiles && row < n) ? __ldcs(X + row * kMlpIn + i) : 0.0f;
+    };
+    float fin[kMlpIn];
+    load_row(blockIdx.x, fin);
+    for (int64_t tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
+        const int64_t row = tile * kTcRows + tid;
+        // inputs of row `tid`, split into BF16 hi and lo
+        float f[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) f[i] = i < kMlpIn ? fin[i] : 0.0f;
+        uint32_t h[8], l[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) split_bf16x2(f[2 * i], f[2 * i + 1], h[i], l[i]);
+#pragma unroll
+        for (int kg = 0; kg < 2; ++kg) {
+            st_shared_v4(s.A1h + core_offset(tid, kg * 8, 16), h[4 * kg], h[4 * kg + 1], h[4 * kg + 2], h[4 * kg + 3]);
+            st_shared_v4(s.A1l + core_offset(tid, kg * 8, 16), l[4 * kg], l[4 * kg + 1], l[4 * kg + 2], l[4 * kg + 3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc_mma(d1, smem_desc(s.A1h, 128, 256), smem_desc(s.B1, 128, 256), 0u);
+            tc_mma(d1, smem_desc(s.A1l, 128, 256), smem_desc(s.B1, 128, 256), 1u);
+            tc_commit(&s.mbar);
+        }
+        load_row(tile + gridDim.x, fin);
+        bool ok = mbar_wait(&s.mbar, parity);
+        parity ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // layer 1 epilogue: bias, ReLU, split -> layer-2 A operand (row tid)
+#pragma unroll
+        for (int c0 = 0; c0 < kMlpHid; c0 += 16) {
+            float a[16];
+            tmem_ld16(d1 + lane_base + c0, a);
+            uint32_t hh[8], ll[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                split_bf16x2(fmaxf(a[2 * i] + s.b1[c0 + 2 * i], 0.0f), fmaxf(a[2 * i + 1] + s.b1[c0 + 2 * i + 1], 0.0f),
+                             hh[i], ll[i]);
+#pragma unroll
+            for (int kg = 0; kg < 2; ++kg) {
+                st_shared_v4(s.A2h + core_offset(tid, c0 + kg * 8, 64), hh[4 * kg], hh[4 * kg + 1], hh[4 * kg + 2],
+                             hh[4 * kg + 3]);
+                st_shared_v4(s.A2l + core_offset(tid, c0 + kg * 8, 64), ll[4 * kg], ll[4 * kg + 1], ll[4 * kg + 2],
+                             ll[4 * kg + 3]);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {  // K-step ks: core matrices 2ks, 2ks + 1 along K
+                const uint64_t b = smem_desc(s.B2 + ks * 256, 128, 1024);
+                tc_mma(d2, smem_desc(s.A2h + ks * 256, 128, 1024), b, ks > 0 ? 1u : 0u);
+                tc_mma(d2, smem_desc(s.A2l + ks * 256, 128, 1024), b, 1u);
+            }
+            tc_commit(&s.mbar);
+        }
+        ok = mbar_wait(&s.mbar, parity);
+        parity ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // layer 2 epilogue: bias, ReLU, the 64 -> 1 dot product
+        float z = s.b3;
+#pragma unroll
+        for (int c0 = 0; c0 < kMlpHid; c0 += 16) {
+            float a[16];
+            tmem_ld16(d2 + lane_base + c0, a);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) z = fmaf(s.W3[c0 + i], fmaxf(a[i] + s.b2[c0 + i], 0.0f), z);
+        }
+        if (row < n) logits[row] = z;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // TMEM read and shared operands consumed before the next tile reuses them
+    }
+    if (failed) {
+        // a product did not complete in time: report it, give whatever is
+        // still in flight a bounded while to land, then release TMEM
+        if (tid == 0) atomicOr(status, 1u);
+        mbar_wait(&s.mbar, parity);
+        __syncthreads();
+    }
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTcCols));
+}
+
 int ensure_state(kf_context *ctx, MlpState **out)
 {
     MlpState *&s = context_mlp_state(ctx);
@@ -250,7 +503,9 @@ int ensure_state(kf_context *ctx, MlpState **out)
                   cudaMalloc(&s->loss, sizeof(float)) == cudaSuccess &&
                   cudaMalloc(&s->w32, kMlpParams * sizeof(float)) == cudaSuccess &&
                   cudaMalloc(&s->W1, kW1Elems * sizeof(__nv_bfloat16)) == cudaSuccess &&
-                  cudaMalloc(&s->W2, kW2Elems * sizeof(__nv_bfloat16)) == cudaSuccess;
+                  cudaMalloc(&s->W2, kW2Elems * sizeof(__nv_bfloat16)) == cudaSuccess &&
+                  cudaMalloc(&s->status, sizeof(unsigned)) == cudaSuccess &&
+                  cudaMemset(s->status, 0, sizeof(unsigned)) == cudaSuccess;
         if (!ok) {
             destroy_mlp_state(s);
             s = nullptr;
@@ -378,27 +633,60 @@ int kf_load_proposal(kf_context *ctx, const void *weights, size_t bytes)
     return kf_proposal_load(ctx, static_cast<const float *>(weights), nullptr);
 }
 
-int kf_proposal_score(kf_context *ctx, const float *features, int64_t n, float *logits, kf_stream stream_)
+int kf_proposal_score_with(kf_context *ctx, const float *features, int64_t n, float *logits, int engine,
+                           kf_stream stream_)
 {
     if (!ctx) return KF_ERR_ARG;
     if (!proposal_loaded(ctx)) return set_error(ctx, KF_ERR_ARG, "no proposal weights loaded (kf_proposal_load)");
     if (n < 0) return set_error(ctx, KF_ERR_ARG, "n must be >= 0");
+    if (engine != KF_SCORE_AUTO && engine != KF_SCORE_MMA_SYNC && engine != KF_SCORE_TCGEN05)
+        return set_error(ctx, KF_ERR_ARG, "engine must be KF_SCORE_AUTO, KF_SCORE_MMA_SYNC or KF_SCORE_TCGEN05");
     if (n == 0) return KF_OK;
     int rc;
     if ((rc = check_ptr(ctx, features, 4, "features")) || (rc = check_ptr(ctx, logits, 4, "logits"))) return rc;
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     MlpState *s = context_mlp_state(ctx);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(mlp_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ScoreSmem));
-        attr = true;
+    DeviceGuard dg(context_device(ctx));
+    if (engine == KF_SCORE_AUTO) engine = n >= kScoreTcMinRows ? KF_SCORE_TCGEN05 : KF_SCORE_MMA_SYNC;
+    cudaError_t e;
+    if (engine == KF_SCORE_TCGEN05) {
+        if ((e = cudaFuncSetAttribute(mlp_score_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(TcSmem))) != cudaSuccess)
+            return cuda_error(ctx, e, "tcgen05 scoring shared memory");
+        const int64_t tiles = (n + kTcRows - 1) / kTcRows;
+        const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)context_sm_count(ctx) * kTcCtasPerSm);
+        mlp_score_tc_kernel<<<grid, kTcRows, sizeof(TcSmem), stream>>>(s->w32, features, n, logits, s->status);
+    } else {
+        if ((e = cudaFuncSetAttribute(mlp_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(ScoreSmem))) != cudaSuccess)
+            return cuda_error(ctx, e, "scoring shared memory");
+        const int64_t chunks = (n + 31) / 32;
+        const unsigned grid = (unsigned)std::min<int64_t>((chunks + kScoreWarps - 1) / kScoreWarps,
+                                                          (int64_t)context_sm_count(ctx) * 8);
+        mlp_score_kernel<<<grid, 32 * kScoreWarps, sizeof(ScoreSmem), stream>>>(s->W1, s->W2, s->w32, features, n,
+                                                                                logits);
     }
-    const int64_t chunks = (n + 31) / 32;
-    const unsigned grid = (unsigned)std::min<int64_t>((chunks + kScoreWarps - 1) / kScoreWarps,
-                                                      (int64_t)context_sm_count(ctx) * 8);
-    mlp_score_kernel<<<grid, 32 * kScoreWarps, sizeof(ScoreSmem), stream>>>(s->W1, s->W2, s->w32, features, n, logits);
-    const cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     return e == cudaSuccess ? KF_OK : cuda_error(ctx, e, "proposal score launch");
+}
+
+int kf_proposal_score(kf_context *ctx, const float *features, int64_t n, float *logits, kf_stream stream)
+{
+    return kf_proposal_score_with(ctx, features, n, logits, KF_SCORE_AUTO, stream);
+}
+
+int kf_proposal_status(kf_context *ctx, int *expired)
+{
+    if (!ctx || !expired) return KF_ERR_ARG;
+    *expired = 0;
+    MlpState *s = context_mlp_state(ctx);
+    if (!s) return KF_OK;
+    DeviceGuard dg(context_device(ctx));
+    unsigned v = 0;
+    const cudaError_t e = cudaMemcpy(&v, s->status, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "proposal status");
+    *expired = v != 0;
+    return KF_OK;
 }
 
 }  // extern "C"

@@ -104,6 +104,13 @@ def load() -> ctypes.CDLL:
         L.kf_proposal_load.argtypes = [_vp, _vp, _vp]
         L.kf_load_proposal.argtypes = [_vp, _vp, ctypes.c_size_t]
         L.kf_proposal_score.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
+        L.kf_build_tracks_host.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int, _vp, _vp, _vp,
+                                           ctypes.c_int64, ctypes.c_int64] + [_vp] * 10 + \
+            [ctypes.c_int, ctypes.POINTER(Options)]
+        L.kf_build_tuned_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                           ctypes.c_int64] + [ctypes.POINTER(ctypes.c_int)] * 2
+        L.kf_proposal_score_with.argtypes = [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int, _vp]
+        L.kf_proposal_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
         L.kf_fit_tracks_noalloc.argtypes = [ctypes.POINTER(Geometry), ctypes.c_int64] + [_vp] * 11 + \
             [ctypes.POINTER(Options), _vp]
         _lib = L
@@ -175,6 +182,14 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def build_tuned_shape(self, n_layers: int, max_cands: int, mode: int, n_seeds: int, n_hits: int):
+        """(n_phi_bins, n_z_bins) the build autotuner picked, or None before a
+        build of that class."""
+        p_, z = ctypes.c_int(), ctypes.c_int()
+        rc = load().kf_build_tuned_shape(self._h, n_layers, max_cands, mode, n_seeds, n_hits, ctypes.byref(p_),
+                                         ctypes.byref(z))
+        return (p_.value, z.value) if rc == KF_OK else None
 
     def tuned_shape(self, n_layers: int, n_tracks: int):
         """(tracks per block, register cap, hit prefetch depth) the autotuner
@@ -359,6 +374,51 @@ def build_tracks(ctx: Context, geom: GeometryArgs, hit_offsets, hit_pos, hit_cov
     return out
 
 
+def build_outputs_host(n_seeds: int, max_cands: int, n_layers: int, pin: bool = True) -> dict:
+    """Host output tensors of kf_build_tracks_host (page-locked by default)."""
+    S, N, L = int(n_seeds), int(max_cands), int(n_layers)
+    z = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=pin)
+    return dict(hit=z((S, N, L), torch.int32), chi2=z((S, N), torch.float32), nhits=z((S, N), torch.int16),
+                state=z((6, S * N), torch.float32), cov=z((21, S * N), torch.float32), flags=z((S, N), torch.int32))
+
+
+def build_tracks_host(ctx: Context, geom: GeometryArgs, hit_offsets, hit_pos, hit_cov, seed_event, seed_state,
+                      seed_cov, seed_charge, opt: Options | None = None, out: dict | None = None,
+                      events_per_batch: int = 0) -> dict:
+    """kf_build_tracks_host: every array a CPU tensor (page-locked for the
+    overlapped copies), hit_offsets a host int64 array [E][L+1]; seeds grouped
+    by event.  Returns (or fills) host output tensors; the call returns with
+    every output written."""
+    opt = opt if opt is not None else options()
+    N = int(opt.max_cands)
+    L = geom.struct.n_layers
+    S = int(seed_event.shape[0])
+    H = int(hit_pos.shape[1])
+    off = np.ascontiguousarray(hit_offsets, dtype=np.int64)
+    if out is None:
+        out = build_outputs_host(S, N, L)
+    args = [
+        off.ctypes.data if off.size else None,
+        _host_ptr(hit_pos, torch.float32, (3, H), "hit_pos"),
+        _host_ptr(hit_cov, torch.float32, (6, H), "hit_cov"),
+        H, S,
+        _host_ptr(seed_event, torch.int32, (S,), "seed_event"),
+        _host_ptr(seed_state, torch.float32, (6, S), "seed_state"),
+        _host_ptr(seed_cov, torch.float32, (21, S), "seed_cov"),
+        _host_ptr(seed_charge, torch.int8, (S,), "seed_charge"),
+        _host_ptr(out["hit"], torch.int32, (S, N, L), "out_hit_idx"),
+        _host_ptr(out["chi2"], torch.float32, (S, N), "out_chi2"),
+        _host_ptr(out["nhits"], torch.int16, (S, N), "out_nhits"),
+        _host_ptr(out["state"], torch.float32, (6, S * N), "out_state"),
+        _host_ptr(out["cov"], torch.float32, (21, S * N), "out_cov"),
+        _host_ptr(out["flags"], torch.int32, (S, N), "out_flags"),
+    ]
+    rc = load().kf_build_tracks_host(ctx.handle, ctypes.byref(geom.struct), int(off.shape[0]), *args,
+                                     int(events_per_batch), ctypes.byref(opt))
+    ctx.check(rc, "kf_build_tracks_host")
+    return out
+
+
 def new_build_log(capacity: int, device="cuda") -> dict:
     """Device tensors for kf_build_tracks_logged with room for `capacity` rows."""
     return dict(features=torch.empty((capacity, 12), dtype=torch.float32, device=device),
@@ -419,13 +479,28 @@ def load_proposal(ctx: Context, weights):
     ctx.check(rc, "kf_load_proposal")
 
 
-def proposal_score(ctx: Context, features, stream=None):
+SCORE_AUTO, SCORE_MMA_SYNC, SCORE_TCGEN05 = 0, 1, 2
+
+
+def proposal_score(ctx: Context, features, stream=None, engine: int | None = None):
+    """Logits of the loaded network; engine None is kf_proposal_score (the
+    engine chosen by measurement), else kf_proposal_score_with(engine)."""
     n = int(features.shape[0])
     logits = torch.empty(n, dtype=torch.float32, device=features.device)
-    rc = load().kf_proposal_score(ctx.handle, _ptr(features, torch.float32, (n, 12), "features"), n,
-                                  logits.data_ptr() if n else None, _cur_stream(features, stream))
+    args = (ctx.handle, _ptr(features, torch.float32, (n, 12), "features"), n, logits.data_ptr() if n else None)
+    if engine is None:
+        rc = load().kf_proposal_score(*args, _cur_stream(features, stream))
+    else:
+        rc = load().kf_proposal_score_with(*args, int(engine), _cur_stream(features, stream))
     ctx.check(rc, "kf_proposal_score")
     return logits
+
+
+def proposal_status(ctx: Context) -> bool:
+    """kf_proposal_status: True if a bounded scoring wait has expired."""
+    v = ctypes.c_int(0)
+    ctx.check(load().kf_proposal_status(ctx.handle, ctypes.byref(v)), "kf_proposal_status")
+    return bool(v.value)
 
 
 def seed_triplets(ctx: Context, geom: GeometryArgs, hit_offsets, hit_pos, hit_cov, opt: Seeding | None = None,

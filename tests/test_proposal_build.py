@@ -4,9 +4,16 @@
   training rows against the oracle's (same (seed, candidate, layer, hit)
   keys, features within FP32 tolerance, identical labels).
 * use_proposal: the GPU build against the oracle's proposal build with the
-  same weights, the ranking taken in the scoring's precision on both sides
-  (bfloat16 inputs, W1, W2 and first hidden layer): at least 99.9% identical
-  hit assignments, as for the plain build.
+  network the build ranks with (W1, W2, W3 in BF16, biases in FP32) evaluated
+  in FP64: at least 99.9% identical hit assignments over the six builds of a
+  network and noise level (99.8% for each: a near-tie in a best-hit build
+  turns the whole track), and every seed whose hits differ traced to a
+  near-tie -- a decision that
+  FP32 against FP64 can turn: a hit within 1e-3 (relative) of its window's
+  edge or of the chi2 cut, two children of equal hit count within 1e-4
+  (relative) in chi2, or a top-k boundary whose logits are within 2e-2 (1 +
+  |z|) (the GPU's features come from its FP32 prediction).  Random and
+  GPU-trained networks, 100x and 300x noise, N in {1, 6}, top-k in {1, 2, 4}.
 * A network trained on the GPU from the logged rows against no network at
   all (the same top-k cut taken in hit order): what the ranking gains.
 """
@@ -97,22 +104,64 @@ def test_logged_build(kf, ctx, oracle, N):
     assert (g["labels"][ig] == o["labels"][io]).mean() >= 0.999
 
 
-@pytest.mark.parametrize("N,topk,nf", [(1, 1, 100), (6, 1, 100), (6, 2, 300)])
-def test_proposal_parity(kf, ctx, oracle, N, topk, nf):
-    """Random network; dense noise so that many windows hold more than topk
-    hits."""
+# how close to flipping a decision must be for FP32 against FP64 to turn it:
+# window edge, chi2 cut, ranking of children, top-k logits (the oracle's
+# out_margin columns)
+NEAR_TIE = np.array([1e-3, 1e-3, 1e-4, 2e-2])
+
+
+def untraced_mismatches(gpu, ref):
+    """Seeds whose hits differ between the GPU and the oracle with no near-tie
+    anywhere in their build."""
+    differ = (gpu["hit"] != ref["hit"]).reshape(len(gpu["hit"]), -1).any(1)
+    near = (ref["margin"] < NEAR_TIE).any(1)
+    return np.nonzero(differ & ~near)[0], float(near.mean())
+
+
+@pytest.fixture(scope="module")
+def trained_weights(kf, ctx, oracle):
+    """A network trained on the GPU from the plain build's logged rows of
+    separate events (100x noise)."""
+    ev = synth.make_build_events(60, 4, 1000, noise_factor=100)
+    log = kf.new_build_log(1_000_000)
+    gpu_build(kf, ctx, ev, oracle_seeds(oracle, ev), log=log, max_cands=6)
+    n = kf.log_rows(log)
+    w = _t(mlp_oracle.init_params(np.random.default_rng(9)), torch.float32)
+    kf.proposal_train(ctx, w, log["features"][:n].contiguous(), log["labels"][:n].contiguous(), epochs=8,
+                      batch=1024, lr=2e-3)
+    torch.cuda.synchronize()
+    return w.cpu().numpy()
+
+
+@pytest.mark.parametrize("net", ["random", "trained"])
+@pytest.mark.parametrize("nf", [100, 300])
+def test_proposal_parity(kf, ctx, oracle, trained_weights, net, nf):
+    """Dense noise, so that many windows hold more than topk hits."""
     ev = synth.make_build_events(52, 1, 800, noise_factor=nf)
     seeds = oracle_seeds(oracle, ev)
-    w = mlp_oracle.init_params(np.random.default_rng(7))
+    w = (mlp_oracle.init_params(np.random.default_rng(7)).astype(np.float32) if net == "random"
+         else trained_weights)
     kf.proposal_load(ctx, _t(w, torch.float32))
-    gpu = gpu_build(kf, ctx, ev, seeds, max_cands=N, use_proposal=1, topk=topk)
-    ref = oracle.build_events(ev, seeds=seeds, max_cands=N, mlp=w.astype(np.float32).astype(np.float64),
-                              topk=topk, mlp_bf16=True)
-    plain = oracle.build_events(ev, seeds=seeds, max_cands=N)
-    assert identical_fraction(gpu, ref) >= 0.999
-    assert identical_fraction(ref, plain) < 0.999  # the network did choose
-    e_g, e_r = eff(ev, gpu), eff(ev, ref)
-    assert abs(e_g["efficiency"] - e_r["efficiency"]) <= 0.005
+    wi = mlp_oracle.inference_weights(w)
+    chose = False
+    same = total = 0
+    for N in (1, 6):
+        plain = oracle.build_events(ev, seeds=seeds, max_cands=N)
+        for topk in (1, 2, 4):
+            gpu = gpu_build(kf, ctx, ev, seeds, max_cands=N, use_proposal=1, topk=topk)
+            ref = oracle.build_events(ev, seeds=seeds, max_cands=N, mlp=wi, topk=topk, margins=True)
+            # one near-tie turns a whole best-hit (N = 1) track: 14 of its 800 x 14
+            # assignments; 99.8% per build, 99.9% over the six builds
+            assert identical_fraction(gpu, ref) >= 0.998, (N, topk, identical_fraction(gpu, ref))
+            same += int((gpu["hit"] == ref["hit"]).sum())
+            total += gpu["hit"].size
+            bad, near_share = untraced_mismatches(gpu, ref)
+            assert bad.size == 0, (N, topk, bad, ref["margin"][bad], near_share)
+            e_g, e_r = eff(ev, gpu), eff(ev, ref)
+            assert abs(e_g["efficiency"] - e_r["efficiency"]) <= 0.005
+            chose |= identical_fraction(ref, plain) < 0.999
+    assert same >= 0.999 * total, same / total
+    assert chose  # the network did choose
 
 
 def test_constant_network_parity(kf, ctx, oracle):
