@@ -40,6 +40,10 @@ N_LAYERS = 10
 # Jacobian 88, J C J^T 308, scattering 42, local-frame update 255.  The routed
 # form also spends about 30 flops per update on its routing tests (not counted).
 FLOPS_PER_TRACK_LAYER = 768
+# the proposal network per scored row: 2 (12 x 64 + 64 x 64 + 64) multiply-adds
+# (the split activations issue each layer-1 and layer-2 product twice; that
+# doubling is not counted)
+ROW_FLOPS = 2 * (12 * 64 + 64 * 64 + 64)
 # algorithmic HBM bytes per track at 10 layers: seed 108 + charge 1 + mask 4 +
 # hits 10 x 36 in, state/cov 108 + chi2 4 + ndof 2 + flags 4 out
 BYTES_PER_TRACK = 108 + 1 + 4 + 36 * N_LAYERS + 108 + 4 + 2 + 4
@@ -66,6 +70,8 @@ def parse():
     p.add_argument("--train-events", type=int, default=3, help="events logged to train the proposal")
     p.add_argument("--seed-events", type=int, default=4, help="build-workload events seeded from hits")
     p.add_argument("--train-epochs", type=int, default=4)
+    p.add_argument("--dense-events", type=int, default=8, help="100x-noise events of the learned comparison (0: skip)")
+    p.add_argument("--no-scoring", action="store_true", help="skip the scoring engines' comparison")
     return p.parse_args()
 
 
@@ -104,11 +110,11 @@ def measured_peaks():
 
 def kernel_source_hash(unit: str = "kf_fit.cu") -> str:
     """Hash of a kernel's sources (its translation unit, by default the fit's,
-    and every header it includes from the package or include/) and of the
-    build script."""
+    and every header it includes from the package's csrc/) and of the build
+    script.  The public header include/kf.h (declarations and their
+    documentation) is left out."""
     import re
     csrc = os.path.join(ROOT, "paper_1705_02876_gb300", "csrc")
-    inc = os.path.join(ROOT, "include")
     todo, seen = [os.path.join(csrc, unit)], []
     while todo:
         p = todo.pop()
@@ -116,10 +122,8 @@ def kernel_source_hash(unit: str = "kf_fit.cu") -> str:
             continue
         seen.append(p)
         for name in re.findall(r'#include\s+"([^"]+)"', open(p).read()):
-            for d in (csrc, inc):
-                if os.path.exists(os.path.join(d, name)):
-                    todo.append(os.path.join(d, name))
-                    break
+            if os.path.exists(os.path.join(csrc, name)):
+                todo.append(os.path.join(csrc, name))
     h = hashlib.sha256()
     for p in sorted(seen) + [os.path.join(ROOT, "paper_1705_02876_gb300", "build.py")]:
         with open(p, "rb") as f:
@@ -392,6 +396,7 @@ def bench_build(args, kf, ctx, dev, stream, rank, world):
         "dram_bytes_source": "ncu capture of the 64-event call (build kernel + binning), committed summary",
         "kernel_source_hash": build_hash}
     q = metrics.efficiency_fake_rate(best, ev.seed_track, ev.hit_track, ev.track_nhits)
+    e2e = bench_build_e2e(args, kf, ctx, ev, fit_out, b_out, chosen)
     ms_plain = timed(step_plain, max(2, args.build_steps // 2))
     qp = metrics.efficiency_fake_rate(np.concatenate([o["hit"][:, 0].cpu().numpy() for o in plain_outs if o is not None]),
                                       ev.seed_track, ev.hit_track, ev.track_nhits)
@@ -407,8 +412,40 @@ def bench_build(args, kf, ctx, dev, stream, rank, world):
            "plain": {"value": S / (ms_plain * 1e-3), "unit": "seeds/s", "ms_per_step": ms_plain,
                      "form": "FP32 only, one launch per event", "efficiency": qp["efficiency"],
                      "fake_rate": qp["fake_rate"]},
-           "learned": learned, "seeding": seeding}
+           "learned": learned, "seeding": seeding, "e2e": e2e,
+           "tuned_bins": ctx.build_tuned_shape(Lb, chosen.max_cands, 0, S, int(ev.hit_pos.shape[1]))}
     return out
+
+
+def bench_build_e2e(args, kf, ctx, ev, fit_out, b_out, opt):
+    """The build end to end through kf_build_tracks_host: hits, seeds and
+    outputs in pinned host memory, every byte crossing the host link inside the
+    timed region (batches of 16 events, uploads, builds and downloads
+    overlapped on three streams); checked equal to the device build."""
+    import torch
+    pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dt).pin_memory()
+    hin = dict(hit_pos=pin(ev.hit_pos, torch.float32), hit_cov=pin(ev.hit_cov, torch.float32),
+               seed_event=pin(ev.seed_event, torch.int32), seed_state=fit_out["state"].cpu().pin_memory(),
+               seed_cov=fit_out["cov"].cpu().pin_memory(), seed_charge=pin(ev.seed_fit.charge, torch.int8))
+    geom = kf.GeometryArgs.of(ev.build_geom)
+    hout = kf.build_outputs_host(ev.n_seeds, opt.max_cands, ev.build_geom.n_layers)
+
+    def step():
+        kf.build_tracks_host(ctx, geom, ev.hit_offsets, **hin, opt=opt, out=hout, events_per_batch=16)
+
+    for _ in range(2):
+        step()
+    n = max(3, args.build_steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(n):
+        step()
+    ms = (time.perf_counter() - t0) * 1e3 / n
+    same = bool(np.array_equal(hout["hit"].numpy(), b_out["hit"].cpu().numpy()))
+    h2d = sum(v.numel() * v.element_size() for v in hin.values())
+    d2h = sum(v.numel() * v.element_size() for v in hout.values())
+    return {"value": ev.n_seeds / (ms * 1e-3), "unit": "seeds/s", "ms_per_step": ms, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "link_gbs": (h2d + d2h) / (ms * 1e-3) / 1e9, "equals_device_build": same,
+            "form": "kf_build_tracks_host: pinned host buffers, 16-event batches, copies overlapped with the builds"}
 
 
 def bench_seeding(args, kf, ctx, dev, stream, ev, build_geom, hp, hc, timed):
@@ -449,11 +486,30 @@ def bench_seeding(args, kf, ctx, dev, stream, ev, build_geom, hp, hc, timed):
     st = np.where((trk[0] >= 0) & (trk[0] == trk[1]) & (trk[1] == trk[2]), trk[0], -1)
     q = metrics.efficiency_fake_rate(b_out["hit"][:, 0].cpu().numpy(), st, ev.hit_track, ev.track_nhits,
                                      eligible_tracks=ev.seed_track[ev.seed_event < E])
+    # efficiency against fakes at tighter seeding cuts (the same chain, once each)
+    points = {}
+    for name, cuts in (("d0_0.10_dz_0.5", dict(d0_max=0.10, dz_max=0.5)),
+                       ("d0_0.05_dz_0.4", dict(d0_max=0.05, dz_max=0.4))):
+        so = kf.seeding(**cuts)
+        sd = kf.seed_triplets(ctx, g3, soff, shp, shc, opt=so, stream=stream)
+        m = int(sd["charge"].shape[0])
+        fo = kf.fit_outputs(m, dev)
+        kf.fit_tracks(ctx, g3, sd["seed_state"], sd["seed_cov"], sd["charge"], sd["hit_pos"], sd["hit_cov"],
+                      sd["hit_mask"], out=fo, stream=stream)
+        bo = kf.build_tracks(ctx, build_geom, ev.hit_offsets[:E], hp, hc, sd["event"], fo["state"], fo["cov"],
+                             sd["charge"], stream=stream)
+        t2 = ev.seed_hit_track[sd["hits"].cpu().numpy()]
+        s2 = np.where((t2[0] >= 0) & (t2[0] == t2[1]) & (t2[1] == t2[2]), t2[0], -1)
+        q2 = metrics.efficiency_fake_rate(bo["hit"][:, 0].cpu().numpy(), s2, ev.hit_track, ev.track_nhits,
+                                          eligible_tracks=ev.seed_track[ev.seed_event < E])
+        points[name] = {"seeds": m, "efficiency": q2["efficiency"], "fake_rate": q2["fake_rate"],
+                        "hit_purity": q2["hit_purity"]}
     return {"value": E / (ms_chain * 1e-3), "unit": "events/s", "ms_per_step": ms_chain, "events": E,
             "seeds": n, "seeds_per_event": n / E, "true_seed_share": float((st >= 0).mean()),
             "form": "triplet search + seed inputs + 3-layer seed fit + build of every seed, default cuts "
                     "(pT > 0.3 GeV, d0 < 0.15 cm, |z0| < 4 cm, dz < 0.8 cm; both charges above 2 GeV)",
             "efficiency": q["efficiency"], "fake_rate": q["fake_rate"], "hit_purity": q["hit_purity"],
+            "operating_points": points,
             "search": {"value": n_hits / (ms_seed * 1e-3), "unit": "seed-layer hits/s", "ms_per_step": ms_seed,
                        "seed_layer_hits": n_hits, "events_per_s": E / (ms_seed * 1e-3),
                        "form": "binning + triplet search + count read-back + seed inputs"}}
@@ -494,11 +550,95 @@ def bench_learned(args, kf, ctx, dev, stream, rank, ev, seed_geom, d_sf, fit_out
 
     ms = timed(step_learned, args.build_steps)
     q = metrics.efficiency_fake_rate(b_out["hit"][:, 0].cpu().numpy(), ev.seed_track, ev.hit_track, ev.track_nhits)
-    return {"value": ev.n_seeds / (ms * 1e-3), "unit": "seeds/s", "ms_per_step": ms, "topk": 4,
+    dense = bench_learned_dense(args, kf, ctx, dev, stream, rank, timed) if args.dense_events > 0 else None
+    kf.proposal_load(ctx, w, stream=stream)
+    return {"value": ev.n_seeds / (ms * 1e-3), "unit": "seeds/s", "ms_per_step": ms, "topk": 4, "dense": dense,
             "efficiency": q["efficiency"], "fake_rate": q["fake_rate"], "hit_purity": q["hit_purity"],
             "training": {"rows": n, "events": args.train_events, "epochs": args.train_epochs,
                          "loss_first_last": [losses[0], losses[-1]], "seconds": round(train_s, 3)},
             "windows_above_topk": float((win > 4).mean()), "mean_window_hits": float(win.mean())}
+
+
+def bench_learned_dense(args, kf, ctx, dev, stream, rank, timed):
+    """Where windows hold more hits than top-k: 100x noise (1,000 tracks per
+    event, 100,000 noise hits per build layer).  A network trained (by the
+    library's kernels) on the plain build's rows of separate 100x events
+    ranks each window's hits; against the exhaustive chi2 search and the
+    same top-k cut without a network (hit order).  Seeds fitted on the GPU."""
+    import torch
+    from paper_1705_02876_gb300 import metrics, synth
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(dev, dtype=dt)
+
+    def load(ev):
+        sf = ev.seed_fit
+        fo = kf.fit_tracks(ctx, kf.GeometryArgs.of(sf.geom), **kf.to_device(sf, dev), stream=stream)
+        return dict(geom=kf.GeometryArgs.of(ev.build_geom), hp=t(ev.hit_pos, torch.float32),
+                    hc=t(ev.hit_cov, torch.float32), se=t(ev.seed_event, torch.int32), st=fo["state"],
+                    cv=fo["cov"], sq=t(sf.charge, torch.int8))
+
+    tr = synth.make_build_events(60 + 1000 * rank, 4, 1000, noise_factor=100)
+    d = load(tr)
+    log = kf.new_build_log(2_000_000, dev)
+    kf.build_tracks(ctx, d["geom"], tr.hit_offsets, d["hp"], d["hc"], d["se"], d["st"], d["cv"], d["sq"],
+                    stream=stream, log=log)
+    torch.cuda.synchronize()
+    n = kf.log_rows(log)
+    w = torch.from_numpy(synth.proposal_init(np.random.default_rng(19 + rank))).to(dev, torch.float32)
+    kf.proposal_train(ctx, w, log["features"][:n].contiguous(), log["labels"][:n].contiguous(), epochs=8,
+                      batch=1024, lr=2e-3, stream=stream)
+    ev = synth.make_build_events(61 + 1000 * rank, args.dense_events, 1000, noise_factor=100)
+    d = load(ev)
+    res = {"workload": f"build geometry, {args.dense_events} events x 1,000 tracks, 100x uniform noise hits "
+                       "(100,000 per build layer per event), N = 6", "training_rows": n}
+    for name, opt, weights in (("exhaustive", kf.options(), None),
+                               ("learned_top1", kf.options(use_proposal=1, topk=1), w),
+                               ("learned_top4", kf.options(use_proposal=1, topk=4), w),
+                               ("blind_top1", kf.options(use_proposal=1, topk=1), torch.zeros_like(w))):
+        if weights is not None:
+            kf.proposal_load(ctx, weights, stream=stream)
+        out = None
+
+        def step():
+            nonlocal out
+            out = kf.build_tracks(ctx, d["geom"], ev.hit_offsets, d["hp"], d["hc"], d["se"], d["st"], d["cv"],
+                                  d["sq"], opt=opt, out=out, stream=stream)
+
+        ms = timed(step, max(3, args.build_steps // 2))
+        q = metrics.efficiency_fake_rate(out["hit"][:, 0].cpu().numpy(), ev.seed_track, ev.hit_track,
+                                         ev.track_nhits)
+        res[name] = {"value": ev.n_seeds / (ms * 1e-3), "unit": "seeds/s", "ms_per_step": ms,
+                     "efficiency": q["efficiency"], "fake_rate": q["fake_rate"], "hit_purity": q["hit_purity"]}
+    return res
+
+
+def bench_scoring(args, kf, ctx, dev):
+    """The proposal's batched scoring on both tensor-core engines, on the same
+    rows: mma.sync (warp-level, accumulators in registers) and tcgen05 (128-row
+    CTA tiles, accumulators in tensor memory); kf_proposal_score's automatic
+    choice per size."""
+    import torch
+    from paper_1705_02876_gb300 import synth
+    w = torch.from_numpy(synth.proposal_init(np.random.default_rng(5))).to(dev, torch.float32)
+    kf.proposal_load(ctx, w)
+    res = {"form": "12 -> 64 -> 64 -> 1, BF16 weights, split BF16 activations (hi + lo), FP32 accumulation",
+           "algorithmic_flops_per_row": ROW_FLOPS, "sizes": {}}
+    for n in (1 << 16, 1 << 20, 1 << 24):
+        X = torch.randn(n, 12, device=dev, dtype=torch.float32)
+        row = {}
+        for name, eng in (("mma_sync", kf.SCORE_MMA_SYNC), ("tcgen05", kf.SCORE_TCGEN05), ("auto", None)):
+            for _ in range(3):
+                kf.proposal_score(ctx, X, engine=eng)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(10):
+                kf.proposal_score(ctx, X, engine=eng)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / 10
+            row[name] = {"ms": ms, "rows_per_s": n / (ms * 1e-3), "tflops": n * ROW_FLOPS / (ms * 1e-3) / 1e12}
+        res["sizes"][str(n)] = row
+    return res
 
 
 def bench_ragged(args, kf, ctx, dev, stream, rank):
@@ -535,7 +675,8 @@ def bench_ragged(args, kf, ctx, dev, stream, rank):
         res[name] = {"value": T / (ms * 1e-3), "unit": "tracks/s", "ms_per_step": ms,
                      "launches_per_step": 1 if mode != kf.LAUNCH_PER_EVENT else len(b.event_offsets) - 1}
     shape = ctx.tuned_shape(b.geom.n_layers, T)
-    res["tuned_shape"] = ({"tracks_per_block": shape[0], "reg_cap": shape[1], "hit_prefetch": shape[2]}
+    res["tuned_shape"] = ({"tracks_per_block": shape[0], "reg_cap": shape[1], "hit_prefetch": shape[2],
+                           "tracks_per_thread": shape[3]}
                           if shape else None)
     return res
 
@@ -646,6 +787,7 @@ def main():
         parts = [int(v) for v in args.shape.split(":")]
         chosen.tracks_per_block, chosen.reg_cap = parts[0], parts[1]
         chosen.hit_prefetch = parts[2] if len(parts) > 2 else 1
+        chosen.tracks_per_thread = parts[3] if len(parts) > 3 else 1
 
     def step(opt=chosen, o=out):
         kf.fit_tracks(ctx, geom, **d_in, event_offsets=batch.event_offsets, opt=opt, out=o, stream=stream)
@@ -723,7 +865,7 @@ def main():
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     tuned = (ctx.tuned_shape(N_LAYERS, T) if not args.shape
-             else (chosen.tracks_per_block, chosen.reg_cap, chosen.hit_prefetch))
+             else (chosen.tracks_per_block, chosen.reg_cap, chosen.hit_prefetch, chosen.tracks_per_thread or 1))
     line = {
         "metric": METRIC, "value": value, "unit": "tracks/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -732,6 +874,7 @@ def main():
                    "l2": "inputs larger than L2 (1.18 GB per step), not flushed",
                    "tracks_per_block": tuned[0] if tuned else None, "reg_cap": tuned[1] if tuned else None,
                    "hit_prefetch": tuned[2] if tuned else None,
+                   "tracks_per_thread": tuned[3] if tuned else None,
                    "parallelism": f"replicas{world}"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": traffic,
@@ -761,7 +904,13 @@ def main():
             "learned_seeds_per_s": b["learned"]["value"], "efficiency": b["efficiency"],
             "fake_rate": b["fake_rate"], "learned_efficiency": b["learned"]["efficiency"],
             "call_ms": r["call_ms"], "fp32_frac": r["fp32_frac"], "dram_frac": r["dram_frac"],
-            "dram_bytes_per_call": r["dram_bytes_per_call"]}
+            "dram_bytes_per_call": r["dram_bytes_per_call"], "e2e_seeds_per_s": b["e2e"]["value"],
+            "tuned_bins": b["tuned_bins"]}
+        dn = b["learned"].get("dense")
+        if dn:
+            line["build_summary"]["dense_100x"] = {k: {"seeds_per_s": dn[k]["value"], "efficiency": dn[k]["efficiency"],
+                                                       "hit_purity": dn[k]["hit_purity"]}
+                                                   for k in ("exhaustive", "learned_top1", "learned_top4", "blind_top1")}
     else:
         del line["build_summary"]
     if not args.no_ragged:
@@ -769,6 +918,8 @@ def main():
     if not args.no_transport:
         line["transport6x6"] = bench_transport(args, kf, ctx, dev, stream)
     line["smoother"] = bench_smoother(args, kf, ctx, dev, stream, batch, d_in)
+    if not args.no_scoring:
+        line["proposal_scoring"] = bench_scoring(args, kf, ctx, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch, T)
     if rank == 0:

@@ -104,7 +104,8 @@ typedef struct {
                                 its gain (S^-1 and K) in float-float; 0 = off */
     /* launch shape (fit) */
     int launch_mode;         /* KF_LAUNCH_* */
-    int tracks_per_block;    /* 0 = autotuned, else 32, 64, 128 or 256 */
+    int tracks_per_block;    /* threads per block of the persistent fit (tracks, at one per thread):
+                                0 = autotuned, else 32, 64, 128 or 256 */
     int reg_cap;             /* registers per thread of the persistent fit: 0 = autotuned,
                                 -1 = uncapped, 168, 128, 96 or 80 */
     int hit_prefetch;        /* layers of hits the persistent fit loads ahead of their
@@ -122,6 +123,9 @@ typedef struct {
     int n_z_bins;            /* ... and in z (0 = autotuned); at most 16,384 bins */
     int use_proposal;        /* 1: the learned proposal keeps the top-k in-window hits */
     int topk;
+    /* launch shape (fit), continued */
+    int tracks_per_thread;   /* tracks each thread of the persistent fit carries: 0 = autotuned,
+                                1, or 2 (two tracks on the packed FP32x2 instructions) */
 } kf_options;
 
 /* Fill *opt with the defaults: routed precision (cond_max 1e4, pT in
@@ -226,8 +230,10 @@ int kf_fit_tracks_host(kf_context *ctx, const kf_geometry *geom, int64_t n_track
  * leaves the bin grid 0 an autotuner chooses it: the first call of a workload
  * class (layers, N, mode, the seed and hit counts' sizes in powers of two)
  * times five grids of up to 16,384 bins on the caller's buffers and keeps the
- * fastest (kf_build_tuned_shape reports it); the results do not depend on the
- * grid.
+ * fastest (kf_build_tuned_shape reports it); with the learned proposal it
+ * also chooses between one proposal pass and a speculative plain pass whose
+ * flagged seeds alone are rebuilt with the proposal.  The results depend on
+ * neither choice.
  *
  * geom: the layers to build over (host).
  * hit_offsets: host, [n_events][L + 1]; the hits of event e on layer l are
@@ -283,14 +289,17 @@ int kf_build_tracks_host(kf_context *ctx, const kf_geometry *geom, int n_events,
                          const kf_options *opt);
 
 /*
- * The hit-bin grid the build autotuner picked for builds of n_layers layers,
- * N = max_cands, mode (0 plain, 1 logged, 2 learned proposal), n_seeds seeds
- * and n_hits hits (their size classes, powers of two), with the grid left to
- * the tuner (opt->n_phi_bins = opt->n_z_bins = 0).  KF_ERR_ARG if no such
- * build has run on ctx.
+ * The shape the build autotuner picked for builds of n_layers layers, N =
+ * max_cands, mode (0 plain, 1 logged, 2 learned proposal), n_seeds seeds and
+ * n_hits hits (their size classes, powers of two), with the bin grid left to
+ * the tuner (opt->n_phi_bins = opt->n_z_bins = 0): the grid, and for the
+ * learned proposal whether it runs speculatively (*speculative = 1: a plain
+ * pass flags the seeds one of whose windows held more than topk hits and the
+ * proposal pass rebuilds those only; the others' builds are the same either
+ * way).  speculative may be NULL.  KF_ERR_ARG if no such build has run on ctx.
  */
 int kf_build_tuned_shape(kf_context *ctx, int n_layers, int max_cands, int mode, int64_t n_seeds, int64_t n_hits,
-                         int *n_phi_bins, int *n_z_bins);
+                         int *n_phi_bins, int *n_z_bins, int *speculative);
 
 /*
  * kf_build_tracks that also records the training set of the learned proposal
@@ -476,9 +485,9 @@ int kf_seed_fetch(kf_context *ctx, const kf_geometry *geom, const float *hit_pos
  *   track); out_flags [T] as kf_fit_tracks (INVERSION_FAILED also when a
  *   predicted covariance could not be factorised, the layer then keeping its
  *   filtered estimate).
- * Scratch: 136 L bytes per track, kept by the context (KF_ERR_NOMEM).
- * One thread per track, one launch; opt->launch_mode and the shape are
- * ignored.
+ * No scratch: the backward pass recomputes each layer's prediction from the
+ * filtered estimate the forward pass left in the outputs.  One thread per
+ * track, one launch; opt->launch_mode and the shape are ignored.
  */
 int kf_smooth_tracks(kf_context *ctx, const kf_geometry *geom, int64_t n_tracks, const float *seed_state,
                      const float *seed_cov, const int8_t *charge, const float *hit_pos, const float *hit_cov,
@@ -501,12 +510,13 @@ int kf_transport_batch(kf_context *ctx, int64_t n, const float *J, float *C, kf_
 /*
  * Launch shape the autotuner picked for the persistent fit of n_layers layers
  * and a batch of n_tracks' size class (powers of two), once a KF_LAUNCH_AUTO
- * fit of that class has run on ctx.  Writes tracks per block, the register
- * cap per thread (-1: uncapped) and the hit prefetch depth (kf_options).
- * KF_ERR_ARG if that class has not been tuned.
+ * fit of that class has run on ctx.  Writes threads per block, the register
+ * cap per thread (-1: uncapped), the hit prefetch depth and the tracks per
+ * thread (kf_options; tracks_per_thread may be NULL).  KF_ERR_ARG if that
+ * class has not been tuned.
  */
 int kf_fit_tuned_shape(kf_context *ctx, int n_layers, int64_t n_tracks, int *tracks_per_block,
-                       int *reg_cap, int *hit_prefetch);
+                       int *reg_cap, int *hit_prefetch, int *tracks_per_thread);
 
 /*
  * The fit for callers that cannot allocate device memory.  The paper has no
@@ -534,9 +544,10 @@ int kf_fit_tuned_shape(kf_context *ctx, int n_layers, int64_t n_tracks, int *tra
  *     a launch that would hold more than 16,384 resident warps (the 32-bit
  *     counter must not wrap while every warp makes its last claim; a GB300
  *     holds at most 152 x 64 = 9,728).
- *   - No tuning runs.  The shape is opt->tracks_per_block, opt->reg_cap and
- *     opt->hit_prefetch where set, else 64 tracks per block, no register cap
- *     and the register prefetch (depth 1).  Only the (block, cap, depth)
+ *   - No tuning runs.  The shape is opt->tracks_per_block, opt->reg_cap,
+ *     opt->hit_prefetch and opt->tracks_per_thread where set, else 64 threads
+ *     per block, no register cap, the register prefetch (depth 1) and one
+ *     track per thread.  Only the (block, cap, depth)
  *     combinations the autotuner of kf_fit_tracks chooses from are compiled
  *     in: blocks 32/64/128/256 with cap none/168/128/96/80 at depth 1 (cap
  *     168 only below 256 threads, cap 96 only below 256), and at depths 2

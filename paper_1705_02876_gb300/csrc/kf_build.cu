@@ -47,9 +47,13 @@ struct BuildState {
         cudaEvent_t in_done = nullptr, built = nullptr, out_done = nullptr;
         bool used = false;
     } slot[3];
-    // autotuned bin grids: (L, N, mode, seeds' size class, hits' size class, fixed n_phi, fixed n_z)
-    // -> (n_phi, n_z)
-    std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<int, int>> tuned;
+    // autotuned shapes: (L, N, mode, seeds' size class, hits' size class, fixed n_phi, fixed n_z)
+    // -> (n_phi, n_z, speculative: the learned build as a flagging plain pass plus a proposal pass)
+    std::map<std::tuple<int, int, int, int, int, int, int>, std::tuple<int, int, int>> tuned;
+    // the speculative learned build's per-seed flags, flagged-seed list and its length
+    int32_t *seed_flag = nullptr, *seed_list = nullptr;
+    unsigned *list_count = nullptr;
+    size_t flag_capacity = 0, list_capacity = 0, count_capacity = 0;
 };
 
 void destroy_build_state(BuildState *s)
@@ -69,6 +73,9 @@ void destroy_build_state(BuildState *s)
     cudaFree(s->bin_cnt);
     cudaFree(s->seg_off);
     cudaFree(s->ev_off);
+    cudaFree(s->seed_flag);
+    cudaFree(s->seed_list);
+    cudaFree(s->list_count);
     delete s;
 }
 
@@ -108,6 +115,13 @@ struct BuildParams {
     int topk;
     const __nv_bfloat16 *mlp_W1, *mlp_W2;
     const float *mlp_w32;
+    // the learned build in two passes: the plain pass flags (flag_over > 0)
+    // every seed one of whose windows held more than flag_over hits; the
+    // proposal pass builds only the seeds of seed_list (*list_count of them)
+    int flag_over;
+    int32_t *seed_flag;
+    const int32_t *seed_list;
+    const unsigned *list_count;
 };
 
 constexpr int kMaxN = 8;
@@ -193,15 +207,93 @@ __device__ __forceinline__ bool key_less(unsigned long long a64, uint32_t a32, u
 }
 
 // Shared memory: back-pointers [L][128], update slots [kSlotSize][128], then
-// (proposal only) the network's weights and each warp's 32 staged input rows
-// (FP32, kStageLd floats each).
+// (proposal only) each warp's 32 staged input rows (FP32, kStageLd floats
+// each).
 constexpr int kStageLd = 12;
 __host__ __device__ constexpr size_t build_smem_base(int L) { return ((size_t)(L + kSlotSize) * 128 * 4 + 127) / 128 * 128; }
-constexpr size_t kBuildSmemMlp = sizeof(MlpSmemWeights) + 4 * 32 * kStageLd * sizeof(float);
+constexpr size_t kBuildSmemMlp = 4 * 32 * kStageLd * sizeof(float);
 
-// At most 128 registers (four blocks per SM) in every mode: the proposal's
-// scoring path, rare where windows hold few hits, spills rather than taking
-// registers from the common path.
+// What ranking a candidate's window needs: the window, its segment, the
+// prediction the hits are tested against (position, radial direction, the
+// local C_tt, C_tz, C_zz) and the proposal's candidate inputs cf[3..11].
+struct RankIn {
+    Window win;
+    int64_t seg_lo;
+    float x0, x1, x2, nx, ny, ctt, ctz, czz;
+    float cf[kMlpIn];
+    bool wide;
+};
+
+// The learned proposal's ranking of the windows wider than topk of one warp
+// (warp-collective: every lane calls it, converged; lanes without a wide
+// window take part in the scoring with empty rows).  A wide window's lane
+// walks its hits one per round; the warp scores the round's 32 rows on the
+// tensor cores (weights read through L1 from the loaded copies); each lane
+// keeps its topk hits by logit (logit desc, hit index asc) in hb.
+__device__ __forceinline__ void rank_window(const BuildParams &p, const RankIn &in, float *xs, uint32_t *hb)
+{
+    const int lane = threadIdx.x & 31;
+    const MlpWeightsRef mw{reinterpret_cast<const uint32_t *>(p.mlp_W1), reinterpret_cast<const uint32_t *>(p.mlp_W2),
+                           p.mlp_w32 + kOffB1, p.mlp_w32 + kOffB2, p.mlp_w32 + kOffW3, p.mlp_w32[kOffB3]};
+    float tz[kMaxN];
+    uint32_t hk[kMaxN];
+#pragma unroll
+    for (int k = 0; k < kMaxN; ++k) {
+        tz[k] = -INFINITY;
+        hk[k] = in.wide ? kNoKey : hb[k];
+    }
+    WindowCursor cur;
+    if (in.wide) cur.start(in.win);
+    bool more = in.wide;
+    const float xp[3] = {in.x0, in.x1, in.x2};
+    while (__any_sync(0xffffffffu, more)) {
+        const uint32_t hr = more ? cur.next(p, in.win) : kNoKey;
+        more = hr != kNoKey;
+        float feat[kMlpIn];
+#pragma unroll
+        for (int i = 0; i < kMlpIn; ++i) feat[i] = 0.0f;
+        if (more) {
+            float m[3], v[6], dc;
+            const int64_t hg = in.seg_lo + hr;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) m[i] = p.hit_pos[i * p.H + hg];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) v[i] = p.hit_cov[i * p.H + hg];
+            hit_eval(xp, in.nx, in.ny, in.ctt, in.ctz, in.czz, m, v, &dc, feat);
+#pragma unroll
+            for (int i = 3; i < kMlpIn; ++i) feat[i] = in.cf[i];
+        }
+        __syncwarp();  // the previous round's rows are read
+#pragma unroll
+        for (int i = 0; i < kMlpIn; ++i) xs[lane * kStageLd + i] = feat[i];
+        const float z = mlp_score_warp_split(mw, xs, kStageLd);
+        if (more) {
+            float cv = z;
+            uint32_t hv = hr;
+#pragma unroll
+            for (int k2 = 0; k2 < kMaxN; ++k2) {
+                const bool before = k2 < p.topk && (cv > tz[k2] || (cv == tz[k2] && hv < hk[k2]));
+                const float t1 = tz[k2];
+                const uint32_t t2 = hk[k2];
+                tz[k2] = before ? cv : t1;
+                hk[k2] = before ? hv : t2;
+                cv = before ? t1 : cv;
+                hv = before ? t2 : hv;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxN; ++k) hb[k] = hk[k];
+}
+
+// The seeds the plain pass flagged, appended to list in no fixed order.
+__global__ void flagged_seeds_kernel(const int32_t *flag, int64_t S, int32_t *list, unsigned *count)
+{
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x)
+        if (flag[s]) list[atomicAdd(count, 1u)] = (int32_t)s;
+}
+
+// At most 128 registers (four blocks per SM) in every mode.
 template <int G, int MODE>
 __global__ void __launch_bounds__(128, 4) build_kernel(const BuildParams p)
 {
@@ -210,23 +302,22 @@ __global__ void __launch_bounds__(128, 4) build_kernel(const BuildParams p)
     const int L = p.g.L;
     int32_t *bp = smem;                                   // [L][128] back-pointers
     float *slots = reinterpret_cast<float *>(smem + L * 128);  // [kSlotSize][128]
-    MlpWeightsRef mref{};
-    float *xs = nullptr;  // this warp's staged input rows [32][kStageLd]
-    if (MODE == kModeProposal) {
-        unsigned char *base = reinterpret_cast<unsigned char *>(smem) + build_smem_base(L);
-        MlpSmemWeights *mw = reinterpret_cast<MlpSmemWeights *>(base);
-        xs = reinterpret_cast<float *>(base + sizeof(MlpSmemWeights)) + (threadIdx.x >> 5) * 32 * kStageLd;
-        mlp_load_weights(mw, p.mlp_W1, p.mlp_W2, p.mlp_w32);
-        __syncthreads();
-        mref = MlpWeightsRef{reinterpret_cast<const uint32_t *>(mw->W1t), reinterpret_cast<const uint32_t *>(mw->W2t),
-                             mw->b1, mw->b2, mw->W3, mw->b3};
-    }
+    float *xs = nullptr;  // this warp's staged input rows [32][kStageLd] (proposal)
+    if (MODE == kModeProposal)
+        xs = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(smem) + build_smem_base(L)) +
+             (threadIdx.x >> 5) * 32 * kStageLd;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int slot = lane % G, gbase = lane - slot;
     // G = 6: five groups per warp; lanes 30 and 31 form an idle group of two
     const bool lane_ok = lane < SEEDS_PER_WARP * G;
-    const int64_t s = ((int64_t)blockIdx.x * 4 + warp) * SEEDS_PER_WARP + lane / G;
-    const bool seed_ok = lane_ok && s < p.S;
+    const int64_t k_seed = ((int64_t)blockIdx.x * 4 + warp) * SEEDS_PER_WARP + lane / G;
+    int64_t s = k_seed;
+    bool seed_ok = lane_ok && k_seed < p.S;
+    if (p.seed_list) {  // the listed seeds only; a warp without one has nothing to do
+        seed_ok = lane_ok && k_seed < (int64_t)*p.list_count;
+        s = seed_ok ? p.seed_list[k_seed] : 0;
+        if (!__any_sync(0xffffffffu, seed_ok)) return;
+    }
     const int N = p.N;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << gbase);
 
@@ -235,6 +326,7 @@ __global__ void __launch_bounds__(128, 4) build_kernel(const BuildParams p)
     int nhits = 0;
     bool stopped = false;
     uint32_t flags = 0;
+    bool over = false;  // a window of this lane's candidates held more than flag_over hits
     int nc = 1;
     const int ev_in = seed_ok ? p.seed_event[s] - p.event_base : 0;
     const bool ev_ok = ev_in >= 0 && ev_in < p.n_events;  // a seed of an unknown event builds nothing
@@ -394,50 +486,26 @@ __global__ void __launch_bounds__(128, 4) build_kernel(const BuildParams p)
                 }
             }
             const bool wide = n_in > cap;
+            if (MODE == kModePlain && p.flag_over > 0) over |= n_in > p.flag_over;
             if (MODE == kModeProposal && __any_sync(0xffffffffu, wide)) {
-                // a wide window keeps its topk best hits by logit (logit desc,
-                // hit index asc); one hit per ranking lane per round, scored
-                // by the warp
-                float tz[kMaxN];
+                // a wide window keeps its topk best hits by logit
+                RankIn in;
+                in.win = win;
+                in.seg_lo = seg_lo;
+                in.x0 = x[0];
+                in.x1 = x[1];
+                in.x2 = x[2];
+                in.nx = nx;
+                in.ny = ny;
+                in.ctt = ctt;
+                in.ctz = ctz;
+                in.czz = czz;
+                in.wide = wide;
+                float cf[kMlpIn];
+                cand_features(cf);
 #pragma unroll
-                for (int k = 0; k < kMaxN; ++k) tz[k] = -INFINITY;
-                if (wide) {
-#pragma unroll
-                    for (int k = 0; k < kMaxN; ++k) hb[k] = kNoKey;
-                    cur.start(win);
-                }
-                bool more = wide;
-                while (__any_sync(0xffffffffu, more)) {
-                    const uint32_t hr = more ? cur.next(p, win) : kNoKey;
-                    more = hr != kNoKey;
-                    float feat[kMlpIn];
-#pragma unroll
-                    for (int i = 0; i < kMlpIn; ++i) feat[i] = 0.0f;
-                    if (more) {
-                        float m[3], v[6], dc;
-                        load_hit(hr, m, v);
-                        hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, feat);
-                        cand_features(feat);
-                    }
-                    __syncwarp();  // the previous round's rows are read
-#pragma unroll
-                    for (int i = 0; i < kMlpIn; ++i) xs[lane * kStageLd + i] = feat[i];
-                    const float z = mlp_score_warp_split(mref, xs, kStageLd);
-                    if (more) {
-                        float cv = z;
-                        uint32_t hv = hr;
-#pragma unroll
-                        for (int k2 = 0; k2 < kMaxN; ++k2) {
-                            const bool before = k2 < p.topk && (cv > tz[k2] || (cv == tz[k2] && hv < hb[k2]));
-                            const float t1 = tz[k2];
-                            const uint32_t t2 = hb[k2];
-                            tz[k2] = before ? cv : t1;
-                            hb[k2] = before ? hv : t2;
-                            cv = before ? t1 : cv;
-                            hv = before ? t2 : hv;
-                        }
-                    }
-                }
+                for (int i = 3; i < kMlpIn; ++i) in.cf[i] = cf[i];
+                rank_window(p, in, xs, hb);
             }
             if (MODE == kModeProposal || !wide) {
                 // the full chi2 for the collected (or ranked) hits, loads
@@ -590,6 +658,11 @@ __global__ void __launch_bounds__(128, 4) build_kernel(const BuildParams p)
             bp[l * 128 + threadIdx.x] = (int32_t)(((uint32_t)new_parent << 27) | new_hit);
         }
         __syncwarp();
+    }
+    if (MODE == kModePlain && p.flag_over > 0) {
+        // OR over the seed's lanes (the group's lanes are contiguous)
+        const unsigned ov = __ballot_sync(0xffffffffu, over && seed_ok);
+        if (seed_ok && slot == 0) p.seed_flag[s] = (ov >> gbase) & ((G == 32 ? 0xffffffffu : (1u << G) - 1u)) ? 1 : 0;
     }
     if (!seed_ok) return;
     const int N_ = p.N;
@@ -759,6 +832,10 @@ int build_run(kf_context *ctx, const FitGeom &g, const kf_options &o, const Buil
     p.mlp_W1 = W1;
     p.mlp_W2 = W2;
     p.mlp_w32 = w32;
+    p.flag_over = 0;
+    p.seed_flag = nullptr;
+    p.seed_list = nullptr;
+    p.list_count = nullptr;
     // lanes per seed: the smallest group that holds N candidates (6 for N = 5
     // or 6, so that a warp holds five seeds instead of four)
     const int G = p.N == 1 ? 1 : p.N <= 2 ? 2 : p.N <= 4 ? 4 : p.N <= 6 ? 6 : 8;
@@ -774,9 +851,18 @@ int build_run(kf_context *ctx, const FitGeom &g, const kf_options &o, const Buil
         {build_kernel<4, kModePlain>, build_kernel<4, kModeLog>, build_kernel<4, kModeProposal>},
         {build_kernel<6, kModePlain>, build_kernel<6, kModeLog>, build_kernel<6, kModeProposal>},
         {build_kernel<8, kModePlain>, build_kernel<8, kModeLog>, build_kernel<8, kModeProposal>}};
-    const Kernel kern = table[G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 6 ? 3 : 4][mode];
-    // one build: the binning for the grid (n_phi, n_z), then the kernel
-    auto enqueue = [&](int nphi, int nz) -> cudaError_t {
+    const int gi = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 6 ? 3 : 4;
+    const Kernel kern = table[gi][mode];
+    const int smem_plain = (int)((size_t)L * 128 * sizeof(int32_t) + (size_t)kSlotSize * 128 * sizeof(float));
+    if (mode == kModeProposal && (!grow(&st->seed_flag, st->flag_capacity, (size_t)b.n_seeds) ||
+                                  !grow(&st->seed_list, st->list_capacity, (size_t)b.n_seeds) ||
+                                  !grow(&st->list_count, st->count_capacity, 1)))
+        return set_error(ctx, KF_ERR_NOMEM, "could not allocate the build's scratch");
+    // one build: the binning for the grid (n_phi, n_z), then the kernel; the
+    // speculative learned build runs the plain kernel, flagging every seed one
+    // of whose windows held more than topk hits, then the proposal kernel on
+    // the flagged seeds only (the others' builds are the same either way)
+    auto enqueue = [&](int nphi, int nz, int spec) -> cudaError_t {
         const BinGrid bgr{nphi, nz, g.z_half};
         cudaError_t e1 = bin_hits(b.seg_off, (int64_t)n_seg, b.max_seg, b.hit_pos, b.n_hits, bgr, st->bkey,
                                   st->bin_off, st->bin_cnt, context_sm_count(ctx), stream);
@@ -788,25 +874,46 @@ int build_run(kf_context *ctx, const FitGeom &g, const kf_options &o, const Buil
         if ((e1 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
             return e1;
         if (log && (e1 = cudaMemsetAsync(log->count, 0, sizeof(uint64_t), stream)) != cudaSuccess) return e1;
-        if (b.n_seeds > 0) kern<<<grid, 128, smem, stream>>>(q);
+        if (b.n_seeds == 0) return cudaGetLastError();
+        if (mode == kModeProposal && spec) {
+            const Kernel kp = table[gi][kModePlain];
+            if ((e1 = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_plain)) !=
+                cudaSuccess)
+                return e1;
+            BuildParams q1 = q;
+            q1.flag_over = o.topk;
+            q1.seed_flag = st->seed_flag;
+            kp<<<grid, 128, smem_plain, stream>>>(q1);
+            if ((e1 = cudaMemsetAsync(st->list_count, 0, sizeof(unsigned), stream)) != cudaSuccess) return e1;
+            const unsigned cg = (unsigned)std::min<int64_t>((b.n_seeds + 255) / 256, (int64_t)context_sm_count(ctx) * 8);
+            flagged_seeds_kernel<<<cg, 256, 0, stream>>>(st->seed_flag, b.n_seeds, st->seed_list, st->list_count);
+            q.seed_list = st->seed_list;
+            q.list_count = st->list_count;
+        }
+        kern<<<grid, 128, smem, stream>>>(q);
         return cudaGetLastError();
     };
     // the shape: the one tuned for this workload class, or tuned now on the
     // caller's own buffers (a build only reads its inputs and overwrites its
     // outputs; the training log restarts its count)
     const auto key = std::make_tuple(L, p.N, mode, size_class(b.n_seeds), size_class(b.n_hits), o.n_phi_bins, o.n_z_bins);
-    std::pair<int, int> shape;
+    std::tuple<int, int, int> shape;
     cudaError_t e = cudaSuccess;
     auto it = st->tuned.find(key);
     if (it != st->tuned.end()) {
         shape = it->second;
     } else {
-        std::vector<std::pair<int, int>> cand;
-        for (const auto &gr : kBinGrids)
-            if ((!o.n_phi_bins || o.n_phi_bins == gr[0]) && (!o.n_z_bins || o.n_z_bins == gr[1]))
-                cand.emplace_back(gr[0], gr[1]);
-        if (cand.empty())  // a fixed grid outside the tuner's list
-            cand.emplace_back(o.n_phi_bins ? o.n_phi_bins : 256, o.n_z_bins ? o.n_z_bins : 64);
+        std::vector<std::tuple<int, int, int>> cand;
+        for (int spec = 0; spec <= (mode == kModeProposal ? 1 : 0); ++spec) {
+            for (const auto &gr : kBinGrids)
+                if ((!o.n_phi_bins || o.n_phi_bins == gr[0]) && (!o.n_z_bins || o.n_z_bins == gr[1]))
+                    cand.emplace_back(gr[0], gr[1], spec);
+            if (!o.n_phi_bins && !o.n_z_bins) continue;
+            bool listed = false;
+            for (const auto &c : cand) listed |= std::get<2>(c) == spec;
+            if (!listed)  // a fixed grid outside the tuner's list
+                cand.emplace_back(o.n_phi_bins ? o.n_phi_bins : 256, o.n_z_bins ? o.n_z_bins : 64, spec);
+        }
         shape = cand[0];
         if (cand.size() > 1) {
             cudaEvent_t ta, tb;
@@ -814,9 +921,10 @@ int build_run(kf_context *ctx, const FitGeom &g, const kf_options &o, const Buil
             cudaEventCreate(&tb);
             float best = 1e30f;
             for (const auto &c : cand) {
-                if ((e = enqueue(c.first, c.second)) != cudaSuccess) break;
+                if ((e = enqueue(std::get<0>(c), std::get<1>(c), std::get<2>(c))) != cudaSuccess) break;
                 cudaEventRecord(ta, stream);
-                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = enqueue(c.first, c.second);
+                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep)
+                    e = enqueue(std::get<0>(c), std::get<1>(c), std::get<2>(c));
                 cudaEventRecord(tb, stream);
                 if (e != cudaSuccess || (e = cudaEventSynchronize(tb)) != cudaSuccess) break;
                 float ms = 0.0f;
@@ -832,7 +940,8 @@ int build_run(kf_context *ctx, const FitGeom &g, const kf_options &o, const Buil
         }
         st->tuned[key] = shape;
     }
-    if ((e = enqueue(shape.first, shape.second)) != cudaSuccess) return cuda_error(ctx, e, "build launch");
+    if ((e = enqueue(std::get<0>(shape), std::get<1>(shape), std::get<2>(shape))) != cudaSuccess)
+        return cuda_error(ctx, e, "build launch");
     return KF_OK;
 }
 
@@ -966,15 +1075,16 @@ extern "C" int kf_build_tracks_logged(kf_context *ctx, const kf_geometry *geom, 
 }
 
 extern "C" int kf_build_tuned_shape(kf_context *ctx, int n_layers, int max_cands, int mode, int64_t n_seeds,
-                                    int64_t n_hits, int *n_phi_bins, int *n_z_bins)
+                                    int64_t n_hits, int *n_phi_bins, int *n_z_bins, int *speculative)
 {
     if (!ctx || !n_phi_bins || !n_z_bins) return KF_ERR_ARG;
     BuildState *st = context_build_state(ctx);
     if (st) {
         auto it = st->tuned.find(std::make_tuple(n_layers, max_cands, mode, size_class(n_seeds), size_class(n_hits), 0, 0));
         if (it != st->tuned.end()) {
-            *n_phi_bins = it->second.first;
-            *n_z_bins = it->second.second;
+            *n_phi_bins = std::get<0>(it->second);
+            *n_z_bins = std::get<1>(it->second);
+            if (speculative) *speculative = std::get<2>(it->second);
             return KF_OK;
         }
     }

@@ -16,33 +16,26 @@
 // transport's transverse block (well conditioned), and Cp^-1 (a Cholesky
 // factorisation of Cp scaled to unit diagonal) only multiplies the scattering
 // noise, so the FP32 rounding that Cp's correlations amplify enters A scaled
-// by |Q| / |Cp|; the other factor is never formed.  The forward pass keeps the
-// predicted state, the predicted local covariance, G and Q of every layer in
-// context scratch ([L][40][T] floats); the filtered state and local
-// covariance (with the frame) go to the output arrays, which the backward
-// pass overwrites with the smoothed ones.
+// by |Q| / |Cp|; the other factor is never formed.  The forward pass writes
+// the filtered state and local covariance (with the frame) of every layer to
+// the output arrays; the backward pass reads them, recomputes the prediction
+// of layer l+1 from the filtered estimate of layer l (the same propagation,
+// transport and scattering as the forward pass, on the same state bits: xp, G
+// and Q come out identical, Cp differs by the rounding of the stored local
+// covariance), and overwrites them with the smoothed ones.  Nothing else is
+// stored: a track's filtered estimates (108 B per layer) are read back while
+// still in L2, and each output line reaches DRAM once, smoothed.
 #include "kf.h"
 #include "kf_api_internal.h"
 #include "kf_fit.cuh"
 
 namespace kf {
 
-struct SmoothState {
-    float *buf = nullptr;
-    size_t cap = 0;  // floats
-};
+struct SmoothState {};  // the smoother keeps no scratch
 
-void destroy_smooth_state(SmoothState *s)
-{
-    if (!s) return;
-    cudaFree(s->buf);
-    delete s;
-}
+void destroy_smooth_state(SmoothState *s) { delete s; }
 
 namespace {
-
-constexpr int kScr = 40;  // scratch floats per track-layer: xp 6, Cp 15, G 13, Q 6
-constexpr int kScrXp = 0, kScrCp = 6, kScrG = 21, kScrQ = 34;
 
 struct SmoothIO {
     int64_t T;
@@ -53,7 +46,6 @@ struct SmoothIO {
     float *out_state, *out_cov;  // [L][6][T], [L][21][T]
     int16_t *out_reached;
     uint32_t *out_flags;
-    float *scr;  // [L][kScr][T]
 };
 
 __device__ __forceinline__ void local_of(const float c[21], float nx, float ny, float cl[15])
@@ -101,6 +93,24 @@ __device__ __forceinline__ void local_jacobian(const Jac &J, float nx0, float ny
     g[12] = J.jzpz;
 }
 
+// The scattering noise of layer l on the momentum block, packed (px,px)
+// (py,px) (py,py) (pz,px) (pz,py) (pz,pz): theta0^2 (|p|^2 I3 - p p^T).
+__device__ __forceinline__ void scattering_q6(const float xn[6], float inv_r, float x_over_x0, float q6[6])
+{
+#pragma unroll
+    for (int i = 0; i < 6; ++i) q6[i] = 0.0f;
+    if (!(x_over_x0 > 0.0f)) return;
+    float p2;
+    const float t2 = scattering_theta2(xn, inv_r, x_over_x0, p2);
+    const float px = xn[3], py = xn[4], pz = xn[5];
+    q6[0] = t2 * (p2 - px * px);
+    q6[1] = -t2 * px * py;
+    q6[2] = t2 * (p2 - py * py);
+    q6[3] = -t2 * pz * px;
+    q6[4] = -t2 * pz * py;
+    q6[5] = t2 * (p2 - pz * pz);
+}
+
 // Registers capped at 128 (four blocks, 16 warps per SM) with a small spill:
 // 2.23 ms on the fit workload against 2.46 ms uncapped (237 registers, eight
 // warps); caps of 102 and 85 registers spill more and are slower.
@@ -113,7 +123,6 @@ __global__ void __launch_bounds__(128, 4) smooth_kernel(const FitGeom g, const R
     const int L = g.L;
     float *slot = slots + threadIdx.x;
     const int stride = blockDim.x;
-    auto scr = [&](int l, int i) -> float & { return io.scr[((int64_t)l * kScr + i) * T + t]; };
     auto ost = [&](int l, int i) -> float & { return io.out_state[((int64_t)l * 6 + i) * T + t]; };
     auto ocv = [&](int l, int i) -> float & { return io.out_cov[((int64_t)l * 21 + i) * T + t]; };
 
@@ -122,18 +131,17 @@ __global__ void __launch_bounds__(128, 4) smooth_kernel(const FitGeom g, const R
     bool finite = true;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        x[i] = io.seed_state[i * T + t];
+        x[i] = __ldcs(io.seed_state + i * T + t);
         finite = finite && isfinite(x[i]);
     }
 #pragma unroll
     for (int i = 0; i < 21; ++i) {
-        c[i] = io.seed_cov[i * T + t];
+        c[i] = __ldcs(io.seed_cov + i * T + t);
         finite = finite && isfinite(c[i]);
     }
     const float qkb = (float)io.charge[t] * g.qk;
     const uint32_t mask = io.hit_mask[t];
     uint32_t flags = finite ? 0u : (uint32_t)KF_FLAG_NAN_INPUT;
-    float nx0 = 1.0f, ny0 = 0.0f;
     int K = 0;
     for (int l = 0; l < L && finite; ++l) {
         float xn[6], s;
@@ -147,53 +155,25 @@ __global__ void __launch_bounds__(128, 4) smooth_kernel(const FitGeom g, const R
             break;
         }
         const float nx1 = xn[0] * g.inv_r[l], ny1 = xn[1] * g.inv_r[l];
-        if (l > 0) {
-            float gj[13];
-            local_jacobian(J, nx0, ny0, nx1, ny1, gj);
-#pragma unroll
-            for (int i = 0; i < 13; ++i) scr(l, kScrG + i) = gj[i];
-        }
         transport(J, c);
         {
-            // the scattering noise on the momentum block, kept for the backward pass
-            float q6[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-            if (g.xx0[l] > 0.0f) {
-                float p2;
-                const float t2 = scattering_theta2(xn, g.inv_r[l], g.xx0[l], p2);
-                const float px = xn[3], py = xn[4], pz = xn[5];
-                q6[0] = t2 * (p2 - px * px);
-                q6[1] = -t2 * px * py;
-                q6[2] = t2 * (p2 - py * py);
-                q6[3] = -t2 * pz * px;
-                q6[4] = -t2 * pz * py;
-                q6[5] = t2 * (p2 - pz * pz);
-            }
+            float q6[6];
+            scattering_q6(xn, g.inv_r[l], g.xx0[l], q6);
             c[pk(3, 3)] += q6[0];
             c[pk(4, 3)] += q6[1];
             c[pk(4, 4)] += q6[2];
             c[pk(5, 3)] += q6[3];
             c[pk(5, 4)] += q6[4];
             c[pk(5, 5)] += q6[5];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) scr(l, kScrQ + i) = q6[i];
         }
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            x[i] = xn[i];
-            scr(l, kScrXp + i) = xn[i];
-        }
-        {
-            float cl[15];
-            local_of(c, nx1, ny1, cl);
-#pragma unroll
-            for (int i = 0; i < 15; ++i) scr(l, kScrCp + i) = cl[i];
-        }
+        for (int i = 0; i < 6; ++i) x[i] = xn[i];
         if ((mask >> l) & 1u) {
             float m[3], v[6], d = 0.0f;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) m[i] = io.hit_pos[((int64_t)l * 3 + i) * T + t];
+            for (int i = 0; i < 3; ++i) m[i] = __ldcs(io.hit_pos + ((int64_t)l * 3 + i) * T + t);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) v[i] = io.hit_cov[((int64_t)l * 6 + i) * T + t];
+            for (int i = 0; i < 6; ++i) v[i] = __ldcs(io.hit_cov + ((int64_t)l * 6 + i) * T + t);
             bool hit_ok = true;
 #pragma unroll
             for (int i = 0; i < 3; ++i) hit_ok = hit_ok && isfinite(m[i]);
@@ -220,8 +200,6 @@ __global__ void __launch_bounds__(128, 4) smooth_kernel(const FitGeom g, const R
             ocv(l, 15) = nx1;
             ocv(l, 16) = ny1;
         }
-        nx0 = nx1;
-        ny0 = ny1;
         K = l + 1;
     }
     if (!finite) K = 0;
@@ -244,18 +222,33 @@ __global__ void __launch_bounds__(128, 4) smooth_kernel(const FitGeom g, const R
     for (int l = K - 2; l >= 0; --l) {
         float xf[6], cf[15], cp[15], xp[6], gj[13], q6[6];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) xf[i] = ost(l, i);
+        for (int i = 0; i < 6; ++i) xf[i] = __ldlu(&ost(l, i));  // the filtered estimate's last read
 #pragma unroll
-        for (int i = 0; i < 15; ++i) cf[i] = ocv(l, i);
-        const float nxl = ocv(l, 15), nyl = ocv(l, 16);
+        for (int i = 0; i < 15; ++i) cf[i] = __ldlu(&ocv(l, i));
+        const float nxl = __ldlu(&ocv(l, 15)), nyl = __ldlu(&ocv(l, 16));
+        {
+            // the prediction of layer l+1 from the filtered estimate of layer
+            // l, as the forward pass made it (the track reached layer l+1 there)
+            float c21[21];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) xp[i] = scr(l + 1, kScrXp + i);
+            for (int i = 0; i < 6; ++i)
 #pragma unroll
-        for (int i = 0; i < 15; ++i) cp[i] = scr(l + 1, kScrCp + i);
-#pragma unroll
-        for (int i = 0; i < 13; ++i) gj[i] = scr(l + 1, kScrG + i);
-#pragma unroll
-        for (int i = 0; i < 6; ++i) q6[i] = scr(l + 1, kScrQ + i);
+                for (int j = 0; j <= i; ++j) c21[pk(i, j)] = cart_of(cf, nxl, nyl, i, j);
+            float sd;
+            Jac J;
+            propagate(xf, qkb, g.r[l + 1], xp, sd, &J);
+            const float nx1 = xp[0] * g.inv_r[l + 1], ny1 = xp[1] * g.inv_r[l + 1];
+            local_jacobian(J, nxl, nyl, nx1, ny1, gj);
+            transport(J, c21);
+            scattering_q6(xp, g.inv_r[l + 1], g.xx0[l + 1], q6);
+            c21[pk(3, 3)] += q6[0];
+            c21[pk(4, 3)] += q6[1];
+            c21[pk(4, 4)] += q6[2];
+            c21[pk(5, 3)] += q6[3];
+            c21[pk(5, 4)] += q6[4];
+            c21[pk(5, 5)] += q6[5];
+            local_of(c21, nx1, ny1, cp);
+        }
         // Cholesky of Cp scaled to unit diagonal: S = D Cp D, D = diag(Cp)^-1/2
         float dsc[5], Lc[15];
         bool ok = true;
@@ -398,11 +391,11 @@ __global__ void __launch_bounds__(128, 4) smooth_kernel(const FitGeom g, const R
         nx = nxl;
         ny = nyl;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) ost(l, i) = xs[i];
+        for (int i = 0; i < 6; ++i) __stcs(&ost(l, i), xs[i]);  // final: streamed out
 #pragma unroll
         for (int i = 0; i < 6; ++i)
 #pragma unroll
-            for (int j = 0; j <= i; ++j) ocv(l, pk(i, j)) = cart_of(cs, nx, ny, i, j);
+            for (int j = 0; j <= i; ++j) __stcs(&ocv(l, pk(i, j)), cart_of(cs, nx, ny, i, j));
     }
     // layers not reached (and every layer of a track with a non-finite input)
     for (int l = K; l < L; ++l) {
@@ -442,19 +435,8 @@ extern "C" int kf_smooth_tracks(kf_context *ctx, const kf_geometry *geom, int64_
         (rc = check_ptr(ctx, out_reached, 2, "out_reached")) || (rc = check_ptr(ctx, out_flags, 4, "out_flags")))
         return rc;
     DeviceGuard dg(context_device(ctx));
-    SmoothState *&st = context_smooth_state(ctx);
-    if (!st) st = new SmoothState;
-    const size_t need = (size_t)g.L * kScr * (size_t)n_tracks;
-    if (need > st->cap) {
-        cudaFree(st->buf);
-        st->buf = nullptr;
-        st->cap = 0;
-        if (cudaMalloc(&st->buf, need * sizeof(float)) != cudaSuccess)
-            return set_error(ctx, KF_ERR_NOMEM, "could not allocate %zu bytes of smoother scratch", need * 4);
-        st->cap = need;
-    }
     SmoothIO io{n_tracks, seed_state, seed_cov, charge, hit_pos, hit_cov, hit_mask,
-                out_state, out_cov, out_reached, out_flags, st->buf};
+                out_state, out_cov, out_reached, out_flags};
     const unsigned blocks = (unsigned)((n_tracks + 127) / 128);
     smooth_kernel<<<blocks, 128, kSlotSize * 128 * sizeof(float), reinterpret_cast<cudaStream_t>(stream_)>>>(
         g, make_routing(o), io);

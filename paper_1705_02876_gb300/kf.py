@@ -51,7 +51,7 @@ class Options(ctypes.Structure):
                 ("hit_sigma_rphi", ctypes.c_float), ("hit_sigma_z", ctypes.c_float),
                 ("window_max_dphi", ctypes.c_float), ("window_max_dz", ctypes.c_float),
                 ("n_phi_bins", ctypes.c_int), ("n_z_bins", ctypes.c_int),
-                ("use_proposal", ctypes.c_int), ("topk", ctypes.c_int)]
+                ("use_proposal", ctypes.c_int), ("topk", ctypes.c_int), ("tracks_per_thread", ctypes.c_int)]
 
 
 _lib = None
@@ -90,8 +90,7 @@ def load() -> ctypes.CDLL:
         L.kf_smooth_tracks.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int64] + [_vp] * 10 + \
             [ctypes.POINTER(Options), _vp]
         L.kf_transport_batch.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp]
-        L.kf_fit_tuned_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_int),
-                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.kf_fit_tuned_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int64] + [ctypes.POINTER(ctypes.c_int)] * 4
         L.kf_build_tracks.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int, _vp, _vp, _vp,
                                       ctypes.c_int64, ctypes.c_int64] + [_vp] * 10 + \
             [ctypes.POINTER(Options), _vp]
@@ -108,7 +107,7 @@ def load() -> ctypes.CDLL:
                                            ctypes.c_int64, ctypes.c_int64] + [_vp] * 10 + \
             [ctypes.c_int, ctypes.POINTER(Options)]
         L.kf_build_tuned_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
-                                           ctypes.c_int64] + [ctypes.POINTER(ctypes.c_int)] * 2
+                                           ctypes.c_int64] + [ctypes.POINTER(ctypes.c_int)] * 3
         L.kf_proposal_score_with.argtypes = [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int, _vp]
         L.kf_proposal_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
         L.kf_fit_tracks_noalloc.argtypes = [ctypes.POINTER(Geometry), ctypes.c_int64] + [_vp] * 11 + \
@@ -184,19 +183,20 @@ class Context:
             pass
 
     def build_tuned_shape(self, n_layers: int, max_cands: int, mode: int, n_seeds: int, n_hits: int):
-        """(n_phi_bins, n_z_bins) the build autotuner picked, or None before a
-        build of that class."""
-        p_, z = ctypes.c_int(), ctypes.c_int()
+        """(n_phi_bins, n_z_bins, speculative) the build autotuner picked, or
+        None before a build of that class."""
+        p_, z, sp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         rc = load().kf_build_tuned_shape(self._h, n_layers, max_cands, mode, n_seeds, n_hits, ctypes.byref(p_),
-                                         ctypes.byref(z))
-        return (p_.value, z.value) if rc == KF_OK else None
+                                         ctypes.byref(z), ctypes.byref(sp))
+        return (p_.value, z.value, sp.value) if rc == KF_OK else None
 
     def tuned_shape(self, n_layers: int, n_tracks: int):
-        """(tracks per block, register cap, hit prefetch depth) the autotuner
-        picked, or None before a fit of that size class."""
-        b, t, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        rc = load().kf_fit_tuned_shape(self._h, n_layers, n_tracks, ctypes.byref(b), ctypes.byref(t), ctypes.byref(d))
-        return (b.value, t.value, d.value) if rc == KF_OK else None
+        """(threads per block, register cap, hit prefetch depth, tracks per
+        thread) the autotuner picked, or None before a fit of that size class."""
+        b, t, d, p_ = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        rc = load().kf_fit_tuned_shape(self._h, n_layers, n_tracks, ctypes.byref(b), ctypes.byref(t), ctypes.byref(d),
+                                       ctypes.byref(p_))
+        return (b.value, t.value, d.value, p_.value) if rc == KF_OK else None
 
 
 class GeometryArgs:

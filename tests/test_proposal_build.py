@@ -164,6 +164,26 @@ def test_proposal_parity(kf, ctx, oracle, trained_weights, net, nf):
     assert chose  # the network did choose
 
 
+def test_proposal_parity_sparse_windows(kf, ctx, oracle):
+    """The build workload's density (10x noise), where few windows hold more
+    than topk hits: the autotuner may run the learned build speculatively (a
+    plain pass flags the seeds with a wider window, the proposal pass rebuilds
+    those); either way the result is the FP64 network's build."""
+    ev = synth.make_build_events(56, 2, 1000)
+    seeds = oracle_seeds(oracle, ev)
+    w = mlp_oracle.init_params(np.random.default_rng(11)).astype(np.float32)
+    kf.proposal_load(ctx, _t(w, torch.float32))
+    wi = mlp_oracle.inference_weights(w)
+    for topk in (1, 2):
+        gpu = gpu_build(kf, ctx, ev, seeds, max_cands=6, use_proposal=1, topk=topk)
+        shape = ctx.build_tuned_shape(ev.build_geom.n_layers, 6, 2, ev.n_seeds, ev.hit_pos.shape[1])
+        assert shape is not None and shape[2] in (0, 1)
+        ref = oracle.build_events(ev, seeds=seeds, max_cands=6, mlp=wi, topk=topk, margins=True)
+        assert identical_fraction(gpu, ref) >= 0.999
+        bad, near_share = untraced_mismatches(gpu, ref)
+        assert bad.size == 0, (topk, bad, ref["margin"][bad], near_share)
+
+
 def test_constant_network_parity(kf, ctx, oracle):
     """All logits equal: both sides keep the lowest hit indices."""
     ev = synth.make_build_events(53, 1, 800, noise_factor=100)
