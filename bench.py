@@ -675,8 +675,7 @@ def bench_ragged(args, kf, ctx, dev, stream, rank):
         res[name] = {"value": T / (ms * 1e-3), "unit": "tracks/s", "ms_per_step": ms,
                      "launches_per_step": 1 if mode != kf.LAUNCH_PER_EVENT else len(b.event_offsets) - 1}
     shape = ctx.tuned_shape(b.geom.n_layers, T)
-    res["tuned_shape"] = ({"tracks_per_block": shape[0], "reg_cap": shape[1], "hit_prefetch": shape[2],
-                           "tracks_per_thread": shape[3]}
+    res["tuned_shape"] = ({"tracks_per_block": shape[0], "reg_cap": shape[1], "hit_prefetch": shape[2]}
                           if shape else None)
     return res
 
@@ -787,7 +786,6 @@ def main():
         parts = [int(v) for v in args.shape.split(":")]
         chosen.tracks_per_block, chosen.reg_cap = parts[0], parts[1]
         chosen.hit_prefetch = parts[2] if len(parts) > 2 else 1
-        chosen.tracks_per_thread = parts[3] if len(parts) > 3 else 1
 
     def step(opt=chosen, o=out):
         kf.fit_tracks(ctx, geom, **d_in, event_offsets=batch.event_offsets, opt=opt, out=o, stream=stream)
@@ -865,7 +863,7 @@ def main():
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     tuned = (ctx.tuned_shape(N_LAYERS, T) if not args.shape
-             else (chosen.tracks_per_block, chosen.reg_cap, chosen.hit_prefetch, chosen.tracks_per_thread or 1))
+             else (chosen.tracks_per_block, chosen.reg_cap, chosen.hit_prefetch))
     line = {
         "metric": METRIC, "value": value, "unit": "tracks/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -874,7 +872,6 @@ def main():
                    "l2": "inputs larger than L2 (1.18 GB per step), not flushed",
                    "tracks_per_block": tuned[0] if tuned else None, "reg_cap": tuned[1] if tuned else None,
                    "hit_prefetch": tuned[2] if tuned else None,
-                   "tracks_per_thread": tuned[3] if tuned else None,
                    "parallelism": f"replicas{world}"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": traffic,

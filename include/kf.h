@@ -104,8 +104,7 @@ typedef struct {
                                 its gain (S^-1 and K) in float-float; 0 = off */
     /* launch shape (fit) */
     int launch_mode;         /* KF_LAUNCH_* */
-    int tracks_per_block;    /* threads per block of the persistent fit (tracks, at one per thread):
-                                0 = autotuned, else 32, 64, 128 or 256 */
+    int tracks_per_block;    /* 0 = autotuned, else 32, 64, 128 or 256 */
     int reg_cap;             /* registers per thread of the persistent fit: 0 = autotuned,
                                 -1 = uncapped, 168, 128, 96 or 80 */
     int hit_prefetch;        /* layers of hits the persistent fit loads ahead of their
@@ -123,9 +122,6 @@ typedef struct {
     int n_z_bins;            /* ... and in z (0 = autotuned); at most 16,384 bins */
     int use_proposal;        /* 1: the learned proposal keeps the top-k in-window hits */
     int topk;
-    /* launch shape (fit), continued */
-    int tracks_per_thread;   /* tracks each thread of the persistent fit carries: 0 = autotuned,
-                                1, or 2 (two tracks on the packed FP32x2 instructions) */
 } kf_options;
 
 /* Fill *opt with the defaults: routed precision (cond_max 1e4, pT in
@@ -510,13 +506,12 @@ int kf_transport_batch(kf_context *ctx, int64_t n, const float *J, float *C, kf_
 /*
  * Launch shape the autotuner picked for the persistent fit of n_layers layers
  * and a batch of n_tracks' size class (powers of two), once a KF_LAUNCH_AUTO
- * fit of that class has run on ctx.  Writes threads per block, the register
- * cap per thread (-1: uncapped), the hit prefetch depth and the tracks per
- * thread (kf_options; tracks_per_thread may be NULL).  KF_ERR_ARG if that
- * class has not been tuned.
+ * fit of that class has run on ctx.  Writes tracks per block, the register
+ * cap per thread (-1: uncapped) and the hit prefetch depth (kf_options).
+ * KF_ERR_ARG if that class has not been tuned.
  */
 int kf_fit_tuned_shape(kf_context *ctx, int n_layers, int64_t n_tracks, int *tracks_per_block,
-                       int *reg_cap, int *hit_prefetch, int *tracks_per_thread);
+                       int *reg_cap, int *hit_prefetch);
 
 /*
  * The fit for callers that cannot allocate device memory.  The paper has no
@@ -544,10 +539,9 @@ int kf_fit_tuned_shape(kf_context *ctx, int n_layers, int64_t n_tracks, int *tra
  *     a launch that would hold more than 16,384 resident warps (the 32-bit
  *     counter must not wrap while every warp makes its last claim; a GB300
  *     holds at most 152 x 64 = 9,728).
- *   - No tuning runs.  The shape is opt->tracks_per_block, opt->reg_cap,
- *     opt->hit_prefetch and opt->tracks_per_thread where set, else 64 threads
- *     per block, no register cap, the register prefetch (depth 1) and one
- *     track per thread.  Only the (block, cap, depth)
+ *   - No tuning runs.  The shape is opt->tracks_per_block, opt->reg_cap and
+ *     opt->hit_prefetch where set, else 64 tracks per block, no register cap
+ *     and the register prefetch (depth 1).  Only the (block, cap, depth)
  *     combinations the autotuner of kf_fit_tracks chooses from are compiled
  *     in: blocks 32/64/128/256 with cap none/168/128/96/80 at depth 1 (cap
  *     168 only below 256 threads, cap 96 only below 256), and at depths 2

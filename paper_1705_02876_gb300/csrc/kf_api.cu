@@ -40,8 +40,8 @@ struct kf_context {
     unsigned *d_counter = nullptr;  // persistent-kernel work counter
     cudaStream_t capture_stream = nullptr;
     std::string err;
-    // (L, log2 size, precision, fixed block, fixed cap, fixed depth, fixed tracks per thread) -> shape
-    std::map<std::tuple<int, int, int, int, int, int, int>, kf::FitShape> tuned;
+    // (L, log2 size, precision, fixed block, fixed cap, fixed depth) -> shape
+    std::map<std::tuple<int, int, int, int, int, int>, kf::FitShape> tuned;
     std::vector<GraphEntry> graphs;
     uint64_t clock = 0;
     kf::BuildState *build = nullptr;
@@ -139,8 +139,6 @@ int check_options(kf_context *ctx, const kf_options &o)
         return set_error(ctx, KF_ERR_ARG, "reg_cap must be 0, -1, 168, 128, 96 or 80");
     if (o.hit_prefetch != 0 && o.hit_prefetch != 1 && o.hit_prefetch != 2 && o.hit_prefetch != 4)
         return set_error(ctx, KF_ERR_ARG, "hit_prefetch must be 0, 1, 2 or 4");
-    if (o.tracks_per_thread < 0 || o.tracks_per_thread > 2)
-        return set_error(ctx, KF_ERR_ARG, "tracks_per_thread must be 0, 1 or 2");
     return KF_OK;
 }
 
@@ -172,7 +170,6 @@ void kf_options_default(kf_options *o)
     o->n_z_bins = 0;
     o->use_proposal = 0;
     o->topk = 4;
-    o->tracks_per_thread = 0;
 }
 
 int kf_context_create(kf_context **out, int device)
@@ -236,9 +233,9 @@ cudaError_t enqueue_persistent(kf_context *ctx, const FitGeom &g, const Routing 
                                const FitShape &sh, cudaStream_t stream, bool use_graph)
 {
     const int block = sh.block;
-    const int per_sm = persistent_blocks_per_sm(block, sh.cap, sh.depth, sh.tpt);
+    const int per_sm = persistent_blocks_per_sm(block, sh.cap, sh.depth);
     if (per_sm <= 0) return cudaErrorInvalidConfiguration;
-    const int64_t units = (io.T + 32 * sh.tpt - 1) / (32 * sh.tpt);  // one per warp at a time
+    const int64_t units = (io.T + 31) / 32;
     const int64_t want = (units * 32 + block - 1) / block;
     const int grid = (int)std::min<int64_t>((int64_t)ctx->sm_count * per_sm, std::max<int64_t>(want, 1));
     cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
@@ -246,11 +243,10 @@ cudaError_t enqueue_persistent(kf_context *ctx, const FitGeom &g, const Routing 
     if (!use_graph || capst != cudaStreamCaptureStatusNone) {
         cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned), stream);
         if (e != cudaSuccess) return e;
-        return launch_fit_persistent(g, rt, io, block, sh.cap, sh.depth, sh.tpt, grid, ctx->d_counter, stream);
+        return launch_fit_persistent(g, rt, io, block, sh.cap, sh.depth, grid, ctx->d_counter, stream);
     }
     for (auto &e : ctx->graphs) {
-        if (e.shape.block == block && e.shape.cap == sh.cap && e.shape.depth == sh.depth && e.shape.tpt == sh.tpt &&
-            e.grid == grid &&
+        if (e.shape.block == block && e.shape.cap == sh.cap && e.shape.depth == sh.depth && e.grid == grid &&
             same_bytes(&e.g, &g, sizeof g) &&
             same_bytes(&e.rt, &rt, sizeof rt) && same_bytes(&e.io, &io, sizeof io)) {
             e.last_use = ++ctx->clock;
@@ -262,7 +258,7 @@ cudaError_t enqueue_persistent(kf_context *ctx, const FitGeom &g, const Routing 
     if (e != cudaSuccess) return e;
     cudaError_t e1 = cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned), ctx->capture_stream);
     cudaError_t e2 = e1 == cudaSuccess
-                         ? launch_fit_persistent(g, rt, io, block, sh.cap, sh.depth, sh.tpt, grid, ctx->d_counter,
+                         ? launch_fit_persistent(g, rt, io, block, sh.cap, sh.depth, grid, ctx->d_counter,
                                                  ctx->capture_stream)
                          : e1;
     e = cudaStreamEndCapture(ctx->capture_stream, &graph);
@@ -286,32 +282,31 @@ cudaError_t enqueue_persistent(kf_context *ctx, const FitGeom &g, const Routing 
     return cudaGraphLaunch(exec, stream);
 }
 
-// Time every compiled (tracks per block, register cap, hit prefetch depth,
-// tracks per thread) shape on the caller's own buffers (the fit is
-// idempotent: it reads its inputs and overwrites its outputs) and keep the
-// fastest for this layer count, size class and precision.  Skipped while the
-// stream is being captured.  fixed (fields 0 = free; cap -1 = uncapped)
-// restricts the search to matching shapes.
+// Time every compiled (tracks per block, register cap, hit prefetch depth)
+// shape on the caller's own buffers (the fit is idempotent: it reads its
+// inputs and overwrites its outputs) and keep the fastest for this layer
+// count, size class and precision.  Skipped while the stream is being
+// captured.  fixed (fields 0 = free; cap -1 = uncapped) restricts the search
+// to matching shapes.
 FitShape tune_shape(kf_context *ctx, const FitGeom &g, const Routing &rt, const FitIO &io, cudaStream_t stream,
                     const FitShape &fixed)
 {
-    const auto key = std::make_tuple(g.L, size_class(io.T), rt.mode, fixed.block, fixed.cap, fixed.depth, fixed.tpt);
+    const auto key = std::make_tuple(g.L, size_class(io.T), rt.mode, fixed.block, fixed.cap, fixed.depth);
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) return it->second;
     FitShape cand[64];
     int n = 0;
     {
-        int all_b[64], all_c[64], all_d[64], all_t[64];
-        const int m = persistent_shapes(all_b, all_c, all_d, all_t, 64);
+        int all_b[64], all_c[64], all_d[64];
+        const int m = persistent_shapes(all_b, all_c, all_d, 64);
         for (int i = 0; i < m; ++i)
             if ((!fixed.block || all_b[i] == fixed.block) &&
                 (!fixed.cap || all_c[i] == (fixed.cap < 0 ? 0 : fixed.cap)) &&
-                (!fixed.depth || all_d[i] == fixed.depth) && (!fixed.tpt || all_t[i] == fixed.tpt))
-                cand[n++] = FitShape{all_b[i], all_c[i], all_d[i], all_t[i]};
+                (!fixed.depth || all_d[i] == fixed.depth))
+                cand[n++] = FitShape{all_b[i], all_c[i], all_d[i]};
     }
     if (n == 0)
-        return FitShape{fixed.block ? fixed.block : 128, fixed.cap > 0 ? fixed.cap : 0, fixed.depth ? fixed.depth : 1,
-                        fixed.tpt ? fixed.tpt : 1};
+        return FitShape{fixed.block ? fixed.block : 128, fixed.cap > 0 ? fixed.cap : 0, fixed.depth ? fixed.depth : 1};
     cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(stream, &capst);
     if (capst != cudaStreamCaptureStatusNone) return cand[0];
@@ -393,9 +388,9 @@ int kf_fit_tracks(kf_context *ctx, const kf_geometry *geom, int64_t n_tracks, co
             e = launch_fit_plain(g, rt, io, event_offsets[ev], event_offsets[ev + 1], block ? block : 128, stream);
         break;
     default: {
-        FitShape shape{block, o.reg_cap < 0 ? 0 : o.reg_cap, o.hit_prefetch, o.tracks_per_thread};
-        if (!block || !o.reg_cap || !o.hit_prefetch || !o.tracks_per_thread)
-            shape = tune_shape(ctx, g, rt, io, stream, FitShape{block, o.reg_cap, o.hit_prefetch, o.tracks_per_thread});
+        FitShape shape{block, o.reg_cap < 0 ? 0 : o.reg_cap, o.hit_prefetch};
+        if (!block || !o.reg_cap || !o.hit_prefetch)
+            shape = tune_shape(ctx, g, rt, io, stream, FitShape{block, o.reg_cap, o.hit_prefetch});
         e = enqueue_persistent(ctx, g, rt, io, shape, stream, true);
     }
     }
@@ -404,16 +399,15 @@ int kf_fit_tracks(kf_context *ctx, const kf_geometry *geom, int64_t n_tracks, co
 }
 
 int kf_fit_tuned_shape(kf_context *ctx, int n_layers, int64_t n_tracks, int *tracks_per_block, int *reg_cap,
-                       int *hit_prefetch, int *tracks_per_thread)
+                       int *hit_prefetch)
 {
     if (!ctx || !tracks_per_block || !reg_cap || !hit_prefetch) return KF_ERR_ARG;
     for (int mode = 1; mode >= 0; --mode) {
-        auto it = ctx->tuned.find(std::make_tuple(n_layers, size_class(n_tracks), mode, 0, 0, 0, 0));
+        auto it = ctx->tuned.find(std::make_tuple(n_layers, size_class(n_tracks), mode, 0, 0, 0));
         if (it != ctx->tuned.end()) {
             *tracks_per_block = it->second.block;
             *reg_cap = it->second.cap ? it->second.cap : -1;
             *hit_prefetch = it->second.depth;
-            if (tracks_per_thread) *tracks_per_thread = it->second.tpt;
             return KF_OK;
         }
     }

@@ -7,7 +7,6 @@
 
 #include "kf.h"
 #include "kf_fit.cuh"
-#include "kf_pair.cuh"
 
 namespace kf {
 
@@ -203,209 +202,41 @@ __global__ void __launch_bounds__(BLOCK, MINB) fit_persistent_kernel(const FitGe
     }
 }
 
-// Two tracks per thread on the packed FP32x2 instructions (kf_pair.cuh):
-// tracks t (.x) and t + 32 (.y), the steps and stop rules of fit_track.  A
-// track that stops writes its outputs at once; its lane of the packed values
-// is not used again.  Hits are loaded for the next layer while this one is
-// fitted, as fit_track<1> does.
-__device__ __forceinline__ void fit_pair(const FitGeom &g, const Routing &rt, const FitIO &io, int64_t t0,
-                                         float *slot, int stride)
-{
-    const int64_t T = io.T;
-    const int64_t tt[2] = {t0, t0 + 32};
-    unsigned live = (tt[0] < T ? 1u : 0u) | (tt[1] < T ? 2u : 0u);
-    const int64_t tl[2] = {tt[0], tt[1] < T ? tt[1] : tt[0]};  // loads of an absent track repeat the first
-    float2 x[6], c[21];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) x[i] = make_float2(__ldcs(io.seed_state + i * T + tl[0]), __ldcs(io.seed_state + i * T + tl[1]));
-#pragma unroll
-    for (int i = 0; i < 21; ++i) c[i] = make_float2(__ldcs(io.seed_cov + i * T + tl[0]), __ldcs(io.seed_cov + i * T + tl[1]));
-    const float2 qkb = make_float2((float)io.charge[tl[0]] * g.qk, (float)io.charge[tl[1]] * g.qk);
-    const uint32_t mask[2] = {__ldcs(io.hit_mask + tl[0]), __ldcs(io.hit_mask + tl[1])};
-    uint32_t flags[2] = {0u, 0u};
-    int nhits[2] = {0, 0};
-    float2 chi2 = f2(0.0f);
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        bool fin = true;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) fin = fin && isfinite(lane_of(x[i], k));
-#pragma unroll
-        for (int i = 0; i < 21; ++i) fin = fin && isfinite(lane_of(c[i], k));
-        if (!fin) flags[k] = KF_FLAG_NAN_INPUT;
-    }
-    // write track k's outputs (its seed, for a non-finite input) and retire it
-    auto finish = [&](int k) {
-        const int64_t t = tt[k];
-        float xo[6], co[21];
-        float ch = lane_of(chi2, k);
-        int nh = nhits[k];
-        if (flags[k] & KF_FLAG_NAN_INPUT) {
-#pragma unroll
-            for (int i = 0; i < 6; ++i) xo[i] = io.seed_state[i * T + t];
-#pragma unroll
-            for (int i = 0; i < 21; ++i) co[i] = io.seed_cov[i * T + t];
-            ch = 0.0f;
-            nh = 0;
-        } else {
-#pragma unroll
-            for (int i = 0; i < 6; ++i) xo[i] = lane_of(x[i], k);
-#pragma unroll
-            for (int i = 0; i < 21; ++i) co[i] = lane_of(c[i], k);
-        }
-#pragma unroll
-        for (int i = 0; i < 6; ++i) __stcs(io.out_state + i * T + t, xo[i]);
-#pragma unroll
-        for (int i = 0; i < 21; ++i) __stcs(io.out_cov + i * T + t, co[i]);
-        __stcs(io.out_chi2 + t, ch);
-        io.out_ndof[t] = (int16_t)(3 * nh - 6);
-        io.out_flags[t] = flags[k];
-        live &= ~(1u << k);
-    };
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-        if ((live >> k & 1u) && (flags[k] & kStop)) finish(k);
-    const float *hp = io.hit_pos, *hc = io.hit_cov;
-    float2 m[3], v[6];
-    auto load_hits = [&](int l, float2 mm[3], float2 vv[6]) {
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            if ((live >> k & 1u) && ((mask[k] >> l) & 1u)) {
-#pragma unroll
-                for (int i = 0; i < 3; ++i) set_lane(mm[i], k, __ldcs(hp + (int64_t)(3 * l + i) * T + tt[k]));
-#pragma unroll
-                for (int i = 0; i < 6; ++i) set_lane(vv[i], k, __ldcs(hc + (int64_t)(6 * l + i) * T + tt[k]));
-            } else {
-#pragma unroll
-                for (int i = 0; i < 3; ++i) set_lane(mm[i], k, 0.0f);
-#pragma unroll
-                for (int i = 0; i < 6; ++i) set_lane(vv[i], k, i == 0 || i == 2 || i == 5 ? 1.0f : 0.0f);
-            }
-        }
-    };
-    if (live) load_hits(0, m, v);
-    for (int l = 0; l < g.L && live; ++l) {
-        float2 mn[3], vn[6];
-        if (l + 1 < g.L) load_hits(l + 1, mn, vn);
-        float2 xn[6];
-        Jac2 J;
-        const unsigned ok = propagate2(x, qkb, g.r[l], xn, J);
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            if (!(live >> k & 1u)) continue;
-            if (!(ok >> k & 1u)) {
-                flags[k] |= KF_FLAG_UNREACHABLE;
-                finish(k);
-            } else if (fabsf(lane_of(xn[2], k)) > g.z_half) {
-                flags[k] |= KF_FLAG_LEFT_BARREL;
-                finish(k);
-            }
-        }
-        if (!live) break;
-        transport2(J, c);
-        if (g.xx0[l] > 0.0f) add_scattering2(xn, g.inv_r[l], g.xx0[l], c);
-#pragma unroll
-        for (int i = 0; i < 6; ++i) x[i] = xn[i];
-        const unsigned has = live & (((mask[0] >> l) & 1u) | (((mask[1] >> l) & 1u) << 1));
-        if (has) {
-            float2 d;
-            int st[2];
-            update2(x, c, m, v, rt, has, d, st, slot, stride);
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                if (!(has >> k & 1u)) continue;
-                const float dk = lane_of(d, k);
-                if (st[k] == 1 || !isfinite(dk)) {
-                    bool hit_ok = true;
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) hit_ok = hit_ok && isfinite(lane_of(m[i], k));
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) hit_ok = hit_ok && isfinite(lane_of(v[i], k));
-                    if (!hit_ok) {
-                        flags[k] |= KF_FLAG_NAN_INPUT;
-                        finish(k);
-                        continue;
-                    }
-                }
-                if (st[k] == 1) {
-                    flags[k] |= KF_FLAG_INVERSION_FAILED;
-                } else {
-                    set_lane(chi2, k, lane_of(chi2, k) + dk);
-                    ++nhits[k];
-                    if (st[k] >= 2) flags[k] |= KF_FLAG_FP64_PATH;
-                    if (st[k] == 3) flags[k] |= KF_FLAG_PSD_REPAIRED;
-                }
-            }
-        }
-        if (l + 1 < g.L) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) m[i] = mn[i];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) v[i] = vn[i];
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-        if (live >> k & 1u) finish(k);
-}
-
-// Persistent kernel of fit_pair: each warp claims 64-track units (lane i fits
-// tracks 64 u + i and 64 u + 32 + i).
-template <int BLOCK, int MINB>
-__global__ void __launch_bounds__(BLOCK, MINB) fit_pair_kernel(const FitGeom g, const Routing rt, const FitIO io,
-                                                                unsigned *counter)
-{
-    __shared__ float slots[kSlotSize * BLOCK];
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned n_units = (unsigned)((io.T + 63) / 64);
-    for (;;) {
-        unsigned u = 0;
-        if (lane == 0) u = atomicAdd(counter, 1u);
-        u = __shfl_sync(0xffffffffu, u, 0);
-        if (u >= n_units) break;
-        fit_pair(g, rt, io, (int64_t)u * 64 + lane, slots + threadIdx.x, BLOCK);
-    }
-}
-
 using PersistentFn = void (*)(FitGeom, Routing, FitIO, unsigned *);
 
 // Dynamic shared memory of a shape: DEPTH + 1 stages of 9 floats per thread.
 constexpr size_t ring_bytes(int block, int depth) { return depth > 1 ? (size_t)(depth + 1) * 9 * block * 4 : 0; }
 
-// (block, register cap, hit prefetch depth, tracks per thread) shapes the
-// autotuner chooses from; cap 0 = none.  A cap of R registers is
+// (block, register cap, hit prefetch depth) shapes the autotuner chooses
+// from; cap 0 = none.  A cap of R registers is
 // __launch_bounds__(BLOCK, 65536 / (R * BLOCK)).
 struct Shape {
-    int block, cap, depth, tpt;
+    int block, cap, depth;
     PersistentFn fn;
 };
 const Shape kShapes[] = {
-    {32, 0, 1, 1, fit_persistent_kernel<32, 1, 1>},     {64, 0, 1, 1, fit_persistent_kernel<64, 1, 1>},
-    {128, 0, 1, 1, fit_persistent_kernel<128, 1, 1>},   {256, 0, 1, 1, fit_persistent_kernel<256, 1, 1>},
-    {32, 168, 1, 1, fit_persistent_kernel<32, 12, 1>},  {64, 168, 1, 1, fit_persistent_kernel<64, 6, 1>},
-    {128, 168, 1, 1, fit_persistent_kernel<128, 3, 1>}, {32, 128, 1, 1, fit_persistent_kernel<32, 16, 1>},
-    {64, 128, 1, 1, fit_persistent_kernel<64, 8, 1>},   {128, 128, 1, 1, fit_persistent_kernel<128, 4, 1>},
-    {256, 128, 1, 1, fit_persistent_kernel<256, 2, 1>}, {32, 96, 1, 1, fit_persistent_kernel<32, 20, 1>},
-    {64, 96, 1, 1, fit_persistent_kernel<64, 10, 1>},   {128, 96, 1, 1, fit_persistent_kernel<128, 5, 1>},
-    {32, 80, 1, 1, fit_persistent_kernel<32, 24, 1>},   {64, 80, 1, 1, fit_persistent_kernel<64, 12, 1>},
-    {128, 80, 1, 1, fit_persistent_kernel<128, 6, 1>},  {256, 80, 1, 1, fit_persistent_kernel<256, 3, 1>},
-    {32, 128, 2, 1, fit_persistent_kernel<32, 16, 2>},  {64, 128, 2, 1, fit_persistent_kernel<64, 8, 2>},
-    {128, 128, 2, 1, fit_persistent_kernel<128, 4, 2>}, {256, 128, 2, 1, fit_persistent_kernel<256, 2, 2>},
-    {32, 96, 2, 1, fit_persistent_kernel<32, 20, 2>},   {64, 96, 2, 1, fit_persistent_kernel<64, 10, 2>},
-    {128, 96, 2, 1, fit_persistent_kernel<128, 5, 2>},  {32, 128, 4, 1, fit_persistent_kernel<32, 16, 4>},
-    {64, 128, 4, 1, fit_persistent_kernel<64, 8, 4>},   {128, 128, 4, 1, fit_persistent_kernel<128, 4, 4>},
-    {256, 128, 4, 1, fit_persistent_kernel<256, 2, 4>}, {32, 96, 4, 1, fit_persistent_kernel<32, 20, 4>},
-    {64, 96, 4, 1, fit_persistent_kernel<64, 10, 4>},   {128, 96, 4, 1, fit_persistent_kernel<128, 5, 4>},
-    // two tracks per thread (hits one layer ahead in registers)
-    {32, 0, 1, 2, fit_pair_kernel<32, 1>},              {64, 0, 1, 2, fit_pair_kernel<64, 1>},
-    {128, 0, 1, 2, fit_pair_kernel<128, 1>},            {64, 168, 1, 2, fit_pair_kernel<64, 6>},
-    {128, 168, 1, 2, fit_pair_kernel<128, 3>},
+    {32, 0, 1, fit_persistent_kernel<32, 1, 1>},     {64, 0, 1, fit_persistent_kernel<64, 1, 1>},
+    {128, 0, 1, fit_persistent_kernel<128, 1, 1>},   {256, 0, 1, fit_persistent_kernel<256, 1, 1>},
+    {32, 168, 1, fit_persistent_kernel<32, 12, 1>},  {64, 168, 1, fit_persistent_kernel<64, 6, 1>},
+    {128, 168, 1, fit_persistent_kernel<128, 3, 1>}, {32, 128, 1, fit_persistent_kernel<32, 16, 1>},
+    {64, 128, 1, fit_persistent_kernel<64, 8, 1>},   {128, 128, 1, fit_persistent_kernel<128, 4, 1>},
+    {256, 128, 1, fit_persistent_kernel<256, 2, 1>}, {32, 96, 1, fit_persistent_kernel<32, 20, 1>},
+    {64, 96, 1, fit_persistent_kernel<64, 10, 1>},   {128, 96, 1, fit_persistent_kernel<128, 5, 1>},
+    {32, 80, 1, fit_persistent_kernel<32, 24, 1>},   {64, 80, 1, fit_persistent_kernel<64, 12, 1>},
+    {128, 80, 1, fit_persistent_kernel<128, 6, 1>},  {256, 80, 1, fit_persistent_kernel<256, 3, 1>},
+    {32, 128, 2, fit_persistent_kernel<32, 16, 2>},  {64, 128, 2, fit_persistent_kernel<64, 8, 2>},
+    {128, 128, 2, fit_persistent_kernel<128, 4, 2>}, {256, 128, 2, fit_persistent_kernel<256, 2, 2>},
+    {32, 96, 2, fit_persistent_kernel<32, 20, 2>},   {64, 96, 2, fit_persistent_kernel<64, 10, 2>},
+    {128, 96, 2, fit_persistent_kernel<128, 5, 2>},  {32, 128, 4, fit_persistent_kernel<32, 16, 4>},
+    {64, 128, 4, fit_persistent_kernel<64, 8, 4>},   {128, 128, 4, fit_persistent_kernel<128, 4, 4>},
+    {256, 128, 4, fit_persistent_kernel<256, 2, 4>}, {32, 96, 4, fit_persistent_kernel<32, 20, 4>},
+    {64, 96, 4, fit_persistent_kernel<64, 10, 4>},   {128, 96, 4, fit_persistent_kernel<128, 5, 4>},
 };
 
-const Shape *find_shape(int block, int cap, int depth, int tpt)
+const Shape *find_shape(int block, int cap, int depth)
 {
     for (const Shape &sh : kShapes)
-        if (sh.block == block && sh.cap == cap && sh.depth == depth && sh.tpt == tpt) return &sh;
+        if (sh.block == block && sh.cap == cap && sh.depth == depth) return &sh;
     return nullptr;
 }
 
@@ -440,9 +271,9 @@ cudaError_t launch_fit_plain(const FitGeom &g, const Routing &rt, const FitIO &i
     return cudaGetLastError();
 }
 
-int persistent_blocks_per_sm(int block, int cap, int depth, int tpt)
+int persistent_blocks_per_sm(int block, int cap, int depth)
 {
-    const Shape *sh = find_shape(block, cap, depth, tpt);
+    const Shape *sh = find_shape(block, cap, depth);
     if (!sh) return 0;
     int n = 0;
     if (prepare_shape(sh) != cudaSuccess ||
@@ -451,7 +282,7 @@ int persistent_blocks_per_sm(int block, int cap, int depth, int tpt)
     return n;
 }
 
-int persistent_shapes(int *blocks, int *caps, int *depths, int *tpts, int max_n)
+int persistent_shapes(int *blocks, int *caps, int *depths, int max_n)
 {
     int n = 0;
     for (const Shape &sh : kShapes)
@@ -459,16 +290,15 @@ int persistent_shapes(int *blocks, int *caps, int *depths, int *tpts, int max_n)
             blocks[n] = sh.block;
             caps[n] = sh.cap;
             depths[n] = sh.depth;
-            tpts[n] = sh.tpt;
             ++n;
         }
     return n;
 }
 
 cudaError_t launch_fit_persistent(const FitGeom &g, const Routing &rt, const FitIO &io, int block, int cap, int depth,
-                                  int tpt, int grid, unsigned *counter, cudaStream_t stream)
+                                  int grid, unsigned *counter, cudaStream_t stream)
 {
-    const Shape *sh = find_shape(block, cap, depth, tpt);
+    const Shape *sh = find_shape(block, cap, depth);
     if (!sh) return cudaErrorInvalidValue;
     const cudaError_t e = prepare_shape(sh);
     if (e != cudaSuccess) return e;

@@ -34,11 +34,10 @@ struct FitIO {
     uint32_t *out_flags;
 };
 
-// A persistent-fit launch shape: threads per block, register cap (0 = none),
-// hit prefetch depth (layers ahead) and tracks per thread (1, or 2 on the
-// packed FP32x2 instructions).
+// A persistent-fit launch shape: threads per block, register cap (0 = none)
+// and hit prefetch depth (layers ahead).
 struct FitShape {
-    int block, cap, depth, tpt;
+    int block, cap, depth;
 };
 
 // status word bits written by the persistent kernels (device scratch)
@@ -49,16 +48,15 @@ cudaError_t launch_fit_plain(const FitGeom &g, const Routing &rt, const FitIO &i
                              int64_t t_end, int block, cudaStream_t stream);
 // Persistent kernel: grid = `grid` blocks of `block` threads with registers
 // capped at `cap` per thread (0 = no cap), hits loaded `depth` layers ahead
-// (1: registers; 2, 4: a cp.async ring in shared memory), tpt tracks per
-// thread (1, or 2); warps claim units of 32 tpt tracks from *counter, which
-// must read 0 at launch.
+// (1: registers; 2, 4: a cp.async ring in shared memory); warps claim 32-track
+// units from *counter, which must read 0 at launch.
 cudaError_t launch_fit_persistent(const FitGeom &g, const Routing &rt, const FitIO &io, int block, int cap,
-                                  int depth, int tpt, int grid, unsigned *counter, cudaStream_t stream);
+                                  int depth, int grid, unsigned *counter, cudaStream_t stream);
 // Blocks of the persistent kernel of this shape that fit on one SM at once on
 // the current device: 0 if the shape is not compiled in, -1 if a CUDA call
 // (the shared-memory opt-in or the occupancy query) failed.
-int persistent_blocks_per_sm(int block, int cap, int depth, int tpt);
-// The (block, cap, depth, tpt) shapes compiled in; returns how many were written.
-int persistent_shapes(int *blocks, int *caps, int *depths, int *tpts, int max_n);
+int persistent_blocks_per_sm(int block, int cap, int depth);
+// The (block, cap, depth) shapes compiled in; returns how many were written.
+int persistent_shapes(int *blocks, int *caps, int *depths, int max_n);
 
 }  // namespace kf

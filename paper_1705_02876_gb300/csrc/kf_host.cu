@@ -99,11 +99,10 @@ extern "C" int kf_fit_tracks_host(kf_context *ctx, const kf_geometry *geom, int6
     const int cap = o.reg_cap < 0 ? 0 : (o.reg_cap ? o.reg_cap : 128);
     DeviceGuard dg(context_device(ctx));
     const int depth = o.hit_prefetch ? o.hit_prefetch : 1;
-    const int tpt = o.tracks_per_thread ? o.tracks_per_thread : 1;
-    const int per_sm = persistent_blocks_per_sm(block, cap, depth, tpt);
+    const int per_sm = persistent_blocks_per_sm(block, cap, depth);
     if (per_sm < 1)
-        return set_error(ctx, KF_ERR_ARG, "no persistent fit of %d threads per block, cap %d, hit prefetch %d, %d tracks "
-                         "per thread", block, cap, depth, tpt);
+        return set_error(ctx, KF_ERR_ARG, "no persistent fit of %d tracks per block, cap %d, hit prefetch %d", block,
+                         cap, depth);
     const int grid = per_sm * context_sm_count(ctx);
     int64_t C = chunk_tracks ? chunk_tracks : (int64_t(1) << 18);
     C = std::min<int64_t>(C, n_tracks);
@@ -155,10 +154,10 @@ extern "C" int kf_fit_tracks_host(kf_context *ctx, const kf_geometry *geom, int6
                            static_cast<int16_t *>(dev[9]),
                            static_cast<uint32_t *>(dev[10])};
             cudaStream_t s = hp->stream[0];
-            const int64_t units = (n_tracks + 32 * tpt - 1) / (32 * tpt);
+            const int64_t units = (n_tracks + 31) / 32;
             const int grid_n = (int)std::min<int64_t>(grid, std::max<int64_t>((units * 32 + block - 1) / block, 1));
             cudaError_t e = cudaMemsetAsync(hp->counter, 0, sizeof(unsigned), s);
-            if (e == cudaSuccess) e = launch_fit_persistent(g, rt, io, block, cap, depth, tpt, grid_n, hp->counter, s);
+            if (e == cudaSuccess) e = launch_fit_persistent(g, rt, io, block, cap, depth, grid_n, hp->counter, s);
             const cudaError_t e2 = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return cuda_error(ctx, e, "host-buffer fit");
             if (e2 != cudaSuccess) return cuda_error(ctx, e2, "host-buffer fit");
@@ -218,7 +217,7 @@ extern "C" int kf_fit_tracks_host(kf_context *ctx, const kf_geometry *geom, int6
                      reinterpret_cast<float *>(b + lay.out_chi2),
                      reinterpret_cast<int16_t *>(b + lay.out_ndof),
                      reinterpret_cast<uint32_t *>(b + lay.out_flags)};
-            e = launch_fit_persistent(g, rt, io, block, cap, depth, tpt, grid, hp->counter + k, s);
+            e = launch_fit_persistent(g, rt, io, block, cap, depth, grid, hp->counter + k, s);
         }
         out(out_state, lay.out_state, 4, 6);
         out(out_cov, lay.out_cov, 4, 21);

@@ -87,11 +87,10 @@ extern "C" int kf_fit_tracks_noalloc(const kf_geometry *geom, int64_t n_tracks, 
     const int block = o.tracks_per_block ? o.tracks_per_block : 64;
     const int cap = o.reg_cap > 0 ? o.reg_cap : 0;
     const int depth = o.hit_prefetch ? o.hit_prefetch : 1;
-    const int tpt = o.tracks_per_thread ? o.tracks_per_thread : 1;
-    const int per_sm = persistent_blocks_per_sm(block, cap, depth, tpt);
+    const int per_sm = persistent_blocks_per_sm(block, cap, depth);
     if (per_sm == 0) return KF_ERR_ARG;  // this (block, cap, depth) combination is not compiled in
     if (per_sm < 0) return KF_ERR_CUDA;
-    const int64_t units = (n_tracks + 32 * tpt - 1) / (32 * tpt);
+    const int64_t units = (n_tracks + 31) / 32;
     const int64_t want = (units * 32 + block - 1) / block;
     const int grid = (int)std::min<int64_t>((int64_t)sms * per_sm, want);
     // every resident warp makes one claim past the last unit before it stops:
@@ -101,7 +100,7 @@ extern "C" int kf_fit_tracks_noalloc(const kf_geometry *geom, int64_t n_tracks, 
                    out_state, out_cov, out_chi2, out_ndof, out_flags};
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     if (cudaMemsetAsync(counter, 0, sizeof(unsigned), stream) != cudaSuccess) return KF_ERR_CUDA;
-    if (launch_fit_persistent(g, make_routing(o), io, block, cap, depth, tpt, grid, counter, stream) != cudaSuccess)
+    if (launch_fit_persistent(g, make_routing(o), io, block, cap, depth, grid, counter, stream) != cudaSuccess)
         return KF_ERR_CUDA;
     return KF_OK;
 }

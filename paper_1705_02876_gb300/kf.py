@@ -51,7 +51,7 @@ class Options(ctypes.Structure):
                 ("hit_sigma_rphi", ctypes.c_float), ("hit_sigma_z", ctypes.c_float),
                 ("window_max_dphi", ctypes.c_float), ("window_max_dz", ctypes.c_float),
                 ("n_phi_bins", ctypes.c_int), ("n_z_bins", ctypes.c_int),
-                ("use_proposal", ctypes.c_int), ("topk", ctypes.c_int), ("tracks_per_thread", ctypes.c_int)]
+                ("use_proposal", ctypes.c_int), ("topk", ctypes.c_int)]
 
 
 _lib = None
@@ -90,7 +90,7 @@ def load() -> ctypes.CDLL:
         L.kf_smooth_tracks.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int64] + [_vp] * 10 + \
             [ctypes.POINTER(Options), _vp]
         L.kf_transport_batch.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp]
-        L.kf_fit_tuned_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int64] + [ctypes.POINTER(ctypes.c_int)] * 4
+        L.kf_fit_tuned_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int64] + [ctypes.POINTER(ctypes.c_int)] * 3
         L.kf_build_tracks.argtypes = [_vp, ctypes.POINTER(Geometry), ctypes.c_int, _vp, _vp, _vp,
                                       ctypes.c_int64, ctypes.c_int64] + [_vp] * 10 + \
             [ctypes.POINTER(Options), _vp]
@@ -191,12 +191,11 @@ class Context:
         return (p_.value, z.value, sp.value) if rc == KF_OK else None
 
     def tuned_shape(self, n_layers: int, n_tracks: int):
-        """(threads per block, register cap, hit prefetch depth, tracks per
-        thread) the autotuner picked, or None before a fit of that size class."""
-        b, t, d, p_ = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        rc = load().kf_fit_tuned_shape(self._h, n_layers, n_tracks, ctypes.byref(b), ctypes.byref(t), ctypes.byref(d),
-                                       ctypes.byref(p_))
-        return (b.value, t.value, d.value, p_.value) if rc == KF_OK else None
+        """(tracks per block, register cap, hit prefetch depth) the autotuner
+        picked, or None before a fit of that size class."""
+        b, t, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        rc = load().kf_fit_tuned_shape(self._h, n_layers, n_tracks, ctypes.byref(b), ctypes.byref(t), ctypes.byref(d))
+        return (b.value, t.value, d.value) if rc == KF_OK else None
 
 
 class GeometryArgs:

@@ -139,30 +139,6 @@ def test_hit_prefetch_depths(kf, ctx, oracle, block):
         run_gpu(kf, ctx, b, hit_prefetch=3)
 
 
-@pytest.mark.parametrize("shape", [(32, -1), (64, -1), (128, -1), (64, 168), (128, 168)])
-@pytest.mark.parametrize("precision", [0, 1])
-def test_two_tracks_per_thread(kf, ctx, oracle, shape, precision):
-    """The fit with two tracks per thread on the packed FP32x2 instructions:
-    ragged events whose units hold one track of a pair, missing hits, loopers
-    and tracks leaving the barrel (one track of a pair stopping while the other
-    goes on), a non-finite seed and a non-finite hit; against the oracle, and
-    with the stop flags, ndof and non-finite handling of the one-track fit."""
-    b = synth.make_fit_batch(38, [901, 1, 33, 2100, 65], geom=synth.toy_geometry(17), hit_eff=0.9,
-                             pt_lo=0.2, pt_hi=5.0, pt_dist="loguniform", eta_max=2.0)
-    deep = np.nonzero(b.crossed[:6].all(0) & (b.hit_mask >> 4 & 1).astype(bool))[0]
-    b.seed_state[3, deep[0]] = np.nan
-    b.hit_pos[4, 1, deep[1]] = np.inf
-    ref = oracle.fit_batch(b)
-    gpu = run_gpu(kf, ctx, b, tracks_per_block=shape[0], reg_cap=shape[1], hit_prefetch=1, tracks_per_thread=2,
-                  precision_mode=precision)
-    compare(gpu, ref)
-    one = run_gpu(kf, ctx, b, tracks_per_block=shape[0], reg_cap=-1 if shape[1] < 0 else 168, hit_prefetch=1,
-                  tracks_per_thread=1, precision_mode=precision)
-    gf, of = gpu["flags"].view(np.uint32), one["flags"].view(np.uint32)
-    assert np.array_equal(gf & STOP, of & STOP) and np.array_equal(gpu["ndof"], one["ndof"])
-    assert (gf & STOP).any() and gf[deep[0]] & 8 and gf[deep[1]] & 8
-
-
 def test_stops_flags_and_anisotropic_hits(kf, ctx, oracle):
     """Loopers that cannot reach the outer layers, tracks leaving the barrel,
     off-diagonal hit covariances (sigma_r != sigma_rphi), NaN inputs."""
