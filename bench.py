@@ -703,16 +703,18 @@ def bench_smoother(args, kf, ctx, dev, stream, batch, d_in):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / n
     T, L = batch.n_tracks, batch.geom.n_layers
-    # DRAM bytes per track: fit inputs 473, per layer 160 B of scratch written and
-    # read back, 108 B of filtered estimates written and read back, 108 B of
-    # smoothed estimates written
-    per_track = 113 + 36 * L + L * (2 * 160 + 2 * 108 + 108)
-    # inputs and the smoothed outputs alone (no scratch, no filtered round trip)
+    # bytes per track the kernel moves: fit inputs 473, per layer 108 B of
+    # filtered estimates written and read back and 108 B of smoothed ones written
+    per_track = 113 + 36 * L + L * 3 * 108 + 2 + 4
+    # inputs and the smoothed outputs alone (the filtered estimates read back from L2)
     io_track = 113 + 36 * L + L * 108 + 2 + 4
+    hbm = measured_peaks().get("hbm_gbs")
+    io_gbs = io_track * T / (ms * 1e-3) / 1e9
     return {"value": T / (ms * 1e-3), "unit": "tracks/s", "ms_per_step": ms, "layers": L,
-            "hbm_gbs_algorithmic": per_track * T / (ms * 1e-3) / 1e9,
-            "hbm_gbs_inputs_outputs": io_track * T / (ms * 1e-3) / 1e9,
-            "form": "one thread per track: routed forward fit keeping every layer, then the backward pass"}
+            "gbs_kernel_bytes": per_track * T / (ms * 1e-3) / 1e9, "hbm_gbs_inputs_outputs": io_gbs,
+            "hbm_frac_inputs_outputs": io_gbs / hbm if hbm else None,
+            "form": "one thread per track: routed forward fit keeping every layer's filtered estimate, then the "
+                    "backward pass recomputing each prediction"}
 
 
 def bench_transport(args, kf, ctx, dev, stream):
