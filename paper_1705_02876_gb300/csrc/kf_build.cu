@@ -1,8 +1,9 @@
 // Combinatorial track building on sm_103a (Sections 3, 3.1 and 4.3):
 //   bin_hits          - counting sort of every (event, layer)'s hits into
 //                       phi x z bins (Section 3: hits partitioned spatially
-//                       for a fast look-up of the compatible ones), three
-//                       kernels over all segments (kf_bins.cuh);
+//                       for a fast look-up of the compatible ones), a
+//                       shared-memory count per segment and a scatter over
+//                       all segments (kf_bins.cuh);
 //   build_kernel      - the clone engine, all layers in one launch: each
 //                       seed's candidates occupy a group of G >= N lanes of
 //                       a warp (G in 1, 2, 4, 6, 8); every lane propagates
@@ -29,10 +30,10 @@
 namespace kf {
 
 struct BuildState {
-    size_t hit_capacity = 0, bin_capacity = 0, seg_capacity = 0, cnt_capacity = 0;
+    size_t hit_capacity = 0, bin_capacity = 0, seg_capacity = 0, rank_capacity = 0;
     float4 *bkey = nullptr;  // binned hits: (phi, z, index within the segment as bits, radius)
     int32_t *bin_off = nullptr;
-    int32_t *bin_cnt = nullptr;  // per (segment, bin) counts, then cursors, of the binning
+    int32_t *hit_rank = nullptr;  // the binning's rank of each hit within its bin
     int64_t *seg_off = nullptr;  // device copy of the segment bounds [n_seg + 1]
     int64_t *ev_off = nullptr;   // device copy of hit_offsets [n_events][L + 1]
     size_t ev_capacity = 0;
@@ -70,7 +71,7 @@ void destroy_build_state(BuildState *s)
         if (h) cudaStreamDestroy(h);
     cudaFree(s->bkey);
     cudaFree(s->bin_off);
-    cudaFree(s->bin_cnt);
+    cudaFree(s->hit_rank);
     cudaFree(s->seg_off);
     cudaFree(s->ev_off);
     cudaFree(s->seed_flag);
@@ -207,83 +208,196 @@ __device__ __forceinline__ bool key_less(unsigned long long a64, uint32_t a32, u
 }
 
 // Shared memory: back-pointers [L][128], update slots [kSlotSize][128], then
-// (proposal only) each warp's 32 staged input rows (FP32, kStageLd floats
-// each).
+// (proposal only) the parking columns [kWcWords][128] and each warp's 32
+// staged input rows (FP32, kStageLd floats each).
 constexpr int kStageLd = 12;
 __host__ __device__ constexpr size_t build_smem_base(int L) { return ((size_t)(L + kSlotSize) * 128 * 4 + 127) / 128 * 128; }
-constexpr size_t kBuildSmemMlp = 4 * 32 * kStageLd * sizeof(float);
 
-// What ranking a candidate's window needs: the window, its segment, the
-// prediction the hits are tested against (position, radial direction, the
-// local C_tt, C_tz, C_zz) and the proposal's candidate inputs cf[3..11].
-struct RankIn {
-    Window win;
-    int64_t seg_lo;
-    float x0, x1, x2, nx, ny, ctt, ctz, czz;
-    float cf[kMlpIn];
-    bool wide;
+// Proposal mode: where a lane parks, in shared memory, what walking the wide
+// windows needs ([kWcWords][128] words, one column per thread; the candidate
+// state x, C goes to the thread's update slot, idle at that point).  While
+// the warp walks the wide windows the candidate state is out of the
+// registers, so that the scoring's fragments do not spill it.
+constexpr int kWcHb = 0;                        // [kMaxN] collected (or ranked) hits
+constexpr int kWcNx = 8, kWcNy = 9, kWcCtt = 10, kWcCtz = 11, kWcCzz = 12;
+constexpr int kWcSegLo = 13;                    // 2 words
+constexpr int kWcBo = 15;                       // 2 words
+constexpr int kWcPhic = 17, kWcDphi = 18, kWcZ = 19, kWcDz = 20;
+constexpr int kWcIz0 = 21, kWcIz1 = 22, kWcIp0 = 23, kWcNphi = 24;
+constexpr int kWcNhits = 25, kWcQkb = 26;      // the candidate's hit count, its charge x field term
+constexpr int kWcWords = 27;
+constexpr size_t kBuildSmemMlp = (size_t)(kWcWords * 128 + 4 * 32 * kStageLd) * sizeof(float);
+
+// What scan_wide reads besides the parked columns.
+struct WideArgs {
+    const float4 *bkey;
+    const float *hit_pos, *hit_cov;
+    int64_t H;
+    int n_phi, topk, l, L;
+    const __nv_bfloat16 *W1, *W2;
+    const float *w32;
 };
 
-// The learned proposal's ranking of the windows wider than topk of one warp
-// (warp-collective: every lane calls it, converged; lanes without a wide
-// window take part in the scoring with empty rows).  A wide window's lane
-// walks its hits one per round; the warp scores the round's 32 rows on the
-// tensor cores (weights read through L1 from the loaded copies); each lane
-// keeps its topk hits by logit (logit desc, hit index asc) in hb.
-__device__ __forceinline__ void rank_window(const BuildParams &p, const RankIn &in, float *xs, uint32_t *hb)
+// The windows of one warp wider than topk, walked by the whole warp
+// (warp-collective: every lane calls it, converged; every lane has parked its
+// columns).  Each wide lane walks its own window, and the warp's other lanes
+// join the wide lanes as helpers, spread evenly: an owner served by R lanes
+// has its window's key sequence (each z row's key runs, in order) split by
+// position modulo R, so that every key is visited once.  Each round every
+// lane advances to its next in-window hit and the warp scores the round's 32
+// rows together on the tensor cores (weights read through L1); a wide lane
+// keeps its own pairs in its top-k list, (logit desc, hit index asc), and a
+// helper's pair goes to its owner by shuffle only if it beats the owner's
+// current topk-th entry.  The owner's list is written back to its hit
+// column.  Few wide lanes with long windows take about one round per 32 keys;
+// many wide lanes take about one round per hit of the longest window.  The
+// proposal's candidate inputs are computed here from the owner's parked
+// state, as the kernel computes them: log10 of the covariance diagonal,
+// q/pT, the layer's fraction l / L and the layers missed so far.
+__device__ __forceinline__ void scan_wide(const WideArgs p, bool wide, const float *slots_w, float *wc_w, float *xs)
 {
+    constexpr unsigned kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const MlpWeightsRef mw{reinterpret_cast<const uint32_t *>(p.mlp_W1), reinterpret_cast<const uint32_t *>(p.mlp_W2),
-                           p.mlp_w32 + kOffB1, p.mlp_w32 + kOffB2, p.mlp_w32 + kOffW3, p.mlp_w32[kOffB3]};
+    const int wbase = threadIdx.x - lane;
+    const unsigned wmask = __ballot_sync(kAll, wide);
+    const int W = __popc(wmask), nh = 32 - W;
+    // this lane's owner, its position among the owner's R serving lanes
+    int oi, sub;
+    if (wide) {
+        oi = __popc(wmask & ((1u << lane) - 1u));
+        sub = 0;
+    } else {
+        const int h = __popc(~wmask & ((1u << lane) - 1u));
+        oi = h % W;
+        sub = 1 + h / W;
+    }
+    unsigned om = wmask;
+    for (int i = 0; i < oi; ++i) om &= om - 1u;
+    const int owner = __ffs(om) - 1;
+    const int R = 1 + (oi < nh ? (nh - oi + W - 1) / W : 0);
+    volatile const float *oc = wc_w + wbase + owner;
+    volatile const float *os = slots_w + wbase + owner;
+    auto col = [&](int f) { return oc[f * 128]; };
+    auto icol = [&](int f) { return __float_as_int(oc[f * 128]); };
+    // the owner's candidate inputs, staged once in this lane's row
+    {
+        float *row = xs + lane * kStageLd;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) row[3 + i] = log10f(fmaxf(os[(kSlotC + pk(i, i)) * 128], 1e-30f));
+        const float px3 = os[(kSlotX + 3) * 128], px4 = os[(kSlotX + 4) * 128];
+        row[9] = copysignf(rsqrtf(px3 * px3 + px4 * px4), col(kWcQkb));
+        row[10] = __fdiv_rn((float)p.l, (float)p.L);  // correctly rounded, whatever the division flags
+        row[11] = (float)(p.l - icol(kWcNhits));
+    }
+    // the owner's key runs: z rows iz0..iz1, each one contiguous run of bins
+    // (two past the wrap at +-pi), run index ri = 2 (iz - iz0) + r
+    const int nphi = p.n_phi;
+    const int ip0 = icol(kWcIp0), iz0 = icol(kWcIz0), iz1 = icol(kWcIz1);
+    const int a0 = ip0 < 0 ? ip0 + nphi : (ip0 >= nphi ? ip0 - nphi : ip0);
+    const int e0 = a0 + icol(kWcNphi);
+    const int b0 = min(e0, nphi), b1 = e0 > nphi ? e0 - nphi : 0;
+    const int32_t *bo = reinterpret_cast<const int32_t *>(((unsigned long long)(uint32_t)icol(kWcBo + 1) << 32) |
+                                                          (uint32_t)icol(kWcBo));
+    const int64_t seg_lo =
+        (int64_t)(((unsigned long long)(uint32_t)icol(kWcSegLo + 1) << 32) | (uint32_t)icol(kWcSegLo));
+    // q: the next key to visit; while q >= kb, q - kb keys remain to skip past
+    // the current run's end
+    int ri = -1, q = sub, kb = 0;
+    auto next_hit = [&]() -> uint32_t {
+        for (;;) {
+            while (q >= kb) {
+                const int over = q - kb;
+                ++ri;
+                const int iz = iz0 + (ri >> 1);
+                if (iz > iz1) {
+                    q = kb = 0;
+                    return kNoKey;
+                }
+                const int r = ri & 1;
+                const int ra = r ? 0 : a0, rb = r ? b1 : b0;
+                if (ra >= rb) {
+                    q = over;
+                    kb = 0;
+                    continue;
+                }
+                const int32_t *rowp = bo + iz * nphi;
+                const int ka = rowp[ra];
+                kb = rowp[rb];
+                q = ka + over;
+            }
+            const float4 k = p.bkey[seg_lo + q];
+            q += R;
+            if (fabsf(wrap_pi(k.x - col(kWcPhic))) <= col(kWcDphi) && fabsf(k.y - col(kWcZ)) <= col(kWcDz))
+                return (uint32_t)__float_as_int(k.z);
+        }
+    };
     float tz[kMaxN];
     uint32_t hk[kMaxN];
 #pragma unroll
     for (int k = 0; k < kMaxN; ++k) {
         tz[k] = -INFINITY;
-        hk[k] = in.wide ? kNoKey : hb[k];
+        hk[k] = kNoKey;
     }
-    WindowCursor cur;
-    if (in.wide) cur.start(in.win);
-    bool more = in.wide;
-    const float xp[3] = {in.x0, in.x1, in.x2};
-    while (__any_sync(0xffffffffu, more)) {
-        const uint32_t hr = more ? cur.next(p, in.win) : kNoKey;
-        more = hr != kNoKey;
-        float feat[kMlpIn];
+    auto insert_top = [&](float cv, uint32_t hv) {
 #pragma unroll
-        for (int i = 0; i < kMlpIn; ++i) feat[i] = 0.0f;
+        for (int k2 = 0; k2 < kMaxN; ++k2) {
+            const bool before = k2 < p.topk && (cv > tz[k2] || (cv == tz[k2] && hv < hk[k2]));
+            const float t1 = tz[k2];
+            const uint32_t t2 = hk[k2];
+            tz[k2] = before ? cv : t1;
+            hk[k2] = before ? hv : t2;
+            cv = before ? t1 : cv;
+            hv = before ? t2 : hv;
+        }
+    };
+    bool more = true;
+    while (__any_sync(kAll, more)) {
+        const uint32_t hl = more ? next_hit() : kNoKey;
+        more = hl != kNoKey;
+        float f3[3] = {0.0f, 0.0f, 0.0f};
         if (more) {
             float m[3], v[6], dc;
-            const int64_t hg = in.seg_lo + hr;
+            const int64_t hg = seg_lo + hl;
 #pragma unroll
             for (int i = 0; i < 3; ++i) m[i] = p.hit_pos[i * p.H + hg];
 #pragma unroll
             for (int i = 0; i < 6; ++i) v[i] = p.hit_cov[i * p.H + hg];
-            hit_eval(xp, in.nx, in.ny, in.ctt, in.ctz, in.czz, m, v, &dc, feat);
-#pragma unroll
-            for (int i = 3; i < kMlpIn; ++i) feat[i] = in.cf[i];
+            const float xp[3] = {os[(kSlotX + 0) * 128], os[(kSlotX + 1) * 128], os[(kSlotX + 2) * 128]};
+            hit_eval(xp, col(kWcNx), col(kWcNy), col(kWcCtt), col(kWcCtz), col(kWcCzz), m, v, &dc, f3);
         }
         __syncwarp();  // the previous round's rows are read
 #pragma unroll
-        for (int i = 0; i < kMlpIn; ++i) xs[lane * kStageLd + i] = feat[i];
+        for (int i = 0; i < 3; ++i) xs[lane * kStageLd + i] = f3[i];
+        const MlpWeightsRef mw{reinterpret_cast<const uint32_t *>(p.W1), reinterpret_cast<const uint32_t *>(p.W2),
+                               p.w32 + kOffB1, p.w32 + kOffB2, p.w32 + kOffW3, p.w32[kOffB3]};
         const float z = mlp_score_warp_split(mw, xs, kStageLd);
-        if (more) {
-            float cv = z;
-            uint32_t hv = hr;
+        if (more && wide) insert_top(z, hl);
+        // a helper's pair goes to its owner if it beats the owner's topk-th
+        float tl = -INFINITY;
+        uint32_t th = kNoKey;
 #pragma unroll
-            for (int k2 = 0; k2 < kMaxN; ++k2) {
-                const bool before = k2 < p.topk && (cv > tz[k2] || (cv == tz[k2] && hv < hk[k2]));
-                const float t1 = tz[k2];
-                const uint32_t t2 = hk[k2];
-                tz[k2] = before ? cv : t1;
-                hk[k2] = before ? hv : t2;
-                cv = before ? t1 : cv;
-                hv = before ? t2 : hv;
+        for (int k = 0; k < kMaxN; ++k)
+            if (k == p.topk - 1) {
+                tl = tz[k];
+                th = hk[k];
             }
+        tl = __shfl_sync(kAll, tl, owner);
+        th = __shfl_sync(kAll, th, owner);
+        const bool offer = more && !wide && (z > tl || (z == tl && hl < th));
+        for (unsigned mo = __ballot_sync(kAll, offer); mo; mo &= mo - 1u) {
+            const int j = __ffs(mo) - 1;
+            const float cv = __shfl_sync(kAll, z, j);
+            const uint32_t hv = __shfl_sync(kAll, hl, j);
+            const int oj = __shfl_sync(kAll, owner, j);
+            if (lane == oj) insert_top(cv, hv);
         }
     }
+    if (wide) {
+        volatile float *mine = wc_w + threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < kMaxN; ++k) hb[k] = hk[k];
+        for (int k = 0; k < kMaxN; ++k) mine[(kWcHb + k) * 128] = __int_as_float((int)hk[k]);
+    }
+    __syncwarp();
 }
 
 // The seeds the plain pass flagged, appended to list in no fixed order.
@@ -298,14 +412,21 @@ template <int G, int MODE>
 __global__ void __launch_bounds__(128, 4) build_kernel(const BuildParams p)
 {
     constexpr int SEEDS_PER_WARP = 32 / G;
+    // a lane's child list (it gives at most N <= kMaxN hit children) and the
+    // first scan's buffer: kMaxN entries each (lists sized to G measured no
+    // faster: their shorter loops cost the plain kernel spills at 128 registers)
+    constexpr int NL = kMaxN, HB = kMaxN;
     extern __shared__ __align__(128) int32_t smem[];
     const int L = p.g.L;
     int32_t *bp = smem;                                   // [L][128] back-pointers
     float *slots = reinterpret_cast<float *>(smem + L * 128);  // [kSlotSize][128]
-    float *xs = nullptr;  // this warp's staged input rows [32][kStageLd] (proposal)
-    if (MODE == kModeProposal)
-        xs = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(smem) + build_smem_base(L)) +
-             (threadIdx.x >> 5) * 32 * kStageLd;
+    // (proposal only) this thread's parking columns [kWcWords][128] and this
+    // warp's staged input rows [32][kStageLd]
+    float *wc = nullptr, *xs = nullptr;
+    if (MODE == kModeProposal) {
+        wc = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(smem) + build_smem_base(L));
+        xs = wc + kWcWords * 128 + (threadIdx.x >> 5) * 32 * kStageLd;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int slot = lane % G, gbase = lane - slot;
     // G = 6: five groups per warp; lanes 30 and 31 form an idle group of two
@@ -367,20 +488,20 @@ __global__ void __launch_bounds__(128, 4) build_kernel(const BuildParams p)
         }
         // this candidate's best compatible hits, sorted by (chi2, hit index);
         // lr = each entry's row in the training log (logging only)
-        float lc[kMaxN];
-        uint32_t lh[kMaxN], lr[kMaxN];
+        float lc[NL];
+        uint32_t lh[NL], lr[NL];
 #pragma unroll
-        for (int k = 0; k < kMaxN; ++k) {
+        for (int k = 0; k < NL; ++k) {
             lc[k] = INFINITY;
             lh[k] = kNoKey;
             lr[k] = kNoKey;
         }
         auto insert = [&](float dc, uint32_t hl, uint32_t row) {
-            if (!(dc < lc[kMaxN - 1] || (dc == lc[kMaxN - 1] && hl < lh[kMaxN - 1]))) return;
+            if (!(dc < lc[NL - 1] || (dc == lc[NL - 1] && hl < lh[NL - 1]))) return;
             float cv = dc;
             uint32_t hv = hl, rv = row;
 #pragma unroll
-            for (int k2 = 0; k2 < kMaxN; ++k2) {
+            for (int k2 = 0; k2 < NL; ++k2) {
                 const bool before = cv < lc[k2] || (cv == lc[k2] && hv < lh[k2]);
                 const float tc = lc[k2];
                 const uint32_t th = lh[k2], tr = lr[k2];
@@ -393,7 +514,7 @@ __global__ void __launch_bounds__(128, 4) build_kernel(const BuildParams p)
             }
         };
         const int64_t seg = (int64_t)ev * (L + 1) + l;
-        const int64_t seg_lo = seed_ok ? p.ev_off[seg] : 0;
+        int64_t seg_lo = seed_ok ? p.ev_off[seg] : 0;
         Window win{};
         float nx = 0.0f, ny = 0.0f, ctt = 0.0f, ctz = 0.0f, czz = 0.0f;
         if (reached) {
@@ -444,12 +565,11 @@ __global__ void __launch_bounds__(128, 4) build_kernel(const BuildParams p)
             // first pass: the window's hits are collected (cheap bin reads
             // only) while there are at most `cap`; one more marks the window
             // as wide
-            const int cap = MODE == kModeProposal ? p.topk : kMaxN;
-            uint32_t hb[kMaxN];
+            const int cap = MODE == kModeProposal ? p.topk : HB;
+            uint32_t hb[HB];
 #pragma unroll
-            for (int k = 0; k < kMaxN; ++k) hb[k] = kNoKey;
+            for (int k = 0; k < HB; ++k) hb[k] = kNoKey;
             int n_in = 0;
-            WindowCursor cur;
             if (reached) {
                 // each z row's bins are one contiguous key run (two past the
                 // wrap at +-pi): one pair of bin-offset loads per run, then
@@ -476,7 +596,7 @@ __global__ void __launch_bounds__(128, 4) build_kernel(const BuildParams p)
                                     fabsf(kk[j].y - win.z) <= win.dz) {
                                     const uint32_t hl = (uint32_t)__float_as_int(kk[j].z);
 #pragma unroll
-                                    for (int k = 0; k < kMaxN; ++k)
+                                    for (int k = 0; k < HB; ++k)
                                         if (k == n_in && n_in < cap) hb[k] = hl;
                                     ++n_in;
                                 }
@@ -488,38 +608,70 @@ __global__ void __launch_bounds__(128, 4) build_kernel(const BuildParams p)
             const bool wide = n_in > cap;
             if (MODE == kModePlain && p.flag_over > 0) over |= n_in > p.flag_over;
             if (MODE == kModeProposal && __any_sync(0xffffffffu, wide)) {
-                // a wide window keeps its topk best hits by logit
-                RankIn in;
-                in.win = win;
-                in.seg_lo = seg_lo;
-                in.x0 = x[0];
-                in.x1 = x[1];
-                in.x2 = x[2];
-                in.nx = nx;
-                in.ny = ny;
-                in.ctt = ctt;
-                in.ctz = ctz;
-                in.czz = czz;
-                in.wide = wide;
-                float cf[kMlpIn];
-                cand_features(cf);
+                // a wide window keeps its topk best hits by logit: park this
+                // lane's state, walk the warp's wide windows, take it back
+                volatile float *vs = slots + threadIdx.x;
+                volatile float *vw = wc + threadIdx.x;
 #pragma unroll
-                for (int i = 3; i < kMlpIn; ++i) in.cf[i] = cf[i];
-                rank_window(p, in, xs, hb);
+                for (int i = 0; i < 6; ++i) vs[(kSlotX + i) * 128] = x[i];
+#pragma unroll
+                for (int i = 0; i < 21; ++i) vs[(kSlotC + i) * 128] = c[i];
+#pragma unroll
+                for (int k = 0; k < kMaxN; ++k) vw[(kWcHb + k) * 128] = __int_as_float((int)hb[k]);
+                vw[kWcNx * 128] = nx;
+                vw[kWcNy * 128] = ny;
+                vw[kWcCtt * 128] = ctt;
+                vw[kWcCtz * 128] = ctz;
+                vw[kWcCzz * 128] = czz;
+                vw[kWcSegLo * 128] = __int_as_float((int)(uint32_t)(unsigned long long)seg_lo);
+                vw[(kWcSegLo + 1) * 128] = __int_as_float((int)(uint32_t)((unsigned long long)seg_lo >> 32));
+                const unsigned long long bo_bits = reinterpret_cast<unsigned long long>(win.bo);
+                vw[kWcBo * 128] = __int_as_float((int)(uint32_t)bo_bits);
+                vw[(kWcBo + 1) * 128] = __int_as_float((int)(uint32_t)(bo_bits >> 32));
+                vw[kWcPhic * 128] = win.phic;
+                vw[kWcDphi * 128] = win.dphi;
+                vw[kWcZ * 128] = win.z;
+                vw[kWcDz * 128] = win.dz;
+                vw[kWcIz0 * 128] = __int_as_float(win.iz0);
+                vw[kWcIz1 * 128] = __int_as_float(win.iz1);
+                vw[kWcIp0 * 128] = __int_as_float(win.ip0);
+                vw[kWcNphi * 128] = __int_as_float(win.nphi);
+                vw[kWcNhits * 128] = __int_as_float(nhits);
+                vw[kWcQkb * 128] = qkb;
+                __syncwarp();
+                const WideArgs wa{p.bkey,    p.hit_pos, p.hit_cov, p.H,       p.bg.n_phi,
+                                  p.topk,    l,         L,         p.mlp_W1, p.mlp_W2, p.mlp_w32};
+                scan_wide(wa, wide, slots, wc, xs);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) x[i] = vs[(kSlotX + i) * 128];
+#pragma unroll
+                for (int i = 0; i < 21; ++i) c[i] = vs[(kSlotC + i) * 128];
+#pragma unroll
+                for (int k = 0; k < kMaxN; ++k) hb[k] = (uint32_t)__float_as_int(vw[(kWcHb + k) * 128]);
+                nx = vw[kWcNx * 128];
+                ny = vw[kWcNy * 128];
+                ctt = vw[kWcCtt * 128];
+                ctz = vw[kWcCtz * 128];
+                czz = vw[kWcCzz * 128];
+                seg_lo = (int64_t)(((unsigned long long)(uint32_t)__float_as_int(vw[(kWcSegLo + 1) * 128]) << 32) |
+                                   (uint32_t)__float_as_int(vw[kWcSegLo * 128]));
             }
             if (MODE == kModeProposal || !wide) {
                 // the full chi2 for the collected (or ranked) hits, loads
                 // issued together
 #pragma unroll
-                for (int k2 = 0; k2 < kMaxN; ++k2) {
+                for (int k2 = 0; k2 < HB; ++k2) {
                     if (hb[k2] == kNoKey) continue;
                     float m[3], v[6], dc, f3[3];
                     load_hit(hb[k2], m, v);
                     if (hit_eval(x, nx, ny, ctt, ctz, czz, m, v, &dc, f3) && dc <= p.chi2_cut)
                         insert(dc, hb[k2], kNoKey);
                 }
-            } else {
-                // exhaustive search of a window wider than the buffer
+            } else if (!(MODE == kModePlain && p.flag_over > 0)) {
+                // exhaustive search of a window wider than the buffer (the
+                // flagging pass leaves it: its seed is built again by the
+                // proposal pass)
+                WindowCursor cur;
                 cur.start(win);
                 for (uint32_t hl = cur.next(p, win); hl != kNoKey; hl = cur.next(p, win)) {
                     float m[3], v[6], dc, f3[3];
@@ -609,14 +761,14 @@ __global__ void __launch_bounds__(128, 4) build_kernel(const BuildParams p)
                 if ((b32 & 0x7ffffffu) != 0u) {  // pop the head of the list
                     if (MODE == kModeLog && lr[0] != kNoKey) p.log_y[lr[0]] = 1.0f;  // the pair survives
 #pragma unroll
-                    for (int k = 0; k < kMaxN - 1; ++k) {
+                    for (int k = 0; k < NL - 1; ++k) {
                         lc[k] = lc[k + 1];
                         lh[k] = lh[k + 1];
                         lr[k] = lr[k + 1];
                     }
-                    lc[kMaxN - 1] = INFINITY;
-                    lh[kMaxN - 1] = kNoKey;
-                    lr[kMaxN - 1] = kNoKey;
+                    lc[NL - 1] = INFINITY;
+                    lh[NL - 1] = kNoKey;
+                    lr[NL - 1] = kNoKey;
                     ++taken;
                 } else {
                     hole_taken = true;
@@ -756,7 +908,8 @@ bool reserve_bins(BuildState *st, const kf_options &o, int n_events, int L, int6
     const size_t n_seg = (size_t)n_events * L;
     const int nb = bins_needed(o);
     return grow(&st->bkey, st->hit_capacity, (size_t)n_hits) &&
-           grow(&st->bin_off, st->bin_capacity, n_seg * (nb + 1)) && grow(&st->bin_cnt, st->cnt_capacity, n_seg * nb);
+           grow(&st->bin_off, st->bin_capacity, n_seg * (nb + 1)) &&
+           grow(&st->hit_rank, st->rank_capacity, (size_t)n_hits);
 }
 
 // One build on device buffers: events [0, n_events) of the batch (ev_off, the
@@ -842,8 +995,8 @@ int build_run(kf_context *ctx, const FitGeom &g, const kf_options &o, const Buil
     const int64_t seeds_per_block = 4 * (32 / G);
     const unsigned grid = (unsigned)((b.n_seeds + seeds_per_block - 1) / seeds_per_block);
     const int mode = o.use_proposal ? kModeProposal : log ? kModeLog : kModePlain;
-    const int smem = (int)(mode == kModeProposal ? build_smem_base(L) + kBuildSmemMlp
-                                                 : (size_t)L * 128 * sizeof(int32_t) + (size_t)kSlotSize * 128 * sizeof(float));
+    const int smem_plain = (int)build_smem_base(L);
+    const int smem = (int)(mode == kModeProposal ? smem_plain + kBuildSmemMlp : smem_plain);
     using Kernel = void (*)(const BuildParams);
     static const Kernel table[5][3] = {
         {build_kernel<1, kModePlain>, build_kernel<1, kModeLog>, build_kernel<1, kModeProposal>},
@@ -853,7 +1006,6 @@ int build_run(kf_context *ctx, const FitGeom &g, const kf_options &o, const Buil
         {build_kernel<8, kModePlain>, build_kernel<8, kModeLog>, build_kernel<8, kModeProposal>}};
     const int gi = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 6 ? 3 : 4;
     const Kernel kern = table[gi][mode];
-    const int smem_plain = (int)((size_t)L * 128 * sizeof(int32_t) + (size_t)kSlotSize * 128 * sizeof(float));
     if (mode == kModeProposal && (!grow(&st->seed_flag, st->flag_capacity, (size_t)b.n_seeds) ||
                                   !grow(&st->seed_list, st->list_capacity, (size_t)b.n_seeds) ||
                                   !grow(&st->list_count, st->count_capacity, 1)))
@@ -865,7 +1017,7 @@ int build_run(kf_context *ctx, const FitGeom &g, const kf_options &o, const Buil
     auto enqueue = [&](int nphi, int nz, int spec) -> cudaError_t {
         const BinGrid bgr{nphi, nz, g.z_half};
         cudaError_t e1 = bin_hits(b.seg_off, (int64_t)n_seg, b.max_seg, b.hit_pos, b.n_hits, bgr, st->bkey,
-                                  st->bin_off, st->bin_cnt, context_sm_count(ctx), stream);
+                                  st->bin_off, st->hit_rank, context_sm_count(ctx), stream);
         if (e1 != cudaSuccess) return e1;
         BuildParams q = p;
         q.bg = bgr;

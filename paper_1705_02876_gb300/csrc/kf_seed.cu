@@ -38,8 +38,8 @@ struct SeedState {
     size_t key_cap = 0;
     int32_t *bin_off = nullptr;
     size_t bin_cap = 0;
-    int32_t *bin_cnt = nullptr;
-    size_t cnt_cap = 0;
+    int32_t *hit_rank = nullptr;  // the binning's rank of each hit within its bin
+    size_t rank_cap = 0;
     int64_t *seg_off = nullptr;
     size_t seg_cap = 0;
     int32_t *trip = nullptr;  // [5][trip_cap]: event, h0, h1, h2 (global), charge
@@ -54,7 +54,7 @@ void destroy_seed_state(SeedState *s)
     if (!s) return;
     cudaFree(s->bkey);
     cudaFree(s->bin_off);
-    cudaFree(s->bin_cnt);
+    cudaFree(s->hit_rank);
     cudaFree(s->seg_off);
     cudaFree(s->trip);
     cudaFree(s->count);
@@ -415,7 +415,7 @@ extern "C" int kf_seed_triplets(kf_context *ctx, const kf_geometry *geom, int n_
     };
     bool ok = grow((void **)&st->bkey, st->key_cap, (size_t)n_hits, sizeof(float4)) &&
               grow((void **)&st->bin_off, st->bin_cap, n_seg * (nb + 1), sizeof(int32_t)) &&
-              grow((void **)&st->bin_cnt, st->cnt_cap, n_seg * nb, sizeof(int32_t)) &&
+              grow((void **)&st->hit_rank, st->rank_cap, (size_t)n_hits, sizeof(int32_t)) &&
               grow((void **)&st->seg_off, st->seg_cap, n_seg + 1, sizeof(int64_t));
     if (ok && !st->count) ok = cudaMalloc(&st->count, sizeof(unsigned long long)) == cudaSuccess;
     if (!ok) return set_error(ctx, KF_ERR_NOMEM, "could not allocate the seeding scratch");
@@ -430,7 +430,7 @@ extern "C" int kf_seed_triplets(kf_context *ctx, const kf_geometry *geom, int n_
     BinGrid bg{o.n_phi_bins, o.n_z_bins, g.z_half};
     int64_t max_seg = 0;
     for (size_t i = 0; i < n_seg; ++i) max_seg = std::max<int64_t>(max_seg, seg[i + 1] - seg[i]);
-    if ((e = bin_hits(st->seg_off, (int64_t)n_seg, max_seg, hit_pos, n_hits, bg, st->bkey, st->bin_off, st->bin_cnt,
+    if ((e = bin_hits(st->seg_off, (int64_t)n_seg, max_seg, hit_pos, n_hits, bg, st->bkey, st->bin_off, st->hit_rank,
                       context_sm_count(ctx), stream)) != cudaSuccess)
         return cuda_error(ctx, e, "seeding binning");
 
