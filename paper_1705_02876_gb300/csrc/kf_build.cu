@@ -198,14 +198,6 @@ struct WindowCursor {
     }
 };
 
-// Order of children: (hits desc, chi2 asc, candidate asc, hit index asc) as
-// a two-word key compared lexicographically: k64 = (63 - hits) << 32 | the
-// bits of chi2 (non-negative floats order as their bit patterns), k32 =
-// candidate slot << 27 | (hit index within the layer + 1), 0 for the hole.
-__device__ __forceinline__ bool key_less(unsigned long long a64, uint32_t a32, unsigned long long b64, uint32_t b32)
-{
-    return a64 < b64 || (a64 == b64 && a32 < b32);
-}
 
 // Shared memory: back-pointers [L][128], update slots [kSlotSize][128], then
 // (proposal only) the parking columns [kWcWords][128] and each warp's 32
@@ -706,59 +698,51 @@ __global__ void __launch_bounds__(128, 4) build_kernel(const BuildParams p)
             }
         }
         // merge the group's lists: N rounds of a group arg-min; the head of a
-        // lane is its best hit child, then its hole child
+        // lane is its best hit child, then its hole child.  A round's offers
+        // come from distinct slots, so (hits desc, chi2 asc, slot asc) orders
+        // them totally and fits one 64-bit key, (63 - hits) << 35 | the bits
+        // of chi2 (non-negative floats order as their bit patterns) << 3 |
+        // slot; ~0 offers nothing.  The taker of the round's child reads the
+        // winner's hit by one more shuffle.
         int taken = 0;  // hit children of this lane already selected
         bool hole_taken = false;
-        unsigned long long my64 = 0;
-        uint32_t my32 = kNoKey;
         int new_parent = -1;
         uint32_t new_hit = 0;  // hit index + 1, 0 = hole
         float new_chi2 = 0.0f;
         int new_nhits = 0;
         int n_new = 0;
         for (int r = 0; r < N; ++r) {
-            // head of this lane
-            if (valid && taken < N && lh[0] != kNoKey) {
-                my64 = ((unsigned long long)(63 - (nhits + 1)) << 32) | __float_as_uint(chi2 + lc[0]);
-                my32 = ((uint32_t)slot << 27) | (lh[0] + 1u);
-            } else if (valid && !hole_taken) {
-                my64 = ((unsigned long long)(63 - nhits) << 32) | __float_as_uint(chi2);
-                my32 = (uint32_t)slot << 27;
-            } else {
-                my64 = ~0ull;
-                my32 = kNoKey;
-            }
-            unsigned long long b64 = my64;
-            uint32_t b32 = my32;
+            const bool offer_hit = valid && taken < N && lh[0] != kNoKey;
+            const bool offer = offer_hit || (valid && !hole_taken);
+            const int kh = offer_hit ? nhits + 1 : nhits;
+            const float kc = offer_hit ? chi2 + lc[0] : chi2;
+            unsigned long long bk = offer ? ((unsigned long long)(63 - kh) << 35) |
+                                                ((unsigned long long)__float_as_uint(kc) << 3) | (unsigned)slot
+                                          : ~0ull;
 #pragma unroll
             for (int d = 1; d < G; d <<= 1) {
-                unsigned long long o64;
-                uint32_t o32;
+                unsigned long long o;
                 if constexpr ((G & (G - 1)) == 0) {  // butterfly within a power-of-two group
-                    o64 = __shfl_xor_sync(gmask, b64, d, G);
-                    o32 = __shfl_xor_sync(gmask, b32, d, G);
+                    o = __shfl_xor_sync(gmask, bk, d, G);
                 } else {  // G = 6: pairs, then slots 0-3, then the two halves crossed
                     const int ps = d == 1 ? (slot ^ 1) : d == 2 ? (slot < 4 ? slot ^ 2 : slot)
                                                                 : (slot < 4 ? 4 + (slot & 1) : slot - 4);
                     const int src_lane = lane_ok ? gbase + ps : lane;
-                    o64 = __shfl_sync(gmask, b64, src_lane, 32);
-                    o32 = __shfl_sync(gmask, b32, src_lane, 32);
+                    o = __shfl_sync(gmask, bk, src_lane, 32);
                 }
-                if (key_less(o64, o32, b64, b32)) {
-                    b64 = o64;
-                    b32 = o32;
-                }
+                bk = o < bk ? o : bk;
             }
-            if (b32 == kNoKey) break;
-            const int win_slot = (int)(b32 >> 27);
+            if (bk == ~0ull) break;
+            const int win_slot = (int)(bk & 7u);
+            const uint32_t whit = __shfl_sync(gmask, offer_hit ? lh[0] + 1u : 0u, gbase + win_slot, 32);
             if (slot == r) {
                 new_parent = win_slot;
-                new_hit = b32 & 0x7ffffffu;
-                new_nhits = 63 - (int)(b64 >> 32);
-                new_chi2 = __uint_as_float((uint32_t)(b64 & 0xffffffffu));
+                new_hit = whit;
+                new_nhits = 63 - (int)(bk >> 35);
+                new_chi2 = __uint_as_float((uint32_t)(bk >> 3));
             }
             if (slot == win_slot) {
-                if ((b32 & 0x7ffffffu) != 0u) {  // pop the head of the list
+                if (offer_hit) {  // pop the head of the list
                     if (MODE == kModeLog && lr[0] != kNoKey) p.log_y[lr[0]] = 1.0f;  // the pair survives
 #pragma unroll
                     for (int k = 0; k < NL - 1; ++k) {
