@@ -269,14 +269,25 @@ constexpr int kTcCtasPerSm = 4;               // 4 x 128 = the SM's 512 TMEM col
 constexpr uint32_t kTcWaitLimit = 1u << 24;   // mbarrier polls before a wait gives up
 
 struct __align__(128) TcSmem {
-    uint8_t A1h[kTcRows * 32], A1l[kTcRows * 32];    // inputs, K = 16 (12 used)
+    uint8_t A1h[kTcRows * 32], A1l[kTcRows * 32];    // inputs, K = 16 (12 used, 3 bias columns)
     uint8_t A2h[kTcRows * 128], A2l[kTcRows * 128];  // first hidden layer, K = 64
-    uint8_t B1[kMlpHid * 32];                         // W1^T: N = 64 x K = 16
+    uint8_t B1[kMlpHid * 32];                         // W1^T and b1's parts: N = 64 x K = 16
     uint8_t B2[kMlpHid * 128];                        // W2^T: N = 64 x K = 64
-    float b1[kMlpHid], b2[kMlpHid], W3[kMlpHid], b3;
+    uint8_t B2b[kMlpHid * 32];                        // b2's parts: N = 64 x K = 16 (3 used)
+    float W3[kMlpHid], b3;
     unsigned long long mbar;
     uint32_t taddr;
 };
+
+// A bias b as three BF16 parts whose sum is b exactly (8 significant bits
+// each: FP32's 24), so that a product with 1.0 on the tensor cores adds b.
+__device__ __forceinline__ void bf16_parts3(float b, __nv_bfloat16 p[3])
+{
+    p[0] = __float2bfloat16(b);
+    const float r1 = b - __bfloat162float(p[0]);
+    p[1] = __float2bfloat16(r1);
+    p[2] = __float2bfloat16(r1 - __bfloat162float(p[1]));
+}
 
 __device__ __forceinline__ uint32_t core_offset(int r, int k, int K)
 {
@@ -330,46 +341,52 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *mbar, uint32_t par
     return false;
 }
 
-// 16 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+// 32 consecutive FP32 columns of this thread's TMEM lane, without the wait
+// (tmem_wait() before the values are used).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32])
 {
-    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void st_shared_v4(uint8_t *p, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
 {
     *reinterpret_cast<uint4 *>(p) = make_uint4(a, b, c, d);
 }
 
-__global__ void __launch_bounds__(kTcRows) mlp_score_tc_kernel(const float *w32, const float *X, int64_t n,
-                                                               float *logits, unsigned *status)
+__global__ void __launch_bounds__(kTcRows, kTcCtasPerSm) mlp_score_tc_kernel(const float *w32, const float *X,
+                                                                              int64_t n, float *logits,
+                                                                              unsigned *status)
 {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     TcSmem &s = *reinterpret_cast<TcSmem *>(tc_smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5;
-    // weights: W1^T and W2^T in BF16, K-major core matrices
-    for (int i = tid; i < kMlpHid * 16; i += kTcRows) {
-        const int nn = i >> 4, k = i & 15;
-        const __nv_bfloat16 v = __float2bfloat16(k < kMlpIn ? w32[kOffW1 + k * kMlpHid + nn] : 0.0f);
-        *reinterpret_cast<__nv_bfloat16 *>(s.B1 + core_offset(nn, k, 16)) = v;
+    // weights: W1^T with b1's parts as its K rows 12..14, W2^T, and b2's parts
+    // (K rows 0..2 of B2b), in BF16, K-major core matrices
+    for (int nn = tid; nn < kMlpHid; nn += kTcRows) {
+        __nv_bfloat16 p1[3], p2[3];
+        bf16_parts3(w32[kOffB1 + nn], p1);
+        bf16_parts3(w32[kOffB2 + nn], p2);
+        for (int k = 0; k < 16; ++k) {
+            const __nv_bfloat16 v = k < kMlpIn ? __float2bfloat16(w32[kOffW1 + k * kMlpHid + nn])
+                                    : k < kMlpIn + 3 ? p1[k - kMlpIn]
+                                                     : __float2bfloat16(0.0f);
+            *reinterpret_cast<__nv_bfloat16 *>(s.B1 + core_offset(nn, k, 16)) = v;
+            *reinterpret_cast<__nv_bfloat16 *>(s.B2b + core_offset(nn, k, 16)) = k < 3 ? p2[k] : __float2bfloat16(0.0f);
+        }
+        s.W3[nn] = w32[kOffW3 + nn];
     }
     for (int i = tid; i < kMlpHid * kMlpHid; i += kTcRows) {
         const int nn = i >> 6, k = i & 63;
         *reinterpret_cast<__nv_bfloat16 *>(s.B2 + core_offset(nn, k, 64)) =
             __float2bfloat16(w32[kOffW2 + k * kMlpHid + nn]);
-    }
-    for (int i = tid; i < kMlpHid; i += kTcRows) {
-        s.b1[i] = w32[kOffB1 + i];
-        s.b2[i] = w32[kOffB2 + i];
-        s.W3[i] = w32[kOffW3 + i];
     }
     if (tid == 0) {
         s.b3 = w32[kOffB3];
@@ -389,6 +406,7 @@ __global__ void __launch_bounds__(kTcRows) mlp_score_tc_kernel(const float *w32,
     const uint32_t tmem = s.taddr;
     const uint32_t d1 = tmem, d2 = tmem + kMlpHid;      // accumulators: columns 0..63 and 64..127
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lanes
+    const float b3 = s.b3;
     uint32_t parity = 0;
     bool failed = false;
     const int64_t tiles = (n + kTcRows - 1) / kTcRows;
@@ -403,10 +421,11 @@ __global__ void __launch_bounds__(kTcRows) mlp_score_tc_kernel(const float *w32,
     load_row(blockIdx.x, fin);
     for (int64_t tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
         const int64_t row = tile * kTcRows + tid;
-        // inputs of row `tid`, split into BF16 hi and lo
+        // inputs of row `tid` and three 1s (the bias columns), split into BF16
+        // hi and lo (1 is exact: its lo part is 0)
         float f[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) f[i] = i < kMlpIn ? fin[i] : 0.0f;
+        for (int i = 0; i < 16; ++i) f[i] = i < kMlpIn ? fin[i] : i < kMlpIn + 3 ? 1.0f : 0.0f;
         uint32_t h[8], l[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) split_bf16x2(f[2 * i], f[2 * i + 1], h[i], l[i]);
@@ -431,24 +450,30 @@ __global__ void __launch_bounds__(kTcRows) mlp_score_tc_kernel(const float *w32,
             break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // layer 1 epilogue: bias, ReLU, split -> layer-2 A operand (row tid)
+        // layer 1 epilogue (the bias is in the accumulator): ReLU, split ->
+        // layer-2 A operand (row tid)
 #pragma unroll
-        for (int c0 = 0; c0 < kMlpHid; c0 += 16) {
-            float a[16];
-            tmem_ld16(d1 + lane_base + c0, a);
-            uint32_t hh[8], ll[8];
+        for (int c0 = 0; c0 < kMlpHid; c0 += 32) {
+            uint32_t a[32];
+            tmem_ld32(d1 + lane_base + c0, a);
+            tmem_wait();
+            uint32_t hh[16], ll[16];
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-                split_bf16x2(fmaxf(a[2 * i] + s.b1[c0 + 2 * i], 0.0f), fmaxf(a[2 * i + 1] + s.b1[c0 + 2 * i + 1], 0.0f),
-                             hh[i], ll[i]);
+            for (int i = 0; i < 16; ++i)
+                split_bf16x2(fmaxf(__uint_as_float(a[2 * i]), 0.0f), fmaxf(__uint_as_float(a[2 * i + 1]), 0.0f), hh[i],
+                             ll[i]);
 #pragma unroll
-            for (int kg = 0; kg < 2; ++kg) {
+            for (int kg = 0; kg < 4; ++kg) {
                 st_shared_v4(s.A2h + core_offset(tid, c0 + kg * 8, 64), hh[4 * kg], hh[4 * kg + 1], hh[4 * kg + 2],
                              hh[4 * kg + 3]);
                 st_shared_v4(s.A2l + core_offset(tid, c0 + kg * 8, 64), ll[4 * kg], ll[4 * kg + 1], ll[4 * kg + 2],
                              ll[4 * kg + 3]);
             }
         }
+        // layer 1's inputs are consumed: A1h row tid becomes (1, 1, 1, 0, ...),
+        // the A operand of layer 2's bias product
+        st_shared_v4(s.A1h + core_offset(tid, 0, 16), 0x3F803F80u, 0x00003F80u, 0u, 0u);
+        st_shared_v4(s.A1h + core_offset(tid, 8, 16), 0u, 0u, 0u, 0u);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -460,6 +485,7 @@ __global__ void __launch_bounds__(kTcRows) mlp_score_tc_kernel(const float *w32,
                 tc_mma(d2, smem_desc(s.A2h + ks * 256, 128, 1024), b, ks > 0 ? 1u : 0u);
                 tc_mma(d2, smem_desc(s.A2l + ks * 256, 128, 1024), b, 1u);
             }
+            tc_mma(d2, smem_desc(s.A1h, 128, 256), smem_desc(s.B2b, 128, 256), 1u);  // + b2
             tc_commit(&s.mbar);
         }
         ok = mbar_wait(&s.mbar, parity);
@@ -469,14 +495,20 @@ __global__ void __launch_bounds__(kTcRows) mlp_score_tc_kernel(const float *w32,
             break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // layer 2 epilogue: bias, ReLU, the 64 -> 1 dot product
-        float z = s.b3;
+        // layer 2 epilogue (the bias is in the accumulator): ReLU, the 64 -> 1
+        // dot product
+        uint32_t a[64];
+        tmem_ld32(d2 + lane_base, a);
+        tmem_ld32(d2 + lane_base + 32, a + 32);
+        tmem_wait();
+        float z = b3;
 #pragma unroll
-        for (int c0 = 0; c0 < kMlpHid; c0 += 16) {
-            float a[16];
-            tmem_ld16(d2 + lane_base + c0, a);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) z = fmaf(s.W3[c0 + i], fmaxf(a[i] + s.b2[c0 + i], 0.0f), z);
+        for (int c = 0; c < kMlpHid; c += 4) {
+            const float4 w = *reinterpret_cast<const float4 *>(s.W3 + c);
+            z = fmaf(w.x, fmaxf(__uint_as_float(a[c]), 0.0f), z);
+            z = fmaf(w.y, fmaxf(__uint_as_float(a[c + 1]), 0.0f), z);
+            z = fmaf(w.z, fmaxf(__uint_as_float(a[c + 2]), 0.0f), z);
+            z = fmaf(w.w, fmaxf(__uint_as_float(a[c + 3]), 0.0f), z);
         }
         if (row < n) logits[row] = z;
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
