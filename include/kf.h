@@ -122,12 +122,13 @@ typedef struct {
     int n_z_bins;            /* ... and in z (0 = autotuned); at most 16,384 bins */
     int use_proposal;        /* 1: the learned proposal keeps the top-k in-window hits */
     int topk;
+    int build_variant;       /* learned build: -1 autotuned, 0 one proposal pass, 1 speculative */
 } kf_options;
 
 /* Fill *opt with the defaults: routed precision (cond_max 1e4, pT in
  * [0.25, 200], gain_max 0), automatic launch, N = 6, chi2 cut 30, 3-sigma window
  * capped at 0.05 rad and 5 cm, 0.01/0.1 cm nominal resolution, autotuned hit
- * bins, proposal off, top-k 4. */
+ * bins, proposal off, top-k 4, the learned build's form autotuned. */
 void kf_options_default(kf_options *opt);
 
 /* Create a context on CUDA device `device` (requires compute capability
@@ -228,8 +229,9 @@ int kf_fit_tracks_host(kf_context *ctx, const kf_geometry *geom, int64_t n_track
  * times five grids of up to 16,384 bins on the caller's buffers and keeps the
  * fastest (kf_build_tuned_shape reports it); with the learned proposal it
  * also chooses between one proposal pass and a speculative plain pass whose
- * flagged seeds alone are rebuilt with the proposal.  The results depend on
- * neither choice.
+ * flagged seeds alone are rebuilt with the proposal (opt->build_variant
+ * fixes that choice: 0 the single pass, 1 the speculative form).  The results
+ * depend on neither choice.
  *
  * geom: the layers to build over (host).
  * hit_offsets: host, [n_events][L + 1]; the hits of event e on layer l are

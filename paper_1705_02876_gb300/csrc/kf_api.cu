@@ -170,6 +170,7 @@ void kf_options_default(kf_options *o)
     o->n_z_bins = 0;
     o->use_proposal = 0;
     o->topk = 4;
+    o->build_variant = -1;
 }
 
 int kf_context_create(kf_context **out, int device)

@@ -48,9 +48,10 @@ struct BuildState {
         cudaEvent_t in_done = nullptr, built = nullptr, out_done = nullptr;
         bool used = false;
     } slot[3];
-    // autotuned shapes: (L, N, mode, seeds' size class, hits' size class, fixed n_phi, fixed n_z)
+    // autotuned shapes: (L, N, mode, seeds' size class, hits' size class, fixed n_phi, fixed n_z,
+    // fixed form of the learned build)
     // -> (n_phi, n_z, speculative: the learned build as a flagging plain pass plus a proposal pass)
-    std::map<std::tuple<int, int, int, int, int, int, int>, std::tuple<int, int, int>> tuned;
+    std::map<std::tuple<int, int, int, int, int, int, int, int>, std::tuple<int, int, int>> tuned;
     // the speculative learned build's per-seed flags, flagged-seed list and its length
     int32_t *seed_flag = nullptr, *seed_list = nullptr;
     unsigned *list_count = nullptr;
@@ -1032,7 +1033,9 @@ int build_run(kf_context *ctx, const FitGeom &g, const kf_options &o, const Buil
     // the shape: the one tuned for this workload class, or tuned now on the
     // caller's own buffers (a build only reads its inputs and overwrites its
     // outputs; the training log restarts its count)
-    const auto key = std::make_tuple(L, p.N, mode, size_class(b.n_seeds), size_class(b.n_hits), o.n_phi_bins, o.n_z_bins);
+    const int fixed_spec = mode == kModeProposal ? o.build_variant : -1;
+    const auto key = std::make_tuple(L, p.N, mode, size_class(b.n_seeds), size_class(b.n_hits), o.n_phi_bins, o.n_z_bins,
+                                     fixed_spec);
     std::tuple<int, int, int> shape;
     cudaError_t e = cudaSuccess;
     auto it = st->tuned.find(key);
@@ -1041,6 +1044,7 @@ int build_run(kf_context *ctx, const FitGeom &g, const kf_options &o, const Buil
     } else {
         std::vector<std::tuple<int, int, int>> cand;
         for (int spec = 0; spec <= (mode == kModeProposal ? 1 : 0); ++spec) {
+            if (fixed_spec >= 0 && spec != fixed_spec) continue;
             for (const auto &gr : kBinGrids)
                 if ((!o.n_phi_bins || o.n_phi_bins == gr[0]) && (!o.n_z_bins || o.n_z_bins == gr[1]))
                     cand.emplace_back(gr[0], gr[1], spec);
@@ -1097,6 +1101,8 @@ int check_build_args(kf_context *ctx, const kf_geometry *geom, const kf_options 
                          "chi2_cut, window_nsigma and the window caps must be positive, hit sigmas non-negative");
     if (o.n_phi_bins < 0 || o.n_z_bins < 0 || (int64_t)o.n_phi_bins * o.n_z_bins > 16384)
         return set_error(ctx, KF_ERR_ARG, "n_phi_bins x n_z_bins must be 1..16384 (0: tuned)");
+    if (o.build_variant < -1 || o.build_variant > 1)
+        return set_error(ctx, KF_ERR_ARG, "build_variant must be -1 (tuned), 0 or 1");
     if (o.use_proposal) {
         if (log) return set_error(ctx, KF_ERR_ARG, "the training log records the plain build: use_proposal must be 0");
         if (o.topk < 1 || o.topk > kMaxN) return set_error(ctx, KF_ERR_ARG, "topk must be 1..8");
@@ -1216,7 +1222,8 @@ extern "C" int kf_build_tuned_shape(kf_context *ctx, int n_layers, int max_cands
     if (!ctx || !n_phi_bins || !n_z_bins) return KF_ERR_ARG;
     BuildState *st = context_build_state(ctx);
     if (st) {
-        auto it = st->tuned.find(std::make_tuple(n_layers, max_cands, mode, size_class(n_seeds), size_class(n_hits), 0, 0));
+        auto it =
+            st->tuned.find(std::make_tuple(n_layers, max_cands, mode, size_class(n_seeds), size_class(n_hits), 0, 0, -1));
         if (it != st->tuned.end()) {
             *n_phi_bins = std::get<0>(it->second);
             *n_z_bins = std::get<1>(it->second);

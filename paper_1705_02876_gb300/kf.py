@@ -51,7 +51,7 @@ class Options(ctypes.Structure):
                 ("hit_sigma_rphi", ctypes.c_float), ("hit_sigma_z", ctypes.c_float),
                 ("window_max_dphi", ctypes.c_float), ("window_max_dz", ctypes.c_float),
                 ("n_phi_bins", ctypes.c_int), ("n_z_bins", ctypes.c_int),
-                ("use_proposal", ctypes.c_int), ("topk", ctypes.c_int)]
+                ("use_proposal", ctypes.c_int), ("topk", ctypes.c_int), ("build_variant", ctypes.c_int)]
 
 
 _lib = None

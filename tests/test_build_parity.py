@@ -149,7 +149,8 @@ def test_full_pipeline_seed_fit_then_build(kf, ctx, oracle):
 def test_argument_errors(kf, ctx):
     ev = synth.make_build_events(26, 1, 50)
     seeds = dict(state=ev.seed_fit.seed_state, cov=ev.seed_fit.seed_cov)
-    for bad, match in (({"max_cands": 9}, "max_cands"), ({"n_phi_bins": 1024, "n_z_bins": 64}, "n_phi_bins")):
+    for bad, match in (({"max_cands": 9}, "max_cands"), ({"n_phi_bins": 1024, "n_z_bins": 64}, "n_phi_bins"),
+                       ({"build_variant": 2}, "build_variant")):
         with pytest.raises(kf.KFError, match=match):
             gpu_build(kf, ctx, ev, seeds, **bad)
     off = ev.hit_offsets.copy()

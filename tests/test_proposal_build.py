@@ -184,6 +184,29 @@ def test_proposal_parity_sparse_windows(kf, ctx, oracle):
         assert bad.size == 0, (topk, bad, ref["margin"][bad], near_share)
 
 
+@pytest.mark.parametrize("nf", [10, 100])
+def test_learned_build_both_forms(kf, ctx, oracle, nf):
+    """Both forms the autotuner chooses between, each forced: one proposal
+    pass over every seed (build_variant 0) and the speculative form, a plain
+    pass flagging the seeds with a window wider than topk and a proposal pass
+    over those (1).  Each is the FP64 network's build, every mismatch traced
+    to a near-tie, and the two agree with each other."""
+    ev = synth.make_build_events(57, 1, 800, noise_factor=nf)
+    seeds = oracle_seeds(oracle, ev)
+    w = mlp_oracle.init_params(np.random.default_rng(12)).astype(np.float32)
+    kf.proposal_load(ctx, _t(w, torch.float32))
+    wi = mlp_oracle.inference_weights(w)
+    ref = oracle.build_events(ev, seeds=seeds, max_cands=6, mlp=wi, topk=4, margins=True)
+    outs = []
+    for variant in (0, 1):
+        gpu = gpu_build(kf, ctx, ev, seeds, max_cands=6, use_proposal=1, topk=4, build_variant=variant)
+        assert identical_fraction(gpu, ref) >= 0.999
+        bad, near_share = untraced_mismatches(gpu, ref)
+        assert bad.size == 0, (variant, bad, ref["margin"][bad], near_share)
+        outs.append(gpu)
+    assert (outs[0]["hit"] == outs[1]["hit"]).mean() >= 0.9999
+
+
 def test_constant_network_parity(kf, ctx, oracle):
     """All logits equal: both sides keep the lowest hit indices."""
     ev = synth.make_build_events(53, 1, 800, noise_factor=100)
